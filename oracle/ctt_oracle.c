@@ -36,8 +36,10 @@
  * inner linear multigrid V-cycle on the block-diagonal linearisation
  *   (Lap + c) e = -F_psi,  (Lap + (1/3) grad div) e_W = -F_W,
  *   c = dF_psi/du = -(5/12) K^2 psi^4 - (7/8) psi^-8 AtAt + 2 pi (5 rho0 psi^4 + rho2),
- * smoothed by sequential lexicographic Gauss-Seidel; restriction is the mean of
- * the 8 children, prolongation is cell-centred trilinear (3/4, 1/4 per axis).
+ * with the psi row scaled by psi^-5 (so that the K^2 direction is a constant), smoothed by
+ * sequential lexicographic Gauss-Seidel, with an exact bordered solve of the psi row on the
+ * coarsest level; restriction is the mean of the 8 children, prolongation is cell-centred
+ * trilinear (3/4, 1/4 per axis).
  * This is the multigrid family the paper names (Key features, "Fast").
  *
  * Arrays are x-fastest, index i + nx (j + ny k), no ghost cells.
@@ -379,7 +381,8 @@ int ora_residual(const ora_grid *g, const double *u, const double *W, const doub
 typedef struct {
     ora_grid g;
     long N;
-    double *c;   /* linearisation coefficient */
+    double *a;   /* psi-row coefficient of Lap (psi^-5 on the finest level) */
+    double *c;   /* psi-row diagonal coefficient (psi^-5 dF_psi/du on the finest level) */
     double *f;   /* 4N right-hand side: psi row then 3 W rows */
     double *e;   /* 4N correction */
     double *r;   /* 4N scratch residual */
@@ -397,7 +400,7 @@ static double diag_d2(const ora_grid *g, int a)
     return w / (g->h[a] * g->h[a]);
 }
 
-/* lexicographic Gauss-Seidel sweeps on (Lap + c) e = f and the momentum operator */
+/* lexicographic Gauss-Seidel sweeps on (a Lap + c) e = f and the momentum operator */
 static void gs_sweeps(ora_level *L, int sweeps)
 {
     const ora_grid *g = &L->g;
@@ -408,8 +411,8 @@ static void gs_sweeps(ora_level *L, int sweeps)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i) {
                     long p = lin(g, i, j, k);
-                    double rp = L->f[p] - (lap_at(g, L->e, i, j, k) + L->c[p] * L->e[p]);
-                    L->e[p] += rp / (dl + L->c[p]);
+                    double rp = L->f[p] - (L->a[p] * lap_at(g, L->e, i, j, k) + L->c[p] * L->e[p]);
+                    L->e[p] += rp / (L->a[p] * dl + L->c[p]);
                     for (int a = 0; a < 3; ++a) {
                         double ra = L->f[(1 + a) * N + p] - momop_at(g, L->e + N, a, i, j, k);
                         L->e[(1 + a) * N + p] += ra / (dl + diag_d2(g, a) / 3.0);
@@ -425,7 +428,7 @@ static void linear_residual(ora_level *L)
         for (int j = 0; j < g->n[1]; ++j)
             for (int i = 0; i < g->n[0]; ++i) {
                 long p = lin(g, i, j, k);
-                L->r[p] = L->f[p] - (lap_at(g, L->e, i, j, k) + L->c[p] * L->e[p]);
+                L->r[p] = L->f[p] - (L->a[p] * lap_at(g, L->e, i, j, k) + L->c[p] * L->e[p]);
                 for (int a = 0; a < 3; ++a)
                     L->r[(1 + a) * N + p] = L->f[(1 + a) * N + p] - momop_at(g, L->e + N, a, i, j, k);
             }
@@ -442,6 +445,65 @@ static void remove_means(const ora_grid *g, double *e4, long N)
     }
 }
 
+/*
+ * Exact solve of the psi row on the coarsest level: (a Lap + c) e = f, bordered on periodic
+ * boxes by a constant Lagrange multiplier and the constraint sum e = 0.  The matrix is built by
+ * applying the operator to unit vectors and solved by Gaussian elimination with partial
+ * pivoting.  Overwrites the psi part of L->e.  Returns 0, or -1 if allocation fails.
+ */
+static int coarse_psi_direct(ora_level *L)
+{
+    const ora_grid *g = &L->g;
+    long N = L->N;
+    int per = g->bc == 0;
+    long m = N + per;
+    double *A = calloc((size_t)(m * m), sizeof(double));
+    double *x = calloc((size_t)m, sizeof(double));
+    double *unit = calloc((size_t)N, sizeof(double));
+    if (!A || !x || !unit) { free(A); free(x); free(unit); return -1; }
+    for (long q = 0; q < N; ++q) {
+        unit[q] = 1.0;
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    long p = lin(g, i, j, k);
+                    A[p * m + q] = L->a[p] * lap_at(g, unit, i, j, k) + L->c[p] * unit[p];
+                }
+        unit[q] = 0.0;
+    }
+    if (per) {
+        for (long p = 0; p < N; ++p) {
+            A[p * m + N] = 1.0;
+            A[N * m + p] = 1.0;
+        }
+    }
+    for (long p = 0; p < N; ++p) x[p] = L->f[p];
+    for (long k = 0; k < m; ++k) {
+        long piv = k;
+        for (long i = k + 1; i < m; ++i)
+            if (fabs(A[i * m + k]) > fabs(A[piv * m + k])) piv = i;
+        if (piv != k) {
+            for (long j = 0; j < m; ++j) {
+                double t = A[k * m + j]; A[k * m + j] = A[piv * m + j]; A[piv * m + j] = t;
+            }
+            double t = x[k]; x[k] = x[piv]; x[piv] = t;
+        }
+        for (long i = k + 1; i < m; ++i) {
+            double l = A[i * m + k] / A[k * m + k];
+            for (long j = k; j < m; ++j) A[i * m + j] -= l * A[k * m + j];
+            x[i] -= l * x[k];
+        }
+    }
+    for (long k = m - 1; k >= 0; --k) {
+        double s = x[k];
+        for (long j = k + 1; j < m; ++j) s -= A[k * m + j] * x[j];
+        x[k] = s / A[k * m + k];
+    }
+    for (long p = 0; p < N; ++p) L->e[p] = x[p];
+    free(A); free(x); free(unit);
+    return 0;
+}
+
 static void vcycle(ora_level *lv, int l, int nlev, int nu1, int nu2, int csweeps)
 {
     ora_level *L = &lv[l];
@@ -450,6 +512,7 @@ static void vcycle(ora_level *lv, int l, int nlev, int nu1, int nu2, int csweeps
     if (l == nlev - 1) {
         gs_sweeps(L, csweeps);
         remove_means(&L->g, L->e, N);
+        if (L->N <= 1000) coarse_psi_direct(L);
         return;
     }
     gs_sweeps(L, nu1);
@@ -514,11 +577,12 @@ int ora_solve(const ora_grid *g0, const double *rho0, const double *rho2, const 
         }
         lv[l].g = g;
         lv[l].N = ncells(&g);
+        lv[l].a = calloc(lv[l].N, sizeof(double));
         lv[l].c = calloc(lv[l].N, sizeof(double));
         lv[l].f = calloc(4 * lv[l].N, sizeof(double));
         lv[l].e = calloc(4 * lv[l].N, sizeof(double));
         lv[l].r = calloc(4 * lv[l].N, sizeof(double));
-        if (!lv[l].c || !lv[l].f || !lv[l].e || !lv[l].r) ok = 0;
+        if (!lv[l].a || !lv[l].c || !lv[l].f || !lv[l].e || !lv[l].r) ok = 0;
     }
     if (!ok) { status = -1; it = 0; goto done; }
     for (it = 0; it <= max_outer; ++it) {
@@ -536,8 +600,20 @@ int ora_solve(const ora_grid *g0, const double *rho0, const double *rho2, const 
         if (tol > 0.0 && mx <= tol) { status = 0; break; }
         if (tol <= 0.0 && (mx == 0.0 || (it >= 3 && mx > 0.9 * mx_hist[it - 3]))) { status = 1; break; }
         if (it == max_outer) break;
-        for (long p = 0; p < 4 * N; ++p) lv[0].f[p] = -F[p];
-        for (int l = 1; l < levels; ++l) ora_restrict(&lv[l].g, lv[l - 1].c, lv[l].c);
+        /* The psi row is scaled by psi^-5: then the change of K^2, whose direction in F_psi is
+         * psi^5, is a constant, which the zero-mean projection of the correction absorbs. */
+        for (long p = 0; p < N; ++p) {
+            double ps5 = pow(psibg_at(g0, (int)(p % g0->n[0]), (int)((p / g0->n[0]) % g0->n[1]),
+                                      (int)(p / ((long)g0->n[0] * g0->n[1]))) + u[p], -5.0);
+            lv[0].a[p] = ps5;
+            lv[0].c[p] *= ps5;
+            lv[0].f[p] = -ps5 * F[p];
+        }
+        for (long p = N; p < 4 * N; ++p) lv[0].f[p] = -F[p];
+        for (int l = 1; l < levels; ++l) {
+            ora_restrict(&lv[l].g, lv[l - 1].a, lv[l].a);
+            ora_restrict(&lv[l].g, lv[l - 1].c, lv[l].c);
+        }
         vcycle(lv, 0, levels, nu1, nu2, csweeps);
         for (long p = 0; p < N; ++p) u[p] += lv[0].e[p];
         for (long p = 0; p < 3 * N; ++p) W[p] += lv[0].e[N + p];
@@ -549,7 +625,7 @@ int ora_solve(const ora_grid *g0, const double *rho0, const double *rho2, const 
 done:
     if (iters) *iters = it;
     for (int l = 0; l < levels; ++l) {
-        free(lv[l].c); free(lv[l].f); free(lv[l].e); free(lv[l].r);
+        free(lv[l].a); free(lv[l].c); free(lv[l].f); free(lv[l].e); free(lv[l].r);
     }
     free(lv); free(F); free(mx_hist);
     return status;
