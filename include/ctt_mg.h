@@ -1,0 +1,153 @@
+/*
+ * ctt_mg.h -- C ABI of the GB300 CTT constraint multigrid library (libctt_mg.so).
+ *
+ * The library solves the Hamiltonian and momentum constraints of numerical
+ * relativity initial data (GRTresna, arXiv:2501.13046, Summary, eq:Ham and
+ * eq:Mom), given the matter projections rho and S_i, in the conformal
+ * transverse-traceless form with a conformally flat metric and constant K:
+ *
+ *   F_psi  = Lap u - (K^2/12) psi^5 + (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi)
+ *   F_W,i  = Lap W_i + (1/3) d_i d_j W_j - 8 pi (psi^6 S_i - m_i)
+ *   H = -8 psi^-5 F_psi,  M_i = psi^-6 F_W,i,
+ *   psi = 1 + sum_p m_p / (2 |x - x_p|) + u,   At_ij = d_i W_j + d_j W_i - (2/3) delta_ij d_k W_k,
+ *
+ * with rho = rho0 + psi^-4 rho2 (rho2 = gradient energy of a scalar field), on a
+ * cell-centred uniform grid (x_i = lo + (i + 1/2) h) with 2nd- or 4th-order
+ * centred stencils, periodic or Robin 1/r boundaries (Key features, "Boundary
+ * conditions"), by multigrid (Key features, "Fast").  On periodic boxes K^2 is
+ * set every outer iteration by the discrete integrability condition
+ * sum_cells F_psi = 0, the gauge is <u> = <W_i> = 0, and m_i = <8 pi psi^6 S_i>;
+ * elsewhere K is the configured constant and m_i = 0.  The constraint norms
+ * are evaluated every outer iteration (Key features, "Diagnostics").
+ *
+ * Conventions for every call:
+ *   - Field arrays hold N = n[0]*n[1]*n[2] doubles, x fastest: index i + n0 (j + n1 k),
+ *     no ghost cells.  W and S are 3 such arrays back to back (x, y, z components).
+ *   - on_device = 1: the pointer is CUDA device memory on the library's current device
+ *     (for instance a torch tensor's data_ptr()); on_device = 0: host memory.
+ *   - The caller owns every buffer it passes; the library copies inputs on the call and
+ *     never keeps caller pointers (except the optional workspace, see mg_create).
+ *   - Every call returns a status; nothing aborts, throws or traps.  mg_last_error()
+ *     gives a one-line description of the last failure on the calling thread.
+ *   - A context is not thread safe; calls on one context must be serialised.
+ *   - All device work of a context is issued on the CUDA stream given to mg_create.
+ */
+#ifndef CTT_MG_H
+#define CTT_MG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = 1,   /* bad size, pointer, order, level count, NaN/inf input  */
+    MG_ERR_UNSUPPORTED = 2,   /* a feature outside this library (e.g. non-flat metric) */
+    MG_ERR_CUDA = 3,          /* a CUDA runtime call failed                            */
+    MG_ERR_OOM = 4,           /* device or host allocation failed / workspace too small */
+    MG_ERR_STATE = 5,         /* call out of order (e.g. solve before set_sources)     */
+    MG_ERR_NOT_CONVERGED = 6, /* max_outer iterations used without reaching tol        */
+    MG_ERR_DIVERGED = 7,      /* a norm became NaN/inf or grew for 3 outer iterations  */
+    MG_ERR_TIMEOUT = 8        /* a bounded device-side wait ran out                     */
+} mg_status;
+
+enum { MG_BC_PERIODIC = 0, MG_BC_ROBIN = 1 };
+enum { MG_FP64 = 0, MG_MIXED = 1 };            /* inner V-cycle in FP64, or FP32 under FP64 defect correction */
+enum { MG_K_FIXED = 0, MG_K_INTEGRABILITY = 1 };
+
+typedef struct {
+    int n[3];             /* cells per axis; every level above the coarsest must have even sizes */
+    double lo[3], hi[3];  /* box; h[a] = (hi[a] - lo[a]) / n[a]                                   */
+    int order;            /* 2 or 4                                                               */
+    int bc;               /* MG_BC_PERIODIC or MG_BC_ROBIN (1/r falloff about the origin)         */
+    int levels;           /* multigrid levels, 0 = coarsen while all sizes are even and halve to >= 3 */
+    int precision;        /* MG_FP64 or MG_MIXED                                                  */
+    int k_mode;           /* MG_K_INTEGRABILITY (periodic only) or MG_K_FIXED                     */
+    double K;             /* used when k_mode == MG_K_FIXED                                       */
+    int npunct;           /* 0..2 bare punctures (Robin boxes only)                               */
+    double punct_m[2];
+    double punct_x[2][3];
+    double tol;           /* stop when max(|H|, |M_i|) <= tol (default 1e-10)                     */
+    int max_outer;        /* outer (defect-correction) iterations (default 60)                    */
+    int nu_pre, nu_post;  /* red-black sweeps before / after the coarse correction (default 2, 2) */
+    int coarse_sweeps;    /* red-black sweeps on the coarsest level (default 60)                  */
+    int use_graph;        /* 1 = replay each outer iteration as a captured CUDA graph (default 1) */
+    long long spin_limit; /* bound on any device-side wait, in polls (default 1<<24)              */
+} mg_config;
+
+typedef struct {
+    int outer_iters;      /* residual evaluations made minus one                                  */
+    int converged;        /* 1 when max(|H|, |M_i|) <= tol                                        */
+    double K;             /* final K (negative root on periodic boxes: expanding slice)          */
+    double K2;            /* final K^2                                                            */
+    double norms[4];      /* final max |H|, max |M_x|, max |M_y|, max |M_z|                       */
+    double mom_mean[3];   /* m_i removed from the momentum source (periodic), else 0              */
+    const double *history;/* 4 norms per outer iteration, owned by the context, valid until the next solve */
+    int history_len;      /* rows in history                                                     */
+    double device_ms;     /* device time of the solve (CUDA events on the context's stream)       */
+    long long kernel_launches; /* library kernels launched by this solve (0 if use_graph == 0)    */
+} mg_solve_info;
+
+/* Fill *cfg with defaults: order 2, periodic, integrability K, MG_MIXED, tol 1e-10, ... */
+mg_status mg_config_default(mg_config *cfg);
+
+/* Device bytes the context needs for cfg (states, sources, all levels, reduction scratch). */
+mg_status mg_workspace_size(const mg_config *cfg, size_t *bytes);
+
+/*
+ * Create a context for one problem.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * workspace: NULL lets the library allocate its device memory itself; otherwise a device
+ * buffer of at least mg_workspace_size() bytes, 256-byte aligned, owned by the caller and
+ * kept alive until mg_destroy (for instance a torch uint8 tensor).
+ */
+mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, size_t workspace_bytes,
+                    struct mg_ctx **out);
+
+/* Conformal metric gt_ij (6 arrays xx, xy, xz, yy, yz, zz) or NULL.  Only the flat metric
+ * (NULL, or exactly delta_ij everywhere) is supported; anything else returns MG_ERR_UNSUPPORTED
+ * (non-conformally-flat data is listed as forthcoming in the paper's feature list). */
+mg_status mg_set_conformal_metric(struct mg_ctx *ctx, const double *gt, int on_device);
+
+/* Matter sources: rho = rho0 + psi^-4 rho2; S_i lower-index momentum density.  rho2 may be NULL (0). */
+mg_status mg_set_sources(struct mg_ctx *ctx, const double *rho0, const double *rho2, const double *Sx,
+                         const double *Sy, const double *Sz, int on_device);
+
+/* Initial guess for u (N) and W (3N); either may be NULL (zero).  Default: u = 0, W = 0.
+ * On periodic boxes the means are projected out at the start of mg_solve. */
+mg_status mg_set_initial_guess(struct mg_ctx *ctx, const double *u, const double *W, int on_device);
+
+/* Iterate until max(|H|, |M_i|) <= tol.  info may be NULL. */
+mg_status mg_solve(struct mg_ctx *ctx, mg_solve_info *info);
+
+/* Copy out u (N doubles), W (3N doubles) and K; any pointer may be NULL. */
+mg_status mg_get_solution(struct mg_ctx *ctx, double *u, double *W, double *K, int on_device);
+
+/* Evaluate the constraints at the current state: out = max |H|, max |M_x|, |M_y|, |M_z|. */
+mg_status mg_residual_norms(struct mg_ctx *ctx, double out[4]);
+
+/* Write H (N) and M (3N) at the current state (either may be NULL). */
+mg_status mg_constraint_fields(struct mg_ctx *ctx, double *H, double *M, int on_device);
+
+/*
+ * Measurement aid: launch one kernel of the solve `reps` times back to back on the context's
+ * stream, bracketed by CUDA events, at the current state (call after mg_solve or
+ * mg_residual_norms).  which: 0 = one red-black colour pass of the finest-level smoother,
+ * 1 = residual + restriction of the finest level, 2 = outer FP64 residual pass 1.
+ * Returns the mean device time per launch and the algorithmic DRAM bytes one launch must
+ * move (every array it reads once, every array it writes once).  The solver state is not
+ * changed except for scratch buffers.
+ */
+mg_status mg_time_kernel(struct mg_ctx *ctx, int which, int reps, double *ms_per_launch, double *bytes_per_launch);
+
+void mg_destroy(struct mg_ctx *ctx);
+
+const char *mg_status_string(mg_status s);
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTT_MG_H */

@@ -1,0 +1,531 @@
+// ctt_mg.cu -- C ABI of the CTT constraint multigrid (see include/ctt_mg.h).
+//
+// Solve (GRTresna, arXiv:2501.13046, eq:Ham/eq:Mom; multigrid, "Key features: Fast"):
+//   outer loop in FP64 -- residual, K^2 from the discrete integrability sum on periodic
+//   boxes, constraint norms (Key features, "Diagnostics"), convergence test;
+//   inner solve -- one linear V-cycle on the block-diagonal linearisation, in FP64
+//   (MG_FP64) or FP32 (MG_MIXED: FP32 smoothing/residual/transfer under FP64 defect
+//   correction); update u += e, W += e_W in FP64 (zero-mean corrections on periodic boxes).
+// Each outer iteration after the first is one replay of a captured CUDA graph; the only
+// host synchronisation per iteration is the read of K^2 and the four norms.
+#include "mg_common.cuh"
+
+namespace ctt {
+
+thread_local std::string g_last_error;
+
+mg_status fail(mg_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+}  // namespace ctt
+
+using namespace ctt;
+
+namespace {
+mg_status validate(const mg_config *c)
+{
+    if (!c) return fail(MG_ERR_INVALID_ARG, "null config");
+    for (int a = 0; a < 3; ++a) {
+        if (c->n[a] < 3) return fail(MG_ERR_INVALID_ARG, "n[a] must be >= 3");
+        if (!(c->hi[a] > c->lo[a])) return fail(MG_ERR_INVALID_ARG, "hi must exceed lo");
+    }
+    if ((long long)c->n[0] * c->n[1] * c->n[2] > (1LL << 31)) return fail(MG_ERR_INVALID_ARG, "grid too large");
+    if (c->order != 2 && c->order != 4) return fail(MG_ERR_INVALID_ARG, "order must be 2 or 4");
+    if (c->bc != MG_BC_PERIODIC && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "bad bc");
+    if (c->precision != MG_FP64 && c->precision != MG_MIXED) return fail(MG_ERR_INVALID_ARG, "bad precision");
+    if (c->k_mode != MG_K_FIXED && c->k_mode != MG_K_INTEGRABILITY) return fail(MG_ERR_INVALID_ARG, "bad k_mode");
+    if (c->k_mode == MG_K_INTEGRABILITY && c->bc != MG_BC_PERIODIC)
+        return fail(MG_ERR_INVALID_ARG, "integrability K needs a periodic box");
+    if (c->npunct < 0 || c->npunct > 2) return fail(MG_ERR_INVALID_ARG, "npunct must be 0..2");
+    if (c->npunct > 0 && c->bc == MG_BC_PERIODIC)
+        return fail(MG_ERR_UNSUPPORTED, "punctures need Robin boundaries");
+    if (!(c->tol >= 0.0) || c->max_outer < 0 || c->nu_pre < 0 || c->nu_post < 0 || c->coarse_sweeps < 1)
+        return fail(MG_ERR_INVALID_ARG, "bad iteration parameters");
+    if (!std::isfinite(c->K)) return fail(MG_ERR_INVALID_ARG, "K not finite");
+    int lv = c->levels > 0 ? c->levels : auto_levels(c->n);
+    for (int l = 0; l + 1 < lv; ++l)
+        for (int a = 0; a < 3; ++a) {
+            int m = c->n[a] >> l;
+            if ((m << l) != c->n[a] || m % 2 != 0 || m / 2 < 3)
+                return fail(MG_ERR_INVALID_ARG, "levels: every level above the coarsest needs even sizes >= 6");
+        }
+    return MG_OK;
+}
+
+struct Layout {
+    size_t X, SRC, R, partial, scal, total;
+    std::vector<size_t> eA, eB, f, c;
+};
+
+Layout layout_for(const mg_config *c)
+{
+    Layout L{};
+    int lv = c->levels > 0 ? c->levels : auto_levels(c->n);
+    size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
+    size_t tb = c->precision == MG_FP64 ? 8 : 4;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+    L.X = take(4 * N * 8);
+    L.SRC = take(5 * N * 8);
+    L.R = take(5 * N * 8);
+    for (int l = 0; l < lv; ++l) {
+        size_t Nl = ((size_t)(c->n[0] >> l)) * (c->n[1] >> l) * (c->n[2] >> l);
+        L.eA.push_back(take(4 * Nl * tb));
+        L.eB.push_back(take(4 * Nl * tb));
+        L.f.push_back(take(4 * Nl * tb));
+        L.c.push_back(take(2 * Nl * tb));
+    }
+    L.partial = take((size_t)kRedBlocks * 8 * 8);
+    L.scal = take(sizeof(Scalars));
+    L.total = off;
+    return L;
+}
+
+
+mg_status residual_any(mg_ctx *x, double *HM)
+{
+    if (x->tbytes == 8) return x->cfg.order == 2 ? engine_residual<double, 2>(x, HM) : engine_residual<double, 4>(x, HM);
+    return x->cfg.order == 2 ? engine_residual<float, 2>(x, HM) : engine_residual<float, 4>(x, HM);
+}
+
+mg_status iteration_any(mg_ctx *x)
+{
+    if (x->tbytes == 8) return x->cfg.order == 2 ? engine_iteration<double, 2>(x) : engine_iteration<double, 4>(x);
+    return x->cfg.order == 2 ? engine_iteration<float, 2>(x) : engine_iteration<float, 4>(x);
+}
+
+mg_status project_gauge(mg_ctx *x) { return engine_project_gauge(x); }
+
+mg_status start_any(mg_ctx *x)
+{
+    CKS(project_gauge(x));
+    return residual_any(x, nullptr);
+}
+
+// Capture fn's launches on the context stream into an executable graph; count its kernel nodes.
+template <class Fn>
+mg_status capture(mg_ctx *x, Fn &&fn, cudaGraphExec_t *exec, long long *kernels)
+{
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(x->stream, cudaStreamCaptureModeThreadLocal));
+    mg_status st = fn(x);
+    cudaError_t e = cudaStreamEndCapture(x->stream, &graph);
+    CKS(st);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    size_t n = 0;
+    cudaGraphGetNodes(graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    cudaGraphGetNodes(graph, nodes.data(), &n);
+    long long k = 0;
+    for (auto &nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *kernels = k;
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        return fail(MG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    }
+    return MG_OK;
+}
+
+mg_status copy_in(double *dst, const double *src, size_t n, int on_device, cudaStream_t st)
+{
+    if (!src) {
+        CK(cudaMemsetAsync(dst, 0, n * 8, st));
+        return MG_OK;
+    }
+    CK(cudaMemcpyAsync(dst, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    return MG_OK;
+}
+
+mg_status copy_out(double *dst, const double *src, size_t n, int on_device, cudaStream_t st)
+{
+    if (!dst) return MG_OK;
+    CK(cudaMemcpyAsync(dst, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    return MG_OK;
+}
+
+// Order the library's private stream after the caller's stream (entry) and the caller's
+// stream after the library's work (exit), so every call behaves as if issued on the caller's stream.
+mg_status enter(mg_ctx *x)
+{
+    CK(cudaEventRecord(x->ev_in, x->user_stream));
+    CK(cudaStreamWaitEvent(x->stream, x->ev_in, 0));
+    return MG_OK;
+}
+
+mg_status leave(mg_ctx *x, mg_status st)
+{
+    cudaError_t e1 = cudaEventRecord(x->ev_out, x->stream);
+    cudaError_t e2 = cudaStreamWaitEvent(x->user_stream, x->ev_out, 0);
+    if (st == MG_OK && (e1 != cudaSuccess || e2 != cudaSuccess))
+        return fail(MG_ERR_CUDA, "stream ordering event failed");
+    return st;
+}
+
+bool host_finite(const double *p, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+mg_status mg_config_default(mg_config *c)
+{
+    if (!c) return fail(MG_ERR_INVALID_ARG, "null config");
+    std::memset(c, 0, sizeof(*c));
+    for (int a = 0; a < 3; ++a) {
+        c->n[a] = 32;
+        c->lo[a] = 0.0;
+        c->hi[a] = 16.0;
+    }
+    c->order = 2;
+    c->bc = MG_BC_PERIODIC;
+    c->levels = 0;
+    c->precision = MG_MIXED;
+    c->k_mode = MG_K_INTEGRABILITY;
+    c->K = 0.0;
+    c->tol = 1e-10;
+    c->max_outer = 60;
+    c->nu_pre = 2;
+    c->nu_post = 2;
+    c->coarse_sweeps = 60;
+    c->use_graph = 1;
+    c->spin_limit = 1LL << 24;
+    return MG_OK;
+}
+
+mg_status mg_workspace_size(const mg_config *cfg, size_t *bytes)
+{
+    CKS(validate(cfg));
+    if (!bytes) return fail(MG_ERR_INVALID_ARG, "null bytes");
+    *bytes = layout_for(cfg).total;
+    return MG_OK;
+}
+
+mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, size_t workspace_bytes, mg_ctx **out)
+{
+    if (!out) return fail(MG_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    CKS(validate(cfg));
+    Layout lay = layout_for(cfg);
+    if (workspace && ((uintptr_t)workspace % 256 != 0 || workspace_bytes < lay.total))
+        return fail(MG_ERR_INVALID_ARG, "workspace misaligned or smaller than mg_workspace_size()");
+    mg_ctx *x = new (std::nothrow) mg_ctx();
+    if (!x) return fail(MG_ERR_OOM, "host allocation");
+    x->cfg = *cfg;
+    x->user_stream = (cudaStream_t)cuda_stream;
+    x->nlev = cfg->levels > 0 ? cfg->levels : auto_levels(cfg->n);
+    x->N = (size_t)cfg->n[0] * cfg->n[1] * cfg->n[2];
+    x->tbytes = cfg->precision == MG_FP64 ? 8 : 4;
+    mg_status st = MG_OK;
+    do {
+        if (workspace) {
+            x->ws = workspace;
+        } else {
+            cudaError_t e = cudaMalloc(&x->ws, lay.total);
+            if (e != cudaSuccess) { st = fail(MG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); break; }
+            x->own_ws = true;
+        }
+        x->ws_bytes = lay.total;
+        char *b = (char *)x->ws;
+        x->X = (double *)(b + lay.X);
+        x->SRC = (double *)(b + lay.SRC);
+        x->R = (double *)(b + lay.R);
+        x->partial = (double *)(b + lay.partial);
+        x->scal = (Scalars *)(b + lay.scal);
+        for (int l = 0; l < x->nlev; ++l) {
+            LevelBufs L;
+            Geo &g = L.geo;
+            std::memset(&g, 0, sizeof(g));
+            for (int a = 0; a < 3; ++a) {
+                g.n[a] = cfg->n[a] >> l;
+                g.lo[a] = cfg->lo[a];
+                g.h[a] = (cfg->hi[a] - cfg->lo[a]) / cfg->n[a] * (double)(1 << l);
+            }
+            g.npunct = cfg->npunct;
+            for (int p = 0; p < cfg->npunct; ++p) {
+                g.pm[p] = cfg->punct_m[p];
+                for (int a = 0; a < 3; ++a) g.px[p][a] = cfg->punct_x[p][a];
+            }
+            L.N = (size_t)g.n[0] * g.n[1] * g.n[2];
+            L.eA = b + lay.eA[l];
+            L.eB = b + lay.eB[l];
+            L.f = b + lay.f[l];
+            L.c = b + lay.c[l];
+            x->lev.push_back(L);
+        }
+        if (cudaStreamCreateWithFlags(&x->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            st = fail(MG_ERR_CUDA, "stream/event creation");
+            break;
+        }
+        cudaError_t e = cudaMallocHost(&x->host_scal, sizeof(Scalars));
+        if (e != cudaSuccess) { st = fail(MG_ERR_OOM, "cudaMallocHost"); break; }
+        if (cudaEventCreate(&x->ev0) != cudaSuccess || cudaEventCreate(&x->ev1) != cudaSuccess) {
+            st = fail(MG_ERR_CUDA, "cudaEventCreate");
+            break;
+        }
+        {
+            const int O = cfg->order;
+            st = x->tbytes == 8 ? (O == 2 ? engine_prepare<double, 2>(x) : engine_prepare<double, 4>(x))
+                                : (O == 2 ? engine_prepare<float, 2>(x) : engine_prepare<float, 4>(x));
+            if (st != MG_OK) break;
+        }
+        if ((st = enter(x)) != MG_OK) break;
+        e = cudaMemsetAsync(x->ws, 0, lay.total, x->stream);
+        if (e != cudaSuccess) { st = fail(MG_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e)); break; }
+        if ((st = leave(x, MG_OK)) != MG_OK) break;
+    } while (0);
+    if (st != MG_OK) {
+        mg_destroy(x);
+        return st;
+    }
+    *out = x;
+    return MG_OK;
+}
+
+static mg_status mg_set_conformal_metric_impl(mg_ctx *x, const double *gt, int on_device)
+{
+    if (!gt) return MG_OK;
+    std::vector<double> h(6 * x->N);
+    if (on_device) {
+        CK(cudaMemcpyAsync(h.data(), gt, 6 * x->N * 8, cudaMemcpyDeviceToHost, x->stream));
+        CK(cudaStreamSynchronize(x->stream));
+    } else {
+        std::memcpy(h.data(), gt, 6 * x->N * 8);
+    }
+    const double want[6] = {1, 0, 0, 1, 0, 1};
+    for (int c = 0; c < 6; ++c)
+        for (size_t p = 0; p < x->N; ++p)
+            if (h[c * x->N + p] != want[c])
+                return fail(MG_ERR_UNSUPPORTED, "only the conformally flat metric gt_ij = delta_ij is supported");
+    return MG_OK;
+}
+
+static mg_status mg_set_sources_impl(mg_ctx *x, const double *rho0, const double *rho2, const double *Sx, const double *Sy,
+                         const double *Sz, int on_device)
+{
+    if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");
+    if (!rho0 || !Sx || !Sy || !Sz) return fail(MG_ERR_INVALID_ARG, "rho0 and S must be given");
+    if (!on_device) {
+        const double *ptrs[5] = {rho0, rho2, Sx, Sy, Sz};
+        for (int a = 0; a < 5; ++a)
+            if (ptrs[a] && !host_finite(ptrs[a], x->N)) return fail(MG_ERR_INVALID_ARG, "non-finite source value");
+    }
+    CKS(copy_in(x->SRC, rho0, x->N, on_device, x->stream));
+    CKS(copy_in(x->SRC + x->N, rho2, x->N, on_device, x->stream));
+    CKS(copy_in(x->SRC + 2 * x->N, Sx, x->N, on_device, x->stream));
+    CKS(copy_in(x->SRC + 3 * x->N, Sy, x->N, on_device, x->stream));
+    CKS(copy_in(x->SRC + 4 * x->N, Sz, x->N, on_device, x->stream));
+    x->have_sources = true;
+    return MG_OK;
+}
+
+static mg_status mg_set_initial_guess_impl(mg_ctx *x, const double *u, const double *W, int on_device)
+{
+    if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");
+    CKS(copy_in(x->X, u, x->N, on_device, x->stream));
+    CKS(copy_in(x->X + x->N, W, 3 * x->N, on_device, x->stream));
+    return MG_OK;
+}
+
+static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
+{
+    if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");
+    if (!x->have_sources) return fail(MG_ERR_STATE, "mg_set_sources must come before mg_solve");
+    x->history.clear();
+    long long launches = 0;
+    CK(cudaEventRecord(x->ev0, x->stream));
+    if (x->cfg.use_graph) {
+        if (!x->graph_start) CKS(capture(x, start_any, &x->graph_start, &x->launches_start));
+        CK(cudaGraphLaunch(x->graph_start, x->stream));
+        launches += x->launches_start;
+    } else {
+        CKS(start_any(x));
+    }
+    CK(cudaStreamSynchronize(x->stream));
+    mg_status result = MG_ERR_NOT_CONVERGED;
+    int it = 0, grow = 0;
+    double prev = INFINITY;
+    for (;;) {
+        const Scalars &s = *x->host_scal;
+        double mx = 0.0;
+        bool finite = true;
+        for (int a = 0; a < 4; ++a) {
+            x->history.push_back(s.norms[a]);
+            if (!std::isfinite(s.norms[a])) finite = false;
+            mx = std::max(mx, s.norms[a]);
+        }
+        if (!finite || !std::isfinite(s.K2)) { result = fail(MG_ERR_DIVERGED, "constraint norm is not finite"); break; }
+        if (mx <= x->cfg.tol) { result = MG_OK; break; }
+        grow = mx > prev ? grow + 1 : 0;
+        if (grow >= 3) { result = fail(MG_ERR_DIVERGED, "constraint norm grew for 3 outer iterations"); break; }
+        prev = mx;
+        if (it >= x->cfg.max_outer) { result = fail(MG_ERR_NOT_CONVERGED, "max_outer reached"); break; }
+        if (x->cfg.use_graph) {
+            if (!x->graph_exec) CKS(capture(x, iteration_any, &x->graph_exec, &x->launches_iter));
+            CK(cudaGraphLaunch(x->graph_exec, x->stream));
+            launches += x->launches_iter;
+        } else {
+            CKS(iteration_any(x));
+        }
+        CK(cudaStreamSynchronize(x->stream));
+        ++it;
+    }
+    CK(cudaEventRecord(x->ev1, x->stream));
+    CK(cudaEventSynchronize(x->ev1));
+    if (info) {
+        const Scalars &s = *x->host_scal;
+        info->outer_iters = it;
+        info->converged = result == MG_OK;
+        info->K2 = s.K2;
+        info->K = -std::sqrt(std::max(0.0, s.K2));
+        for (int a = 0; a < 4; ++a) info->norms[a] = s.norms[a];
+        for (int a = 0; a < 3; ++a) info->mom_mean[a] = s.msrc[a];
+        info->history = x->history.data();
+        info->history_len = (int)(x->history.size() / 4);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, x->ev0, x->ev1);
+        info->device_ms = ms;
+        info->kernel_launches = x->cfg.use_graph ? launches : 0;
+    }
+    return result;
+}
+
+static mg_status mg_get_solution_impl(mg_ctx *x, double *u, double *W, double *K, int on_device)
+{
+    if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");
+    CKS(copy_out(u, x->X, x->N, on_device, x->stream));
+    CKS(copy_out(W, x->X + x->N, 3 * x->N, on_device, x->stream));
+    CK(cudaStreamSynchronize(x->stream));
+    if (K) *K = -std::sqrt(std::max(0.0, x->host_scal->K2));
+    return MG_OK;
+}
+
+static mg_status mg_residual_norms_impl(mg_ctx *x, double out[4])
+{
+    if (!x || !out) return fail(MG_ERR_INVALID_ARG, "null argument");
+    if (!x->have_sources) return fail(MG_ERR_STATE, "mg_set_sources must come first");
+    CKS(residual_any(x, nullptr));
+    CK(cudaStreamSynchronize(x->stream));
+    for (int a = 0; a < 4; ++a) out[a] = x->host_scal->norms[a];
+    return MG_OK;
+}
+
+static mg_status mg_constraint_fields_impl(mg_ctx *x, double *H, double *M, int on_device)
+{
+    if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");
+    if (!x->have_sources) return fail(MG_ERR_STATE, "mg_set_sources must come first");
+    // H and M overwrite the pass-1 buffer R (4 of its 5 fields); it is rebuilt on the next residual.
+    CKS(residual_any(x, x->R));
+    CKS(copy_out(H, x->R, x->N, on_device, x->stream));
+    CKS(copy_out(M, x->R + x->N, 3 * x->N, on_device, x->stream));
+    CK(cudaStreamSynchronize(x->stream));
+    return MG_OK;
+}
+
+static mg_status mg_time_kernel_impl(mg_ctx *x, int which, int reps, double *ms_per_launch, double *bytes_per_launch)
+{
+    if (!x || reps < 1 || which < 0 || which > 2) return fail(MG_ERR_INVALID_ARG, "bad argument");
+    float ms = 0.f;
+    const int O = x->cfg.order;
+    if (x->tbytes == 8)
+        CKS(O == 2 ? engine_time_kernel<double, 2>(x, which, reps, &ms) : engine_time_kernel<double, 4>(x, which, reps, &ms));
+    else
+        CKS(O == 2 ? engine_time_kernel<float, 2>(x, which, reps, &ms) : engine_time_kernel<float, 4>(x, which, reps, &ms));
+    double N = (double)x->N, s = (double)x->tbytes, b = 0.0;
+    if (which == 0) b = 0.5 * 14.0 * s * N;               // half of a two-colour sweep: (2 F + 6) s per cell
+    else if (which == 1) b = (10.0 * s + 4.0 * s / 8.0) * N; // read e, f, a, b; write the coarse rhs
+    else b = (9.0 * 8.0 + 5.0 * 8.0) * N;                 // read u, W, 5 sources; write 5 FP64 fields
+    if (ms_per_launch) *ms_per_launch = ms / reps;
+    if (bytes_per_launch) *bytes_per_launch = b;
+    return MG_OK;
+}
+
+// ---- public entry points: argument check, stream ordering, then the implementation
+#define MG_WRAP(call)                                                                                  \
+    do {                                                                                               \
+        if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");                                           \
+        mg_status s0 = enter(x);                                                                       \
+        if (s0 != MG_OK) return s0;                                                                    \
+        return leave(x, call);                                                                         \
+    } while (0)
+
+mg_status mg_set_sources(mg_ctx *x, const double *rho0, const double *rho2, const double *Sx, const double *Sy,
+                         const double *Sz, int on_device)
+{
+    MG_WRAP(mg_set_sources_impl(x, rho0, rho2, Sx, Sy, Sz, on_device));
+}
+mg_status mg_set_initial_guess(mg_ctx *x, const double *u, const double *W, int on_device)
+{
+    MG_WRAP(mg_set_initial_guess_impl(x, u, W, on_device));
+}
+mg_status mg_solve(mg_ctx *x, mg_solve_info *info) { MG_WRAP(mg_solve_impl(x, info)); }
+mg_status mg_set_conformal_metric(mg_ctx *x, const double *gt, int on_device)
+{
+    MG_WRAP(mg_set_conformal_metric_impl(x, gt, on_device));
+}
+mg_status mg_get_solution(mg_ctx *x, double *u, double *W, double *K, int on_device)
+{
+    MG_WRAP(mg_get_solution_impl(x, u, W, K, on_device));
+}
+mg_status mg_residual_norms(mg_ctx *x, double out[4]) { MG_WRAP(mg_residual_norms_impl(x, out)); }
+mg_status mg_constraint_fields(mg_ctx *x, double *H, double *M, int on_device)
+{
+    MG_WRAP(mg_constraint_fields_impl(x, H, M, on_device));
+}
+mg_status mg_time_kernel(mg_ctx *x, int which, int reps, double *ms_per_launch, double *bytes_per_launch)
+{
+    MG_WRAP(mg_time_kernel_impl(x, which, reps, ms_per_launch, bytes_per_launch));
+}
+
+void mg_destroy(mg_ctx *x)
+{
+    if (!x) return;
+    if (x->graph_exec) cudaGraphExecDestroy(x->graph_exec);
+    if (x->graph_start) cudaGraphExecDestroy(x->graph_start);
+    if (x->ev0) cudaEventDestroy(x->ev0);
+    if (x->ev1) cudaEventDestroy(x->ev1);
+    if (x->stream) {
+        cudaStreamSynchronize(x->stream);
+        cudaStreamDestroy(x->stream);
+    }
+    if (x->ev_in) cudaEventDestroy(x->ev_in);
+    if (x->ev_out) cudaEventDestroy(x->ev_out);
+    if (x->host_scal) cudaFreeHost(x->host_scal);
+    if (x->own_ws && x->ws) cudaFree(x->ws);
+    delete x;
+}
+
+const char *mg_status_string(mg_status s)
+{
+    switch (s) {
+    case MG_OK: return "MG_OK";
+    case MG_ERR_INVALID_ARG: return "MG_ERR_INVALID_ARG";
+    case MG_ERR_UNSUPPORTED: return "MG_ERR_UNSUPPORTED";
+    case MG_ERR_CUDA: return "MG_ERR_CUDA";
+    case MG_ERR_OOM: return "MG_ERR_OOM";
+    case MG_ERR_STATE: return "MG_ERR_STATE";
+    case MG_ERR_NOT_CONVERGED: return "MG_ERR_NOT_CONVERGED";
+    case MG_ERR_DIVERGED: return "MG_ERR_DIVERGED";
+    case MG_ERR_TIMEOUT: return "MG_ERR_TIMEOUT";
+    }
+    return "MG_ERR_UNKNOWN";
+}
+
+const char *mg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,776 @@
+// mg_kernels.cuh -- sm_103a kernels of the CTT constraint multigrid.
+//
+// Discrete system (GRTresna, arXiv:2501.13046: eq:Ham, eq:Mom in CTT form with a
+// conformally flat metric and constant K; multigrid per "Key features: Fast"):
+//   F_psi = Lap u - (K^2/12) psi^5 + (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi)
+//   F_W,i = Lap W_i + (1/3) d_i d_j W_j - 8 pi (psi^6 S_i - m_i)
+// Centred cell stencils of order 2 or 4; boundary values are produced on the fly by
+// every kernel (periodic wrap, or Robin 1/r: v(g) = v(clamp(g)) |x_clamp| / |x_g|),
+// so arrays carry no ghost cells and no fill pass exists.
+//
+// Inner problem (defect correction): the block-diagonal linearisation
+//   (Lap + c) e_psi = f_psi,   (Lap + (1/3) grad div) e_W = f_W,
+// smoothed red-black.  Each colour pass reads buffer A and writes buffer B in full
+// (the updated colour plus a copy of the other), so couplings between cells of one
+// colour (4th-order +-2 reach, mixed-derivative corners) are Jacobi and every
+// result is deterministic.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ctt {
+
+constexpr double kPi = 3.14159265358979323846;
+enum { BC_PERIODIC = 0, BC_ROBIN = 1 };
+
+struct Geo {
+    int n[3];
+    double lo[3];
+    double h[3];
+    int npunct;
+    double pm[2];
+    double px[2][3];
+};
+
+template <typename T>
+struct Coef {
+    T ih[3];    // 1/h
+    T ih2[3];   // 1/h^2
+    T dl;       // diagonal of the discrete Laplacian
+    T idW[3];   // 1 / diagonal of the momentum operator row i
+};
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+__device__ __forceinline__ double cellx(const Geo &g, int a, int i) { return g.lo[a] + (i + 0.5) * g.h[a]; }
+
+__device__ __forceinline__ double psi_background(const Geo &g, int i, int j, int k)
+{
+    double v = 1.0;
+    for (int p = 0; p < g.npunct; ++p) {
+        double dx = cellx(g, 0, i) - g.px[p][0];
+        double dy = cellx(g, 1, j) - g.px[p][1];
+        double dz = cellx(g, 2, k) - g.px[p][2];
+        v += g.pm[p] / (2.0 * sqrt(dx * dx + dy * dy + dz * dz));
+    }
+    return v;
+}
+
+// value of f at a cell that may lie outside the box (offsets are at most +-2 per axis)
+template <typename T, int BC>
+__device__ __forceinline__ T fetch_bc(const T *f, const Geo &g, int i, int j, int k)
+{
+    if constexpr (BC == BC_PERIODIC) {
+        i += (i < 0) ? g.n[0] : 0; i -= (i >= g.n[0]) ? g.n[0] : 0;
+        j += (j < 0) ? g.n[1] : 0; j -= (j >= g.n[1]) ? g.n[1] : 0;
+        k += (k < 0) ? g.n[2] : 0; k -= (k >= g.n[2]) ? g.n[2] : 0;
+        return f[i + g.n[0] * (j + g.n[1] * k)];
+    } else {
+        int bi = min(max(i, 0), g.n[0] - 1);
+        int bj = min(max(j, 0), g.n[1] - 1);
+        int bk = min(max(k, 0), g.n[2] - 1);
+        T v = f[bi + g.n[0] * (bj + g.n[1] * bk)];
+        if (bi == i && bj == j && bk == k) return v;
+        double xb = cellx(g, 0, bi), yb = cellx(g, 1, bj), zb = cellx(g, 2, bk);
+        double xg = cellx(g, 0, i), yg = cellx(g, 1, j), zg = cellx(g, 2, k);
+        double rb = sqrt(xb * xb + yb * yb + zb * zb), rg = sqrt(xg * xg + yg * yg + zg * zg);
+        return (T)((double)v * rb / rg);
+    }
+}
+
+// Accessors: value at cell p + (dx, dy, dz) of one field.
+template <typename T>
+struct AccI {   // every offset of the stencil stays inside the box
+    const T *p;
+    int sy, sz;
+    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const { return p[dx + dy * sy + dz * sz]; }
+};
+
+template <typename T, int BC>
+struct AccB {   // near the boundary
+    const T *f;
+    const Geo *g;
+    int i, j, k;
+    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
+    {
+        return fetch_bc<T, BC>(f, *g, i + dx, j + dy, k + dz);
+    }
+};
+
+template <int A, class F>
+__device__ __forceinline__ auto ax(const F &f, int s) { return f(A == 0 ? s : 0, A == 1 ? s : 0, A == 2 ? s : 0); }
+
+template <int A, int B, class F>
+__device__ __forceinline__ auto ax2(const F &f, int s, int t)
+{
+    return f((A == 0 ? s : 0) + (B == 0 ? t : 0), (A == 1 ? s : 0) + (B == 1 ? t : 0),
+             (A == 2 ? s : 0) + (B == 2 ? t : 0));
+}
+
+// first derivative along A, times h
+template <int ORDER, int A, typename T, class F>
+__device__ __forceinline__ T d1(const F &f)
+{
+    if constexpr (ORDER == 2) {
+        return (T)0.5 * (ax<A>(f, 1) - ax<A>(f, -1));
+    } else {
+        return (T)(8.0 / 12.0) * (ax<A>(f, 1) - ax<A>(f, -1)) + (T)(1.0 / 12.0) * (ax<A>(f, -2) - ax<A>(f, 2));
+    }
+}
+
+// compact second derivative along A, times h^2 (centre value passed in)
+template <int ORDER, int A, typename T, class F>
+__device__ __forceinline__ T d2(const F &f, T c)
+{
+    if constexpr (ORDER == 2) {
+        return (ax<A>(f, 1) + ax<A>(f, -1)) - (T)2 * c;
+    } else {
+        return (T)(16.0 / 12.0) * (ax<A>(f, 1) + ax<A>(f, -1)) - (T)(1.0 / 12.0) * (ax<A>(f, 2) + ax<A>(f, -2)) -
+               (T)(30.0 / 12.0) * c;
+    }
+}
+
+// D_A D_B f (A != B), times h_A h_B: tensor product of the first-derivative stencils
+template <int ORDER, int A, int B, typename T, class F>
+__device__ __forceinline__ T dmix(const F &f)
+{
+    if constexpr (ORDER == 2) {
+        return (T)0.25 * ((ax2<A, B>(f, 1, 1) - ax2<A, B>(f, 1, -1)) - (ax2<A, B>(f, -1, 1) - ax2<A, B>(f, -1, -1)));
+    } else {
+        auto inner = [&](int s) {
+            return (T)(8.0 / 12.0) * (ax2<A, B>(f, s, 1) - ax2<A, B>(f, s, -1)) +
+                   (T)(1.0 / 12.0) * (ax2<A, B>(f, s, -2) - ax2<A, B>(f, s, 2));
+        };
+        return (T)(8.0 / 12.0) * (inner(1) - inner(-1)) + (T)(1.0 / 12.0) * (inner(-2) - inner(2));
+    }
+}
+
+template <int ORDER>
+__host__ __device__ constexpr int halo() { return ORDER / 2; }
+
+__device__ __forceinline__ bool is_interior(const Geo &g, int i, int j, int k, int G)
+{
+    return i >= G && i < g.n[0] - G && j >= G && j < g.n[1] - G && k >= G && k < g.n[2] - G;
+}
+
+// ---------------------------------------------------------------------------------------
+// Linear operator of the inner problem at one cell, all 4 rows: out = J e.
+// e0..e3 accessors of the 4 correction fields.  The psi row is a Lap e0 + b e0: on the finest
+// level a = psi^-5 and b = psi^-5 c (the row scaled by psi^-5, which makes the direction of the
+// K^2 change, psi^5, a constant), on coarser levels a and b are their 8-child means.
+template <int ORDER, typename T, class F>
+__device__ __forceinline__ void apply_J(const F &e0, const F &e1, const F &e2, const F &e3, T ca, T cb,
+                                        const Coef<T> &cf, T out[4], T centre[4])
+{
+    centre[0] = e0(0, 0, 0);
+    centre[1] = e1(0, 0, 0);
+    centre[2] = e2(0, 0, 0);
+    centre[3] = e3(0, 0, 0);
+    // psi row
+    T lp = d2<ORDER, 0, T>(e0, centre[0]) * cf.ih2[0] + d2<ORDER, 1, T>(e0, centre[0]) * cf.ih2[1] +
+           d2<ORDER, 2, T>(e0, centre[0]) * cf.ih2[2];
+    out[0] = ca * lp + cb * centre[0];
+    // momentum rows: Lap W_i + (1/3)(D_ii W_i + sum_{j != i} D_i D_j W_j)
+    T dxx = d2<ORDER, 0, T>(e1, centre[1]) * cf.ih2[0];
+    T lx = dxx + d2<ORDER, 1, T>(e1, centre[1]) * cf.ih2[1] + d2<ORDER, 2, T>(e1, centre[1]) * cf.ih2[2];
+    T mx = dmix<ORDER, 0, 1, T>(e2) * (cf.ih[0] * cf.ih[1]) + dmix<ORDER, 0, 2, T>(e3) * (cf.ih[0] * cf.ih[2]);
+    out[1] = lx + (dxx + mx) * (T)(1.0 / 3.0);
+    T dyy = d2<ORDER, 1, T>(e2, centre[2]) * cf.ih2[1];
+    T ly = d2<ORDER, 0, T>(e2, centre[2]) * cf.ih2[0] + dyy + d2<ORDER, 2, T>(e2, centre[2]) * cf.ih2[2];
+    T my = dmix<ORDER, 1, 0, T>(e1) * (cf.ih[1] * cf.ih[0]) + dmix<ORDER, 1, 2, T>(e3) * (cf.ih[1] * cf.ih[2]);
+    out[2] = ly + (dyy + my) * (T)(1.0 / 3.0);
+    T dzz = d2<ORDER, 2, T>(e3, centre[3]) * cf.ih2[2];
+    T lz = d2<ORDER, 0, T>(e3, centre[3]) * cf.ih2[0] + d2<ORDER, 1, T>(e3, centre[3]) * cf.ih2[1] + dzz;
+    T mz = dmix<ORDER, 2, 0, T>(e1) * (cf.ih[2] * cf.ih[0]) + dmix<ORDER, 2, 1, T>(e2) * (cf.ih[2] * cf.ih[1]);
+    out[3] = lz + (dzz + mz) * (T)(1.0 / 3.0);
+}
+
+template <typename T, int ORDER, int BC>
+__device__ __forceinline__ void apply_J_at(const T *e, size_t N, const Geo &g, int i, int j, int k, T ca, T cb,
+                                           const Coef<T> &cf, T out[4], T centre[4])
+{
+    if (is_interior(g, i, j, k, halo<ORDER>())) {
+        int sy = g.n[0], sz = g.n[0] * g.n[1];
+        size_t p = (size_t)i + (size_t)sy * j + (size_t)sz * k;
+        AccI<T> a0{e + p, sy, sz}, a1{e + N + p, sy, sz}, a2{e + 2 * N + p, sy, sz}, a3{e + 3 * N + p, sy, sz};
+        apply_J<ORDER, T>(a0, a1, a2, a3, ca, cb, cf, out, centre);
+    } else {
+        AccB<T, BC> a0{e, &g, i, j, k}, a1{e + N, &g, i, j, k}, a2{e + 2 * N, &g, i, j, k}, a3{e + 3 * N, &g, i, j, k};
+        apply_J<ORDER, T>(a0, a1, a2, a3, ca, cb, cf, out, centre);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Red-black colour pass.  One thread per x-pair (2m, 2m+1): the cell of the active colour
+// is updated, its partner copied, and both are written with one 2-wide store.
+template <typename T, int ORDER, int BC>
+__global__ void __launch_bounds__(256) k_smooth_colour(Geo g, Coef<T> cf, const T *__restrict__ ein,
+                                                       T *__restrict__ eout, const T *__restrict__ f,
+                                                       const T *__restrict__ ab, int colour)
+{
+    using V2 = typename Vec2<T>::type;
+    const int nxp = g.n[0] >> 1;
+    const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const size_t pairs = N >> 1;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < pairs; t += (size_t)gridDim.x * blockDim.x) {
+        int ip = (int)(t % nxp);
+        size_t rest = t / nxp;
+        int j = (int)(rest % g.n[1]);
+        int k = (int)(rest / g.n[1]);
+        int sel = (j + k + colour) & 1;       // which of the pair has the active colour
+        int i = 2 * ip + sel;
+        size_t base = 2 * t;                  // linear index of cell 2*ip in row (j,k)
+        size_t p = base + sel;
+        T ca = ab[p], cb = ab[N + p];
+        T Je[4], ctr[4];
+        apply_J_at<T, ORDER, BC>(ein, N, g, i, j, k, ca, cb, cf, Je, ctr);
+        T nv[4];
+        nv[0] = ctr[0] + (f[p] - Je[0]) / (ca * cf.dl + cb);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nv[1 + a] = ctr[1 + a] + (f[(1 + a) * N + p] - Je[1 + a]) * cf.idW[a];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            T other = ein[a * N + base + (sel ^ 1)];
+            V2 v;
+            if (sel) { v.x = other; v.y = nv[a]; } else { v.x = nv[a]; v.y = other; }
+            *reinterpret_cast<V2 *>(eout + a * N + base) = v;
+        }
+    }
+}
+
+// Residual r = f - J e on the fine level, averaged over the 8 children into the coarse rhs.
+template <typename T, int ORDER, int BC>
+__global__ void __launch_bounds__(256) k_residual_restrict(Geo g, Coef<T> cf, Geo gc, const T *__restrict__ e,
+                                                           const T *__restrict__ f, const T *__restrict__ ab,
+                                                           T *__restrict__ fc)
+{
+    const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const size_t Nc = (size_t)gc.n[0] * gc.n[1] * gc.n[2];
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < Nc; q += (size_t)gridDim.x * blockDim.x) {
+        int I = (int)(q % gc.n[0]);
+        size_t rest = q / gc.n[0];
+        int J = (int)(rest % gc.n[1]);
+        int K = (int)(rest / gc.n[1]);
+        T acc[4] = {0, 0, 0, 0};
+#pragma unroll 1
+        for (int d = 0; d < 8; ++d) {
+            int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
+            size_t p = (size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k);
+            T Je[4], ctr[4];
+            apply_J_at<T, ORDER, BC>(e, N, g, i, j, k, ab[p], ab[N + p], cf, Je, ctr);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] += f[a * N + p] - Je[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fc[a * Nc + q] = acc[a] * (T)0.125;
+    }
+}
+
+// Mean of the 8 children for nf contiguous fields (the psi-row coefficients a and b).
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_mean(Geo gc, const T *__restrict__ fine, T *__restrict__ coarse,
+                                                       int nf)
+{
+    const size_t Nc = (size_t)gc.n[0] * gc.n[1] * gc.n[2];
+    const size_t Nf = 8 * Nc;
+    const int nf0 = 2 * gc.n[0], nf1 = 2 * gc.n[1];
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < Nc; q += (size_t)gridDim.x * blockDim.x) {
+        int I = (int)(q % gc.n[0]);
+        size_t rest = q / gc.n[0];
+        int J = (int)(rest % gc.n[1]);
+        int K = (int)(rest / gc.n[1]);
+        for (int a = 0; a < nf; ++a) {
+            T s = 0;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
+                s += fine[a * Nf + (size_t)i + (size_t)nf0 * ((size_t)j + (size_t)nf1 * k)];
+            }
+            coarse[a * Nc + q] = s * (T)0.125;
+        }
+    }
+}
+
+// Fine correction += cell-centred trilinear interpolation of the coarse correction
+// (weights 3/4 and 1/4 per axis, boundary values of the coarse level from the BC).
+template <typename T, int BC>
+__global__ void __launch_bounds__(256) k_prolong_add(Geo gc, const T *__restrict__ ec, T *__restrict__ ef)
+{
+    const size_t Nc = (size_t)gc.n[0] * gc.n[1] * gc.n[2];
+    const size_t Nf = 8 * Nc;
+    const int nf0 = 2 * gc.n[0], nf1 = 2 * gc.n[1];
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < Nc; q += (size_t)gridDim.x * blockDim.x) {
+        int I = (int)(q % gc.n[0]);
+        size_t rest = q / gc.n[0];
+        int J = (int)(rest % gc.n[1]);
+        int K = (int)(rest / gc.n[1]);
+        bool inner = I >= 1 && I < gc.n[0] - 1 && J >= 1 && J < gc.n[1] - 1 && K >= 1 && K < gc.n[2] - 1;
+#pragma unroll 1
+        for (int a = 0; a < 4; ++a) {
+            const T *fc = ec + a * Nc;
+            T v[3][3][3];
+#pragma unroll
+            for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx)
+                        v[dz + 1][dy + 1][dx + 1] =
+                            inner ? fc[(size_t)(I + dx) + (size_t)gc.n[0] * ((size_t)(J + dy) + (size_t)gc.n[1] * (K + dz))]
+                                  : fetch_bc<T, BC>(fc, gc, I + dx, J + dy, K + dz);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                int sx = (d & 1) ? 1 : -1, sy = ((d >> 1) & 1) ? 1 : -1, sz = (d >> 2) ? 1 : -1;
+                T s = 0;
+#pragma unroll
+                for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+                    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                        for (int cx = 0; cx < 2; ++cx) {
+                            T w = (T)((cx ? 0.25 : 0.75) * (cy ? 0.25 : 0.75) * (cz ? 0.25 : 0.75));
+                            s += w * v[1 + cz * sz][1 + cy * sy][1 + cx * sx];
+                        }
+                size_t pf = (size_t)(2 * I + (d & 1)) +
+                            (size_t)nf0 * ((size_t)(2 * J + ((d >> 1) & 1)) + (size_t)nf1 * (2 * K + (d >> 2)));
+                ef[a * Nf + pf] += s;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Block reductions (warp shuffles + shared memory), deterministic order.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *out /* per block */)
+{
+    __shared__ double sh[32][NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+        for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int a = 0; a < NV; ++a) sh[w][a] = v[a];
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            double s = l < nw ? sh[l][a] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (l == 0) out[a] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <int NV>
+__device__ __forceinline__ void block_max(double (&v)[NV], double *out)
+{
+    __shared__ double sh[32][NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+        for (int o = 16; o > 0; o >>= 1) v[a] = fmax(v[a], __shfl_down_sync(0xffffffffu, v[a], o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int a = 0; a < NV; ++a) sh[w][a] = v[a];
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            double s = l < nw ? sh[l][a] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+            if (l == 0) out[a] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// |x| with NaN mapped to +inf, so that a max-reduction cannot hide it
+__device__ __forceinline__ double absnan(double x) { return (x == x) ? fabs(x) : __longlong_as_double(0x7ff0000000000000ULL); }
+
+// Scalars shared by the outer iteration (device memory).
+struct Scalars {
+    double K2;
+    double msrc[3];
+    double norms[4];
+    double emean[4];
+    double sums[8];
+};
+
+// Final single-block reduction of per-block partial sums: partial[b * NV + a].
+template <int NV>
+__global__ void k_finalize_sum(const double *__restrict__ partial, int nblocks, double *__restrict__ out)
+{
+    double v[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int a = 0; a < NV; ++a) v[a] += partial[b * NV + a];
+    double r[NV];
+    block_sum<NV>(v, r);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < NV; ++a) out[a] = r[a];
+}
+
+template <int NV>
+__global__ void k_finalize_max(const double *__restrict__ partial, int nblocks, double *__restrict__ out)
+{
+    double v[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int a = 0; a < NV; ++a) v[a] = fmax(v[a], partial[b * NV + a]);
+    double r[NV];
+    block_max<NV>(v, r);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < NV; ++a) out[a] = r[a];
+}
+
+// Sums of 4 contiguous fields (block partials).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sum4(const T *__restrict__ x, size_t N, double *__restrict__ partial)
+{
+    double v[4] = {0, 0, 0, 0};
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] += (double)x[a * N + p];
+    double r[4];
+    block_sum<4>(v, r);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 4; ++a) partial[blockIdx.x * 4 + a] = r[a];
+}
+
+// x_a -= sums_a / N for 4 contiguous fields (periodic gauge)
+template <typename T>
+__global__ void __launch_bounds__(256) k_sub_mean4(T *__restrict__ x, size_t N, const double *__restrict__ sums)
+{
+    double m[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) m[a] = sums[a] / (double)N;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) x[a * N + p] -= (T)m[a];
+}
+
+// State update u += e - <e>, W_i += e_i - <e_i> (means only on periodic boxes).
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(double *__restrict__ x, const T *__restrict__ e, size_t N,
+                                                const double *__restrict__ esums, int periodic)
+{
+    double m[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) m[a] = periodic ? esums[a] / (double)N : 0.0;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) x[a * N + p] += (double)e[a * N + p] - m[a];
+}
+
+// ---------------------------------------------------------------------------------------
+// Outer FP64 residual, pass 1.  Per cell:
+//   R0 = Lap u + (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi)       (F_psi before the K^2 term)
+//   R1..3 = Lap W_i + (1/3) d_i d_j W_j - 8 pi psi^6 S_i                   (F_W before adding m_i)
+//   R4 = -(7/8) psi^-8 AtAt + 2 pi (5 rho0 psi^4 + rho2)                  (c before the K^2 term)
+// and block partial sums of (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi), psi^5, 8 pi psi^6 S_i.
+template <int ORDER, class F>
+__device__ __forceinline__ void outer_cell(const F &u, const F &w0, const F &w1, const F &w2, const Coef<double> &cf,
+                                           double &lu, double &aa, double mom[3])
+{
+    double G[3][3];   // G[a][b] = D_a W_b
+    G[0][0] = d1<ORDER, 0, double>(w0) * cf.ih[0];
+    G[1][0] = d1<ORDER, 1, double>(w0) * cf.ih[1];
+    G[2][0] = d1<ORDER, 2, double>(w0) * cf.ih[2];
+    G[0][1] = d1<ORDER, 0, double>(w1) * cf.ih[0];
+    G[1][1] = d1<ORDER, 1, double>(w1) * cf.ih[1];
+    G[2][1] = d1<ORDER, 2, double>(w1) * cf.ih[2];
+    G[0][2] = d1<ORDER, 0, double>(w2) * cf.ih[0];
+    G[1][2] = d1<ORDER, 1, double>(w2) * cf.ih[1];
+    G[2][2] = d1<ORDER, 2, double>(w2) * cf.ih[2];
+    double div = G[0][0] + G[1][1] + G[2][2];
+    aa = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            double A = G[a][b] + G[b][a] - (a == b ? (2.0 / 3.0) * div : 0.0);
+            aa += A * A;
+        }
+    double Je[4], ctr[4];
+    apply_J<ORDER, double>(u, w0, w1, w2, 1.0, 0.0, cf, Je, ctr);   // row 0 with a = 1, b = 0 is Lap u
+    lu = Je[0];
+    mom[0] = Je[1];
+    mom[1] = Je[2];
+    mom[2] = Je[3];
+}
+
+template <int ORDER, int BC>
+__global__ void __launch_bounds__(256) k_outer_pass1(Geo g, Coef<double> cf, const double *__restrict__ x,
+                                                     const double *__restrict__ src, double *__restrict__ R,
+                                                     double *__restrict__ partial)
+{
+    const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const int sy = g.n[0], sz = g.n[0] * g.n[1];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(p % g.n[0]);
+        size_t rest = p / g.n[0];
+        int j = (int)(rest % g.n[1]);
+        int k = (int)(rest / g.n[1]);
+        double lu, aa, mom[3];
+        if (is_interior(g, i, j, k, halo<ORDER>())) {
+            AccI<double> a0{x + p, sy, sz}, a1{x + N + p, sy, sz}, a2{x + 2 * N + p, sy, sz}, a3{x + 3 * N + p, sy, sz};
+            outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom);
+        } else {
+            AccB<double, BC> a0{x, &g, i, j, k}, a1{x + N, &g, i, j, k}, a2{x + 2 * N, &g, i, j, k},
+                a3{x + 3 * N, &g, i, j, k};
+            outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom);
+        }
+        double psi = psi_background(g, i, j, k) + x[p];
+        double rho0 = src[p], rho2 = src[N + p];
+        double ip = 1.0 / psi;
+        double p2 = psi * psi, p4 = p2 * p2, p5 = p4 * psi, p6 = p5 * psi;
+        double ip2 = ip * ip, ip4 = ip2 * ip2, ip7 = ip4 * ip2 * ip, ip8 = ip4 * ip4;
+        double nonlin = 0.125 * aa * ip7 + 2.0 * kPi * (rho0 * p5 + rho2 * psi);
+        R[p] = lu + nonlin;
+        R[4 * N + p] = -0.875 * aa * ip8 + 2.0 * kPi * (5.0 * rho0 * p4 + rho2);
+        acc[0] += nonlin;
+        acc[1] += p5;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double s = 8.0 * kPi * p6 * src[(2 + a) * N + p];
+            R[(1 + a) * N + p] = mom[a] - s;
+            acc[2 + a] += s;
+        }
+    }
+    double r[5];
+    block_sum<5>(acc, r);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 5; ++a) partial[blockIdx.x * 5 + a] = r[a];
+}
+
+// K^2 (integrability or fixed) and the momentum-source means from the pass-1 sums.
+static __global__ void k_outer_scalars(Scalars *s, size_t N, int kmode_integrability, double K2_fixed, int periodic)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    s->K2 = kmode_integrability ? 12.0 * s->sums[0] / s->sums[1] : K2_fixed;
+    for (int a = 0; a < 3; ++a) s->msrc[a] = periodic ? s->sums[2 + a] / (double)N : 0.0;
+}
+
+// Pass 2: final residuals, norm partials, inner right-hand side and coefficients in T:
+//   f = (-psi^-5 F_psi, -F_W,i),  a = psi^-5,  b = psi^-5 c,  c = dF_psi/du.
+// Optionally (HM != nullptr) writes H and M (4 FP64 fields) instead of the inner data.
+template <typename T>
+__global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__restrict__ x, const double *__restrict__ R,
+                                                     const Scalars *__restrict__ s, T *__restrict__ f,
+                                                     T *__restrict__ ab, double *__restrict__ HM,
+                                                     double *__restrict__ partial)
+{
+    const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const double K2 = s->K2;
+    const double m0 = s->msrc[0], m1 = s->msrc[1], m2 = s->msrc[2];
+    double mx[4] = {0, 0, 0, 0};
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(p % g.n[0]);
+        size_t rest = p / g.n[0];
+        int j = (int)(rest % g.n[1]);
+        int k = (int)(rest / g.n[1]);
+        double psi = psi_background(g, i, j, k) + x[p];
+        double p2 = psi * psi, p4 = p2 * p2, p5 = p4 * psi;
+        double ip = 1.0 / psi, ip2 = ip * ip, ip5 = ip2 * ip2 * ip, ip6 = ip5 * ip;
+        double Fp = R[p] - (K2 / 12.0) * p5;
+        double Fw0 = R[N + p] + m0, Fw1 = R[2 * N + p] + m1, Fw2 = R[3 * N + p] + m2;
+        double H = -8.0 * ip5 * Fp;
+        double M0 = ip6 * Fw0, M1 = ip6 * Fw1, M2 = ip6 * Fw2;
+        mx[0] = fmax(mx[0], absnan(H));
+        mx[1] = fmax(mx[1], absnan(M0));
+        mx[2] = fmax(mx[2], absnan(M1));
+        mx[3] = fmax(mx[3], absnan(M2));
+        if (HM) {
+            HM[p] = H;
+            HM[N + p] = M0;
+            HM[2 * N + p] = M1;
+            HM[3 * N + p] = M2;
+        } else {
+            f[p] = (T)(-ip5 * Fp);
+            f[N + p] = (T)(-Fw0);
+            f[2 * N + p] = (T)(-Fw1);
+            f[3 * N + p] = (T)(-Fw2);
+            ab[p] = (T)ip5;
+            ab[N + p] = (T)(ip5 * (R[4 * N + p] - (5.0 / 12.0) * K2 * p4));
+        }
+    }
+    double r[4];
+    block_max<4>(mx, r);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 4; ++a) partial[blockIdx.x * 4 + a] = r[a];
+}
+
+// ---------------------------------------------------------------------------------------
+// Coarsest level: one CTA runs all sweeps in shared memory (same colour passes and ping-pong
+// as the global smoother), then removes the means on periodic boxes and writes e.
+template <typename T, int ORDER, int BC>
+__global__ void __launch_bounds__(512) k_coarse_solve(Geo g, Coef<T> cf, const T *__restrict__ f,
+                                                      const T *__restrict__ ab, T *__restrict__ e, int sweeps,
+                                                      int periodic)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    T *eA = reinterpret_cast<T *>(smem_raw);
+    T *eB = eA + 4 * N;
+    T *fs = eB + 4 * N;
+    T *cs = fs + 4 * N;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        for (int a = 0; a < 4; ++a) {
+            eA[a * N + q] = 0;
+            fs[a * N + q] = f[a * N + q];
+        }
+        cs[q] = ab[q];
+        cs[N + q] = ab[N + q];
+    }
+    __syncthreads();
+    for (int s = 0; s < sweeps; ++s)
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int q = threadIdx.x; q < N; q += blockDim.x) {
+                int i = q % g.n[0], j = (q / g.n[0]) % g.n[1], k = q / (g.n[0] * g.n[1]);
+                if (((i + j + k) & 1) == colour) {
+                    T Je[4], ctr[4];
+                    AccB<T, BC> a0{eA, &g, i, j, k}, a1{eA + N, &g, i, j, k}, a2{eA + 2 * N, &g, i, j, k},
+                        a3{eA + 3 * N, &g, i, j, k};
+                    apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
+                    eB[q] = ctr[0] + (fs[q] - Je[0]) / (cs[q] * cf.dl + cs[N + q]);
+                    for (int a = 0; a < 3; ++a) eB[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
+                } else {
+                    for (int a = 0; a < 4; ++a) eB[a * N + q] = eA[a * N + q];
+                }
+            }
+            __syncthreads();
+            T *t = eA; eA = eB; eB = t;
+        }
+    if (periodic) {
+        double v[4] = {0, 0, 0, 0};
+        for (int q = threadIdx.x; q < N; q += blockDim.x)
+            for (int a = 0; a < 4; ++a) v[a] += (double)eA[a * N + q];
+        double r[4];
+        block_sum<4>(v, r);
+        __shared__ double mean[4];
+        if (threadIdx.x == 0)
+            for (int a = 0; a < 4; ++a) mean[a] = r[a] / N;
+        __syncthreads();
+        for (int q = threadIdx.x; q < N; q += blockDim.x)
+            for (int a = 0; a < 4; ++a) e[a * N + q] = eA[a * N + q] - (T)mean[a];
+    } else {
+        for (int q = threadIdx.x; q < N; q += blockDim.x)
+            for (int a = 0; a < 4; ++a) e[a * N + q] = eA[a * N + q];
+    }
+}
+
+// Coarsest level, psi row only: assemble the dense matrix of a Lap + b (boundary values folded
+// into the columns: periodic wrap, or the Robin ratio |x_b|/|x_g| onto the clamped cell),
+// bordered on periodic boxes by a constant Lagrange multiplier with the constraint <e> = 0,
+// and solve it by Gaussian elimination with partial pivoting in shared memory.  The exact
+// solve keeps the V-cycle contracting when the psi operator is indefinite on its lowest
+// modes (c comparable to the smallest Laplacian eigenvalue), where Gauss-Seidel diverges.
+// Overwrites e[0 .. N).  Shared memory: (m^2 + m) T, m = N + periodic.
+template <typename T, int ORDER, int BC>
+__global__ void __launch_bounds__(512) k_coarse_psi_direct(Geo g, Coef<T> cf, const T *__restrict__ f,
+                                                           const T *__restrict__ ab, T *__restrict__ e,
+                                                           int periodic)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int piv;
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const int m = N + (periodic ? 1 : 0);
+    const int tid = threadIdx.x, bs = blockDim.x;
+    T *A = reinterpret_cast<T *>(smem_raw);
+    T *rhs = A + (size_t)m * m;
+    for (int t = tid; t < m * m; t += bs) A[t] = 0;
+    __syncthreads();
+    const T w1 = ORDER == 2 ? (T)1 : (T)(16.0 / 12.0);
+    const T w2 = ORDER == 2 ? (T)0 : (T)(-1.0 / 12.0);
+    for (int p = tid; p < N; p += bs) {
+        int i = p % g.n[0], j = (p / g.n[0]) % g.n[1], k = p / (g.n[0] * g.n[1]);
+        T a = ab[p], b = ab[N + p];
+        T *row = A + (size_t)p * m;
+        row[p] += a * cf.dl + b;
+        for (int ax = 0; ax < 3; ++ax)
+            for (int s = -2; s <= 2; ++s) {
+                if (s == 0 || (ORDER == 2 && (s == 2 || s == -2))) continue;
+                T w = a * ((s == 1 || s == -1) ? w1 : w2) * cf.ih2[ax];
+                int c[3] = {i, j, k};
+                c[ax] += s;
+                if (BC == BC_PERIODIC) {
+                    c[ax] += c[ax] < 0 ? g.n[ax] : 0;
+                    c[ax] -= c[ax] >= g.n[ax] ? g.n[ax] : 0;
+                    row[c[0] + g.n[0] * (c[1] + g.n[1] * c[2])] += w;
+                } else {
+                    int bc[3] = {min(max(c[0], 0), g.n[0] - 1), min(max(c[1], 0), g.n[1] - 1),
+                                 min(max(c[2], 0), g.n[2] - 1)};
+                    double ratio = 1.0;
+                    if (bc[ax] != c[ax]) {
+                        double xb = cellx(g, 0, bc[0]), yb = cellx(g, 1, bc[1]), zb = cellx(g, 2, bc[2]);
+                        double xg = cellx(g, 0, c[0]), yg = cellx(g, 1, c[1]), zg = cellx(g, 2, c[2]);
+                        ratio = sqrt(xb * xb + yb * yb + zb * zb) / sqrt(xg * xg + yg * yg + zg * zg);
+                    }
+                    row[bc[0] + g.n[0] * (bc[1] + g.n[1] * bc[2])] += (T)((double)w * ratio);
+                }
+            }
+        if (periodic) {
+            row[N] = 1;
+            A[(size_t)N * m + p] = 1;
+        }
+        rhs[p] = f[p];
+    }
+    if (periodic && tid == 0) rhs[N] = 0;
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        if (tid < 32) {   // pivot: largest |A[i][k]|, i >= k (ties: smallest i)
+            T best = (T)-1;
+            int bi = m;
+            for (int i = k + tid; i < m; i += 32) {
+                T v = fabs(A[(size_t)i * m + k]);
+                if (v > best) { best = v; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                T ov = __shfl_down_sync(0xffffffffu, best, o);
+                int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (tid == 0) piv = bi;
+        }
+        __syncthreads();
+        const int pr = piv;
+        if (pr != k) {
+            for (int jj = k + tid; jj <= m; jj += bs) {
+                T *x = jj < m ? &A[(size_t)k * m + jj] : &rhs[k];
+                T *y = jj < m ? &A[(size_t)pr * m + jj] : &rhs[pr];
+                T t = *x; *x = *y; *y = t;
+            }
+            __syncthreads();
+        }
+        const T pv = A[(size_t)k * m + k];
+        for (int i = k + 1 + tid; i < m; i += bs) A[(size_t)i * m + k] /= pv;
+        __syncthreads();
+        const int rows = m - k - 1, cols = m - k;   // cols: A[i][k+1 .. m-1] and rhs[i]
+        for (int t = tid; t < rows * cols; t += bs) {
+            int i = k + 1 + t / cols, jj = t % cols;
+            T l = A[(size_t)i * m + k];
+            if (jj < cols - 1) A[(size_t)i * m + k + 1 + jj] -= l * A[(size_t)k * m + k + 1 + jj];
+            else rhs[i] -= l * rhs[k];
+        }
+        __syncthreads();
+    }
+    for (int k = m - 1; k >= 0; --k) {
+        if (tid == 0) rhs[k] /= A[(size_t)k * m + k];
+        __syncthreads();
+        for (int i = tid; i < k; i += bs) rhs[i] -= A[(size_t)i * m + k] * rhs[k];
+        __syncthreads();
+    }
+    for (int p = tid; p < N; p += bs) e[p] = rhs[p];
+}
+
+}  // namespace ctt

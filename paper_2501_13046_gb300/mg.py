@@ -1,0 +1,204 @@
+"""Thin Python binding of the C ABI in include/ctt_mg.h (libctt_mg.so).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+The functions carry the C names.  Device buffers may be torch tensors (their
+data_ptr() is passed with on_device=1) and host buffers numpy float64 arrays.
+torch supplies device memory (the workspace) and the CUDA stream.
+
+There is no fallback: if the shared library is missing or fails to load, the
+import raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libctt_mg.so")
+
+MG_OK, MG_ERR_INVALID_ARG, MG_ERR_UNSUPPORTED, MG_ERR_CUDA, MG_ERR_OOM, MG_ERR_STATE, \
+    MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED, MG_ERR_TIMEOUT = range(9)
+MG_BC_PERIODIC, MG_BC_ROBIN = 0, 1
+MG_FP64, MG_MIXED = 0, 1
+MG_K_FIXED, MG_K_INTEGRABILITY = 0, 1
+
+EXPORTS = ("mg_config_default", "mg_workspace_size", "mg_create", "mg_set_conformal_metric", "mg_set_sources",
+           "mg_set_initial_guess", "mg_solve", "mg_get_solution", "mg_residual_norms", "mg_constraint_fields",
+           "mg_time_kernel", "mg_destroy", "mg_status_string", "mg_last_error")
+
+
+class mg_config(C.Structure):
+    _fields_ = [
+        ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("order", C.c_int), ("bc", C.c_int),
+        ("levels", C.c_int), ("precision", C.c_int), ("k_mode", C.c_int), ("K", C.c_double), ("npunct", C.c_int),
+        ("punct_m", C.c_double * 2), ("punct_x", (C.c_double * 3) * 2), ("tol", C.c_double), ("max_outer", C.c_int),
+        ("nu_pre", C.c_int), ("nu_post", C.c_int), ("coarse_sweeps", C.c_int), ("use_graph", C.c_int),
+        ("spin_limit", C.c_longlong),
+    ]
+
+
+class mg_solve_info(C.Structure):
+    _fields_ = [
+        ("outer_iters", C.c_int), ("converged", C.c_int), ("K", C.c_double), ("K2", C.c_double),
+        ("norms", C.c_double * 4), ("mom_mean", C.c_double * 3), ("history", C.POINTER(C.c_double)),
+        ("history_len", C.c_int), ("device_ms", C.c_double), ("kernel_launches", C.c_longlong),
+    ]
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, where, detail):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, _lib.mg_status_string(status).decode(), detail))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libctt_mg.so is not built; run __graft_entry__.build() (no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    L.mg_config_default.argtypes = [C.POINTER(mg_config)]
+    L.mg_workspace_size.argtypes = [C.POINTER(mg_config), C.POINTER(C.c_size_t)]
+    L.mg_create.argtypes = [C.POINTER(mg_config), vp, vp, C.c_size_t, C.POINTER(vp)]
+    L.mg_set_conformal_metric.argtypes = [vp, vp, C.c_int]
+    L.mg_set_sources.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int]
+    L.mg_set_initial_guess.argtypes = [vp, vp, vp, C.c_int]
+    L.mg_solve.argtypes = [vp, C.POINTER(mg_solve_info)]
+    L.mg_get_solution.argtypes = [vp, vp, vp, dp, C.c_int]
+    L.mg_residual_norms.argtypes = [vp, dp]
+    L.mg_constraint_fields.argtypes = [vp, vp, vp, C.c_int]
+    L.mg_time_kernel.argtypes = [vp, C.c_int, C.c_int, dp, dp]
+    L.mg_destroy.argtypes = [vp]
+    L.mg_destroy.restype = None
+    L.mg_status_string.argtypes = [C.c_int]
+    L.mg_status_string.restype = C.c_char_p
+    L.mg_last_error.argtypes = []
+    L.mg_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("mg_destroy", "mg_status_string", "mg_last_error"):
+            getattr(L, name).restype = C.c_int
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(st, where, allow=()):
+    if st != MG_OK and st not in allow:
+        raise MGError(st, where, _lib.mg_last_error().decode())
+    return st
+
+
+def _ptr(x):
+    """(pointer, on_device) for a torch tensor, numpy array or None."""
+    if x is None:
+        return None, 0
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "tensor must be contiguous"
+        return x.data_ptr(), int(x.is_cuda)
+    assert isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous
+    return x.ctypes.data, 0
+
+
+def mg_config_default():
+    cfg = mg_config()
+    _check(_lib.mg_config_default(C.byref(cfg)), "mg_config_default")
+    return cfg
+
+
+def mg_workspace_size(cfg):
+    n = C.c_size_t(0)
+    _check(_lib.mg_workspace_size(C.byref(cfg), C.byref(n)), "mg_workspace_size")
+    return n.value
+
+
+def mg_create(cfg, stream=0, workspace=None):
+    """stream: a cudaStream_t as int (e.g. torch.cuda.current_stream().cuda_stream);
+    workspace: optional device tensor of at least mg_workspace_size(cfg) bytes."""
+    out = C.c_void_p()
+    wp, nb = (None, 0) if workspace is None else (workspace.data_ptr(), workspace.numel() * workspace.element_size())
+    _check(_lib.mg_create(C.byref(cfg), C.c_void_p(stream or None), C.c_void_p(wp), nb, C.byref(out)), "mg_create")
+    return out
+
+
+def mg_set_conformal_metric(ctx, gt):
+    p, dev = _ptr(gt)
+    return _check(_lib.mg_set_conformal_metric(ctx, p, dev), "mg_set_conformal_metric")
+
+
+def mg_set_sources(ctx, rho0, rho2, Sx, Sy, Sz):
+    ps = [_ptr(a) for a in (rho0, rho2, Sx, Sy, Sz)]
+    dev = max(d for _, d in ps)
+    return _check(_lib.mg_set_sources(ctx, *[p for p, _ in ps], dev), "mg_set_sources")
+
+
+def mg_set_initial_guess(ctx, u, W):
+    (pu, du), (pw, dw) = _ptr(u), _ptr(W)
+    return _check(_lib.mg_set_initial_guess(ctx, pu, pw, max(du, dw)), "mg_set_initial_guess")
+
+
+def mg_solve(ctx, allow=(MG_ERR_NOT_CONVERGED,)):
+    """Returns (status, info dict)."""
+    info = mg_solve_info()
+    st = _check(_lib.mg_solve(ctx, C.byref(info)), "mg_solve", allow)
+    hist = np.ctypeslib.as_array(info.history, shape=(info.history_len * 4,)).reshape(-1, 4).copy() \
+        if info.history_len > 0 else np.zeros((0, 4))
+    return st, dict(outer_iters=info.outer_iters, converged=bool(info.converged), K=info.K, K2=info.K2,
+                    norms=np.array(info.norms[:]), mom_mean=np.array(info.mom_mean[:]), history=hist,
+                    device_ms=info.device_ms, kernel_launches=info.kernel_launches)
+
+
+def mg_get_solution(ctx, u=None, W=None):
+    (pu, du), (pw, dw) = _ptr(u), _ptr(W)
+    K = C.c_double(0.0)
+    _check(_lib.mg_get_solution(ctx, pu, pw, C.byref(K), max(du, dw)), "mg_get_solution")
+    return K.value
+
+
+def mg_residual_norms(ctx):
+    out = (C.c_double * 4)()
+    _check(_lib.mg_residual_norms(ctx, out), "mg_residual_norms")
+    return np.array(out[:])
+
+
+def mg_constraint_fields(ctx, H=None, M=None):
+    (ph, dh), (pm, dm) = _ptr(H), _ptr(M)
+    return _check(_lib.mg_constraint_fields(ctx, ph, pm, max(dh, dm)), "mg_constraint_fields")
+
+
+def mg_time_kernel(ctx, which, reps):
+    """(ms per launch, algorithmic bytes per launch) of one solver kernel; see the header."""
+    ms, b = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.mg_time_kernel(ctx, which, reps, C.byref(ms), C.byref(b)), "mg_time_kernel")
+    return ms.value, b.value
+
+
+def mg_destroy(ctx):
+    _lib.mg_destroy(ctx)
+
+
+def config_for(problem, precision=MG_MIXED, **overrides):
+    """mg_config for a problem dict of paper_2501_13046_gb300.fields (marshalling only)."""
+    cfg = mg_config_default()
+    n = problem["n"]
+    lo, hi = problem["lo"], problem["hi"]
+    for a in range(3):
+        cfg.n[a] = n[a]
+        cfg.lo[a] = lo if np.isscalar(lo) else lo[a]
+        cfg.hi[a] = hi if np.isscalar(hi) else hi[a]
+    cfg.order = problem["order"]
+    cfg.bc = problem["bc"]
+    cfg.k_mode = problem["kmode"]
+    cfg.K = problem["K"]
+    cfg.precision = precision
+    cfg.npunct = len(problem["punctures"])
+    for p, (m, x) in enumerate(problem["punctures"]):
+        cfg.punct_m[p] = m
+        for a in range(3):
+            cfg.punct_x[p][a] = x[a]
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg

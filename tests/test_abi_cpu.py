@@ -1,0 +1,70 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads and exports
+every entry point include/ctt_mg.h declares, and the ctypes structs match the
+header's layout."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ctt_mg.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2501_13046_gb300 import _build
+    _build.build()
+    from paper_2501_13046_gb300 import mg
+    return mg
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "mg_solve" in names and "mg_create" in names and "mg_residual_norms" in names
+    raw = C.CDLL(lib.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+    assert set(names) <= set(lib.EXPORTS) | {"mg_config_default"}
+
+
+def test_config_defaults_and_workspace_size(lib):
+    cfg = lib.mg_config_default()
+    assert cfg.order == 2 and cfg.tol == 1e-10 and cfg.precision == lib.MG_MIXED and cfg.use_graph == 1
+    cfg.n[0] = cfg.n[1] = cfg.n[2] = 32
+    nbytes = lib.mg_workspace_size(cfg)
+    N = 32 ** 3
+    # FP64 state (4), sources (5), pass-1 output (5) plus FP32 levels (13 arrays, 8/7 geometric)
+    assert nbytes >= 14 * 8 * N + 13 * 4 * N
+    assert nbytes <= 14 * 8 * N + 13 * 4 * N * 8 // 7 + 2 ** 20
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("order", 3, 1), ("bc", 7, 1), ("precision", 5, 1), ("levels", 6, 1), ("coarse_sweeps", 0, 1),
+])
+def test_invalid_configs_are_rejected_on_the_host(lib, field, value, status):
+    cfg = lib.mg_config_default()
+    setattr(cfg, field, value)
+    with pytest.raises(lib.MGError) as e:
+        lib.mg_workspace_size(cfg)
+    assert e.value.status == status
+
+
+def test_punctures_need_robin(lib):
+    cfg = lib.mg_config_default()
+    cfg.npunct = 1
+    with pytest.raises(lib.MGError) as e:
+        lib.mg_workspace_size(cfg)
+    assert e.value.status == lib.MG_ERR_UNSUPPORTED
+
+
+def test_status_strings(lib):
+    L = lib.lib()
+    assert L.mg_status_string(0) == b"MG_OK"
+    assert L.mg_status_string(8) == b"MG_ERR_TIMEOUT"
