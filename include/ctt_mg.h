@@ -141,6 +141,32 @@ mg_status mg_constraint_fields(struct mg_ctx *ctx, double *H, double *M, int on_
  */
 mg_status mg_time_kernel(struct mg_ctx *ctx, int which, int reps, double *ms_per_launch, double *bytes_per_launch);
 
+/*
+ * mg_residual_norms_noalloc -- the constraint norms of mg_residual_norms for a state held by the
+ * caller, computed without allocating anything.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc or any other allocator, for example a host
+ * process whose device memory belongs to a fixed arena or another framework's allocator, or a
+ * loop that must not allocate after start-up.  It takes no context.
+ *
+ *   cfg         grid, order, bc, k_mode, K and punctures (the iteration fields are ignored);
+ *               at most 262144 cells (64^3), larger grids return MG_ERR_INVALID_ARG.
+ *   u, W        device arrays, N and 3N doubles (layout as above); psi = 1 + punctures + u.
+ *   rho0, S     device arrays, N and 3N doubles; rho2 device array or NULL (zero).
+ *   out         host array of 4 doubles: max |H|, max |M_x|, max |M_y|, max |M_z|.
+ *   K2          host pointer or NULL: the K^2 used (integrability value on periodic boxes).
+ *   cuda_stream stream for all work (NULL = legacy default stream); the call synchronises it.
+ *
+ * Scratch: one file-scope device array of 10.54 MB, which every GPU that loads the library
+ * holds until the process exits.  The first call on a device looks up that device's address of
+ * the array (with the device current) and caches it, so make the first call on each device
+ * before any stream capture.  All calls share the array and it keeps the last call's contents;
+ * two calls whose work overlaps on the GPU (different streams, or different threads) race on
+ * it and give undefined results, so serialise them.  The call allocates no device or host memory.
+ */
+mg_status mg_residual_norms_noalloc(const mg_config *cfg, const double *u, const double *W, const double *rho0,
+                                    const double *rho2, const double *S, double out[4], double *K2,
+                                    void *cuda_stream);
+
 void mg_destroy(struct mg_ctx *ctx);
 
 const char *mg_status_string(mg_status s);

@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libctt_mg.so")
 OBJDIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["ctt_mg.cu", "mg_engine_f32_o2.cu", "mg_engine_f32_o4.cu", "mg_engine_f64_o2.cu", "mg_engine_f64_o4.cu"]
+SOURCES = ["ctt_mg.cu", "mg_engine_f32_o2.cu", "mg_engine_f32_o4.cu", "mg_engine_f64_o2.cu", "mg_engine_f64_o4.cu", "mg_noalloc.cu"]
 
 
 def nvcc():

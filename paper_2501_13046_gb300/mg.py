@@ -24,7 +24,7 @@ MG_K_FIXED, MG_K_INTEGRABILITY = 0, 1
 
 EXPORTS = ("mg_config_default", "mg_workspace_size", "mg_create", "mg_set_conformal_metric", "mg_set_sources",
            "mg_set_initial_guess", "mg_solve", "mg_get_solution", "mg_residual_norms", "mg_constraint_fields",
-           "mg_time_kernel", "mg_destroy", "mg_status_string", "mg_last_error")
+           "mg_time_kernel", "mg_residual_norms_noalloc", "mg_destroy", "mg_status_string", "mg_last_error")
 
 
 class mg_config(C.Structure):
@@ -67,6 +67,7 @@ def _load():
     L.mg_residual_norms.argtypes = [vp, dp]
     L.mg_constraint_fields.argtypes = [vp, vp, vp, C.c_int]
     L.mg_time_kernel.argtypes = [vp, C.c_int, C.c_int, dp, dp]
+    L.mg_residual_norms_noalloc.argtypes = [C.POINTER(mg_config), vp, vp, vp, vp, vp, dp, dp, vp]
     L.mg_destroy.argtypes = [vp]
     L.mg_destroy.restype = None
     L.mg_status_string.argtypes = [C.c_int]
@@ -174,6 +175,17 @@ def mg_time_kernel(ctx, which, reps):
     ms, b = C.c_double(0.0), C.c_double(0.0)
     _check(_lib.mg_time_kernel(ctx, which, reps, C.byref(ms), C.byref(b)), "mg_time_kernel")
     return ms.value, b.value
+
+
+def mg_residual_norms_noalloc(cfg, u, W, rho0, rho2, S, stream=0):
+    """Constraint norms (and K^2) of a caller-held device state, with no allocation in the library.
+    u, W, rho0, rho2 (or None), S: contiguous float64 CUDA tensors.  Returns (norms[4], K2)."""
+    out = (C.c_double * 4)()
+    k2 = C.c_double(0.0)
+    ptr = lambda t: None if t is None else t.data_ptr()
+    _check(_lib.mg_residual_norms_noalloc(C.byref(cfg), ptr(u), ptr(W), ptr(rho0), ptr(rho2), ptr(S), out,
+                                          C.byref(k2), C.c_void_p(stream or None)), "mg_residual_norms_noalloc")
+    return np.array(out[:]), k2.value
 
 
 def mg_destroy(ctx):
