@@ -75,6 +75,7 @@ typedef struct {
     int coarse_sweeps;    /* red-black sweeps on the coarsest level (default 60)                  */
     int use_graph;        /* 1 = replay each outer iteration as a captured CUDA graph (default 1) */
     long long spin_limit; /* bound on any device-side wait, in polls (default 1<<24)              */
+    int inner_cycles;     /* V-cycles per outer iteration, 0 = auto (1 for MG_FP64, 2 for MG_MIXED) */
 } mg_config;
 
 typedef struct {

@@ -45,6 +45,7 @@ mg_status validate(const mg_config *c)
     if (!(c->tol >= 0.0) || c->max_outer < 0 || c->nu_pre < 0 || c->nu_post < 0 || c->coarse_sweeps < 1)
         return fail(MG_ERR_INVALID_ARG, "bad iteration parameters");
     if (!std::isfinite(c->K)) return fail(MG_ERR_INVALID_ARG, "K not finite");
+    if (c->inner_cycles < 0 || c->inner_cycles > 8) return fail(MG_ERR_INVALID_ARG, "inner_cycles must be 0..8");
     int lv = c->levels > 0 ? c->levels : auto_levels(c->n);
     for (int l = 0; l + 1 < lv; ++l)
         for (int a = 0; a < 3; ++a) {
@@ -203,6 +204,7 @@ mg_status mg_config_default(mg_config *c)
     c->coarse_sweeps = 60;
     c->use_graph = 1;
     c->spin_limit = 1LL << 24;
+    c->inner_cycles = 0;
     return MG_OK;
 }
 
@@ -225,6 +227,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
     mg_ctx *x = new (std::nothrow) mg_ctx();
     if (!x) return fail(MG_ERR_OOM, "host allocation");
     x->cfg = *cfg;
+    if (x->cfg.inner_cycles == 0) x->cfg.inner_cycles = cfg->precision == MG_FP64 ? 1 : 2;
     x->user_stream = (cudaStream_t)cuda_stream;
     x->nlev = cfg->levels > 0 ? cfg->levels : auto_levels(cfg->n);
     x->N = (size_t)cfg->n[0] * cfg->n[1] * cfg->n[2];
@@ -264,6 +267,8 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
             L.eB = b + lay.eB[l];
             L.f = b + lay.f[l];
             L.c = b + lay.c[l];
+            L.split = l + 1 < x->nlev ? 1 : 0;
+            L.curB = 0;
             x->lev.push_back(L);
         }
         if (cudaStreamCreateWithFlags(&x->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -447,7 +452,7 @@ static mg_status mg_time_kernel_impl(mg_ctx *x, int which, int reps, double *ms_
     else
         CKS(O == 2 ? engine_time_kernel<float, 2>(x, which, reps, &ms) : engine_time_kernel<float, 4>(x, which, reps, &ms));
     double N = (double)x->N, s = (double)x->tbytes, b = 0.0;
-    if (which == 0) b = 0.5 * 14.0 * s * N;               // half of a two-colour sweep: (2 F + 6) s per cell
+    if (which == 0) b = 0.5 * 14.0 * s * N;               // half of a two-colour sweep: (2 F + 6) s per cell (algorithmic)
     else if (which == 1) b = (10.0 * s + 4.0 * s / 8.0) * N; // read e, f, a, b; write the coarse rhs
     else b = (9.0 * 8.0 + 5.0 * 8.0) * N;                 // read u, W, 5 sources; write 5 FP64 fields
     if (ms_per_launch) *ms_per_launch = ms / reps;

@@ -62,6 +62,10 @@ struct LevelBufs {
     Geo geo;
     size_t N;
     void *eA, *eB, *f, *c;   // T arrays: 4N, 4N, 4N, 2N (c holds the psi-row coefficients a, b)
+    int split;               // 1: colour-split storage (every level above the coarsest), 0: plain
+    int curB;                // enqueue-time bookkeeping: 1 when eB holds the current correction
+    void *cur() const { return curB ? eB : eA; }
+    void *alt() const { return curB ? eA : eB; }
 };
 
 template <typename T>

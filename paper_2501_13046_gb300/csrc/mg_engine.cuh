@@ -5,6 +5,38 @@
 
 namespace ctt {
 
+// Block split of a colour pass: shell blocks first, then interior-box blocks.
+inline Regions smooth_regions(const Geo &g, int order, int *grid)
+{
+    Regions r;
+    r.G = order / 2;
+    long long ix = g.n[0] - 2 * r.G, iy = g.n[1] - 2 * r.G, iz = g.n[2] - 2 * r.G;
+    size_t nint = (ix > 0 && iy > 0 && iz > 0) ? (size_t)ix * iy * iz / 2 : 0;
+    size_t nsh = shell_count(g.n, r.G);
+    // one thread per cell: blocks then sweep the box in z order, so neighbouring planes are
+    // reused from L2 while they are still resident
+    int bi = nint ? grid_for(nint, 1 << 24) : 0;
+    int bs = nsh ? grid_for(nsh, 152 * 4) : 0;
+    r.nblk_sh = bs;
+    *grid = std::max(1, bi + bs);
+    return r;
+}
+
+// Block split of residual+restriction over the coarse cells: coarse interior box [1, nc-1)^3, shell.
+inline Regions restrict_regions(const Geo &gc, int *grid)
+{
+    Regions r;
+    r.G = 1;
+    long long ix = gc.n[0] - 2, iy = gc.n[1] - 2, iz = gc.n[2] - 2;
+    size_t nint = (ix > 0 && iy > 0 && iz > 0) ? (size_t)ix * iy * iz : 0;
+    size_t nsh = shell_count(gc.n, 1);
+    int bi = nint ? grid_for(nint, 1 << 24) : 0;
+    int bs = nsh ? grid_for(nsh, 152 * 4) : 0;
+    r.nblk_sh = bs;
+    *grid = std::max(1, bi + bs);
+    return r;
+}
+
 template <class Fn>
 void dispatch_bc(int bc, Fn &&fn)
 {
@@ -12,22 +44,27 @@ void dispatch_bc(int bc, Fn &&fn)
     else fn(std::integral_constant<int, BC_ROBIN>());
 }
 
+// `sweeps` red-black sweeps on a colour-split level.  Each sweep reads the current buffer and
+// writes the alternate one (red half, then black half), then the two swap roles.
 template <typename T, int ORDER>
 mg_status enqueue_sweeps(mg_ctx *x, int l, int sweeps)
 {
     LevelBufs &L = x->lev[l];
     Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
-    size_t pairs = L.N / 2;
-    int grid = grid_for(pairs);
-    for (int s = 0; s < sweeps; ++s)
+    int grid = 0;
+    Regions rg = smooth_regions(L.geo, ORDER, &grid);
+    for (int s = 0; s < sweeps; ++s) {
+        const T *X = (const T *)L.cur();
+        T *Y = (T *)L.alt();
         for (int colour = 0; colour < 2; ++colour) {
-            const T *ein = (const T *)(colour == 0 ? L.eA : L.eB);
-            T *eout = (T *)(colour == 0 ? L.eB : L.eA);
+            const T *O = colour == 0 ? X : Y;
             dispatch_bc(x->cfg.bc, [&](auto B) {
                 k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, kThreads, 0, x->stream>>>(
-                    L.geo, cf, ein, eout, (const T *)L.f, (const T *)L.c, colour);
+                    L.geo, cf, X, O, Y, (const T *)L.f, (const T *)L.c, colour, rg);
             });
         }
+        L.curB ^= 1;
+    }
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -56,45 +93,42 @@ mg_status enqueue_coarse(mg_ctx *x, int l)
         }
         return MG_OK;
     }
-    // coarsest level too large for one CTA: global colour passes, then the periodic mean projection
-    if (L.geo.n[0] % 2 != 0) return fail(MG_ERR_UNSUPPORTED, "coarsest level too large for one CTA and odd in x");
-    CK(cudaMemsetAsync(L.eA, 0, 4 * L.N * tb, x->stream));
-    CKS(enqueue_sweeps<T, ORDER>(x, l, x->cfg.coarse_sweeps));
-    if (periodic) {
-        int g = grid_for(L.N, kRedBlocks);
-        k_sum4<T><<<g, kThreads, 0, x->stream>>>((const T *)L.eA, L.N, x->partial);
-        k_finalize_sum<4><<<1, 256, 0, x->stream>>>(x->partial, g, x->scal->emean);
-        k_sub_mean4<T><<<grid_for(L.N), kThreads, 0, x->stream>>>((T *)L.eA, L.N, x->scal->emean);
-        CK(cudaGetLastError());
-    }
-    return MG_OK;
+    return fail(MG_ERR_UNSUPPORTED, "coarsest level too large for the one-CTA coarse solve; use more levels");
 }
 
+// One V-cycle on J e = f.  first: the finest correction starts at zero; otherwise the cycle
+// continues from the current finest correction (coarser levels always start at zero).
 template <typename T, int ORDER>
-mg_status enqueue_vcycle(mg_ctx *x)
+mg_status enqueue_vcycle(mg_ctx *x, bool first)
 {
     const int Lc = x->nlev - 1;
     size_t tb = sizeof(T);
     for (int l = 0; l < Lc; ++l) {
         LevelBufs &L = x->lev[l];
-        CK(cudaMemsetAsync(L.eA, 0, 4 * L.N * tb, x->stream));
+        if (l > 0 || first) {
+            L.curB = 0;
+            CK(cudaMemsetAsync(L.eA, 0, 4 * L.N * tb, x->stream));
+        }
         CKS(enqueue_sweeps<T, ORDER>(x, l, x->cfg.nu_pre));
         LevelBufs &C = x->lev[l + 1];
         Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
+        int rgrid = 0;
+        Regions rr = restrict_regions(C.geo, &rgrid);
         dispatch_bc(x->cfg.bc, [&](auto B) {
-            k_residual_restrict<T, ORDER, decltype(B)::value><<<grid_for(C.N), kThreads, 0, x->stream>>>(
-                L.geo, cf, C.geo, (const T *)L.eA, (const T *)L.f, (const T *)L.c, (T *)C.f);
+            k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, kThreads, 0, x->stream>>>(
+                L.geo, cf, C.geo, (const T *)L.cur(), (const T *)L.f, (const T *)L.c, (T *)C.f, C.split, rr);
         });
         CK(cudaGetLastError());
     }
+    x->lev[Lc].curB = 0;
     CKS(enqueue_coarse<T, ORDER>(x, Lc));
     for (int l = Lc - 1; l >= 0; --l) {
         LevelBufs &L = x->lev[l];
         LevelBufs &C = x->lev[l + 1];
-        if (x->cfg.bc == MG_BC_PERIODIC)
-            k_prolong_add<T, BC_PERIODIC><<<grid_for(C.N), kThreads, 0, x->stream>>>(C.geo, (const T *)C.eA, (T *)L.eA);
-        else
-            k_prolong_add<T, BC_ROBIN><<<grid_for(C.N), kThreads, 0, x->stream>>>(C.geo, (const T *)C.eA, (T *)L.eA);
+        dispatch_bc(x->cfg.bc, [&](auto B) {
+            k_prolong_add<T, decltype(B)::value><<<grid_for(C.N, 1 << 24), kThreads, 0, x->stream>>>(
+                L.geo, C.geo, (const T *)C.cur(), (T *)L.cur(), C.split);
+        });
         CK(cudaGetLastError());
         CKS(enqueue_sweeps<T, ORDER>(x, l, x->cfg.nu_post));
     }
@@ -117,7 +151,7 @@ mg_status enqueue_residual(mg_ctx *x, double *HM)
     k_outer_scalars<<<1, 1, 0, x->stream>>>(x->scal, x->N, x->cfg.k_mode == MG_K_INTEGRABILITY, K2f,
                                            x->cfg.bc == MG_BC_PERIODIC);
     k_outer_pass2<T><<<g1, kThreads, 0, x->stream>>>(L0.geo, x->X, x->R, x->scal, (T *)L0.f, (T *)L0.c, HM,
-                                                     x->partial);
+                                                     x->partial, L0.split);
     k_finalize_max<4><<<1, 256, 0, x->stream>>>(x->partial, g1, x->scal->norms);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(x->host_scal, x->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, x->stream));
@@ -129,18 +163,20 @@ mg_status enqueue_iteration(mg_ctx *x)
 {
     for (int l = 1; l < x->nlev; ++l) {
         LevelBufs &C = x->lev[l];
-        k_restrict_mean<T><<<grid_for(C.N), kThreads, 0, x->stream>>>(C.geo, (const T *)x->lev[l - 1].c, (T *)C.c, 2);
+        k_restrict_mean<T><<<grid_for(C.N), kThreads, 0, x->stream>>>(x->lev[l - 1].geo, C.geo,
+                                                                       (const T *)x->lev[l - 1].c, (T *)C.c, 2, C.split);
     }
     CK(cudaGetLastError());
-    CKS(enqueue_vcycle<T, ORDER>(x));
+    for (int cyc = 0; cyc < x->cfg.inner_cycles; ++cyc) CKS(enqueue_vcycle<T, ORDER>(x, cyc == 0));
     int periodic = x->cfg.bc == MG_BC_PERIODIC;
     LevelBufs &L0 = x->lev[0];
     if (periodic) {
         int g = grid_for(x->N, kRedBlocks);
-        k_sum4<T><<<g, kThreads, 0, x->stream>>>((const T *)L0.eA, x->N, x->partial);
+        k_sum4<T><<<g, kThreads, 0, x->stream>>>((const T *)L0.cur(), x->N, x->partial);
         k_finalize_sum<4><<<1, 256, 0, x->stream>>>(x->partial, g, x->scal->emean);
     }
-    k_update<T><<<grid_for(x->N), kThreads, 0, x->stream>>>(x->X, (const T *)L0.eA, x->N, x->scal->emean, periodic);
+    k_update<T><<<grid_for(x->N), kThreads, 0, x->stream>>>(L0.geo, x->X, (const T *)L0.cur(), x->N, x->scal->emean,
+                                                            periodic, L0.split);
     CK(cudaGetLastError());
     return enqueue_residual<T, ORDER>(x, nullptr);
 }
@@ -172,17 +208,21 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
     CK(cudaEventRecord(x->ev0, x->stream));
     for (int r = 0; r < reps; ++r) {
         if (which == 0) {
-            int grid = grid_for(L.N / 2);
+            if (!L.split) return fail(MG_ERR_INVALID_ARG, "one-level hierarchy has no global smoother");
+            int grid = 0;
+            Regions rg = smooth_regions(L.geo, ORDER, &grid);
             dispatch_bc(x->cfg.bc, [&](auto B) {
                 k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, kThreads, 0, x->stream>>>(
-                    L.geo, cf, (const T *)L.eA, (T *)L.eB, (const T *)L.f, (const T *)L.c, r & 1);
+                    L.geo, cf, (const T *)L.eA, (const T *)L.eA, (T *)L.eB, (const T *)L.f, (const T *)L.c, r & 1, rg);
             });
         } else if (which == 1) {
             if (x->nlev < 2) return fail(MG_ERR_INVALID_ARG, "one-level hierarchy has no restriction");
             LevelBufs &Cl = x->lev[1];
+            int rgrid = 0;
+            Regions rr = restrict_regions(Cl.geo, &rgrid);
             dispatch_bc(x->cfg.bc, [&](auto B) {
-                k_residual_restrict<T, ORDER, decltype(B)::value><<<grid_for(Cl.N), kThreads, 0, x->stream>>>(
-                    L.geo, cf, Cl.geo, (const T *)L.eA, (const T *)L.f, (const T *)L.c, (T *)Cl.f);
+                k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, kThreads, 0, x->stream>>>(
+                    L.geo, cf, Cl.geo, (const T *)L.eA, (const T *)L.f, (const T *)L.c, (T *)Cl.f, Cl.split, rr);
             });
         } else {
             Coef<double> cd = make_coef<double>(L.geo, x->cfg.order);

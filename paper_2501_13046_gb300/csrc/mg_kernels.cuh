@@ -187,139 +187,330 @@ __device__ __forceinline__ void apply_J(const F &e0, const F &e1, const F &e2, c
     out[3] = lz + (dzz + mz) * (T)(1.0 / 3.0);
 }
 
-template <typename T, int ORDER, int BC>
-__device__ __forceinline__ void apply_J_at(const T *e, size_t N, const Geo &g, int i, int j, int k, T ca, T cb,
-                                           const Coef<T> &cf, T out[4], T centre[4])
+// ---------------------------------------------------------------------------------------
+// Storage of a level's fields.  Every level above the coarsest is colour-split: a field of N
+// cells is [colour 0 half | colour 1 half], cell (i,j,k) with colour c = (i+j+k) & 1 and
+// linear index lin = i + nx (j + ny k) sits at c N/2 + lin/2 (nx even, so the two cells of an
+// x-pair have different colours and share lin/2).  A colour pass then reads and writes only
+// the halves it needs, and every neighbour load of a warp is contiguous.  The coarsest level
+// (possibly odd-sized, handled by one CTA) is plain: cell at lin.
+__device__ __forceinline__ size_t sidx(const Geo &g, int i, int j, int k, size_t N, int split)
 {
-    if (is_interior(g, i, j, k, halo<ORDER>())) {
-        int sy = g.n[0], sz = g.n[0] * g.n[1];
-        size_t p = (size_t)i + (size_t)sy * j + (size_t)sz * k;
-        AccI<T> a0{e + p, sy, sz}, a1{e + N + p, sy, sz}, a2{e + 2 * N + p, sy, sz}, a3{e + 3 * N + p, sy, sz};
+    size_t lin = (size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k);
+    return split ? (((i + j + k) & 1) ? N / 2 : 0) + (lin >> 1) : lin;
+}
+
+// Interior accessor of a colour-split field around a cell with pair index m = lin/2 and
+// sel = lin & 1.  A neighbour (dx,dy,dz) lies in the half of the other colour when dx+dy+dz is
+// odd, and at pair index m + floor((sel + dx)/2) + dy nx/2 + dz nx ny/2, i.e. m + dx/2 for even
+// dx and m + sel + (dx-1)/2 for odd dx.  The four base pointers absorb m and sel, so every
+// offset below is a compile-time combination of dy, dz with 32-bit strides.
+template <typename T>
+struct AccS {
+    const T *se, *so, *oe, *oo;   // same-colour half + m, + m + sel; other-colour half + m, + m + sel
+    int nxh, plane;
+    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
+    {
+        const bool other = (dx + dy + dz) & 1;
+        const bool odd = dx & 1;
+        const T *b = other ? (odd ? oo : oe) : (odd ? so : se);
+        const int xo = odd ? ((dx - 1) >> 1) : (dx >> 1);
+        return b[xo + dy * nxh + dz * plane];
+    }
+};
+
+// Boundary accessor of a colour-split field: cells of the centre's colour c are read from
+// `same`, cells of the other colour from `other` (both are full field bases).
+template <typename T, int BC>
+struct AccB2 {
+    const T *same, *other;
+    const Geo *g;
+    size_t N;
+    int i, j, k, c;
+    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
+    {
+        int p[3] = {i + dx, j + dy, k + dz};
+        int q[3];
+        bool outside = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int n = g->n[a];
+            if (BC == BC_PERIODIC) {
+                q[a] = p[a] + (p[a] < 0 ? n : 0) - (p[a] >= n ? n : 0);
+            } else {
+                q[a] = min(max(p[a], 0), n - 1);
+                outside |= q[a] != p[a];
+            }
+        }
+        int c2 = (q[0] + q[1] + q[2]) & 1;
+        size_t lin = (size_t)q[0] + (size_t)g->n[0] * ((size_t)q[1] + (size_t)g->n[1] * q[2]);
+        T v = (c2 == c ? same : other)[(c2 ? N / 2 : 0) + (lin >> 1)];
+        if (BC == BC_ROBIN && outside) {
+            double xb = cellx(*g, 0, q[0]), yb = cellx(*g, 1, q[1]), zb = cellx(*g, 2, q[2]);
+            double xg = cellx(*g, 0, p[0]), yg = cellx(*g, 1, p[1]), zg = cellx(*g, 2, p[2]);
+            return (T)((double)v * sqrt(xb * xb + yb * yb + zb * zb) / sqrt(xg * xg + yg * yg + zg * zg));
+        }
+        return v;
+    }
+};
+
+// J e at cell (i,j,k) of a colour-split level; X holds the cell's colour, O the other colour.
+// INTERIOR: every stencil point lies inside the box (fast accessor), else the boundary accessor.
+template <typename T, int ORDER, int BC, bool INTERIOR>
+__device__ __forceinline__ void apply_J_split(const T *X, const T *O, size_t N, const Geo &g, int i, int j, int k,
+                                              T ca, T cb, const Coef<T> &cf, T out[4], T centre[4])
+{
+    const int c = (i + j + k) & 1;
+    if constexpr (INTERIOR) {
+        const size_t Nh = N / 2;
+        const unsigned lin = (unsigned)i + (unsigned)g.n[0] * ((unsigned)j + (unsigned)g.n[1] * (unsigned)k);
+        const unsigned m = lin >> 1;
+        const int sel = (int)(lin & 1), nxh = g.n[0] >> 1, plane = nxh * g.n[1];
+        const T *Xs = X + (c ? Nh : 0) + m, *Oo = O + (c ? 0 : Nh) + m;
+        AccS<T> a0{Xs, Xs + sel, Oo, Oo + sel, nxh, plane};
+        AccS<T> a1{Xs + N, Xs + N + sel, Oo + N, Oo + N + sel, nxh, plane};
+        AccS<T> a2{Xs + 2 * N, Xs + 2 * N + sel, Oo + 2 * N, Oo + 2 * N + sel, nxh, plane};
+        AccS<T> a3{Xs + 3 * N, Xs + 3 * N + sel, Oo + 3 * N, Oo + 3 * N + sel, nxh, plane};
         apply_J<ORDER, T>(a0, a1, a2, a3, ca, cb, cf, out, centre);
     } else {
-        AccB<T, BC> a0{e, &g, i, j, k}, a1{e + N, &g, i, j, k}, a2{e + 2 * N, &g, i, j, k}, a3{e + 3 * N, &g, i, j, k};
+        AccB2<T, BC> a0{X, O, &g, N, i, j, k, c}, a1{X + N, O + N, &g, N, i, j, k, c},
+            a2{X + 2 * N, O + 2 * N, &g, N, i, j, k, c}, a3{X + 3 * N, O + 3 * N, &g, N, i, j, k, c};
         apply_J<ORDER, T>(a0, a1, a2, a3, ca, cb, cf, out, centre);
     }
+}
+
+// Cells of a box split into two block-uniform regions so that no warp mixes the fast interior
+// stencil with the boundary one: the interior box [G, n-G)^3 and the shell around it.
+struct Regions {
+    int G;               // halo width (cells within G of a face form the shell)
+    int nblk_sh;         // blocks [0, nblk_sh) take the shell (scheduled first: the shell is the
+                         // slower path, so it overlaps the interior instead of trailing it)
+};
+
+// t-th cell of the interior box [G, n-G)^3 of colour `colour` (x fastest); returns false past
+// the end.  32-bit index arithmetic (grids hold at most 2^31 cells).
+__device__ __forceinline__ bool interior_cell(const Geo &g, int G, int colour, unsigned t, int &i, int &j, int &k)
+{
+    const unsigned ix = g.n[0] - 2 * G, iy = g.n[1] - 2 * G, iz = g.n[2] - 2 * G;
+    if ((int)ix <= 0 || (int)iy <= 0 || (int)iz <= 0) return false;
+    const unsigned per_row = ix >> 1;   // ix is even
+    const unsigned row = t / per_row;
+    if (row >= iy * iz) return false;
+    const unsigned q = t - row * per_row;
+    const unsigned jj = row % iy;
+    j = G + (int)jj;
+    k = G + (int)((row - jj) / iy);
+    i = G + ((colour + j + k + G) & 1) + 2 * (int)q;
+    return true;
+}
+
+// t-th cell of the shell (cells within G of a face), all colours; returns false past the end.
+__device__ __forceinline__ bool shell_cell(const Geo &g, int G, unsigned t, int &i, int &j, int &k)
+{
+    const unsigned nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int iz = g.n[2] - 2 * G, iy = g.n[1] - 2 * G;
+    const unsigned G2 = 2 * G;
+    if (iz <= 0 || iy <= 0) {   // the whole box is shell
+        if (t >= nx * ny * nz) return false;
+        i = (int)(t % nx); j = (int)((t / nx) % ny); k = (int)(t / (nx * ny));
+        return true;
+    }
+    const unsigned A = G2 * nx * ny;                   // z-faces: k < G or k >= nz - G
+    if (t < A) {
+        i = (int)(t % nx); j = (int)((t / nx) % ny);
+        int kk = (int)(t / (nx * ny));
+        k = kk < G ? kk : (int)nz - 2 * G + kk;
+        return true;
+    }
+    t -= A;
+    const unsigned B = (unsigned)iz * G2 * nx;          // y-faces of the remaining planes
+    if (t < B) {
+        i = (int)(t % nx);
+        int jj = (int)((t / nx) % G2);
+        k = G + (int)(t / (nx * G2));
+        j = jj < G ? jj : (int)ny - 2 * G + jj;
+        return true;
+    }
+    t -= B;
+    const unsigned C = (unsigned)iz * (unsigned)iy * G2;  // x-faces of the remaining rows
+    if (t >= C) return false;
+    int ii = (int)(t % G2);
+    unsigned row = t / G2;
+    j = G + (int)(row % (unsigned)iy);
+    k = G + (int)(row / (unsigned)iy);
+    i = ii < G ? ii : g.n[0] - 2 * G + ii;
+    return true;
+}
+
+__host__ __device__ inline size_t shell_count(const int n[3], int G)
+{
+    size_t N = (size_t)n[0] * n[1] * n[2];
+    long long ix = n[0] - 2 * G, iy = n[1] - 2 * G, iz = n[2] - 2 * G;
+    if (ix <= 0 || iy <= 0 || iz <= 0) return N;
+    return N - (size_t)ix * iy * iz;
 }
 
 // ---------------------------------------------------------------------------------------
-// Red-black colour pass.  One thread per x-pair (2m, 2m+1): the cell of the active colour
-// is updated, its partner copied, and both are written with one 2-wide store.
+// Red-black colour pass on a colour-split level.  Blocks [0, nblk_sh) update the active-colour
+// cells of the shell, the other blocks those of the interior box.  Old values of the active
+// colour come from X, current values of the other colour from O (X on the first pass of a
+// sweep, Y on the second); the new active-colour values go to Y, so couplings inside a colour
+// are Jacobi and the result is deterministic.
 template <typename T, int ORDER, int BC>
-__global__ void __launch_bounds__(256) k_smooth_colour(Geo g, Coef<T> cf, const T *__restrict__ ein,
-                                                       T *__restrict__ eout, const T *__restrict__ f,
-                                                       const T *__restrict__ ab, int colour)
+__device__ __forceinline__ void smooth_cell(const Geo &g, const Coef<T> &cf, const T *X, const T *O, T *Y, const T *f,
+                                            const T *ab, size_t N, int i, int j, int k, bool interior)
 {
-    using V2 = typename Vec2<T>::type;
-    const int nxp = g.n[0] >> 1;
+    const unsigned lin = (unsigned)i + (unsigned)g.n[0] * ((unsigned)j + (unsigned)g.n[1] * (unsigned)k);
+    const size_t q = (((i + j + k) & 1) ? N / 2 : 0) + (lin >> 1);
+    T ca = ab[q], cb = ab[N + q];
+    T Je[4], ctr[4];
+    if (interior) apply_J_split<T, ORDER, BC, true>(X, O, N, g, i, j, k, ca, cb, cf, Je, ctr);
+    else apply_J_split<T, ORDER, BC, false>(X, O, N, g, i, j, k, ca, cb, cf, Je, ctr);
+    Y[q] = ctr[0] + (f[q] - Je[0]) / (ca * cf.dl + cb);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (f[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
+}
+
+// The shell path is a call: only shell blocks execute it, and it leaves the interior path its registers.
+template <typename T, int ORDER, int BC>
+__device__ __noinline__ void smooth_cell_shell(const Geo &g, const Coef<T> &cf, const T *X, const T *O, T *Y,
+                                               const T *f, const T *ab, size_t N, int i, int j, int k)
+{
+    smooth_cell<T, ORDER, BC>(g, cf, X, O, Y, f, ab, N, i, j, k, false);
+}
+
+template <typename T, int ORDER, int BC>
+__global__ void __launch_bounds__(256, 2) k_smooth_colour(Geo g, Coef<T> cf, const T *__restrict__ X,
+                                                          const T *__restrict__ O, T *__restrict__ Y,
+                                                          const T *__restrict__ f, const T *__restrict__ ab,
+                                                          int colour, Regions rg)
+{
     const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
-    const size_t pairs = N >> 1;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < pairs; t += (size_t)gridDim.x * blockDim.x) {
-        int ip = (int)(t % nxp);
-        size_t rest = t / nxp;
-        int j = (int)(rest % g.n[1]);
-        int k = (int)(rest / g.n[1]);
-        int sel = (j + k + colour) & 1;       // which of the pair has the active colour
-        int i = 2 * ip + sel;
-        size_t base = 2 * t;                  // linear index of cell 2*ip in row (j,k)
-        size_t p = base + sel;
-        T ca = ab[p], cb = ab[N + p];
-        T Je[4], ctr[4];
-        apply_J_at<T, ORDER, BC>(ein, N, g, i, j, k, ca, cb, cf, Je, ctr);
-        T nv[4];
-        nv[0] = ctr[0] + (f[p] - Je[0]) / (ca * cf.dl + cb);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) nv[1 + a] = ctr[1 + a] + (f[(1 + a) * N + p] - Je[1 + a]) * cf.idW[a];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            T other = ein[a * N + base + (sel ^ 1)];
-            V2 v;
-            if (sel) { v.x = other; v.y = nv[a]; } else { v.x = nv[a]; v.y = other; }
-            *reinterpret_cast<V2 *>(eout + a * N + base) = v;
-        }
+    int i, j, k;
+    if ((int)blockIdx.x >= rg.nblk_sh) {
+        const unsigned stride = (unsigned)(gridDim.x - rg.nblk_sh) * blockDim.x;
+        for (unsigned t = (blockIdx.x - rg.nblk_sh) * blockDim.x + threadIdx.x;
+             interior_cell(g, rg.G, colour, t, i, j, k); t += stride)
+            smooth_cell<T, ORDER, BC>(g, cf, X, O, Y, f, ab, N, i, j, k, true);
+    } else {
+        const unsigned stride = (unsigned)rg.nblk_sh * blockDim.x;
+        for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; shell_cell(g, rg.G, t, i, j, k); t += stride)
+            if (((i + j + k) & 1) == colour) smooth_cell_shell<T, ORDER, BC>(g, cf, X, O, Y, f, ab, N, i, j, k);
     }
 }
 
-// Residual r = f - J e on the fine level, averaged over the 8 children into the coarse rhs.
+// Residual r = f - J e on a colour-split fine level, averaged over the 8 children into the
+// coarse rhs (stored colour-split, or plain when the coarse level is the coarsest).  Blocks
+// [0, nblk_sh) take the coarse shell, the others the coarse cells whose children's stencils stay
+// inside the fine box (the coarse interior box [1, nc-1)^3).
+template <typename T, int ORDER, int BC, bool INTERIOR>
+__device__ __forceinline__ void restrict_cell(const Geo &g, const Coef<T> &cf, const Geo &gc, const T *e, const T *f,
+                                              const T *ab, T *fc, size_t N, size_t Nc, int csplit, int I, int J, int K)
+{
+    T acc[4] = {0, 0, 0, 0};
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+        int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
+        size_t p = sidx(g, i, j, k, N, 1);
+        T Je[4], ctr[4];
+        apply_J_split<T, ORDER, BC, INTERIOR>(e, e, N, g, i, j, k, ab[p], ab[N + p], cf, Je, ctr);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a] += f[a * N + p] - Je[a];
+    }
+    size_t pc = sidx(gc, I, J, K, Nc, csplit);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) fc[a * Nc + pc] = acc[a] * (T)0.125;
+}
+
 template <typename T, int ORDER, int BC>
-__global__ void __launch_bounds__(256) k_residual_restrict(Geo g, Coef<T> cf, Geo gc, const T *__restrict__ e,
-                                                           const T *__restrict__ f, const T *__restrict__ ab,
-                                                           T *__restrict__ fc)
+__device__ __noinline__ void restrict_cell_shell(const Geo &g, const Coef<T> &cf, const Geo &gc, const T *e,
+                                                 const T *f, const T *ab, T *fc, size_t N, size_t Nc, int csplit,
+                                                 int I, int J, int K)
+{
+    restrict_cell<T, ORDER, BC, false>(g, cf, gc, e, f, ab, fc, N, Nc, csplit, I, J, K);
+}
+
+template <typename T, int ORDER, int BC>
+__global__ void __launch_bounds__(256, 2) k_residual_restrict(Geo g, Coef<T> cf, Geo gc, const T *__restrict__ e,
+                                                              const T *__restrict__ f, const T *__restrict__ ab,
+                                                              T *__restrict__ fc, int csplit, Regions rg)
 {
     const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
     const size_t Nc = (size_t)gc.n[0] * gc.n[1] * gc.n[2];
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < Nc; q += (size_t)gridDim.x * blockDim.x) {
-        int I = (int)(q % gc.n[0]);
-        size_t rest = q / gc.n[0];
-        int J = (int)(rest % gc.n[1]);
-        int K = (int)(rest / gc.n[1]);
-        T acc[4] = {0, 0, 0, 0};
-#pragma unroll 1
-        for (int d = 0; d < 8; ++d) {
-            int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
-            size_t p = (size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k);
-            T Je[4], ctr[4];
-            apply_J_at<T, ORDER, BC>(e, N, g, i, j, k, ab[p], ab[N + p], cf, Je, ctr);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) acc[a] += f[a * N + p] - Je[a];
+    int I, J, K;
+    if ((int)blockIdx.x >= rg.nblk_sh) {
+        // coarse interior box [1, nc-1)^3, x fastest
+        const int ix = gc.n[0] - 2, iy = gc.n[1] - 2, iz = gc.n[2] - 2;
+        const unsigned total = (ix > 0 && iy > 0 && iz > 0) ? (unsigned)ix * iy * iz : 0;
+        const unsigned stride = (unsigned)(gridDim.x - rg.nblk_sh) * blockDim.x;
+        for (unsigned t = (blockIdx.x - rg.nblk_sh) * blockDim.x + threadIdx.x; t < total; t += stride) {
+            const unsigned r = t / (unsigned)ix;
+            I = 1 + (int)(t - r * (unsigned)ix);
+            J = 1 + (int)(r % (unsigned)iy);
+            K = 1 + (int)(r / (unsigned)iy);
+            restrict_cell<T, ORDER, BC, true>(g, cf, gc, e, f, ab, fc, N, Nc, csplit, I, J, K);
         }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) fc[a * Nc + q] = acc[a] * (T)0.125;
+    } else {
+        const unsigned stride = (unsigned)rg.nblk_sh * blockDim.x;
+        for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; shell_cell(gc, 1, t, I, J, K); t += stride)
+            restrict_cell_shell<T, ORDER, BC>(g, cf, gc, e, f, ab, fc, N, Nc, csplit, I, J, K);
     }
 }
 
-// Mean of the 8 children for nf contiguous fields (the psi-row coefficients a and b).
+// Mean of the 8 children for nf fields (the psi-row coefficients a and b): fine colour-split,
+// coarse colour-split or plain.
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict_mean(Geo gc, const T *__restrict__ fine, T *__restrict__ coarse,
-                                                       int nf)
+__global__ void __launch_bounds__(256) k_restrict_mean(Geo g, Geo gc, const T *__restrict__ fine,
+                                                       T *__restrict__ coarse, int nf, int csplit)
 {
     const size_t Nc = (size_t)gc.n[0] * gc.n[1] * gc.n[2];
     const size_t Nf = 8 * Nc;
-    const int nf0 = 2 * gc.n[0], nf1 = 2 * gc.n[1];
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < Nc; q += (size_t)gridDim.x * blockDim.x) {
         int I = (int)(q % gc.n[0]);
         size_t rest = q / gc.n[0];
         int J = (int)(rest % gc.n[1]);
         int K = (int)(rest / gc.n[1]);
+        size_t pc = sidx(gc, I, J, K, Nc, csplit);
         for (int a = 0; a < nf; ++a) {
             T s = 0;
 #pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
-                s += fine[a * Nf + (size_t)i + (size_t)nf0 * ((size_t)j + (size_t)nf1 * k)];
-            }
-            coarse[a * Nc + q] = s * (T)0.125;
+            for (int d = 0; d < 8; ++d)
+                s += fine[a * Nf + sidx(g, 2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), Nf, 1)];
+            coarse[a * Nc + pc] = s * (T)0.125;
         }
     }
 }
 
-// Fine correction += cell-centred trilinear interpolation of the coarse correction
-// (weights 3/4 and 1/4 per axis, boundary values of the coarse level from the BC).
+// Fine correction (colour-split) += cell-centred trilinear interpolation of the coarse
+// correction (colour-split or plain; weights 3/4 and 1/4 per axis, boundary values from the BC).
 template <typename T, int BC>
-__global__ void __launch_bounds__(256) k_prolong_add(Geo gc, const T *__restrict__ ec, T *__restrict__ ef)
+__global__ void __launch_bounds__(256) k_prolong_add(Geo g, Geo gc, const T *__restrict__ ec, T *__restrict__ ef,
+                                                     int csplit)
 {
     const size_t Nc = (size_t)gc.n[0] * gc.n[1] * gc.n[2];
     const size_t Nf = 8 * Nc;
-    const int nf0 = 2 * gc.n[0], nf1 = 2 * gc.n[1];
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < Nc; q += (size_t)gridDim.x * blockDim.x) {
         int I = (int)(q % gc.n[0]);
         size_t rest = q / gc.n[0];
         int J = (int)(rest % gc.n[1]);
         int K = (int)(rest / gc.n[1]);
-        bool inner = I >= 1 && I < gc.n[0] - 1 && J >= 1 && J < gc.n[1] - 1 && K >= 1 && K < gc.n[2] - 1;
 #pragma unroll 1
         for (int a = 0; a < 4; ++a) {
             const T *fc = ec + a * Nc;
+            AccB2<T, BC> acc{fc, fc, &gc, Nc, I, J, K, 0};
             T v[3][3][3];
 #pragma unroll
             for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
                 for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx)
-                        v[dz + 1][dy + 1][dx + 1] =
-                            inner ? fc[(size_t)(I + dx) + (size_t)gc.n[0] * ((size_t)(J + dy) + (size_t)gc.n[1] * (K + dz))]
-                                  : fetch_bc<T, BC>(fc, gc, I + dx, J + dy, K + dz);
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (csplit) {
+                            v[dz + 1][dy + 1][dx + 1] = acc(dx, dy, dz);
+                        } else {
+                            v[dz + 1][dy + 1][dx + 1] = fetch_bc<T, BC>(fc, gc, I + dx, J + dy, K + dz);
+                        }
+                    }
 #pragma unroll
             for (int d = 0; d < 8; ++d) {
                 int sx = (d & 1) ? 1 : -1, sy = ((d >> 1) & 1) ? 1 : -1, sz = (d >> 2) ? 1 : -1;
@@ -333,9 +524,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(Geo gc, const T *__restrict
                             T w = (T)((cx ? 0.25 : 0.75) * (cy ? 0.25 : 0.75) * (cz ? 0.25 : 0.75));
                             s += w * v[1 + cz * sz][1 + cy * sy][1 + cx * sx];
                         }
-                size_t pf = (size_t)(2 * I + (d & 1)) +
-                            (size_t)nf0 * ((size_t)(2 * J + ((d >> 1) & 1)) + (size_t)nf1 * (2 * K + (d >> 2)));
-                ef[a * Nf + pf] += s;
+                ef[a * Nf + sidx(g, 2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), Nf, 1)] += s;
             }
         }
     }
@@ -458,17 +647,27 @@ __global__ void __launch_bounds__(256) k_sub_mean4(T *__restrict__ x, size_t N, 
         for (int a = 0; a < 4; ++a) x[a * N + p] -= (T)m[a];
 }
 
-// State update u += e - <e>, W_i += e_i - <e_i> (means only on periodic boxes).
+// State update u += e - <e>, W_i += e_i - <e_i> (means only on periodic boxes); e is stored in
+// the finest level's layout (colour-split when split != 0).
 template <typename T>
-__global__ void __launch_bounds__(256) k_update(double *__restrict__ x, const T *__restrict__ e, size_t N,
-                                                const double *__restrict__ esums, int periodic)
+__global__ void __launch_bounds__(256) k_update(Geo g, double *__restrict__ x, const T *__restrict__ e, size_t N,
+                                                const double *__restrict__ esums, int periodic, int split)
 {
     double m[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) m[a] = periodic ? esums[a] / (double)N : 0.0;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        size_t q = p;
+        if (split) {
+            int i = (int)(p % g.n[0]);
+            size_t rest = p / g.n[0];
+            int j = (int)(rest % g.n[1]);
+            int k = (int)(rest / g.n[1]);
+            q = (((i + j + k) & 1) ? N / 2 : 0) + (p >> 1);
+        }
 #pragma unroll
-        for (int a = 0; a < 4; ++a) x[a * N + p] += (double)e[a * N + p] - m[a];
+        for (int a = 0; a < 4; ++a) x[a * N + p] += (double)e[a * N + q] - m[a];
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -568,7 +767,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__restrict__ x, const double *__restrict__ R,
                                                      const Scalars *__restrict__ s, T *__restrict__ f,
                                                      T *__restrict__ ab, double *__restrict__ HM,
-                                                     double *__restrict__ partial)
+                                                     double *__restrict__ partial, int split)
 {
     const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
     const double K2 = s->K2;
@@ -596,12 +795,13 @@ __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__rest
             HM[2 * N + p] = M1;
             HM[3 * N + p] = M2;
         } else {
-            f[p] = (T)(-ip5 * Fp);
-            f[N + p] = (T)(-Fw0);
-            f[2 * N + p] = (T)(-Fw1);
-            f[3 * N + p] = (T)(-Fw2);
-            ab[p] = (T)ip5;
-            ab[N + p] = (T)(ip5 * (R[4 * N + p] - (5.0 / 12.0) * K2 * p4));
+            size_t q = split ? (((i + j + k) & 1) ? N / 2 : 0) + (p >> 1) : p;
+            f[q] = (T)(-ip5 * Fp);
+            f[N + q] = (T)(-Fw0);
+            f[2 * N + q] = (T)(-Fw1);
+            f[3 * N + q] = (T)(-Fw2);
+            ab[q] = (T)ip5;
+            ab[N + q] = (T)(ip5 * (R[4 * N + p] - (5.0 / 12.0) * K2 * p4));
         }
     }
     double r[4];

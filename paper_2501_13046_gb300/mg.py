@@ -33,7 +33,7 @@ class mg_config(C.Structure):
         ("levels", C.c_int), ("precision", C.c_int), ("k_mode", C.c_int), ("K", C.c_double), ("npunct", C.c_int),
         ("punct_m", C.c_double * 2), ("punct_x", (C.c_double * 3) * 2), ("tol", C.c_double), ("max_outer", C.c_int),
         ("nu_pre", C.c_int), ("nu_post", C.c_int), ("coarse_sweeps", C.c_int), ("use_graph", C.c_int),
-        ("spin_limit", C.c_longlong),
+        ("spin_limit", C.c_longlong), ("inner_cycles", C.c_int),
     ]
 
 
