@@ -170,6 +170,26 @@ mg_status mg_residual_norms_noalloc(const mg_config *cfg, const double *u, const
 
 void mg_destroy(struct mg_ctx *ctx);
 
+/*
+ * Batched solves (many independent problems of uneven grid sizes).
+ * All instances must share order, bc, precision and k_mode; sizes, boxes and sources differ.
+ * Each instance owns its workspace and a private stream; mg_batch_solve captures the outer
+ * iteration of every instance into one CUDA graph (one parallel branch per instance) and
+ * replays it, one launch and one host synchronisation per round for the whole batch, until
+ * every instance has met its tolerance (converged instances keep iterating in lock step; their
+ * residual only decreases further) or the largest max_outer is reached.
+ *   infos: count entries (may be NULL); infos[b].outer_iters is the round at which instance b
+ *   first met its tolerance; infos[b].device_ms the batch time up to the end of that round.
+ */
+typedef struct mg_batch mg_batch;
+mg_status mg_batch_create(int count, const mg_config *cfgs, void *cuda_stream, mg_batch **out);
+mg_status mg_batch_set_sources(mg_batch *bt, int b, const double *rho0, const double *rho2, const double *Sx,
+                               const double *Sy, const double *Sz, int on_device);
+mg_status mg_batch_set_initial_guess(mg_batch *bt, int b, const double *u, const double *W, int on_device);
+mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms);
+mg_status mg_batch_get_solution(mg_batch *bt, int b, double *u, double *W, double *K, int on_device);
+void mg_batch_destroy(mg_batch *bt);
+
 const char *mg_status_string(mg_status s);
 const char *mg_last_error(void);
 

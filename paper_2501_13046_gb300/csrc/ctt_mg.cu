@@ -534,3 +534,239 @@ const char *mg_status_string(mg_status s)
 const char *mg_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ====================================================================== batched solves
+struct mg_batch {
+    std::vector<mg_ctx *> ctx;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;   // master stream: graph launches, fork/join of the branches
+    cudaEvent_t ev_fork = nullptr, ev_in = nullptr, ev_out = nullptr;
+    std::vector<cudaEvent_t> ev_join, ev_round;
+    cudaGraphExec_t graph_start = nullptr, graph_iter = nullptr;
+    long long launches_start = 0, launches_iter = 0;
+};
+
+namespace {
+
+// Capture `fn(ctx)` of every instance as parallel branches of one graph on the master stream.
+template <class Fn>
+mg_status capture_batch(mg_batch *bt, Fn &&fn, cudaGraphExec_t *exec, long long *kernels)
+{
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal));
+    mg_status st = MG_OK;
+    cudaError_t e = cudaEventRecord(bt->ev_fork, bt->stream);
+    for (size_t b = 0; b < bt->ctx.size() && st == MG_OK && e == cudaSuccess; ++b) {
+        mg_ctx *x = bt->ctx[b];
+        e = cudaStreamWaitEvent(x->stream, bt->ev_fork, 0);
+        if (e == cudaSuccess) st = fn(x);
+        if (st == MG_OK && e == cudaSuccess) e = cudaEventRecord(bt->ev_join[b], x->stream);
+        if (st == MG_OK && e == cudaSuccess) e = cudaStreamWaitEvent(bt->stream, bt->ev_join[b], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(bt->stream, &graph);
+    CKS(st);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(MG_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    size_t n = 0;
+    cudaGraphGetNodes(graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    cudaGraphGetNodes(graph, nodes.data(), &n);
+    long long k = 0;
+    for (auto &nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *kernels = k;
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        return fail(MG_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+    }
+    return MG_OK;
+}
+
+mg_status batch_enter(mg_batch *bt)
+{
+    CK(cudaEventRecord(bt->ev_in, bt->user_stream));
+    CK(cudaStreamWaitEvent(bt->stream, bt->ev_in, 0));
+    for (mg_ctx *x : bt->ctx) CK(cudaStreamWaitEvent(x->stream, bt->ev_in, 0));
+    return MG_OK;
+}
+
+mg_status batch_leave(mg_batch *bt, mg_status st)
+{
+    for (mg_ctx *x : bt->ctx) {
+        if (cudaEventRecord(x->ev_out, x->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(bt->stream, x->ev_out, 0) != cudaSuccess)
+            return st == MG_OK ? fail(MG_ERR_CUDA, "batch ordering event failed") : st;
+    }
+    if (cudaEventRecord(bt->ev_out, bt->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(bt->user_stream, bt->ev_out, 0) != cudaSuccess)
+        return st == MG_OK ? fail(MG_ERR_CUDA, "batch ordering event failed") : st;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mg_batch_destroy(mg_batch *bt)
+{
+    if (!bt) return;
+    if (bt->stream) cudaStreamSynchronize(bt->stream);
+    if (bt->graph_start) cudaGraphExecDestroy(bt->graph_start);
+    if (bt->graph_iter) cudaGraphExecDestroy(bt->graph_iter);
+    for (mg_ctx *x : bt->ctx) mg_destroy(x);
+    for (auto e : bt->ev_join) cudaEventDestroy(e);
+    for (auto e : bt->ev_round) cudaEventDestroy(e);
+    if (bt->ev_fork) cudaEventDestroy(bt->ev_fork);
+    if (bt->ev_in) cudaEventDestroy(bt->ev_in);
+    if (bt->ev_out) cudaEventDestroy(bt->ev_out);
+    if (bt->stream) cudaStreamDestroy(bt->stream);
+    delete bt;
+}
+
+mg_status mg_batch_create(int count, const mg_config *cfgs, void *cuda_stream, mg_batch **out)
+{
+    if (!out || !cfgs || count < 1 || count > 4096) return fail(MG_ERR_INVALID_ARG, "bad batch arguments");
+    *out = nullptr;
+    for (int b = 1; b < count; ++b)
+        if (cfgs[b].order != cfgs[0].order || cfgs[b].bc != cfgs[0].bc || cfgs[b].precision != cfgs[0].precision ||
+            cfgs[b].k_mode != cfgs[0].k_mode)
+            return fail(MG_ERR_INVALID_ARG, "batch instances must share order, bc, precision and k_mode");
+    mg_batch *bt = new (std::nothrow) mg_batch();
+    if (!bt) return fail(MG_ERR_OOM, "host allocation");
+    bt->user_stream = (cudaStream_t)cuda_stream;
+    mg_status st = MG_OK;
+    if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bt->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bt->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        st = fail(MG_ERR_CUDA, "stream/event creation");
+    for (int b = 0; b < count && st == MG_OK; ++b) {
+        mg_ctx *x = nullptr;
+        st = mg_create(&cfgs[b], cuda_stream, nullptr, 0, &x);
+        if (st == MG_OK) bt->ctx.push_back(x);
+        cudaEvent_t e;
+        if (st == MG_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) bt->ev_join.push_back(e);
+        else if (st == MG_OK) st = fail(MG_ERR_CUDA, "event creation");
+    }
+    if (st != MG_OK) {
+        mg_batch_destroy(bt);
+        return st;
+    }
+    *out = bt;
+    return MG_OK;
+}
+
+mg_status mg_batch_set_sources(mg_batch *bt, int b, const double *rho0, const double *rho2, const double *Sx,
+                               const double *Sy, const double *Sz, int on_device)
+{
+    if (!bt || b < 0 || b >= (int)bt->ctx.size()) return fail(MG_ERR_INVALID_ARG, "bad instance");
+    return mg_set_sources(bt->ctx[b], rho0, rho2, Sx, Sy, Sz, on_device);
+}
+
+mg_status mg_batch_set_initial_guess(mg_batch *bt, int b, const double *u, const double *W, int on_device)
+{
+    if (!bt || b < 0 || b >= (int)bt->ctx.size()) return fail(MG_ERR_INVALID_ARG, "bad instance");
+    return mg_set_initial_guess(bt->ctx[b], u, W, on_device);
+}
+
+mg_status mg_batch_get_solution(mg_batch *bt, int b, double *u, double *W, double *K, int on_device)
+{
+    if (!bt || b < 0 || b >= (int)bt->ctx.size()) return fail(MG_ERR_INVALID_ARG, "bad instance");
+    return mg_get_solution(bt->ctx[b], u, W, K, on_device);
+}
+
+mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms)
+{
+    if (!bt) return fail(MG_ERR_INVALID_ARG, "null batch");
+    const int nb = (int)bt->ctx.size();
+    for (mg_ctx *x : bt->ctx)
+        if (!x->have_sources) return fail(MG_ERR_STATE, "every instance needs mg_batch_set_sources first");
+    CKS(batch_enter(bt));
+    mg_status result = MG_OK;
+    do {
+        int max_outer = 0;
+        for (mg_ctx *x : bt->ctx) {
+            x->history.clear();
+            max_outer = std::max(max_outer, x->cfg.max_outer);
+        }
+        while ((int)bt->ev_round.size() < max_outer + 1) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { result = fail(MG_ERR_CUDA, "event creation"); break; }
+            bt->ev_round.push_back(e);
+        }
+        if (result != MG_OK) break;
+        if (!bt->graph_start &&
+            (result = capture_batch(bt, start_any, &bt->graph_start, &bt->launches_start)) != MG_OK)
+            break;
+        if (!bt->graph_iter && (result = capture_batch(bt, iteration_any, &bt->graph_iter, &bt->launches_iter)) != MG_OK)
+            break;
+        cudaEvent_t t0 = bt->ev_round[0];
+        if (cudaEventRecord(t0, bt->stream) != cudaSuccess || cudaGraphLaunch(bt->graph_start, bt->stream) != cudaSuccess ||
+            cudaStreamSynchronize(bt->stream) != cudaSuccess) {
+            result = fail(MG_ERR_CUDA, "batch start");
+            break;
+        }
+        std::vector<int> conv_round(nb, -1);
+        std::vector<float> conv_ms(nb, 0.f);
+        int round = 0, done = 0;
+        for (;;) {
+            float ms = 0.f;
+            if (round > 0) cudaEventElapsedTime(&ms, t0, bt->ev_round[round]);
+            bool any_bad = false;
+            for (int b = 0; b < nb; ++b) {
+                mg_ctx *x = bt->ctx[b];
+                const Scalars &s = *x->host_scal;
+                double mx = 0.0;
+                bool finite = std::isfinite(s.K2);
+                for (int a = 0; a < 4; ++a) {
+                    x->history.push_back(s.norms[a]);
+                    finite = finite && std::isfinite(s.norms[a]);
+                    mx = std::max(mx, s.norms[a]);
+                }
+                if (!finite) any_bad = true;
+                if (conv_round[b] < 0 && finite && mx <= x->cfg.tol) {
+                    conv_round[b] = round;
+                    conv_ms[b] = ms;
+                    ++done;
+                }
+            }
+            if (any_bad) { result = fail(MG_ERR_DIVERGED, "a batch instance's norm is not finite"); break; }
+            if (done == nb) break;
+            if (round >= max_outer) { result = fail(MG_ERR_NOT_CONVERGED, "max_outer reached in the batch"); break; }
+            if (cudaGraphLaunch(bt->graph_iter, bt->stream) != cudaSuccess ||
+                cudaEventRecord(bt->ev_round[round + 1], bt->stream) != cudaSuccess ||
+                cudaStreamSynchronize(bt->stream) != cudaSuccess) {
+                result = fail(MG_ERR_CUDA, "batch iteration");
+                break;
+            }
+            ++round;
+        }
+        float total = 0.f;
+        cudaEventElapsedTime(&total, t0, bt->ev_round[round]);
+        if (total_ms) *total_ms = total;
+        if (infos) {
+            for (int b = 0; b < nb; ++b) {
+                mg_ctx *x = bt->ctx[b];
+                const Scalars &s = *x->host_scal;
+                mg_solve_info &in = infos[b];
+                in.outer_iters = conv_round[b] >= 0 ? conv_round[b] : round;
+                in.converged = conv_round[b] >= 0;
+                in.K2 = s.K2;
+                in.K = -std::sqrt(std::max(0.0, s.K2));
+                for (int a = 0; a < 4; ++a) in.norms[a] = s.norms[a];
+                for (int a = 0; a < 3; ++a) in.mom_mean[a] = s.msrc[a];
+                in.history = x->history.data();
+                in.history_len = (int)(x->history.size() / 4);
+                in.device_ms = conv_round[b] >= 0 ? conv_ms[b] : total;
+                in.kernel_launches = (bt->launches_start + (long long)round * bt->launches_iter) / nb;
+            }
+        }
+    } while (0);
+    return batch_leave(bt, result);
+}
+
+}  // extern "C"

@@ -49,9 +49,9 @@ def cell_centres(n, lo, hi):
 
 
 def _problem(name, n, lo, hi, order, bc, kmode, K, punctures, rho0, rho2, S, **meta):
+    arr = (lambda a: a) if hasattr(rho0, "is_cuda") else np.ascontiguousarray
     return dict(name=name, n=[n] * 3 if np.isscalar(n) else list(n), lo=lo, hi=hi, order=order, bc=bc,
-                kmode=kmode, K=K, punctures=list(punctures), rho0=np.ascontiguousarray(rho0),
-                rho2=np.ascontiguousarray(rho2), S=np.ascontiguousarray(S), meta=meta)
+                kmode=kmode, K=K, punctures=list(punctures), rho0=arr(rho0), rho2=arr(rho2), S=arr(S), meta=meta)
 
 
 def scalar_sources(phi, dphi, Pi, m=1.0):
@@ -147,6 +147,35 @@ def batch_sizes(count=64, sizes=(48, 64, 96, 128, 160), base_seed=4000, a_lo=2e-
     return out
 
 
-def batch_instance(n, a0, seed, L=32.0, order=4):
-    """One instance of the batched workload: modes_periodic with its own seeds and amplitude."""
+def batch_instance(n, a0, seed, L=32.0, order=4, device=None):
+    """One instance of the batched workload: modes_periodic with its own seeds and amplitude
+    (evaluated on `device` with torch when given)."""
+    if device is not None:
+        return modes_periodic_device(n=n, L=L, seed_phi=2 * seed, seed_pi=2 * seed + 1, a0=a0, order=order,
+                                     device=device)
     return modes_periodic(n=n, L=L, seed_phi=2 * seed, seed_pi=2 * seed + 1, a0=a0, order=order)
+
+
+def modes_periodic_device(n=128, L=32.0, seed_phi=2, seed_pi=3, a0=5e-5, phi0=1.0, order=4, m=1.0, device="cuda"):
+    """modes_periodic evaluated with torch float64 on a device (same seeded modes and formulas);
+    for large batches, where host evaluation would dominate.  Returns the same dict with torch
+    tensors for rho0, rho2 and S."""
+    import torch
+    ax = (torch.arange(n, dtype=torch.float64, device=device) + 0.5) * (L / n)
+    Z, Y, X = torch.meshgrid(ax, ax, ax, indexing="ij")
+    phi = torch.full_like(X, phi0)
+    dphi = [torch.zeros_like(X) for _ in range(3)]
+    for kv, A, th in draw_modes(seed_phi, L, a0):
+        arg = kv[0] * X + kv[1] * Y + kv[2] * Z + th
+        phi += A * torch.cos(arg)
+        s = torch.sin(arg)
+        for a in range(3):
+            dphi[a] -= A * kv[a] * s
+    Pi = torch.zeros_like(X)
+    for kv, A, th in draw_modes(seed_pi, L, a0):
+        Pi += A * torch.cos(kv[0] * X + kv[1] * Y + kv[2] * Z + th)
+    rho0 = 0.5 * Pi * Pi + 0.5 * m * m * phi * phi
+    rho2 = 0.5 * (dphi[0] ** 2 + dphi[1] ** 2 + dphi[2] ** 2)
+    S = torch.stack([-Pi * dphi[a] for a in range(3)]).contiguous()
+    return _problem("modes_periodic", n, 0.0, L, order, PERIODIC, K_INTEGRABILITY, 0.0, (), rho0.contiguous(),
+                    rho2.contiguous(), S, seed_phi=seed_phi, seed_pi=seed_pi, a0=a0, phi0=phi0)

@@ -24,7 +24,9 @@ MG_K_FIXED, MG_K_INTEGRABILITY = 0, 1
 
 EXPORTS = ("mg_config_default", "mg_workspace_size", "mg_create", "mg_set_conformal_metric", "mg_set_sources",
            "mg_set_initial_guess", "mg_solve", "mg_get_solution", "mg_residual_norms", "mg_constraint_fields",
-           "mg_time_kernel", "mg_residual_norms_noalloc", "mg_destroy", "mg_status_string", "mg_last_error")
+           "mg_time_kernel", "mg_residual_norms_noalloc", "mg_destroy", "mg_status_string", "mg_last_error",
+           "mg_batch_create", "mg_batch_set_sources", "mg_batch_set_initial_guess", "mg_batch_solve",
+           "mg_batch_get_solution", "mg_batch_destroy")
 
 
 class mg_config(C.Structure):
@@ -70,12 +72,19 @@ def _load():
     L.mg_residual_norms_noalloc.argtypes = [C.POINTER(mg_config), vp, vp, vp, vp, vp, dp, dp, vp]
     L.mg_destroy.argtypes = [vp]
     L.mg_destroy.restype = None
+    L.mg_batch_create.argtypes = [C.c_int, C.POINTER(mg_config), vp, C.POINTER(vp)]
+    L.mg_batch_set_sources.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, C.c_int]
+    L.mg_batch_set_initial_guess.argtypes = [vp, C.c_int, vp, vp, C.c_int]
+    L.mg_batch_solve.argtypes = [vp, C.POINTER(mg_solve_info), dp]
+    L.mg_batch_get_solution.argtypes = [vp, C.c_int, vp, vp, dp, C.c_int]
+    L.mg_batch_destroy.argtypes = [vp]
+    L.mg_batch_destroy.restype = None
     L.mg_status_string.argtypes = [C.c_int]
     L.mg_status_string.restype = C.c_char_p
     L.mg_last_error.argtypes = []
     L.mg_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("mg_destroy", "mg_status_string", "mg_last_error"):
+        if name not in ("mg_destroy", "mg_status_string", "mg_last_error", "mg_batch_destroy"):
             getattr(L, name).restype = C.c_int
     return L
 
@@ -190,6 +199,50 @@ def mg_residual_norms_noalloc(cfg, u, W, rho0, rho2, S, stream=0):
 
 def mg_destroy(ctx):
     _lib.mg_destroy(ctx)
+
+
+def mg_batch_create(cfgs, stream=0):
+    arr = (mg_config * len(cfgs))(*cfgs)
+    out = C.c_void_p()
+    _check(_lib.mg_batch_create(len(cfgs), arr, C.c_void_p(stream or None), C.byref(out)), "mg_batch_create")
+    return out
+
+
+def mg_batch_set_sources(bt, b, rho0, rho2, Sx, Sy, Sz):
+    ps = [_ptr(a) for a in (rho0, rho2, Sx, Sy, Sz)]
+    dev = max(d for _, d in ps)
+    return _check(_lib.mg_batch_set_sources(bt, b, *[p for p, _ in ps], dev), "mg_batch_set_sources")
+
+
+def mg_batch_set_initial_guess(bt, b, u, W):
+    (pu, du), (pw, dw) = _ptr(u), _ptr(W)
+    return _check(_lib.mg_batch_set_initial_guess(bt, b, pu, pw, max(du, dw)), "mg_batch_set_initial_guess")
+
+
+def mg_batch_solve(bt, count, allow=(MG_ERR_NOT_CONVERGED,)):
+    """Returns (status, [info dict per instance], total_ms)."""
+    infos = (mg_solve_info * count)()
+    tot = C.c_double(0.0)
+    st = _check(_lib.mg_batch_solve(bt, infos, C.byref(tot)), "mg_batch_solve", allow)
+    out = []
+    for inf in infos:
+        hist = np.ctypeslib.as_array(inf.history, shape=(inf.history_len * 4,)).reshape(-1, 4).copy() \
+            if inf.history_len > 0 else np.zeros((0, 4))
+        out.append(dict(outer_iters=inf.outer_iters, converged=bool(inf.converged), K=inf.K, K2=inf.K2,
+                        norms=np.array(inf.norms[:]), history=hist, device_ms=inf.device_ms,
+                        kernel_launches=inf.kernel_launches))
+    return st, out, tot.value
+
+
+def mg_batch_get_solution(bt, b, u=None, W=None):
+    (pu, du), (pw, dw) = _ptr(u), _ptr(W)
+    K = C.c_double(0.0)
+    _check(_lib.mg_batch_get_solution(bt, b, pu, pw, C.byref(K), max(du, dw)), "mg_batch_get_solution")
+    return K.value
+
+
+def mg_batch_destroy(bt):
+    _lib.mg_batch_destroy(bt)
 
 
 def config_for(problem, precision=MG_MIXED, **overrides):

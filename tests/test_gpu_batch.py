@@ -1,0 +1,91 @@
+"""Batched solves of uneven grids (one captured graph per round for all instances) against
+solo solves through the same C ABI, and against the oracle's residual."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2501_13046_gb300 import fields  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_13046_gb300 import _build
+    _build.build()
+    from paper_2501_13046_gb300 import mg as m
+    return m
+
+
+def problems():
+    out = []
+    for n, a0, seed in ((24, 3e-5, 7), (32, 6e-5, 8), (48, 4e-5, 9), (40, 8e-5, 10)):
+        out.append(fields.batch_instance(n, a0, seed))
+    return out
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def solo(mg, p, **over):
+    ctx = mg.mg_create(mg.config_for(p, mg.MG_MIXED, **over), torch.cuda.current_stream().cuda_stream)
+    try:
+        mg.mg_set_sources(ctx, *[dev(a) for a in (p["rho0"], p["rho2"], *p["S"])])
+        st, info = mg.mg_solve(ctx)
+        u, W = np.empty(p["rho0"].shape), np.empty((3,) + p["rho0"].shape)
+        mg.mg_get_solution(ctx, u, W)
+    finally:
+        mg.mg_destroy(ctx)
+    return info, u, W
+
+
+def batch(mg, ps, **over):
+    cfgs = [mg.config_for(p, mg.MG_MIXED, **over) for p in ps]
+    bt = mg.mg_batch_create(cfgs, torch.cuda.current_stream().cuda_stream)
+    try:
+        for b, p in enumerate(ps):
+            mg.mg_batch_set_sources(bt, b, *[dev(a) for a in (p["rho0"], p["rho2"], *p["S"])])
+        st, infos, total = mg.mg_batch_solve(bt, len(ps))
+        sols = []
+        for b, p in enumerate(ps):
+            u, W = np.empty(p["rho0"].shape), np.empty((3,) + p["rho0"].shape)
+            mg.mg_batch_get_solution(bt, b, u, W)
+            sols.append((u, W))
+    finally:
+        mg.mg_batch_destroy(bt)
+    return st, infos, total, sols
+
+
+def test_batch_equals_solo_after_the_same_rounds(mg):
+    ps = problems()
+    st, infos, total, sols = batch(mg, ps, tol=0.0, max_outer=4)
+    assert st == mg.MG_ERR_NOT_CONVERGED and total > 0
+    for p, (u, W), inf in zip(ps, sols, infos):
+        info, u1, W1 = solo(mg, p, tol=0.0, max_outer=4)
+        assert np.array_equal(u, u1) and np.array_equal(W, W1)
+        assert np.array_equal(inf["history"], info["history"])
+
+
+def test_batch_converges_and_reports_rounds(mg):
+    ps = problems()
+    st, infos, total, sols = batch(mg, ps, tol=1e-10, max_outer=40)
+    assert st == mg.MG_OK
+    for p, (u, W), inf in zip(ps, sols, infos):
+        info, _, _ = solo(mg, p, tol=1e-10, max_outer=40)
+        assert inf["converged"] and inf["outer_iters"] == info["outer_iters"]
+        assert 0 < inf["device_ms"] <= total
+        g = O.make_grid(p["n"], p["lo"], p["hi"], p["order"], p["bc"])
+        res = O.residual(g, u, W, p["rho0"], p["rho2"], p["S"], O.K_INTEGRABILITY)
+        assert res["norms"].max() <= 1e-10
+
+
+def test_batch_rejects_mixed_orders(mg):
+    p2 = fields.sine_periodic(n=16)
+    p4 = fields.modes_periodic(n=16)
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_batch_create([mg.config_for(p2), mg.config_for(p4)])
+    assert e.value.status == mg.MG_ERR_INVALID_ARG
