@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libctt_mg.so")
 OBJDIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["ctt_mg.cu", "mg_engine_f32_o2.cu", "mg_engine_f32_o4.cu", "mg_engine_f64_o2.cu", "mg_engine_f64_o4.cu", "mg_noalloc.cu"]
+SOURCES = ["ctt_mg.cu", "mg_engine_f32_o2.cu", "mg_engine_f32_o4.cu", "mg_engine_f64_o2.cu", "mg_engine_f64_o4.cu", "mg_noalloc.cu", "unet_conv.cu", "unet_glue.cu"]
 
 
 def nvcc():
@@ -33,7 +33,7 @@ def _stale(lib, deps):
 
 
 def deps():
-    out = [os.path.join(HERE, "..", "include", "ctt_mg.h")]
+    out = [os.path.join(HERE, "..", "include", f) for f in ("ctt_mg.h", "ctt_unet.h")]
     for f in os.listdir(CSRC):
         out.append(os.path.join(CSRC, f))
     return out

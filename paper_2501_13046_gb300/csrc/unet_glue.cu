@@ -1,0 +1,386 @@
+// unet_glue.cu -- the non-convolution kernels of the warm-start network and its training:
+// weight packing, pooling / upsampling and their adjoints, ReLU adjoint, bias gradients, the
+// 1x1 head, MSE loss, Adam, and the conversion between solver fields and network tensors.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "../../include/ctt_unet.h"
+
+namespace {
+
+constexpr int kT = 256;
+
+inline int blocks(long long n) { return (int)std::min<long long>((n + kT - 1) / kT, 152LL * 32); }
+
+__global__ void k_pack_weights(const float *w, int cin, int cout, int mode, __nv_bfloat16 *out)
+{
+    const long long n = 27LL * cin * cout;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        if (mode == 0) {
+            out[q] = __float2bfloat16_rn(w[q]);
+        } else {   // out[t][ci][co] = w[26 - t][co][ci]
+            int co = (int)(q % cout);
+            int ci = (int)((q / cout) % cin);
+            int t = (int)(q / ((long long)cout * cin));
+            out[q] = __float2bfloat16_rn(w[((long long)(26 - t) * cout + co) * cin + ci]);
+        }
+    }
+}
+
+__device__ __forceinline__ long long vox(int i, int j, int k, int n0, int n1) { return i + (long long)n0 * (j + (long long)n1 * k); }
+
+// n = fine size
+__global__ void k_avgpool2(const __nv_bfloat16 *x, int xcs, int xc0, __nv_bfloat16 *y, int ycs, int yc0, int c,
+                           int n0, int n1, int n2)
+{
+    const int m0 = n0 / 2, m1 = n1 / 2, m2 = n2 / 2;
+    const long long n = (long long)m0 * m1 * m2 * c;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int ch = (int)(q % c);
+        long long V = q / c;
+        int I = (int)(V % m0), J = (int)((V / m0) % m1), K = (int)(V / ((long long)m0 * m1));
+        float s = 0.f;
+        for (int d = 0; d < 8; ++d)
+            s += __bfloat162float(x[vox(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), n0, n1) * xcs + xc0 + ch]);
+        y[V * ycs + yc0 + ch] = __float2bfloat16_rn(0.125f * s);
+    }
+}
+
+__global__ void k_avgpool2_bwd(const __nv_bfloat16 *dy, int dcs, int dc0, __nv_bfloat16 *dx, int xcs, int xc0,
+                               int c, int n0, int n1, int n2, int acc)
+{
+    const long long n = (long long)n0 * n1 * n2 * c;
+    const int m0 = n0 / 2, m1 = n1 / 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int ch = (int)(q % c);
+        long long v = q / c;
+        int i = (int)(v % n0), j = (int)((v / n0) % n1), k = (int)(v / ((long long)n0 * n1));
+        float g = 0.125f * __bfloat162float(dy[vox(i / 2, j / 2, k / 2, m0, m1) * dcs + dc0 + ch]);
+        __nv_bfloat16 *d = dx + v * xcs + xc0 + ch;
+        *d = __float2bfloat16_rn(acc ? __bfloat162float(*d) + g : g);
+    }
+}
+
+// n = coarse size
+__global__ void k_upsample2(const __nv_bfloat16 *x, int xcs, int xc0, __nv_bfloat16 *y, int ycs, int yc0, int c,
+                            int n0, int n1, int n2)
+{
+    const int f0 = 2 * n0, f1 = 2 * n1;
+    const long long n = 8LL * n0 * n1 * n2 * c;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int ch = (int)(q % c);
+        long long v = q / c;
+        int i = (int)(v % f0), j = (int)((v / f0) % f1), k = (int)(v / ((long long)f0 * f1));
+        y[v * ycs + yc0 + ch] = x[vox(i / 2, j / 2, k / 2, n0, n1) * xcs + xc0 + ch];
+    }
+}
+
+__global__ void k_upsample2_bwd(const __nv_bfloat16 *dy, int dcs, int dc0, __nv_bfloat16 *dx, int xcs, int xc0,
+                                int c, int n0, int n1, int n2)
+{
+    const int f0 = 2 * n0, f1 = 2 * n1;
+    const long long n = (long long)n0 * n1 * n2 * c;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int ch = (int)(q % c);
+        long long V = q / c;
+        int I = (int)(V % n0), J = (int)((V / n0) % n1), K = (int)(V / ((long long)n0 * n1));
+        float s = 0.f;
+        for (int d = 0; d < 8; ++d)
+            s += __bfloat162float(dy[vox(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), f0, f1) * dcs + dc0 + ch]);
+        dx[V * xcs + xc0 + ch] = __float2bfloat16_rn(s);
+    }
+}
+
+__global__ void k_relu_bwd(__nv_bfloat16 *dy, int dcs, int dc0, const __nv_bfloat16 *y, int ycs, int yc0, int c,
+                           long long nvox)
+{
+    const long long n = nvox * c;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int ch = (int)(q % c);
+        long long v = q / c;
+        if (!(__bfloat162float(y[v * ycs + yc0 + ch]) > 0.f)) dy[v * dcs + dc0 + ch] = __float2bfloat16_rn(0.f);
+    }
+}
+
+// one block per channel slice of up to 32 channels: partial sums over voxels, then atomics
+__global__ void k_bias_grad(const __nv_bfloat16 *dy, int dcs, int dc0, float *db, int c, long long nvox)
+{
+    __shared__ float sh[8][32];
+    const int ch = threadIdx.x & 31, lane_row = threadIdx.x >> 5;
+    const int cbase = blockIdx.y * 32;
+    float s = 0.f;
+    if (cbase + ch < c)
+        for (long long v = blockIdx.x * 8LL + lane_row; v < nvox; v += (long long)gridDim.x * 8)
+            s += __bfloat162float(dy[v * dcs + dc0 + cbase + ch]);
+    sh[lane_row][ch] = s;
+    __syncthreads();
+    if (lane_row == 0 && cbase + ch < c) {
+        float t = 0.f;
+        for (int r = 0; r < 8; ++r) t += sh[r][ch];
+        atomicAdd(db + cbase + ch, t);
+    }
+}
+
+__global__ void k_head_fwd(const __nv_bfloat16 *x, int xcs, int xc0, int cin, const float *w, const float *b,
+                           float *out, int cout, long long nvox)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        float acc[8];
+        for (int o = 0; o < cout; ++o) acc[o] = b[o];
+        for (int c = 0; c < cin; ++c) {
+            float xv = __bfloat162float(x[v * xcs + xc0 + c]);
+            for (int o = 0; o < cout; ++o) acc[o] += w[o * cin + c] * xv;
+        }
+        for (int o = 0; o < cout; ++o) out[v * cout + o] = acc[o];
+    }
+}
+
+// dx = w^T dout (BF16); dw, db accumulated per block in shared memory, then atomics
+__global__ void k_head_bwd(const __nv_bfloat16 *x, int xcs, int xc0, int cin, const float *w, const float *dout,
+                           int cout, __nv_bfloat16 *dx, int dxcs, int dxc0, float *dw, float *db, long long nvox)
+{
+    __shared__ float sdw[8 * 64], sdb[8];
+    for (int q = threadIdx.x; q < cout * cin; q += blockDim.x) sdw[q] = 0.f;
+    if (threadIdx.x < 8) sdb[threadIdx.x] = 0.f;
+    __syncthreads();
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        float g[8];
+        for (int o = 0; o < cout; ++o) {
+            g[o] = dout[v * cout + o];
+            atomicAdd(&sdb[o], g[o]);
+        }
+        for (int c = 0; c < cin; ++c) {
+            float xv = __bfloat162float(x[v * xcs + xc0 + c]);
+            float s = 0.f;
+            for (int o = 0; o < cout; ++o) {
+                s += w[o * cin + c] * g[o];
+                atomicAdd(&sdw[o * cin + c], g[o] * xv);
+            }
+            dx[v * dxcs + dxc0 + c] = __float2bfloat16_rn(s);
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < cout * cin; q += blockDim.x) atomicAdd(dw + q, sdw[q]);
+    if (threadIdx.x < cout) atomicAdd(db + threadIdx.x, sdb[threadIdx.x]);
+}
+
+__global__ void k_mse(const float *out, const float *t, float *dout, float *loss, long long n)
+{
+    __shared__ float sh[kT];
+    float s = 0.f;
+    const float inv = 1.0f / (float)n;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        float d = out[q] - t[q];
+        s += d * d;
+        dout[q] = 2.f * d * inv;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, sh[0] * inv);
+}
+
+__global__ void k_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        float gq = g[q];
+        float mq = b1 * m[q] + (1.f - b1) * gq;
+        float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+        m[q] = mq;
+        v[q] = vq;
+        p[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+    }
+}
+
+// mean of one FP64 field (one block; small problems) -> *mean
+__global__ void k_mean(const double *a, const double *b, long long n, double *mean)
+{
+    __shared__ double sh[kT];
+    double s = 0.0;
+    for (long long q = threadIdx.x; q < n; q += blockDim.x) s += a[q] + (b ? b[q] : 0.0);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *mean = sh[0] / (double)n;
+}
+
+__global__ void k_pack_input(const double *rho0, const double *rho2, const double *S, double K, float s_rho,
+                             float s_S, float s_K, __nv_bfloat16 *x16, long long nvox, const double *mean)
+{
+    const double mu = *mean;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        __align__(16) __nv_bfloat16 o[16];
+        double r = rho0[v] + (rho2 ? rho2[v] : 0.0);
+        o[0] = __float2bfloat16_rn((float)((r - mu) * s_rho));
+        for (int a = 0; a < 3; ++a) o[1 + a] = __float2bfloat16_rn((float)(S[a * nvox + v] * s_S));
+        o[4] = __float2bfloat16_rn((float)(K * s_K));
+        for (int c = 5; c < 16; ++c) o[c] = __float2bfloat16_rn(0.f);
+        uint4 *d = reinterpret_cast<uint4 *>(x16 + v * 16);
+        d[0] = reinterpret_cast<uint4 *>(o)[0];
+        d[1] = reinterpret_cast<uint4 *>(o)[1];
+    }
+}
+
+__global__ void k_unpack_output(const float *out4, float s_u, float s_W, double *u, double *W, long long nvox)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        u[v] = (double)out4[v * 4] * s_u;
+        for (int a = 0; a < 3; ++a) W[a * nvox + v] = (double)out4[v * 4 + 1 + a] * s_W;
+    }
+}
+
+__global__ void k_sub_mean(double *a, long long n, const double *mean)
+{
+    const double mu = *mean;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        a[q] -= mu;
+}
+
+__global__ void k_pack_target(const double *u, const double *W, float s_u, float s_W, float *t4, long long nvox)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        t4[v * 4] = (float)(u[v] / s_u);
+        for (int a = 0; a < 3; ++a) t4[v * 4 + 1 + a] = (float)(W[a * nvox + v] / s_W);
+    }
+}
+
+inline int ok() { return cudaGetLastError() == cudaSuccess ? 0 : 3; }
+
+}  // namespace
+
+extern "C" {
+
+int unet_pack_weights(const float *w, int cin, int cout, int mode, void *out, void *stream)
+{
+    if (!w || !out || cin <= 0 || cout <= 0 || (mode != 0 && mode != 1)) return 1;
+    k_pack_weights<<<blocks(27LL * cin * cout), kT, 0, (cudaStream_t)stream>>>(w, cin, cout, mode, (__nv_bfloat16 *)out);
+    return ok();
+}
+
+int unet_avgpool2(const void *x, int xcs, int xc0, void *y, int ycs, int yc0, int c, int n0, int n1, int n2, void *stream)
+{
+    if (!x || !y || (n0 | n1 | n2) & 1) return 1;
+    k_avgpool2<<<blocks((long long)n0 * n1 * n2 / 8 * c), kT, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16 *)x, xcs, xc0, (__nv_bfloat16 *)y, ycs, yc0, c, n0, n1, n2);
+    return ok();
+}
+
+int unet_avgpool2_bwd(const void *dy, int dcs, int dc0, void *dx, int xcs, int xc0, int c, int n0, int n1, int n2,
+                      int accumulate, void *stream)
+{
+    if (!dy || !dx || (n0 | n1 | n2) & 1) return 1;
+    k_avgpool2_bwd<<<blocks((long long)n0 * n1 * n2 * c), kT, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16 *)dy, dcs, dc0, (__nv_bfloat16 *)dx, xcs, xc0, c, n0, n1, n2, accumulate);
+    return ok();
+}
+
+int unet_upsample2(const void *x, int xcs, int xc0, void *y, int ycs, int yc0, int c, int n0, int n1, int n2, void *stream)
+{
+    if (!x || !y) return 1;
+    k_upsample2<<<blocks(8LL * n0 * n1 * n2 * c), kT, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16 *)x, xcs, xc0, (__nv_bfloat16 *)y, ycs, yc0, c, n0, n1, n2);
+    return ok();
+}
+
+int unet_upsample2_bwd(const void *dy, int dcs, int dc0, void *dx, int xcs, int xc0, int c, int n0, int n1, int n2,
+                       void *stream)
+{
+    if (!dy || !dx) return 1;
+    k_upsample2_bwd<<<blocks((long long)n0 * n1 * n2 * c), kT, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16 *)dy, dcs, dc0, (__nv_bfloat16 *)dx, xcs, xc0, c, n0, n1, n2);
+    return ok();
+}
+
+int unet_relu_bwd(void *dy, int dcs, int dc0, const void *y, int ycs, int yc0, int c, long long nvox, void *stream)
+{
+    if (!dy || !y) return 1;
+    k_relu_bwd<<<blocks(nvox * c), kT, 0, (cudaStream_t)stream>>>((__nv_bfloat16 *)dy, dcs, dc0,
+                                                                   (const __nv_bfloat16 *)y, ycs, yc0, c, nvox);
+    return ok();
+}
+
+int unet_bias_grad(const void *dy, int dcs, int dc0, float *db, int c, long long nvox, void *stream)
+{
+    if (!dy || !db) return 1;
+    dim3 grid((unsigned)std::min<long long>((nvox + 7) / 8, 1024), (c + 31) / 32);
+    k_bias_grad<<<grid, 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)dy, dcs, dc0, db, c, nvox);
+    return ok();
+}
+
+int unet_head_fwd(const void *x, int xcs, int xc0, int cin, const float *w, const float *b, float *out, int cout,
+                  long long nvox, void *stream)
+{
+    if (!x || !w || !b || !out || cout > 8 || cin > 64) return 1;
+    k_head_fwd<<<blocks(nvox), kT, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)x, xcs, xc0, cin, w, b, out,
+                                                               cout, nvox);
+    return ok();
+}
+
+int unet_head_bwd(const void *x, int xcs, int xc0, int cin, const float *w, const float *dout, int cout, void *dx,
+                  int dxcs, int dxc0, float *dw, float *db, long long nvox, void *stream)
+{
+    if (!x || !w || !dout || !dx || !dw || !db || cout > 8 || cin > 64) return 1;
+    k_head_bwd<<<(int)std::min<long long>((nvox + kT - 1) / kT, 152LL * 4), kT, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16 *)x, xcs, xc0, cin, w, dout, cout, (__nv_bfloat16 *)dx, dxcs, dxc0, dw, db, nvox);
+    return ok();
+}
+
+int unet_mse(const float *out, const float *target, float *dout, float *loss, int c, long long nvox, void *stream)
+{
+    if (!out || !target || !dout || !loss) return 1;
+    k_mse<<<(int)std::min<long long>((nvox * c + kT - 1) / kT, 152LL * 8), kT, 0, (cudaStream_t)stream>>>(
+        out, target, dout, loss, nvox * c);
+    return ok();
+}
+
+int unet_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2, float eps, int t,
+              void *stream)
+{
+    if (!p || !g || !m || !v || t < 1) return 1;
+    float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    k_adam<<<blocks(n), kT, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return ok();
+}
+
+int unet_pack_input(const double *rho0, const double *rho2, const double *S, double K, float s_rho, float s_S,
+                    float s_K, void *x16, long long nvox, double *scratch_mean, void *stream)
+{
+    if (!rho0 || !S || !x16 || !scratch_mean) return 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_mean<<<1, kT, 0, st>>>(rho0, rho2, nvox, scratch_mean);
+    k_pack_input<<<blocks(nvox), kT, 0, st>>>(rho0, rho2, S, K, s_rho, s_S, s_K, (__nv_bfloat16 *)x16, nvox,
+                                               scratch_mean);
+    return ok();
+}
+
+int unet_unpack_output(const float *out4, float s_u, float s_W, double *u, double *W, long long nvox,
+                       double *scratch_mean, void *stream)
+{
+    if (!out4 || !u || !W || !scratch_mean) return 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_unpack_output<<<blocks(nvox), kT, 0, st>>>(out4, s_u, s_W, u, W, nvox);
+    for (int a = 0; a < 4; ++a) {
+        double *f = a == 0 ? u : W + (a - 1) * nvox;
+        k_mean<<<1, kT, 0, st>>>(f, nullptr, nvox, scratch_mean + a);
+        k_sub_mean<<<blocks(nvox), kT, 0, st>>>(f, nvox, scratch_mean + a);
+    }
+    return ok();
+}
+
+int unet_pack_target(const double *u, const double *W, float s_u, float s_W, float *t4, long long nvox, void *stream)
+{
+    if (!u || !W || !t4) return 1;
+    k_pack_target<<<blocks(nvox), kT, 0, (cudaStream_t)stream>>>(u, W, s_u, s_W, t4, nvox);
+    return ok();
+}
+
+}  // extern "C"

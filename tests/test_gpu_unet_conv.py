@@ -1,0 +1,111 @@
+"""tcgen05 implicit-GEMM convolutions (forward, input gradient, weight gradient) against the
+FP64 CPU oracle, through the C ABI.  Inputs and weights are BF16-representable, so the only
+differences are the FP32 accumulation order and the BF16 rounding of the forward output:
+bound |y_gpu - y| <= 2^-8 |y| + 1e-5 sum|w||x| per element (FP32 sums, BF16 store)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import conv_ref as R  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def U():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_13046_gb300 import _build
+    _build.build()
+    from paper_2501_13046_gb300 import unet
+    return unet
+
+
+def bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(R.bf16_round(a), dtype=np.float32)).to(torch.bfloat16).cuda()
+
+
+def tohost(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+SHAPES = [(8, 8, 8), (16, 8, 4)]
+PAIRS = [(16, 16), (16, 32), (32, 64), (64, 64), (128, 64), (48, 16), (96, 32)]
+
+
+@pytest.mark.parametrize("cin,cout", PAIRS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_conv_forward(U, cin, cout, shape):
+    nz, ny, nx = shape[2], shape[1], shape[0]
+    rng = np.random.default_rng(cin * 1000 + cout)
+    x = R.bf16_round(rng.standard_normal((nz, ny, nx, cin)))
+    w = R.bf16_round(rng.standard_normal((27, cout, cin)) / np.sqrt(27 * cin))
+    b = rng.standard_normal(cout).astype(np.float32)
+    for relu in (False, True):
+        ref = R.conv_fwd(x, w, b.astype(np.float64), relu=relu)
+        xt = bf16(x)
+        wt = torch.from_numpy(w.astype(np.float32)).cuda()
+        wp = torch.empty(w.shape, dtype=torch.bfloat16, device="cuda")
+        U.pack_weights(wt, cin, cout, 0, wp)
+        y = torch.zeros((nz, ny, nx, cout), dtype=torch.bfloat16, device="cuda")
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        U.conv3d_fwd(xt, wp, torch.from_numpy(b).cuda(), y, (nx, ny, nz), cin, cout, relu, err)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        scale = R.conv_fwd(np.abs(x), np.abs(w))
+        assert np.all(np.abs(tohost(y) - ref) <= 2 ** -8 * np.abs(ref) + 1e-5 * scale + 1e-6)
+
+
+def test_conv_forward_on_channel_slices(U):
+    """Input read from channels [16, 48) of a 64-channel buffer, output written to [32, 48) of 48."""
+    nx, ny, nz, cin, cout = 8, 8, 8, 32, 16
+    rng = np.random.default_rng(5)
+    big = R.bf16_round(rng.standard_normal((nz, ny, nx, 64)))
+    w = R.bf16_round(rng.standard_normal((27, cout, cin)) / 20)
+    ref = R.conv_fwd(big[..., 16:48], w)
+    from paper_2501_13046_gb300.unet import Slice
+    wp = torch.empty(w.shape, dtype=torch.bfloat16, device="cuda")
+    U.pack_weights(torch.from_numpy(w.astype(np.float32)).cuda(), cin, cout, 0, wp)
+    ybuf = torch.full((nz, ny, nx, 48), 7.0, dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U.conv3d_fwd(Slice(bf16(big), 16, 32), wp, None, Slice(ybuf, 32, 16), (nx, ny, nz), cin, cout, False, err)
+    torch.cuda.synchronize()
+    out = tohost(ybuf)
+    assert np.all(out[..., :32] == 7.0)   # outside the slice untouched
+    scale = R.conv_fwd(np.abs(big[..., 16:48]), np.abs(w))
+    assert np.all(np.abs(out[..., 32:48] - ref) <= 2 ** -8 * np.abs(ref) + 1e-5 * scale + 1e-6)
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 48), (32, 96), (64, 64)])
+def test_conv_input_gradient(U, cin, cout):
+    """dX = conv of dY with flipped, transposed weights (packing mode 1), forward kernel."""
+    nx, ny, nz = 8, 8, 8
+    rng = np.random.default_rng(11)
+    dy = R.bf16_round(rng.standard_normal((nz, ny, nx, cout)))
+    w = R.bf16_round(rng.standard_normal((27, cout, cin)) / 10)
+    ref = R.conv_dgrad(dy, w)
+    wp = torch.empty((27, cin, cout), dtype=torch.bfloat16, device="cuda")
+    U.pack_weights(torch.from_numpy(w.astype(np.float32)).cuda(), cin, cout, 1, wp)
+    dx = torch.zeros((nz, ny, nx, cin), dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U.conv3d_fwd(bf16(dy), wp, None, dx, (nx, ny, nz), cout, cin, False, err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    scale = R.conv_dgrad(np.abs(dy), np.abs(w))
+    assert np.all(np.abs(tohost(dx) - ref) <= 2 ** -8 * np.abs(ref) + 1e-5 * scale + 1e-6)
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (48, 16), (64, 64), (128, 64), (96, 32)])
+def test_conv_weight_gradient(U, cin, cout):
+    nx, ny, nz = 16, 8, 8
+    rng = np.random.default_rng(21)
+    x = R.bf16_round(rng.standard_normal((nz, ny, nx, cin)))
+    dy = R.bf16_round(rng.standard_normal((nz, ny, nx, cout)))
+    ref = R.conv_wgrad(x, dy)
+    dw = torch.zeros((27, cout, cin), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U.conv3d_wgrad(bf16(x), bf16(dy), dw, (nx, ny, nz), cin, cout, err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    scale = R.conv_wgrad(np.abs(x), np.abs(dy))   # FP32 accumulation over 1024 voxels
+    np.testing.assert_array_less(np.abs(dw.cpu().numpy() - ref), 1e-5 * scale + 1e-6)
