@@ -197,6 +197,58 @@ def solve_loop(mg, torch, ctx, steps, stream):
     return ev0.elapsed_time(ev1) / 1e3, info
 
 
+def run_warmstart(args):
+    """The learned warm start (its own JSON line): train the U-Net on solver-generated 64^3
+    solutions with the library's tcgen05 kernels, then compare warm-started and psi = 1 batched
+    mixed-precision solves (and an untrained-network control) on fresh 128^3 instances."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_13046_gb300 import fields, mg
+    from paper_2501_13046_gb300 import warmstart as WS
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    data = WS.make_dataset(mg, fields, list(range(10000, 10000 + args.train_samples)), n=64)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    n_train = len(data)
+    sc = WS.fit_scales(data)
+    P = WS.Params(seed=1)
+    control = WS.Params(seed=1)
+    t0 = time.perf_counter()
+    hist = WS.train(P, data, sc, epochs=args.epochs, lr=5e-4, warmup=50, minibatch=8)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    err_train = WS.rel_error(P, sc, data[:16])
+    del data
+    torch.cuda.empty_cache()
+    held = WS.make_dataset(mg, fields, list(range(30000, 30016)), n=64)
+    err_held = WS.rel_error(P, sc, held)
+    del held
+    seeds = list(range(20000, 20000 + args.test_instances))
+    out = {}
+    for name, PP in (("trained", P), ("untrained_control", control)):
+        r = WS.evaluate(mg, fields, PP, sc, seeds, n=128, n_net=64)
+        out[name] = {"accepted": int(sum(r["accepted"])), "cold_vcycle_pairs_mean": float(np.mean(r["cold_iters"])),
+                     "warm_vcycle_pairs_mean": float(np.mean(r["warm_iters"])), "cold_ms": r["cold_ms"],
+                     "warm_ms_incl_inference": r["warm_ms"], "inference_ms": r["infer_ms"],
+                     "fallback_ms": r["fallback_ms"], "instances": r["instances"],
+                     "dropped_unsolvable": r["dropped_unsolvable"],
+                     "cold_solves_per_s": r["instances"] / (r["cold_ms"] * 1e-3),
+                     "warm_solves_per_s": r["instances"] / (r["warm_ms"] * 1e-3)}
+    line = {"metric": "solves/s to |H|,|M|<=1e-10, learned warm start vs psi=1 (128^3 periodic, batched, mixed)",
+            "value": out["trained"]["warm_solves_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16 network (fp32 accumulate) + f32-inner/f64-outer solver", "data": "synthetic",
+            "config": {"workload": "train %d solved 64^3 samples (seeds 10000..), %d epochs; test %d fresh 128^3 "
+                                   "instances (seeds 20000..), network run at 64^3 with restriction/prolongation"
+                                   % (args.train_samples, args.epochs, args.test_instances),
+                       "data_gen_s": t_data, "train_s": t_train, "train_samples_converged": n_train, "loss_first50": float(np.mean(hist[:50])),
+                       "loss_last50": float(np.mean(hist[-50:])), "rel_l2_err_train_u_W": err_train,
+                       "rel_l2_err_heldout_u_W": err_held, **out}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,7 +256,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="bench", choices=["bench", "warmstart"])
+    ap.add_argument("--train-samples", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=12)
+    ap.add_argument("--test-instances", type=int, default=256)
     args = ap.parse_args()
+    if args.workload == "warmstart" and args.impl == "ours":
+        return run_warmstart(args)
     if args.impl == "reference":
         return run_reference(args)
 

@@ -179,7 +179,9 @@ void mg_destroy(struct mg_ctx *ctx);
  * every instance has met its tolerance (converged instances keep iterating in lock step; their
  * residual only decreases further) or the largest max_outer is reached.
  *   infos: count entries (may be NULL); infos[b].outer_iters is the round at which instance b
- *   first met its tolerance; infos[b].device_ms the batch time up to the end of that round.
+ *   first met its tolerance; infos[b].device_ms the batch time up to the end of that round;
+ *   infos[b].converged = 0 for an instance that did not.  An instance whose norm becomes
+ *   non-finite is abandoned (the others continue) and the call returns MG_ERR_DIVERGED.
  */
 typedef struct mg_batch mg_batch;
 mg_status mg_batch_create(int count, const mg_config *cfgs, void *cuda_stream, mg_batch **out);

@@ -74,6 +74,11 @@ int unet_pack_input(const double *rho0, const double *rho2, const double *S, dou
  * periodic boxes), W_i = out_i s_W (zero mean), FP64. */
 int unet_unpack_output(const float *out4, float s_u, float s_W, double *u, double *W, long long nvox,
                        double *scratch_mean, void *stream);
+/* Mean of the 8 children of nfields contiguous FP64 fields, (2 m)^3 -> m^3 (m = m0 x m1 x m2). */
+int unet_restrict2_fields(const double *fine, double *coarse, int nfields, int m0, int m1, int m2, void *stream);
+/* Cell-centred trilinear interpolation (3/4, 1/4 per axis, periodic) of nfields contiguous FP64
+ * fields, m^3 -> (2 m)^3: runs the network at its training resolution for finer grids. */
+int unet_prolong2_fields(const double *coarse, double *fine, int nfields, int m0, int m1, int m2, void *stream);
 /* Training target from a solution: t = (u / s_u, W_x / s_W, W_y / s_W, W_z / s_W), FP32 4 channels. */
 int unet_pack_target(const double *u, const double *W, float s_u, float s_W, float *t4, long long nvox, void *stream);
 

@@ -712,11 +712,11 @@ mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms)
         }
         std::vector<int> conv_round(nb, -1);
         std::vector<float> conv_ms(nb, 0.f);
-        int round = 0, done = 0;
+        std::vector<char> bad(nb, 0);   // a norm became non-finite: the instance is abandoned
+        int round = 0, done = 0, nbad = 0;
         for (;;) {
             float ms = 0.f;
             if (round > 0) cudaEventElapsedTime(&ms, t0, bt->ev_round[round]);
-            bool any_bad = false;
             for (int b = 0; b < nb; ++b) {
                 mg_ctx *x = bt->ctx[b];
                 const Scalars &s = *x->host_scal;
@@ -727,15 +727,20 @@ mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms)
                     finite = finite && std::isfinite(s.norms[a]);
                     mx = std::max(mx, s.norms[a]);
                 }
-                if (!finite) any_bad = true;
-                if (conv_round[b] < 0 && finite && mx <= x->cfg.tol) {
+                if (conv_round[b] < 0 && !bad[b] && !finite) {
+                    bad[b] = 1;
+                    ++nbad;
+                }
+                if (conv_round[b] < 0 && !bad[b] && mx <= x->cfg.tol) {
                     conv_round[b] = round;
                     conv_ms[b] = ms;
                     ++done;
                 }
             }
-            if (any_bad) { result = fail(MG_ERR_DIVERGED, "a batch instance's norm is not finite"); break; }
-            if (done == nb) break;
+            if (done + nbad == nb) {
+                if (nbad) result = fail(MG_ERR_DIVERGED, "a batch instance's norm is not finite");
+                break;
+            }
             if (round >= max_outer) { result = fail(MG_ERR_NOT_CONVERGED, "max_outer reached in the batch"); break; }
             if (cudaGraphLaunch(bt->graph_iter, bt->stream) != cudaSuccess ||
                 cudaEventRecord(bt->ev_round[round + 1], bt->stream) != cudaSuccess ||

@@ -253,6 +253,44 @@ __global__ void k_pack_target(const double *u, const double *W, float s_u, float
     }
 }
 
+// mean of the 8 children of FP64 fields: nf fields of the fine grid (2 m)^3 -> m^3
+__global__ void k_restrict2_f64(const double *fine, double *coarse, int nf, int m0, int m1, int m2)
+{
+    const long long nc = (long long)m0 * m1 * m2, nfv = 8 * nc;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nc * nf; q += (long long)gridDim.x * blockDim.x) {
+        int f = (int)(q / nc);
+        long long V = q - f * nc;
+        int I = (int)(V % m0), J = (int)((V / m0) % m1), K = (int)(V / ((long long)m0 * m1));
+        double s = 0.0;
+        for (int d = 0; d < 8; ++d)
+            s += fine[f * nfv + vox(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), 2 * m0, 2 * m1)];
+        coarse[f * nc + V] = 0.125 * s;
+    }
+}
+
+// cell-centred trilinear interpolation (weights 3/4, 1/4 per axis, periodic) of nf FP64 fields
+// from m^3 to (2 m)^3
+__global__ void k_prolong2_f64(const double *coarse, double *fine, int nf, int m0, int m1, int m2)
+{
+    const long long nc = (long long)m0 * m1 * m2, nfv = 8 * nc;
+    const int f0 = 2 * m0, f1 = 2 * m1;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nfv * nf; q += (long long)gridDim.x * blockDim.x) {
+        int f = (int)(q / nfv);
+        long long v = q - f * nfv;
+        int i = (int)(v % f0), j = (int)((v / f0) % f1), k = (int)(v / ((long long)f0 * f1));
+        int I = i >> 1, J = j >> 1, K = k >> 1;
+        int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
+        double s = 0.0;
+        for (int c = 0; c < 8; ++c) {
+            int a = c & 1, b = (c >> 1) & 1, e = c >> 2;
+            double w = (a ? 0.25 : 0.75) * (b ? 0.25 : 0.75) * (e ? 0.25 : 0.75);
+            int ii = (I + a * sx + m0) % m0, jj = (J + b * sy + m1) % m1, kk = (K + e * sz + m2) % m2;
+            s += w * coarse[f * nc + vox(ii, jj, kk, m0, m1)];
+        }
+        fine[f * nfv + v] = s;
+    }
+}
+
 inline int ok() { return cudaGetLastError() == cudaSuccess ? 0 : 3; }
 
 }  // namespace
@@ -373,6 +411,22 @@ int unet_unpack_output(const float *out4, float s_u, float s_W, double *u, doubl
         k_mean<<<1, kT, 0, st>>>(f, nullptr, nvox, scratch_mean + a);
         k_sub_mean<<<blocks(nvox), kT, 0, st>>>(f, nvox, scratch_mean + a);
     }
+    return ok();
+}
+
+int unet_restrict2_fields(const double *fine, double *coarse, int nfields, int m0, int m1, int m2, void *stream)
+{
+    if (!fine || !coarse || nfields < 1) return 1;
+    k_restrict2_f64<<<blocks((long long)m0 * m1 * m2 * nfields), kT, 0, (cudaStream_t)stream>>>(fine, coarse, nfields,
+                                                                                                 m0, m1, m2);
+    return ok();
+}
+
+int unet_prolong2_fields(const double *coarse, double *fine, int nfields, int m0, int m1, int m2, void *stream)
+{
+    if (!fine || !coarse || nfields < 1) return 1;
+    k_prolong2_f64<<<blocks(8LL * m0 * m1 * m2 * nfields), kT, 0, (cudaStream_t)stream>>>(coarse, fine, nfields, m0,
+                                                                                           m1, m2);
     return ok();
 }
 

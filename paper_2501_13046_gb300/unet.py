@@ -27,6 +27,8 @@ _SIGS = {
     "unet_pack_input": [vp, vp, vp, f64, f32, f32, f32, vp, i64, vp, vp],
     "unet_unpack_output": [vp, f32, f32, vp, vp, i64, vp, vp],
     "unet_pack_target": [vp, vp, f32, f32, vp, i64, vp],
+    "unet_restrict2_fields": [vp, vp, i32, i32, i32, i32, vp],
+    "unet_prolong2_fields": [vp, vp, i32, i32, i32, i32, vp],
 }
 for _n, _a in _SIGS.items():
     getattr(_lib, _n).argtypes = _a
@@ -134,3 +136,11 @@ def unpack_output(out4, s_u, s_W, u, W, nvox, scratch, stream=0):
 
 def pack_target(u, W, s_u, s_W, t4, nvox, stream=0):
     _call("unet_pack_target", _p(u), _p(W), s_u, s_W, _p(t4), nvox, stream)
+
+
+def restrict2_fields(fine, coarse, nfields, m, stream=0):
+    _call("unet_restrict2_fields", _p(fine), _p(coarse), nfields, m[0], m[1], m[2], stream)
+
+
+def prolong2_fields(coarse, fine, nfields, m, stream=0):
+    _call("unet_prolong2_fields", _p(coarse), _p(fine), nfields, m[0], m[1], m[2], stream)
