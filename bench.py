@@ -22,6 +22,9 @@ import time
 
 import numpy as np
 
+from paper_2501_13046_gb300 import replicas
+from paper_2501_13046_gb300.replicas import dist_env
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -90,11 +93,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+def fields_mod():
+    from paper_2501_13046_gb300 import fields
+    return fields
 
 
 def make_problem():
@@ -312,12 +313,8 @@ def main():
         torch.cuda.synchronize()
         secs, info = solve_loop(mg, torch, ctx, args.steps, stream)
         torch.cuda.synchronize()
-    if ws > 1:
-        t = torch.tensor([secs], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
-        dist.barrier()
-    value = ws * args.steps / secs
+    secs = replicas.max_over_ranks(secs, device="cuda")
+    value = replicas.job_throughput(args.steps, secs, ws)
     launches = info["kernel_launches"] * args.steps
 
     # dominant kernel: one finest-level red-black colour pass (timed live on the context stream)
@@ -353,6 +350,18 @@ def main():
     mg.mg_destroy(ctx)
     del work
     torch.cuda.empty_cache()
+    shell = {}
+    q = fields_mod().puncture_shell(n=256)
+    qsrc = [dev(a) for a in (q["rho0"], q["rho2"], *q["S"])]
+    for name, prec in (("mixed", mg.MG_MIXED), ("fp64_plain", mg.MG_FP64)):
+        cq = mg.mg_create(mg.config_for(q, prec, tol=WORKLOAD["tol"], max_outer=60), sp)
+        mg.mg_set_sources(cq, *qsrc)
+        solve_loop(mg, torch, cq, 1, stream)
+        tq, iq = solve_loop(mg, torch, cq, 2, stream)
+        shell[name] = {"solves_per_s": 2 / tq, "outer_iters": iq["outer_iters"], "max_norm": float(iq["norms"].max())}
+        mg.mg_destroy(cq)
+    del qsrc
+    torch.cuda.empty_cache()
     batch_mixed = batch_measure(mg, torch, sp, mg.MG_MIXED, repeats=2)
     torch.cuda.empty_cache()
     batch_fp64 = batch_measure(mg, torch, sp, mg.MG_FP64, repeats=1)
@@ -370,6 +379,8 @@ def main():
     cfgd = dict(WORKLOAD, outer_iters=info["outer_iters"], final_norms=list(info["norms"]), K=info["K"],
                 fp64_plain_solves_per_s=fp64_solves_per_s, fp64_plain_outer_iters=info64["outer_iters"],
                 mixed_over_fp64=value / ws / fp64_solves_per_s,
+                puncture_shell_256={**shell, "workload": "M=1 puncture, [-64,64]^3, 256^3, 4th order, Robin 1/r, "
+                                                          "phi=0.02 exp(-(r-10)^2/4), Pi=0.01 phi, K=0"},
                 batch_64_uneven={"mixed": batch_mixed, "fp64_plain": batch_fp64,
                                  "mixed_over_fp64": batch_mixed["solves_per_s"] / batch_fp64["solves_per_s"],
                                  "workload": "64 periodic instances, n ~ U{48,64,96,128,160}, L=32, 4th order, "

@@ -76,6 +76,7 @@ typedef struct {
     int use_graph;        /* 1 = replay each outer iteration as a captured CUDA graph (default 1) */
     long long spin_limit; /* bound on any device-side wait, in polls (default 1<<24)              */
     int inner_cycles;     /* V-cycles per outer iteration, 0 = auto (1 for MG_FP64, 2 for MG_MIXED) */
+    int block_threads;    /* threads per block of the stencil kernels: 0 = 256, else 64, 128 or 256 */
 } mg_config;
 
 typedef struct {
@@ -168,10 +169,23 @@ mg_status mg_residual_norms_noalloc(const mg_config *cfg, const double *u, const
                                     const double *rho2, const double *S, double out[4], double *K2,
                                     void *cuda_stream);
 
+/*
+ * Autotuner: times candidate settings of (inner_cycles, nu_pre = nu_post, block_threads) on the
+ * given problem (sources as for mg_set_sources; each candidate runs one untimed and one timed solve
+ * from psi = 1 on a private context) and writes the fastest setting that meets base->tol into
+ * *best (the other fields copied from *base), with its solve time in *best_ms.  Results are cached
+ * per (grid size, order, bc, precision, k_mode) for the process, and, when cache_path is not NULL,
+ * in that text file (one line per key; read before tuning, rewritten after).  A cache hit runs no
+ * solve.  Returns MG_ERR_NOT_CONVERGED if no candidate met the tolerance.
+ */
+mg_status mg_autotune(const mg_config *base, const double *rho0, const double *rho2, const double *Sx,
+                      const double *Sy, const double *Sz, int on_device, void *cuda_stream, const char *cache_path,
+                      mg_config *best, double *best_ms);
+
 void mg_destroy(struct mg_ctx *ctx);
 
 /*
- * Batched solves (many independent problems of uneven grid sizes).
+ * Batched solves: many independent problems of uneven grid sizes in one call.
  * All instances must share order, bc, precision and k_mode; sizes, boxes and sources differ.
  * Each instance owns its workspace and a private stream; mg_batch_solve captures the outer
  * iteration of every instance into one CUDA graph (one parallel branch per instance) and

@@ -46,6 +46,8 @@ mg_status validate(const mg_config *c)
         return fail(MG_ERR_INVALID_ARG, "bad iteration parameters");
     if (!std::isfinite(c->K)) return fail(MG_ERR_INVALID_ARG, "K not finite");
     if (c->inner_cycles < 0 || c->inner_cycles > 8) return fail(MG_ERR_INVALID_ARG, "inner_cycles must be 0..8");
+    if (c->block_threads != 0 && c->block_threads != 64 && c->block_threads != 128 && c->block_threads != 256)
+        return fail(MG_ERR_INVALID_ARG, "block_threads must be 0, 64, 128 or 256");
     int lv = c->levels > 0 ? c->levels : auto_levels(c->n);
     for (int l = 0; l + 1 < lv; ++l)
         for (int a = 0; a < 3; ++a) {
@@ -205,6 +207,7 @@ mg_status mg_config_default(mg_config *c)
     c->use_graph = 1;
     c->spin_limit = 1LL << 24;
     c->inner_cycles = 0;
+    c->block_threads = 0;
     return MG_OK;
 }
 
@@ -228,6 +231,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
     if (!x) return fail(MG_ERR_OOM, "host allocation");
     x->cfg = *cfg;
     if (x->cfg.inner_cycles == 0) x->cfg.inner_cycles = cfg->precision == MG_FP64 ? 1 : 2;
+    x->threads = cfg->block_threads > 0 ? cfg->block_threads : 256;
     x->user_stream = (cudaStream_t)cuda_stream;
     x->nlev = cfg->levels > 0 ? cfg->levels : auto_levels(cfg->n);
     x->N = (size_t)cfg->n[0] * cfg->n[1] * cfg->n[2];
@@ -775,3 +779,105 @@ mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms)
 }
 
 }  // extern "C"
+
+// ====================================================================== autotuner
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+namespace {
+
+struct TuneResult {
+    int inner, nu, threads;
+    double ms;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneResult> g_tune_cache;
+
+std::string tune_key(const mg_config *c)
+{
+    std::ostringstream k;
+    k << c->n[0] << ' ' << c->n[1] << ' ' << c->n[2] << ' ' << c->order << ' ' << c->bc << ' ' << c->precision << ' '
+      << c->k_mode;
+    return k.str();
+}
+
+void tune_load(const char *path)
+{
+    if (!path) return;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream in(line);
+        int n0, n1, n2, order, bc, prec, km;
+        TuneResult r;
+        if (in >> n0 >> n1 >> n2 >> order >> bc >> prec >> km >> r.inner >> r.nu >> r.threads >> r.ms) {
+            std::ostringstream k;
+            k << n0 << ' ' << n1 << ' ' << n2 << ' ' << order << ' ' << bc << ' ' << prec << ' ' << km;
+            g_tune_cache.emplace(k.str(), r);
+        }
+    }
+}
+
+void tune_save(const char *path)
+{
+    if (!path) return;
+    std::ofstream f(path, std::ios::trunc);
+    for (auto &kv : g_tune_cache)
+        f << kv.first << ' ' << kv.second.inner << ' ' << kv.second.nu << ' ' << kv.second.threads << ' '
+          << kv.second.ms << '\n';
+}
+
+}  // namespace
+
+extern "C" mg_status mg_autotune(const mg_config *base, const double *rho0, const double *rho2, const double *Sx,
+                                 const double *Sy, const double *Sz, int on_device, void *cuda_stream,
+                                 const char *cache_path, mg_config *best, double *best_ms)
+{
+    CKS(validate(base));
+    if (!best) return fail(MG_ERR_INVALID_ARG, "null best");
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load(cache_path);
+    const std::string key = tune_key(base);
+    auto hit = g_tune_cache.find(key);
+    TuneResult win{0, 0, 0, INFINITY};
+    if (hit != g_tune_cache.end()) {
+        win = hit->second;
+    } else {
+        const int inners_mixed[] = {1, 2, 3}, inners_fp64[] = {1, 2};
+        const int nus[] = {1, 2, 3}, threads[] = {128, 256};
+        const int *inners = base->precision == MG_FP64 ? inners_fp64 : inners_mixed;
+        const int ninner = base->precision == MG_FP64 ? 2 : 3;
+        for (int ii = 0; ii < ninner; ++ii)
+            for (int nu : nus)
+                for (int th : threads) {
+                    mg_config c = *base;
+                    c.inner_cycles = inners[ii];
+                    c.nu_pre = c.nu_post = nu;
+                    c.block_threads = th;
+                    c.use_graph = 1;
+                    mg_ctx *x = nullptr;
+                    CKS(mg_create(&c, cuda_stream, nullptr, 0, &x));
+                    mg_status st = mg_set_sources(x, rho0, rho2, Sx, Sy, Sz, on_device);
+                    mg_solve_info info;
+                    if (st == MG_OK) st = mg_solve(x, &info);            // untimed: captures the graphs
+                    if (st == MG_OK) st = mg_set_initial_guess(x, nullptr, nullptr, 1);
+                    if (st == MG_OK) st = mg_solve(x, &info);
+                    mg_destroy(x);
+                    if (st == MG_OK && info.device_ms < win.ms) win = TuneResult{inners[ii], nu, th, info.device_ms};
+                    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED && st != MG_ERR_DIVERGED) return st;
+                }
+        if (!std::isfinite(win.ms)) return fail(MG_ERR_NOT_CONVERGED, "no autotuner candidate met the tolerance");
+        g_tune_cache[key] = win;
+        tune_save(cache_path);
+    }
+    *best = *base;
+    best->inner_cycles = win.inner;
+    best->nu_pre = best->nu_post = win.nu;
+    best->block_threads = win.threads;
+    if (best_ms) *best_ms = win.ms;
+    return MG_OK;
+}

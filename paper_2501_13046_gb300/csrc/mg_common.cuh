@@ -37,9 +37,9 @@ constexpr int kRedBlocks = 152 * 8;   // reduction partials per pass (grid-strid
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-inline int grid_for(size_t work, int maxb = 152 * 16)
+inline int grid_for(size_t work, int maxb = 152 * 16, int threads = kThreads)
 {
-    size_t b = (work + kThreads - 1) / kThreads;
+    size_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
     return (int)std::min<size_t>(b, (size_t)maxb);
 }
@@ -102,6 +102,7 @@ struct mg_ctx {
     int nlev = 0;
     size_t N = 0;
     size_t tbytes = 8;   // sizeof(T) of the inner solve
+    int threads = 256;   // threads per block of the smoother, residual+restriction and prolongation
     std::vector<ctt::LevelBufs> lev;
     void *ws = nullptr;
     size_t ws_bytes = 0;

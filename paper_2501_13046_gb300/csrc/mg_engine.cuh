@@ -6,7 +6,7 @@
 namespace ctt {
 
 // Block split of a colour pass: shell blocks first, then interior-box blocks.
-inline Regions smooth_regions(const Geo &g, int order, int *grid)
+inline Regions smooth_regions(const Geo &g, int order, int *grid, int threads)
 {
     Regions r;
     r.G = order / 2;
@@ -15,23 +15,23 @@ inline Regions smooth_regions(const Geo &g, int order, int *grid)
     size_t nsh = shell_count(g.n, r.G);
     // one thread per cell: blocks then sweep the box in z order, so neighbouring planes are
     // reused from L2 while they are still resident
-    int bi = nint ? grid_for(nint, 1 << 24) : 0;
-    int bs = nsh ? grid_for(nsh, 152 * 4) : 0;
+    int bi = nint ? grid_for(nint, 1 << 24, threads) : 0;
+    int bs = nsh ? grid_for(nsh, 152 * 4, threads) : 0;
     r.nblk_sh = bs;
     *grid = std::max(1, bi + bs);
     return r;
 }
 
 // Block split of residual+restriction over the coarse cells: coarse interior box [1, nc-1)^3, shell.
-inline Regions restrict_regions(const Geo &gc, int *grid)
+inline Regions restrict_regions(const Geo &gc, int *grid, int threads)
 {
     Regions r;
     r.G = 1;
     long long ix = gc.n[0] - 2, iy = gc.n[1] - 2, iz = gc.n[2] - 2;
     size_t nint = (ix > 0 && iy > 0 && iz > 0) ? (size_t)ix * iy * iz : 0;
     size_t nsh = shell_count(gc.n, 1);
-    int bi = nint ? grid_for(nint, 1 << 24) : 0;
-    int bs = nsh ? grid_for(nsh, 152 * 4) : 0;
+    int bi = nint ? grid_for(nint, 1 << 24, threads) : 0;
+    int bs = nsh ? grid_for(nsh, 152 * 4, threads) : 0;
     r.nblk_sh = bs;
     *grid = std::max(1, bi + bs);
     return r;
@@ -52,14 +52,14 @@ mg_status enqueue_sweeps(mg_ctx *x, int l, int sweeps)
     LevelBufs &L = x->lev[l];
     Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
     int grid = 0;
-    Regions rg = smooth_regions(L.geo, ORDER, &grid);
+    Regions rg = smooth_regions(L.geo, ORDER, &grid, x->threads);
     for (int s = 0; s < sweeps; ++s) {
         const T *X = (const T *)L.cur();
         T *Y = (T *)L.alt();
         for (int colour = 0; colour < 2; ++colour) {
             const T *O = colour == 0 ? X : Y;
             dispatch_bc(x->cfg.bc, [&](auto B) {
-                k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, kThreads, 0, x->stream>>>(
+                k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, x->threads, 0, x->stream>>>(
                     L.geo, cf, X, O, Y, (const T *)L.f, (const T *)L.c, colour, rg);
             });
         }
@@ -113,9 +113,9 @@ mg_status enqueue_vcycle(mg_ctx *x, bool first)
         LevelBufs &C = x->lev[l + 1];
         Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
         int rgrid = 0;
-        Regions rr = restrict_regions(C.geo, &rgrid);
+        Regions rr = restrict_regions(C.geo, &rgrid, x->threads);
         dispatch_bc(x->cfg.bc, [&](auto B) {
-            k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, kThreads, 0, x->stream>>>(
+            k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, x->threads, 0, x->stream>>>(
                 L.geo, cf, C.geo, (const T *)L.cur(), (const T *)L.f, (const T *)L.c, (T *)C.f, C.split, rr);
         });
         CK(cudaGetLastError());
@@ -126,7 +126,7 @@ mg_status enqueue_vcycle(mg_ctx *x, bool first)
         LevelBufs &L = x->lev[l];
         LevelBufs &C = x->lev[l + 1];
         dispatch_bc(x->cfg.bc, [&](auto B) {
-            k_prolong_add<T, decltype(B)::value><<<grid_for(C.N, 1 << 24), kThreads, 0, x->stream>>>(
+            k_prolong_add<T, decltype(B)::value><<<grid_for(C.N, 1 << 24, x->threads), x->threads, 0, x->stream>>>(
                 L.geo, C.geo, (const T *)C.cur(), (T *)L.cur(), C.split);
         });
         CK(cudaGetLastError());
@@ -210,18 +210,18 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
         if (which == 0) {
             if (!L.split) return fail(MG_ERR_INVALID_ARG, "one-level hierarchy has no global smoother");
             int grid = 0;
-            Regions rg = smooth_regions(L.geo, ORDER, &grid);
+            Regions rg = smooth_regions(L.geo, ORDER, &grid, x->threads);
             dispatch_bc(x->cfg.bc, [&](auto B) {
-                k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, kThreads, 0, x->stream>>>(
+                k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, x->threads, 0, x->stream>>>(
                     L.geo, cf, (const T *)L.eA, (const T *)L.eA, (T *)L.eB, (const T *)L.f, (const T *)L.c, r & 1, rg);
             });
         } else if (which == 1) {
             if (x->nlev < 2) return fail(MG_ERR_INVALID_ARG, "one-level hierarchy has no restriction");
             LevelBufs &Cl = x->lev[1];
             int rgrid = 0;
-            Regions rr = restrict_regions(Cl.geo, &rgrid);
+            Regions rr = restrict_regions(Cl.geo, &rgrid, x->threads);
             dispatch_bc(x->cfg.bc, [&](auto B) {
-                k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, kThreads, 0, x->stream>>>(
+                k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, x->threads, 0, x->stream>>>(
                     L.geo, cf, Cl.geo, (const T *)L.eA, (const T *)L.f, (const T *)L.c, (T *)Cl.f, Cl.split, rr);
             });
         } else {

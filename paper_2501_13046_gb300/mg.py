@@ -26,7 +26,7 @@ EXPORTS = ("mg_config_default", "mg_workspace_size", "mg_create", "mg_set_confor
            "mg_set_initial_guess", "mg_solve", "mg_get_solution", "mg_residual_norms", "mg_constraint_fields",
            "mg_time_kernel", "mg_residual_norms_noalloc", "mg_destroy", "mg_status_string", "mg_last_error",
            "mg_batch_create", "mg_batch_set_sources", "mg_batch_set_initial_guess", "mg_batch_solve",
-           "mg_batch_get_solution", "mg_batch_destroy")
+           "mg_batch_get_solution", "mg_batch_destroy", "mg_autotune")
 
 
 class mg_config(C.Structure):
@@ -35,7 +35,7 @@ class mg_config(C.Structure):
         ("levels", C.c_int), ("precision", C.c_int), ("k_mode", C.c_int), ("K", C.c_double), ("npunct", C.c_int),
         ("punct_m", C.c_double * 2), ("punct_x", (C.c_double * 3) * 2), ("tol", C.c_double), ("max_outer", C.c_int),
         ("nu_pre", C.c_int), ("nu_post", C.c_int), ("coarse_sweeps", C.c_int), ("use_graph", C.c_int),
-        ("spin_limit", C.c_longlong), ("inner_cycles", C.c_int),
+        ("spin_limit", C.c_longlong), ("inner_cycles", C.c_int), ("block_threads", C.c_int),
     ]
 
 
@@ -77,6 +77,8 @@ def _load():
     L.mg_batch_set_initial_guess.argtypes = [vp, C.c_int, vp, vp, C.c_int]
     L.mg_batch_solve.argtypes = [vp, C.POINTER(mg_solve_info), dp]
     L.mg_batch_get_solution.argtypes = [vp, C.c_int, vp, vp, dp, C.c_int]
+    L.mg_autotune.argtypes = [C.POINTER(mg_config), vp, vp, vp, vp, vp, C.c_int, vp, C.c_char_p,
+                              C.POINTER(mg_config), dp]
     L.mg_batch_destroy.argtypes = [vp]
     L.mg_batch_destroy.restype = None
     L.mg_status_string.argtypes = [C.c_int]
@@ -239,6 +241,18 @@ def mg_batch_get_solution(bt, b, u=None, W=None):
     K = C.c_double(0.0)
     _check(_lib.mg_batch_get_solution(bt, b, pu, pw, C.byref(K), max(du, dw)), "mg_batch_get_solution")
     return K.value
+
+
+def mg_autotune(cfg, rho0, rho2, Sx, Sy, Sz, stream=0, cache_path=None):
+    """(best mg_config, its solve ms) for this problem; see the header for the candidates and cache."""
+    ps = [_ptr(a) for a in (rho0, rho2, Sx, Sy, Sz)]
+    dev = max(d for _, d in ps)
+    best = mg_config()
+    ms = C.c_double(0.0)
+    _check(_lib.mg_autotune(C.byref(cfg), *[p for p, _ in ps], dev, C.c_void_p(stream or None),
+                            None if cache_path is None else cache_path.encode(), C.byref(best), C.byref(ms)),
+           "mg_autotune")
+    return best, ms.value
 
 
 def mg_batch_destroy(bt):

@@ -6,7 +6,7 @@ entirely in the library's kernels (include/ctt_unet.h): tcgen05 implicit-GEMM co
 FP32 accumulation, and its training (input and weight gradients, pooling/upsampling adjoints,
 MSE loss, Adam on FP32 master weights) likewise.  torch provides device memory and streams.
 
-The solver stays the judge: a warm-started solve runs the same multigrid to the same tolerance,
+The multigrid solver has the last word: a warm-started solve runs the same multigrid to the same tolerance,
 and an instance whose solve from the warm start does not meet it within max_outer is solved
 again from psi = 1, W = 0 (the plain multigrid fallback).
 This module is the layer schedule (which kernel runs on which buffer); it computes nothing itself.
@@ -349,8 +349,8 @@ class Predictor:
 
 
 def evaluate(mg, fields, P, sc, seeds, n=128, n_net=64, chunk=64, stream=0, a_range=(2e-5, 8e-5)):
-    """Warm-started vs psi = 1 batched mixed-precision solves on fresh instances.  Multigrid is
-    the judge: a warm start is accepted when the solve from it meets the tolerance within
+    """Warm-started vs psi = 1 batched mixed-precision solves on fresh instances.  Multigrid has
+    the last word: a warm start is accepted when the solve from it meets the tolerance within
     max_outer; instances that do not are re-solved from psi = 1 and that batch's time is
     charged to the warm variant.  Timings are CUDA-event device times, inference included.
     Returns per-instance rounds (V-cycle pairs) and totals."""

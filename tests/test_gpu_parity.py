@@ -240,3 +240,15 @@ def test_full_size_bench_workload(mg):
     assert res["norms"].max() <= 1.5e-10
     assert res["K2"] == pytest.approx(info["K2"], rel=1e-12)
     assert abs(u.mean()) < 1e-15 and np.abs(W.mean(axis=(1, 2, 3))).max() < 1e-15
+
+
+def test_full_size_puncture_shell_robin(mg):
+    """Single puncture M = 1 in [-64, 64]^3 at 256^3, 4th order, Robin 1/r, Gaussian scalar shell,
+    K = 0, mixed precision: converges to 1e-10 and the oracle's residual of the GPU solution is
+    below 1e-10 at every cell (a property that holds at any size)."""
+    p = fields.puncture_shell(n=256)
+    st, info, u, W = gpu_solve(mg, p, mg.MG_MIXED, tol=1e-10)
+    assert st == mg.MG_OK and info["norms"].max() <= 1e-10
+    res = O.residual(oracle_grid(p), u, W, p["rho0"], p["rho2"], p["S"], O.K_FIXED)
+    assert res["norms"].max() <= 1.5e-10
+    assert 0.0 < u.max() < 0.5          # the regular part stays small and positive near the shell
