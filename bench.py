@@ -324,7 +324,7 @@ def main():
     achieved = bytes0 / (ms0 * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                "kernel": "k_smooth_colour<float,4,periodic> (finest level, one colour pass)",
+                "kernel": "k_smooth_tile<float,4,periodic> (TMA-tiled, finest level, one colour pass)",
                 "ms_per_launch": ms0, "algorithmic_bytes": bytes0, "peak_source": src + " hbm_gbs (copy test)",
                 "fp64_residual_pass1_ms": ms2}
 

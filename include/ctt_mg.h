@@ -76,7 +76,9 @@ typedef struct {
     int use_graph;        /* 1 = replay each outer iteration as a captured CUDA graph (default 1) */
     long long spin_limit; /* bound on any device-side wait, in polls (default 1<<24)              */
     int inner_cycles;     /* V-cycles per outer iteration, 0 = auto (1 for MG_FP64, 2 for MG_MIXED) */
-    int block_threads;    /* threads per block of the stencil kernels: 0 = 256, else 64, 128 or 256 */
+    int block_threads;    /* threads per block of the global-memory stencil kernels: 0 = 256, else 64, 128 or 256 */
+    int smoother;         /* 0 = auto: the TMA-tiled colour pass on FP32 levels with nx, ny multiples of 8,
+                             >= 16 and nz >= 8, the global-memory pass elsewhere; 1 = global-memory pass on every level */
 } mg_config;
 
 typedef struct {
@@ -136,7 +138,8 @@ mg_status mg_constraint_fields(struct mg_ctx *ctx, double *H, double *M, int on_
  * Measurement aid: launch one kernel of the solve `reps` times back to back on the context's
  * stream, bracketed by CUDA events, at the current state (call after mg_solve or
  * mg_residual_norms).  which: 0 = one red-black colour pass of the finest-level smoother,
- * 1 = residual + restriction of the finest level, 2 = outer FP64 residual pass 1.
+ * 1 = residual + restriction of the finest level, 2 = outer FP64 residual pass 1 (its two
+ * kernels, q/div W then the residual parts, and the reduction of the integrability sums).
  * Returns the mean device time per launch and the algorithmic DRAM bytes one launch must
  * move (every array it reads once, every array it writes once).  The solver state is not
  * changed except for scratch buffers.

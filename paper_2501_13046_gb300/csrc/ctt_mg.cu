@@ -10,6 +10,10 @@
 // host synchronisation per iteration is the read of K^2 and the four norms.
 #include "mg_common.cuh"
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 namespace ctt {
 
 thread_local std::string g_last_error;
@@ -48,6 +52,7 @@ mg_status validate(const mg_config *c)
     if (c->inner_cycles < 0 || c->inner_cycles > 8) return fail(MG_ERR_INVALID_ARG, "inner_cycles must be 0..8");
     if (c->block_threads != 0 && c->block_threads != 64 && c->block_threads != 128 && c->block_threads != 256)
         return fail(MG_ERR_INVALID_ARG, "block_threads must be 0, 64, 128 or 256");
+    if (c->smoother != 0 && c->smoother != 1) return fail(MG_ERR_INVALID_ARG, "smoother must be 0 or 1");
     int lv = c->levels > 0 ? c->levels : auto_levels(c->n);
     for (int l = 0; l + 1 < lv; ++l)
         for (int a = 0; a < 3; ++a) {
@@ -59,7 +64,7 @@ mg_status validate(const mg_config *c)
 }
 
 struct Layout {
-    size_t X, SRC, R, partial, scal, total;
+    size_t X, SRC, R, D, partial, scal, total;
     std::vector<size_t> eA, eB, f, c;
 };
 
@@ -74,6 +79,7 @@ Layout layout_for(const mg_config *c)
     L.X = take(4 * N * 8);
     L.SRC = take(5 * N * 8);
     L.R = take(5 * N * 8);
+    L.D = take(4 * N * 8);
     for (int l = 0; l < lv; ++l) {
         size_t Nl = ((size_t)(c->n[0] >> l)) * (c->n[1] >> l) * (c->n[2] >> l);
         L.eA.push_back(take(4 * Nl * tb));
@@ -87,6 +93,39 @@ Layout layout_for(const mg_config *c)
     return L;
 }
 
+
+// Driver entry point of the tensor-map encoder (resolved once; no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 5-D map of a colour-split level buffer (4 fields x 2 colour halves): dims (pair, row, plane,
+// field, half), box (kTileW pairs, tile rows, 1 plane, 4 fields, 1 half).
+bool encode_level_map(CUtensorMap *m, void *base, const Geo &g, size_t N, size_t tb, int order)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t nxh = (cuuint64_t)(g.n[0] / 2);
+    cuuint64_t dims[5] = {nxh, (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], 4, 2};
+    cuuint64_t strides[4] = {nxh * tb, nxh * g.n[1] * tb, N * tb, N / 2 * tb};
+    cuuint32_t box[5] = {(cuuint32_t)kTileW, (cuuint32_t)(kTileY + order), 1, 4, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(m, tb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims,
+                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 mg_status residual_any(mg_ctx *x, double *HM)
 {
@@ -250,6 +289,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         x->X = (double *)(b + lay.X);
         x->SRC = (double *)(b + lay.SRC);
         x->R = (double *)(b + lay.R);
+        x->D = (double *)(b + lay.D);
         x->partial = (double *)(b + lay.partial);
         x->scal = (Scalars *)(b + lay.scal);
         for (int l = 0; l < x->nlev; ++l) {
@@ -273,7 +313,28 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
             L.c = b + lay.c[l];
             L.split = l + 1 < x->nlev ? 1 : 0;
             L.curB = 0;
+            L.tiled = 0;
             x->lev.push_back(L);
+        }
+        {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                st = fail(MG_ERR_CUDA, "device query");
+                break;
+            }
+            for (auto &L : x->lev) {
+                // FP32 levels only: the FP64 tile needs twice the shared memory, leaving one CTA per SM
+                if (cfg->smoother != 0 || x->tbytes != 4 || !tile_eligible(L.geo, L.split)) continue;
+                if (!encode_level_map(&L.tmA, L.eA, L.geo, L.N, x->tbytes, cfg->order) ||
+                    !encode_level_map(&L.tmB, L.eB, L.geo, L.N, x->tbytes, cfg->order)) {
+                    st = fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a level buffer");
+                    break;
+                }
+                L.tg = tile_grid(L.geo, x->sms, x->tbytes == 4 ? 2 : 1);
+                L.tiled = 1;
+            }
+            if (st != MG_OK) break;
         }
         if (cudaStreamCreateWithFlags(&x->stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&x->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -378,6 +439,7 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
             if (!std::isfinite(s.norms[a])) finite = false;
             mx = std::max(mx, s.norms[a]);
         }
+        if (s.err) { result = fail(MG_ERR_TIMEOUT, "a bounded device wait gave up (spin_limit)"); break; }
         if (!finite || !std::isfinite(s.K2)) { result = fail(MG_ERR_DIVERGED, "constraint norm is not finite"); break; }
         if (mx <= x->cfg.tol) { result = MG_OK; break; }
         grow = mx > prev ? grow + 1 : 0;
@@ -458,7 +520,7 @@ static mg_status mg_time_kernel_impl(mg_ctx *x, int which, int reps, double *ms_
     double N = (double)x->N, s = (double)x->tbytes, b = 0.0;
     if (which == 0) b = 0.5 * 14.0 * s * N;               // half of a two-colour sweep: (2 F + 6) s per cell (algorithmic)
     else if (which == 1) b = (10.0 * s + 4.0 * s / 8.0) * N; // read e, f, a, b; write the coarse rhs
-    else b = (9.0 * 8.0 + 5.0 * 8.0) * N;                 // read u, W, 5 sources; write 5 FP64 fields
+    else b = (3.0 + 4.0 + 4.0 + 4.0 + 5.0 + 5.0) * 8.0 * N; // A: read W, write q/div; B: read u, W, q/div, 5 sources, write 5
     if (ms_per_launch) *ms_per_launch = ms / reps;
     if (bytes_per_launch) *bytes_per_launch = b;
     return MG_OK;
@@ -741,6 +803,9 @@ mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms)
                     ++done;
                 }
             }
+            bool timeout = false;
+            for (int b = 0; b < nb; ++b) timeout = timeout || bt->ctx[b]->host_scal->err != 0;
+            if (timeout) { result = fail(MG_ERR_TIMEOUT, "a bounded device wait gave up (spin_limit)"); break; }
             if (done + nbad == nb) {
                 if (nbad) result = fail(MG_ERR_DIVERGED, "a batch instance's norm is not finite");
                 break;

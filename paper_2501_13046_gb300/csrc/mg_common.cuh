@@ -13,6 +13,8 @@
 
 #include "../../include/ctt_mg.h"
 #include "mg_kernels.cuh"
+#include "mg_tile.cuh"
+#include "mg_outer.cuh"
 
 namespace ctt {
 
@@ -64,9 +66,32 @@ struct LevelBufs {
     void *eA, *eB, *f, *c;   // T arrays: 4N, 4N, 4N, 2N (c holds the psi-row coefficients a, b)
     int split;               // 1: colour-split storage (every level above the coarsest), 0: plain
     int curB;                // enqueue-time bookkeeping: 1 when eB holds the current correction
+    int tiled;               // 1: colour passes run the TMA-tiled kernel (tensor maps below)
+    TileGrid tg;
+    CUtensorMap tmA, tmB;    // 5-D maps of eA, eB: (pair, row, plane, field, colour half)
     void *cur() const { return curB ? eB : eA; }
     void *alt() const { return curB ? eA : eB; }
+    const CUtensorMap &tm_cur() const { return curB ? tmB : tmA; }
+    const CUtensorMap &tm_alt() const { return curB ? tmA : tmB; }
 };
+
+// Level eligibility and launch shape of the tiled colour pass; `sms` = multiprocessors.
+inline bool tile_eligible(const Geo &g, int split)
+{
+    return split && g.n[0] % 8 == 0 && g.n[1] % 8 == 0 && g.n[0] >= 16 && g.n[1] >= 16 && g.n[2] >= 8;
+}
+
+inline TileGrid tile_grid(const Geo &g, int sms, int ctas_per_sm)
+{
+    TileGrid t;
+    t.ntx = (g.n[0] / 2 + kTileP - 1) / kTileP;
+    t.nty = g.n[1] / kTileY;
+    int chunks = std::max(1, sms * ctas_per_sm / (t.ntx * t.nty));
+    t.zc = std::max(2, (g.n[2] + chunks - 1) / chunks);
+    return t;
+}
+
+inline int tile_ctas(const Geo &g, const TileGrid &t) { return t.ntx * t.nty * ((g.n[2] + t.zc - 1) / t.zc); }
 
 template <typename T>
 Coef<T> make_coef(const Geo &g, int order)
@@ -82,6 +107,48 @@ Coef<T> make_coef(const Geo &g, int order)
     cf.dl = (T)dl;
     for (int a = 0; a < 3; ++a) cf.idW[a] = (T)(1.0 / (dl + w0 / (g.h[a] * g.h[a]) / 3.0));
     return cf;
+}
+
+inline OuterCoef make_outer_coef(const Geo &g, int order)
+{
+    OuterCoef o;
+    const double w0 = order == 2 ? -2.0 : -30.0 / 12.0;
+    o.k0 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double h = g.h[a], h2 = h * h;
+        o.c1[a] = (order == 2 ? 0.5 : 8.0 / 12.0) / h;
+        o.c2[a] = order == 2 ? 0.0 : (1.0 / 12.0) / h;
+        o.k1[a] = (order == 2 ? 1.0 : 16.0 / 12.0) / h2;
+        o.nk2[a] = order == 2 ? 0.0 : -(1.0 / 12.0) / h2;
+        o.k0 += w0 / h2;
+        o.q1[a] = o.c1[a] / 3.0;
+        o.q2[a] = o.c2[a] / 3.0;
+    }
+    for (int A = 0; A < 3; ++A) {
+        for (int a = 0; a < 3; ++a) {
+            const double s = a == A ? 4.0 / 3.0 : 1.0;
+            o.m1[A][a] = s * o.k1[a];
+            o.nm2[A][a] = s * o.nk2[a];
+        }
+        o.m0[A] = o.k0 + w0 / (3.0 * g.h[A] * g.h[A]);
+    }
+    return o;
+}
+
+// Block split of the FP64 residual pass B: shell blocks first, then interior-box blocks; at most
+// kRedBlocks blocks in all (one reduction partial each).
+inline Regions outer_regions(const Geo &g, int order, int *grid)
+{
+    Regions r;
+    r.G = order / 2;
+    long long ix = g.n[0] - 2 * r.G, iy = g.n[1] - 2 * r.G, iz = g.n[2] - 2 * r.G;
+    size_t nint = (ix > 0 && iy > 0 && iz > 0) ? (size_t)ix * iy * iz : 0;
+    size_t nsh = shell_count(g.n, r.G);
+    int bs = nsh ? grid_for(nsh, 152, kThreads) : 0;
+    int bi = nint ? grid_for(nint, kRedBlocks - bs, kThreads) : 0;
+    r.nblk_sh = bs;
+    *grid = std::max(1, bi + bs);
+    return r;
 }
 
 inline size_t coarse_smem_bytes(size_t Nc, size_t tb) { return 14 * Nc * tb; }
@@ -103,6 +170,7 @@ struct mg_ctx {
     size_t N = 0;
     size_t tbytes = 8;   // sizeof(T) of the inner solve
     int threads = 256;   // threads per block of the smoother, residual+restriction and prolongation
+    int sms = 152;       // multiprocessors of the device
     std::vector<ctt::LevelBufs> lev;
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -110,6 +178,7 @@ struct mg_ctx {
     double *X = nullptr;     // 4N: u, Wx, Wy, Wz
     double *SRC = nullptr;   // 5N: rho0, rho2, Sx, Sy, Sz
     double *R = nullptr;     // 5N: outer pass-1 output
+    double *D = nullptr;     // 4N: q_0, q_1, q_2, div W of the FP64 residual's pass A
     double *partial = nullptr;
     ctt::Scalars *scal = nullptr;
     ctt::Scalars *host_scal = nullptr;   // pinned

@@ -44,6 +44,22 @@ void dispatch_bc(int bc, Fn &&fn)
     else fn(std::integral_constant<int, BC_ROBIN>());
 }
 
+// One colour pass of the TMA-tiled kernel (X: old values, O: other colour, Y: output).
+template <typename T, int ORDER>
+mg_status launch_tile(mg_ctx *x, const LevelBufs &L, const Coef<T> &cf, const CUtensorMap &mX,
+                      const CUtensorMap &mO, const T *X, const T *O, T *Y, int colour)
+{
+    const int grid = tile_ctas(L.geo, L.tg);
+    const size_t smem = tile_smem_bytes<T, ORDER>();
+    dispatch_bc(x->cfg.bc, [&](auto B) {
+        k_smooth_tile<T, ORDER, decltype(B)::value><<<grid, kTileThreads, smem, x->stream>>>(
+            mX, mO, L.geo, cf, X, O, Y, (const T *)L.f, (const T *)L.c, colour, L.tg, &x->scal->err,
+            (long long)x->cfg.spin_limit);
+    });
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
 // `sweeps` red-black sweeps on a colour-split level.  Each sweep reads the current buffer and
 // writes the alternate one (red half, then black half), then the two swap roles.
 template <typename T, int ORDER>
@@ -58,10 +74,15 @@ mg_status enqueue_sweeps(mg_ctx *x, int l, int sweeps)
         T *Y = (T *)L.alt();
         for (int colour = 0; colour < 2; ++colour) {
             const T *O = colour == 0 ? X : Y;
-            dispatch_bc(x->cfg.bc, [&](auto B) {
-                k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, x->threads, 0, x->stream>>>(
-                    L.geo, cf, X, O, Y, (const T *)L.f, (const T *)L.c, colour, rg);
-            });
+            if (L.tiled) {
+                const CUtensorMap &mO = colour == 0 ? L.tm_cur() : L.tm_alt();
+                CKS(launch_tile<T, ORDER>(x, L, cf, L.tm_cur(), mO, X, O, Y, colour));
+            } else {
+                dispatch_bc(x->cfg.bc, [&](auto B) {
+                    k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, x->threads, 0, x->stream>>>(
+                        L.geo, cf, X, O, Y, (const T *)L.f, (const T *)L.c, colour, rg);
+                });
+            }
         }
         L.curB ^= 1;
     }
@@ -135,18 +156,34 @@ mg_status enqueue_vcycle(mg_ctx *x, bool first)
     return MG_OK;
 }
 
+// FP64 residual pass 1 (pass A: q, div W; pass B: R and the integrability sums), then the
+// final reduction of the sums.
+template <int ORDER>
+mg_status enqueue_outer_pass1(mg_ctx *x)
+{
+    LevelBufs &L0 = x->lev[0];
+    Coef<double> cf = make_coef<double>(L0.geo, x->cfg.order);
+    OuterCoef oc = make_outer_coef(L0.geo, x->cfg.order);
+    int gb = 0;
+    Regions rg = outer_regions(L0.geo, ORDER, &gb);
+    dispatch_bc(x->cfg.bc, [&](auto B) {
+        k_outer_div<ORDER, decltype(B)::value><<<grid_for(x->N, 1 << 24), kThreads, 0, x->stream>>>(L0.geo, oc, x->X,
+                                                                                                      x->D);
+        k_outer_pass1q<ORDER, decltype(B)::value><<<gb, kThreads, 0, x->stream>>>(L0.geo, cf, oc, x->X, x->D, x->SRC,
+                                                                                  x->R, x->partial, rg);
+    });
+    k_finalize_sum<5><<<1, 256, 0, x->stream>>>(x->partial, gb, x->scal->sums);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
 // Outer residual.  HM != nullptr: write H, M instead of the inner rhs/coefficient.
 template <typename T, int ORDER>
 mg_status enqueue_residual(mg_ctx *x, double *HM)
 {
     LevelBufs &L0 = x->lev[0];
-    Coef<double> cf = make_coef<double>(L0.geo, x->cfg.order);
+    CKS(enqueue_outer_pass1<ORDER>(x));
     int g1 = grid_for(x->N, kRedBlocks);
-    dispatch_bc(x->cfg.bc, [&](auto B) {
-        k_outer_pass1<ORDER, decltype(B)::value><<<g1, kThreads, 0, x->stream>>>(L0.geo, cf, x->X, x->SRC,
-                                                                                              x->R, x->partial);
-    });
-    k_finalize_sum<5><<<1, 256, 0, x->stream>>>(x->partial, g1, x->scal->sums);
     double K2f = x->cfg.K * x->cfg.K;
     k_outer_scalars<<<1, 1, 0, x->stream>>>(x->scal, x->N, x->cfg.k_mode == MG_K_INTEGRABILITY, K2f,
                                            x->cfg.bc == MG_BC_PERIODIC);
@@ -195,6 +232,10 @@ mg_status engine_prepare(mg_ctx *x)
             cudaFuncSetAttribute(k_coarse_psi_direct<T, ORDER, decltype(B)::value>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxCoarseSmem) != cudaSuccess)
             st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(coarse kernels)");
+        if (cudaFuncSetAttribute(k_smooth_tile<T, ORDER, decltype(B)::value>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<T, ORDER>()) != cudaSuccess)
+            st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(k_smooth_tile)");
     });
     return st;
 }
@@ -209,6 +250,10 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
     for (int r = 0; r < reps; ++r) {
         if (which == 0) {
             if (!L.split) return fail(MG_ERR_INVALID_ARG, "one-level hierarchy has no global smoother");
+            if (L.tiled) {
+                CKS(launch_tile<T, ORDER>(x, L, cf, L.tmA, L.tmA, (const T *)L.eA, (const T *)L.eA, (T *)L.eB, r & 1));
+                continue;
+            }
             int grid = 0;
             Regions rg = smooth_regions(L.geo, ORDER, &grid, x->threads);
             dispatch_bc(x->cfg.bc, [&](auto B) {
@@ -225,12 +270,7 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
                     L.geo, cf, Cl.geo, (const T *)L.eA, (const T *)L.f, (const T *)L.c, (T *)Cl.f, Cl.split, rr);
             });
         } else {
-            Coef<double> cd = make_coef<double>(L.geo, x->cfg.order);
-            int g1 = grid_for(x->N, kRedBlocks);
-            dispatch_bc(x->cfg.bc, [&](auto B) {
-                k_outer_pass1<ORDER, decltype(B)::value><<<g1, kThreads, 0, x->stream>>>(L.geo, cd, x->X, x->SRC, x->R,
-                                                                                         x->partial);
-            });
+            CKS(enqueue_outer_pass1<ORDER>(x));
         }
     }
     CK(cudaGetLastError());

@@ -588,6 +588,8 @@ struct Scalars {
     double norms[4];
     double emean[4];
     double sums[8];
+    unsigned int err;   // nonzero: a bounded wait of a pipelined kernel gave up (MG_ERR_TIMEOUT)
+    unsigned int pad;
 };
 
 // Final single-block reduction of per-block partial sums: partial[b * NV + a].

@@ -40,9 +40,10 @@ def test_config_defaults_and_workspace_size(lib):
     cfg.n[0] = cfg.n[1] = cfg.n[2] = 32
     nbytes = lib.mg_workspace_size(cfg)
     N = 32 ** 3
-    # FP64 state (4), sources (5), pass-1 output (5) plus FP32 levels (13 arrays, 8/7 geometric)
-    assert nbytes >= 14 * 8 * N + 13 * 4 * N
-    assert nbytes <= 14 * 8 * N + 13 * 4 * N * 8 // 7 + 2 ** 20
+    # FP64 state (4), sources (5), pass-1 output (5), q / div W (4) plus FP32 levels (13 arrays, 8/7 geometric)
+    assert nbytes >= 18 * 8 * N + 13 * 4 * N
+    assert nbytes <= 18 * 8 * N + 13 * 4 * N * 8 // 7 + 2 ** 20
+    assert cfg.smoother == 0 and cfg.block_threads == 0
 
 
 @pytest.mark.parametrize("field,value,status", [

@@ -195,6 +195,26 @@ def test_deterministic(mg):
     assert np.array_equal(i1["history"], i2["history"])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["modes_periodic_o4_n32", "puncture_shell_o4_n32", "sine_periodic_o2_n32"])
+def test_tiled_and_global_smoother_agree(mg, case, precision):
+    """The TMA-tiled colour pass (shared-memory tiles, halo from wrap or Robin ghosts) and the
+    global-memory colour pass apply the same operator with the same reads: both solves converge
+    to the floor in the same number of outer iterations (+-1) and to the same root."""
+    p = CASES[case]()
+    prec = mg.MG_FP64 if precision == "fp64" else mg.MG_MIXED
+    st0, i0, u0, W0 = gpu_solve(mg, p, prec, smoother=0)
+    st1, i1, u1, W1 = gpu_solve(mg, p, prec, smoother=1)
+    assert st0 == mg.MG_OK and st1 == mg.MG_OK
+    assert abs(i0["outer_iters"] - i1["outer_iters"]) <= 1
+    # the first residual reductions agree to the inner precision
+    k = min(3, len(i0["history"]), len(i1["history"]))
+    np.testing.assert_allclose(i0["history"][:k], i1["history"][:k], rtol=1e-3 if precision == "mixed" else 1e-9)
+    assert rel(1.0 + u0, 1.0 + u1) < 1e-10
+    if np.abs(W1).max() > 1e-12:
+        assert rel(W0, W1) < 1e-10
+
+
 def test_graph_and_direct_launch_agree(mg):
     p = fields.puncture_shell(n=32, half=16.0)
     _, i1, u1, W1 = gpu_solve(mg, p, mg.MG_MIXED, use_graph=1)
