@@ -79,6 +79,8 @@ typedef struct {
     int block_threads;    /* threads per block of the global-memory stencil kernels: 0 = 256, else 64, 128 or 256 */
     int smoother;         /* 0 = auto: the TMA-tiled colour pass on FP32 levels with nx, ny multiples of 8,
                              >= 16 and nz >= 8, the global-memory pass elsewhere; 1 = global-memory pass on every level */
+    int cycle;            /* coarse-level visits per cycle: 0 or 1 = V-cycle (default), 2 = W-cycle           */
+    double omega;         /* red-black relaxation weight in (0, 2); 0 = 1.0 (plain Gauss-Seidel per colour)   */
 } mg_config;
 
 typedef struct {
@@ -173,7 +175,8 @@ mg_status mg_residual_norms_noalloc(const mg_config *cfg, const double *u, const
                                     void *cuda_stream);
 
 /*
- * Autotuner: times candidate settings of (inner_cycles, nu_pre = nu_post, block_threads) on the
+ * Autotuner: times candidate settings of (inner_cycles in {1, 2, 3} ({1, 2} for MG_FP64),
+ * nu_pre = nu_post in {1, 2, 3}, omega in {1, 1.15, 1.3}; V-cycles) on the
  * given problem (sources as for mg_set_sources; each candidate runs one untimed and one timed solve
  * from psi = 1 on a private context) and writes the fastest setting that meets base->tol into
  * *best (the other fields copied from *base), with its solve time in *best_ms.  Results are cached

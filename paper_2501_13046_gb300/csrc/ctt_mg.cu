@@ -53,6 +53,9 @@ mg_status validate(const mg_config *c)
     if (c->block_threads != 0 && c->block_threads != 64 && c->block_threads != 128 && c->block_threads != 256)
         return fail(MG_ERR_INVALID_ARG, "block_threads must be 0, 64, 128 or 256");
     if (c->smoother != 0 && c->smoother != 1) return fail(MG_ERR_INVALID_ARG, "smoother must be 0 or 1");
+    if (c->cycle < 0 || c->cycle > 2) return fail(MG_ERR_INVALID_ARG, "cycle must be 0, 1 (V) or 2 (W)");
+    if (!(c->omega == 0.0 || (c->omega > 0.0 && c->omega < 2.0)))
+        return fail(MG_ERR_INVALID_ARG, "omega must be 0 (default 1) or in (0, 2)");
     int lv = c->levels > 0 ? c->levels : auto_levels(c->n);
     for (int l = 0; l + 1 < lv; ++l)
         for (int a = 0; a < 3; ++a) {
@@ -271,6 +274,8 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
     x->cfg = *cfg;
     if (x->cfg.inner_cycles == 0) x->cfg.inner_cycles = cfg->precision == MG_FP64 ? 1 : 2;
     x->threads = cfg->block_threads > 0 ? cfg->block_threads : 256;
+    x->omega = cfg->omega > 0.0 ? cfg->omega : 1.0;
+    x->gamma = cfg->cycle == 2 ? 2 : 1;
     x->user_stream = (cudaStream_t)cuda_stream;
     x->nlev = cfg->levels > 0 ? cfg->levels : auto_levels(cfg->n);
     x->N = (size_t)cfg->n[0] * cfg->n[1] * cfg->n[2];
@@ -856,6 +861,7 @@ namespace {
 
 struct TuneResult {
     int inner, nu, threads;
+    double omega;
     double ms;
 };
 
@@ -879,7 +885,7 @@ void tune_load(const char *path)
         std::istringstream in(line);
         int n0, n1, n2, order, bc, prec, km;
         TuneResult r;
-        if (in >> n0 >> n1 >> n2 >> order >> bc >> prec >> km >> r.inner >> r.nu >> r.threads >> r.ms) {
+        if (in >> n0 >> n1 >> n2 >> order >> bc >> prec >> km >> r.inner >> r.nu >> r.threads >> r.omega >> r.ms) {
             std::ostringstream k;
             k << n0 << ' ' << n1 << ' ' << n2 << ' ' << order << ' ' << bc << ' ' << prec << ' ' << km;
             g_tune_cache.emplace(k.str(), r);
@@ -893,7 +899,7 @@ void tune_save(const char *path)
     std::ofstream f(path, std::ios::trunc);
     for (auto &kv : g_tune_cache)
         f << kv.first << ' ' << kv.second.inner << ' ' << kv.second.nu << ' ' << kv.second.threads << ' '
-          << kv.second.ms << '\n';
+          << kv.second.omega << ' ' << kv.second.ms << '\n';
 }
 
 }  // namespace
@@ -908,21 +914,23 @@ extern "C" mg_status mg_autotune(const mg_config *base, const double *rho0, cons
     tune_load(cache_path);
     const std::string key = tune_key(base);
     auto hit = g_tune_cache.find(key);
-    TuneResult win{0, 0, 0, INFINITY};
+    TuneResult win{0, 0, 0, 1.0, INFINITY};
     if (hit != g_tune_cache.end()) {
         win = hit->second;
     } else {
         const int inners_mixed[] = {1, 2, 3}, inners_fp64[] = {1, 2};
-        const int nus[] = {1, 2, 3}, threads[] = {128, 256};
+        const int nus[] = {1, 2, 3};
+        const double omegas[] = {1.0, 1.15, 1.3};
         const int *inners = base->precision == MG_FP64 ? inners_fp64 : inners_mixed;
         const int ninner = base->precision == MG_FP64 ? 2 : 3;
+        const int th = base->block_threads;
         for (int ii = 0; ii < ninner; ++ii)
             for (int nu : nus)
-                for (int th : threads) {
+                for (double om : omegas) {
                     mg_config c = *base;
                     c.inner_cycles = inners[ii];
                     c.nu_pre = c.nu_post = nu;
-                    c.block_threads = th;
+                    c.omega = om;
                     c.use_graph = 1;
                     mg_ctx *x = nullptr;
                     CKS(mg_create(&c, cuda_stream, nullptr, 0, &x));
@@ -932,7 +940,7 @@ extern "C" mg_status mg_autotune(const mg_config *base, const double *rho0, cons
                     if (st == MG_OK) st = mg_set_initial_guess(x, nullptr, nullptr, 1);
                     if (st == MG_OK) st = mg_solve(x, &info);
                     mg_destroy(x);
-                    if (st == MG_OK && info.device_ms < win.ms) win = TuneResult{inners[ii], nu, th, info.device_ms};
+                    if (st == MG_OK && info.device_ms < win.ms) win = TuneResult{inners[ii], nu, th, om, info.device_ms};
                     if (st != MG_OK && st != MG_ERR_NOT_CONVERGED && st != MG_ERR_DIVERGED) return st;
                 }
         if (!std::isfinite(win.ms)) return fail(MG_ERR_NOT_CONVERGED, "no autotuner candidate met the tolerance");
@@ -943,6 +951,7 @@ extern "C" mg_status mg_autotune(const mg_config *base, const double *rho0, cons
     best->inner_cycles = win.inner;
     best->nu_pre = best->nu_post = win.nu;
     best->block_threads = win.threads;
+    best->omega = win.omega;
     if (best_ms) *best_ms = win.ms;
     return MG_OK;
 }

@@ -93,8 +93,9 @@ inline TileGrid tile_grid(const Geo &g, int sms, int ctas_per_sm)
 
 inline int tile_ctas(const Geo &g, const TileGrid &t) { return t.ntx * t.nty * ((g.n[2] + t.zc - 1) / t.zc); }
 
+// omega: red-black relaxation weight (1 = plain Gauss-Seidel within the colour pass).
 template <typename T>
-Coef<T> make_coef(const Geo &g, int order)
+Coef<T> make_coef(const Geo &g, int order, double omega = 1.0)
 {
     Coef<T> cf;
     double w0 = order == 2 ? -2.0 : -30.0 / 12.0;
@@ -105,7 +106,8 @@ Coef<T> make_coef(const Geo &g, int order)
         dl += w0 / (g.h[a] * g.h[a]);
     }
     cf.dl = (T)dl;
-    for (int a = 0; a < 3; ++a) cf.idW[a] = (T)(1.0 / (dl + w0 / (g.h[a] * g.h[a]) / 3.0));
+    for (int a = 0; a < 3; ++a) cf.idW[a] = (T)(omega / (dl + w0 / (g.h[a] * g.h[a]) / 3.0));
+    cf.iom = (T)(1.0 / omega);
     return cf;
 }
 
@@ -171,6 +173,8 @@ struct mg_ctx {
     size_t tbytes = 8;   // sizeof(T) of the inner solve
     int threads = 256;   // threads per block of the smoother, residual+restriction and prolongation
     int sms = 152;       // multiprocessors of the device
+    double omega = 1.0;  // red-black relaxation weight
+    int gamma = 1;       // coarse-level visits per cycle (1 = V, 2 = W)
     std::vector<ctt::LevelBufs> lev;
     void *ws = nullptr;
     size_t ws_bytes = 0;

@@ -66,7 +66,7 @@ template <typename T, int ORDER>
 mg_status enqueue_sweeps(mg_ctx *x, int l, int sweeps)
 {
     LevelBufs &L = x->lev[l];
-    Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
+    Coef<T> cf = make_coef<T>(L.geo, x->cfg.order, x->omega);
     int grid = 0;
     Regions rg = smooth_regions(L.geo, ORDER, &grid, x->threads);
     for (int s = 0; s < sweeps; ++s) {
@@ -96,7 +96,7 @@ mg_status enqueue_coarse(mg_ctx *x, int l)
     LevelBufs &L = x->lev[l];
     const size_t tb = sizeof(T);
     const int periodic = x->cfg.bc == MG_BC_PERIODIC;
-    Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
+    Coef<T> cf = make_coef<T>(L.geo, x->cfg.order, x->omega);
     const size_t smem = coarse_smem_bytes(L.N, tb);
     if (smem <= kMaxCoarseSmem) {
         dispatch_bc(x->cfg.bc, [&](auto B) {
@@ -117,44 +117,46 @@ mg_status enqueue_coarse(mg_ctx *x, int l)
     return fail(MG_ERR_UNSUPPORTED, "coarsest level too large for the one-CTA coarse solve; use more levels");
 }
 
-// One V-cycle on J e = f.  first: the finest correction starts at zero; otherwise the cycle
-// continues from the current finest correction (coarser levels always start at zero).
+// One multigrid cycle on J e = f at level l (the coarsest level is solved directly).  zero: the
+// level's correction starts at zero, else the cycle continues from it.  After pre-smoothing
+// the residual is restricted once; the coarser level is then cycled gamma times on that right-
+// hand side (1: V-cycle, 2: W-cycle), the later visits continuing from its correction, and the
+// result is prolongated and post-smoothed.  The coarsest level is visited once (exact solve).
 template <typename T, int ORDER>
-mg_status enqueue_vcycle(mg_ctx *x, bool first)
+mg_status enqueue_cycle(mg_ctx *x, int l, bool zero)
 {
     const int Lc = x->nlev - 1;
-    size_t tb = sizeof(T);
-    for (int l = 0; l < Lc; ++l) {
-        LevelBufs &L = x->lev[l];
-        if (l > 0 || first) {
-            L.curB = 0;
-            CK(cudaMemsetAsync(L.eA, 0, 4 * L.N * tb, x->stream));
-        }
-        CKS(enqueue_sweeps<T, ORDER>(x, l, x->cfg.nu_pre));
-        LevelBufs &C = x->lev[l + 1];
-        Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
-        int rgrid = 0;
-        Regions rr = restrict_regions(C.geo, &rgrid, x->threads);
-        dispatch_bc(x->cfg.bc, [&](auto B) {
-            k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, x->threads, 0, x->stream>>>(
-                L.geo, cf, C.geo, (const T *)L.cur(), (const T *)L.f, (const T *)L.c, (T *)C.f, C.split, rr);
-        });
-        CK(cudaGetLastError());
+    LevelBufs &L = x->lev[l];
+    if (l == Lc) {   // the coarse solve writes the whole correction
+        L.curB = 0;
+        return enqueue_coarse<T, ORDER>(x, Lc);
     }
-    x->lev[Lc].curB = 0;
-    CKS(enqueue_coarse<T, ORDER>(x, Lc));
-    for (int l = Lc - 1; l >= 0; --l) {
-        LevelBufs &L = x->lev[l];
-        LevelBufs &C = x->lev[l + 1];
-        dispatch_bc(x->cfg.bc, [&](auto B) {
-            k_prolong_add<T, decltype(B)::value><<<grid_for(C.N, 1 << 24, x->threads), x->threads, 0, x->stream>>>(
-                L.geo, C.geo, (const T *)C.cur(), (T *)L.cur(), C.split);
-        });
-        CK(cudaGetLastError());
-        CKS(enqueue_sweeps<T, ORDER>(x, l, x->cfg.nu_post));
+    if (zero) {
+        L.curB = 0;
+        CK(cudaMemsetAsync(L.eA, 0, 4 * L.N * sizeof(T), x->stream));
     }
-    return MG_OK;
+    CKS(enqueue_sweeps<T, ORDER>(x, l, x->cfg.nu_pre));
+    LevelBufs &C = x->lev[l + 1];
+    Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
+    int rgrid = 0;
+    Regions rr = restrict_regions(C.geo, &rgrid, x->threads);
+    dispatch_bc(x->cfg.bc, [&](auto B) {
+        k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, x->threads, 0, x->stream>>>(
+            L.geo, cf, C.geo, (const T *)L.cur(), (const T *)L.f, (const T *)L.c, (T *)C.f, C.split, rr);
+    });
+    CK(cudaGetLastError());
+    const int visits = l + 1 == Lc ? 1 : x->gamma;
+    for (int v = 0; v < visits; ++v) CKS(enqueue_cycle<T, ORDER>(x, l + 1, v == 0));
+    dispatch_bc(x->cfg.bc, [&](auto B) {
+        k_prolong_add<T, decltype(B)::value><<<grid_for(C.N, 1 << 24, x->threads), x->threads, 0, x->stream>>>(
+            L.geo, C.geo, (const T *)C.cur(), (T *)L.cur(), C.split);
+    });
+    CK(cudaGetLastError());
+    return enqueue_sweeps<T, ORDER>(x, l, x->cfg.nu_post);
 }
+
+template <typename T, int ORDER>
+mg_status enqueue_vcycle(mg_ctx *x, bool first) { return enqueue_cycle<T, ORDER>(x, 0, first); }
 
 // FP64 residual pass 1 (pass A: q, div W; pass B: R and the integrability sums), then the
 // final reduction of the sums.

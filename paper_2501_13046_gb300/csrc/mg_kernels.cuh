@@ -37,7 +37,8 @@ struct Coef {
     T ih[3];    // 1/h
     T ih2[3];   // 1/h^2
     T dl;       // diagonal of the discrete Laplacian
-    T idW[3];   // 1 / diagonal of the momentum operator row i
+    T idW[3];   // omega / diagonal of the momentum operator row i (relaxation weight folded in)
+    T iom;      // 1 / omega: the psi-row update divides by (diagonal * iom)
 };
 
 template <typename T> struct Vec2;
@@ -366,7 +367,7 @@ __device__ __forceinline__ void smooth_cell(const Geo &g, const Coef<T> &cf, con
     T Je[4], ctr[4];
     if (interior) apply_J_split<T, ORDER, BC, true>(X, O, N, g, i, j, k, ca, cb, cf, Je, ctr);
     else apply_J_split<T, ORDER, BC, false>(X, O, N, g, i, j, k, ca, cb, cf, Je, ctr);
-    Y[q] = ctr[0] + (f[q] - Je[0]) / (ca * cf.dl + cb);
+    Y[q] = ctr[0] + (f[q] - Je[0]) / ((ca * cf.dl + cb) * cf.iom);
 #pragma unroll
     for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (f[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
 }
@@ -844,7 +845,7 @@ __global__ void __launch_bounds__(512) k_coarse_solve(Geo g, Coef<T> cf, const T
                     AccB<T, BC> a0{eA, &g, i, j, k}, a1{eA + N, &g, i, j, k}, a2{eA + 2 * N, &g, i, j, k},
                         a3{eA + 3 * N, &g, i, j, k};
                     apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
-                    eB[q] = ctr[0] + (fs[q] - Je[0]) / (cs[q] * cf.dl + cs[N + q]);
+                    eB[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * cf.dl + cs[N + q]) * cf.iom);
                     for (int a = 0; a < 3; ++a) eB[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
                 } else {
                     for (int a = 0; a < 4; ++a) eB[a * N + q] = eA[a * N + q];

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
                 a3{sm, ob, oh, pa, 3 * FE};
             T Je[4], ctr[4];
             apply_J<ORDER, T>(a0, a1, a2, a3, ca, cb, cf, Je, ctr);
-            Y[q] = ctr[0] + (fq[0] - Je[0]) / (ca * cf.dl + cb);
+            Y[q] = ctr[0] + (fq[0] - Je[0]) / ((ca * cf.dl + cb) * cf.iom);
 #pragma unroll
             for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (fq[1 + a] - Je[1 + a]) * cf.idW[a];
         }

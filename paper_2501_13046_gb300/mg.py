@@ -36,7 +36,7 @@ class mg_config(C.Structure):
         ("punct_m", C.c_double * 2), ("punct_x", (C.c_double * 3) * 2), ("tol", C.c_double), ("max_outer", C.c_int),
         ("nu_pre", C.c_int), ("nu_post", C.c_int), ("coarse_sweeps", C.c_int), ("use_graph", C.c_int),
         ("spin_limit", C.c_longlong), ("inner_cycles", C.c_int), ("block_threads", C.c_int),
-        ("smoother", C.c_int),
+        ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double),
     ]
 
 

@@ -41,7 +41,7 @@ def test_autotune_picks_a_converging_candidate(mg, tmp_path, precision):
     assert ms > 0
     assert best.inner_cycles in ((1, 2, 3) if prec == mg.MG_MIXED else (1, 2))
     assert best.nu_pre == best.nu_post and best.nu_pre in (1, 2, 3)
-    assert best.block_threads in (128, 256)
+    assert best.omega in (1.0, 1.15, 1.3)
     assert best.tol == base.tol and list(best.n) == list(base.n)
     # the cache file holds this shape's entry
     lines = cache.read_text().split("\n")
@@ -64,8 +64,7 @@ def test_autotune_picks_a_converging_candidate(mg, tmp_path, precision):
 
     # a second call is a cache hit: same choice, same recorded time
     best2, ms2 = mg.mg_autotune(base, *src, stream=sp, cache_path=str(cache))
-    assert (best2.inner_cycles, best2.nu_pre, best2.block_threads) == \
-           (best.inner_cycles, best.nu_pre, best.block_threads)
+    assert (best2.inner_cycles, best2.nu_pre, best2.omega) == (best.inner_cycles, best.nu_pre, best.omega)
     assert ms2 == ms
 
 
@@ -74,8 +73,9 @@ def test_autotune_reads_cache_file(mg, tmp_path):
     p = fields.modes_periodic(n=24)
     base = mg.config_for(p, mg.MG_MIXED, tol=1e-10, max_outer=40)
     cache = tmp_path / "tune.txt"
-    cache.write_text("24 24 24 4 0 %d %d 3 1 128 1.5\n" % (mg.MG_MIXED, base.k_mode))
+    cache.write_text("24 24 24 4 0 %d %d 3 1 128 1.15 1.5\n" % (mg.MG_MIXED, base.k_mode))
     best, ms = mg.mg_autotune(base, *sources(p), stream=torch.cuda.current_stream().cuda_stream,
                               cache_path=str(cache))
     assert (best.inner_cycles, best.nu_pre, best.nu_post, best.block_threads) == (3, 1, 1, 128)
+    assert best.omega == 1.15
     assert ms == 1.5
