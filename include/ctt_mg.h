@@ -116,7 +116,9 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
  * (non-conformally-flat data is listed as forthcoming in the paper's feature list). */
 mg_status mg_set_conformal_metric(struct mg_ctx *ctx, const double *gt, int on_device);
 
-/* Matter sources: rho = rho0 + psi^-4 rho2; S_i lower-index momentum density.  rho2 may be NULL (0). */
+/* Matter sources: rho = rho0 + psi^-4 rho2; S_i lower-index momentum density.  rho2 may be NULL (0).
+ * Returns MG_ERR_INVALID_ARG (and leaves the context without sources) if any value is NaN or
+ * infinite; the check runs on the device after the copy, and the call returns once it is done. */
 mg_status mg_set_sources(struct mg_ctx *ctx, const double *rho0, const double *rho2, const double *Sx,
                          const double *Sy, const double *Sz, int on_device);
 

@@ -67,7 +67,8 @@ mg_status validate(const mg_config *c)
 }
 
 struct Layout {
-    size_t X, SRC, R, D, partial, scal, total;
+    size_t X, SRC, R, D, partial, scal, Gpsi, GW, gj, total;
+    int dense, mpsi, mw;
     std::vector<size_t> eA, eB, f, c;
 };
 
@@ -92,6 +93,20 @@ Layout layout_for(const mg_config *c)
     }
     L.partial = take((size_t)kRedBlocks * 8 * 8);
     L.scal = take(sizeof(Scalars));
+    {
+        const int periodic = c->bc == MG_BC_PERIODIC;
+        int nc[3];
+        for (int a = 0; a < 3; ++a) nc[a] = c->n[a] >> (lv - 1);
+        const int Nc = nc[0] * nc[1] * nc[2];
+        L.dense = lv > 1 && dense_eligible(nc, periodic);
+        L.mpsi = dense_m_psi(Nc, periodic);
+        L.mw = dense_m_w(Nc, periodic);
+        if (L.dense) {
+            L.Gpsi = take((size_t)L.mpsi * L.mpsi * tb);
+            L.GW = take((size_t)L.mw * L.mw * tb);
+            L.gj = take(gj_scratch_elems(L.mw) * 8);
+        }
+    }
     L.total = off;
     return L;
 }
@@ -214,13 +229,6 @@ mg_status leave(mg_ctx *x, mg_status st)
     return st;
 }
 
-bool host_finite(const double *p, size_t n)
-{
-    for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(p[i])) return false;
-    return true;
-}
-
 }  // namespace
 
 // ====================================================================== C ABI
@@ -295,6 +303,14 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         x->SRC = (double *)(b + lay.SRC);
         x->R = (double *)(b + lay.R);
         x->D = (double *)(b + lay.D);
+        x->dense = lay.dense;
+        x->mpsi = lay.mpsi;
+        x->mw = lay.mw;
+        if (lay.dense) {
+            x->Gpsi = b + lay.Gpsi;
+            x->GW = b + lay.GW;
+            x->gj = b + lay.gj;
+        }
         x->partial = (double *)(b + lay.partial);
         x->scal = (Scalars *)(b + lay.scal);
         for (int l = 0; l < x->nlev; ++l) {
@@ -362,6 +378,12 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         if ((st = enter(x)) != MG_OK) break;
         e = cudaMemsetAsync(x->ws, 0, lay.total, x->stream);
         if (e != cudaSuccess) { st = fail(MG_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e)); break; }
+        if (x->dense) {
+            const int O = cfg->order;
+            st = x->tbytes == 8 ? (O == 2 ? engine_dense_setup<double, 2>(x) : engine_dense_setup<double, 4>(x))
+                                : (O == 2 ? engine_dense_setup<float, 2>(x) : engine_dense_setup<float, 4>(x));
+            if (st != MG_OK) break;
+        }
         if ((st = leave(x, MG_OK)) != MG_OK) break;
     } while (0);
     if (st != MG_OK) {
@@ -395,16 +417,20 @@ static mg_status mg_set_sources_impl(mg_ctx *x, const double *rho0, const double
 {
     if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");
     if (!rho0 || !Sx || !Sy || !Sz) return fail(MG_ERR_INVALID_ARG, "rho0 and S must be given");
-    if (!on_device) {
-        const double *ptrs[5] = {rho0, rho2, Sx, Sy, Sz};
-        for (int a = 0; a < 5; ++a)
-            if (ptrs[a] && !host_finite(ptrs[a], x->N)) return fail(MG_ERR_INVALID_ARG, "non-finite source value");
-    }
+    x->have_sources = false;
     CKS(copy_in(x->SRC, rho0, x->N, on_device, x->stream));
     CKS(copy_in(x->SRC + x->N, rho2, x->N, on_device, x->stream));
     CKS(copy_in(x->SRC + 2 * x->N, Sx, x->N, on_device, x->stream));
     CKS(copy_in(x->SRC + 3 * x->N, Sy, x->N, on_device, x->stream));
     CKS(copy_in(x->SRC + 4 * x->N, Sz, x->N, on_device, x->stream));
+    // finiteness of the copied sources, checked on the device (host and device inputs alike)
+    CK(cudaMemsetAsync(&x->scal->nonfinite, 0, sizeof(unsigned int), x->stream));
+    k_flag_nonfinite<<<grid_for(5 * x->N, kRedBlocks), kThreads, 0, x->stream>>>(x->SRC, 5 * x->N, &x->scal->nonfinite);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&x->host_scal->nonfinite, &x->scal->nonfinite, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                       x->stream));
+    CK(cudaStreamSynchronize(x->stream));
+    if (x->host_scal->nonfinite) return fail(MG_ERR_INVALID_ARG, "non-finite source value");
     x->have_sources = true;
     return MG_OK;
 }

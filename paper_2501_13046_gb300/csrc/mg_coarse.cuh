@@ -1,0 +1,190 @@
+// mg_coarse.cuh -- coarsest-level solve by precomputed dense inverses.
+//
+// The coarsest grid of the hierarchy has at most a few hundred cells, so its two linear blocks
+// are solved exactly by multiplying with explicit inverses:
+//   psi row: a Lap + b (a, b: the restricted psi-row coefficients of the current outer iteration),
+//            re-inverted once per outer iteration;
+//   W rows:  Lap W_i + (1/3) (D_ii W_i + sum_{j != i} D_i D_j W_j), which does not depend on the
+//            state, inverted once when the context is created.
+// On periodic boxes both operators annihilate constants; each is bordered by one Lagrange
+// multiplier per field with the constraint <e> = 0, so the inverse maps any right-hand side to
+// the zero-mean solution of the projected problem.  The matrices are assembled from the same
+// stencil code as the smoother (boundary values folded into the columns) and inverted in one
+// CTA; a V-cycle then spends one small matrix-vector kernel on its coarsest level.
+#pragma once
+#include "mg_kernels.cuh"
+
+namespace ctt {
+
+constexpr int kDenseMaxW = 400;   // largest bordered W system (3 N + 3) solved densely
+
+__host__ __device__ inline int dense_m_psi(int N, int periodic) { return N + (periodic ? 1 : 0); }
+__host__ __device__ inline int dense_m_w(int N, int periodic) { return 3 * N + (periodic ? 3 : 0); }
+
+// [A | I] of the psi row, row stride 2m (global scratch, zeroed here).
+template <typename T, typename C, int ORDER, int BC>
+__global__ void __launch_bounds__(512) k_dense_psi_assemble(Geo g, Coef<T> cf, const T *__restrict__ ab,
+                                                            C *__restrict__ aug, int periodic)
+{
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const int m = dense_m_psi(N, periodic), w2 = 2 * m;
+    for (int t = threadIdx.x; t < m * w2; t += blockDim.x) aug[t] = 0;
+    __syncthreads();
+    const double w1 = ORDER == 2 ? 1.0 : 16.0 / 12.0;
+    const double wb = ORDER == 2 ? 0.0 : -1.0 / 12.0;
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        const int i = p % g.n[0], j = (p / g.n[0]) % g.n[1], k = p / (g.n[0] * g.n[1]);
+        const double a = (double)ab[p], b = (double)ab[N + p];
+        C *row = aug + (size_t)p * w2;
+        row[p] += (C)(a * (double)cf.dl + b);
+        for (int ax = 0; ax < 3; ++ax)
+            for (int s = -2; s <= 2; ++s) {
+                if (s == 0 || (ORDER == 2 && (s == 2 || s == -2))) continue;
+                const double w = a * ((s == 1 || s == -1) ? w1 : wb) * (double)cf.ih2[ax];
+                int c[3] = {i, j, k};
+                c[ax] += s;
+                if (BC == BC_PERIODIC) {
+                    c[ax] += c[ax] < 0 ? g.n[ax] : 0;
+                    c[ax] -= c[ax] >= g.n[ax] ? g.n[ax] : 0;
+                    row[c[0] + g.n[0] * (c[1] + g.n[1] * c[2])] += (C)w;
+                } else {
+                    const int bc[3] = {min(max(c[0], 0), g.n[0] - 1), min(max(c[1], 0), g.n[1] - 1),
+                                       min(max(c[2], 0), g.n[2] - 1)};
+                    double ratio = 1.0;
+                    if (bc[ax] != c[ax]) {
+                        const double xb = cellx(g, 0, bc[0]), yb = cellx(g, 1, bc[1]), zb = cellx(g, 2, bc[2]);
+                        const double xg = cellx(g, 0, c[0]), yg = cellx(g, 1, c[1]), zg = cellx(g, 2, c[2]);
+                        ratio = sqrt(xb * xb + yb * yb + zb * zb) / sqrt(xg * xg + yg * yg + zg * zg);
+                    }
+                    row[bc[0] + g.n[0] * (bc[1] + g.n[1] * bc[2])] += (C)(w * ratio);
+                }
+            }
+        if (periodic) {
+            row[N] = 1;
+            aug[(size_t)N * w2 + p] = 1;
+        }
+    }
+    for (int r = threadIdx.x; r < m; r += blockDim.x) aug[(size_t)r * w2 + m + r] = 1;
+}
+
+// [A | I] of the W rows: one CTA per column (field B, cell q) applies the operator to the unit
+// vector e_(B,q) held in shared memory (4 N T) and writes the column; one more CTA (index 3N)
+// writes the multiplier columns and the identity entries of the constraint rows.  aug must be
+// zero beforehand.
+template <typename T, typename C, int ORDER, int BC>
+__global__ void __launch_bounds__(256) k_dense_w_assemble(Geo g, Coef<T> cf, C *__restrict__ aug, int periodic)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *e = reinterpret_cast<T *>(smem_raw);
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const int m = dense_m_w(N, periodic), w2 = 2 * m;
+    const int col = blockIdx.x;
+    if (col >= 3 * N) {   // multiplier columns and their identity entries
+        if (periodic && threadIdx.x < 3) {
+            const int B = threadIdx.x;
+            aug[(size_t)(3 * N + B) * w2 + m + 3 * N + B] = 1;
+        }
+        return;
+    }
+    const int B = col / N, q = col % N;
+    for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) e[t] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) e[(1 + B) * N + q] = 1;
+    __syncthreads();
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        const int i = p % g.n[0], j = (p / g.n[0]) % g.n[1], k = p / (g.n[0] * g.n[1]);
+        AccB<T, BC> a0{e, &g, i, j, k}, a1{e + N, &g, i, j, k}, a2{e + 2 * N, &g, i, j, k}, a3{e + 3 * N, &g, i, j, k};
+        T Je[4], ctr[4];
+        apply_J<ORDER, T>(a0, a1, a2, a3, (T)1, (T)0, cf, Je, ctr);
+        for (int A = 0; A < 3; ++A) aug[(size_t)(A * N + p) * w2 + col] = (C)Je[1 + A];
+    }
+    if (threadIdx.x == 0) {
+        if (periodic) {
+            aug[(size_t)(3 * N + B) * w2 + col] = 1;   // constraint row of field B: sum of its cells
+            aug[(size_t)col * w2 + 3 * N + B] = 1;     // multiplier column of field B
+        }
+        aug[(size_t)col * w2 + m + col] = 1;           // identity block
+    }
+}
+
+// Gauss-Jordan elimination with partial pivoting of the m x 2m augmented matrix [A | I] (row
+// stride 2m) into [I | A^-1]; writes A^-1 (row-major, m x m) as T.  One CTA.  Scratch after the
+// matrix: pivot row (2m), old row k (2m), column factors (m), gj_scratch_elems(m) in all; with
+// smem_ok it is all copied into dynamic shared memory first.  Per column: pivot search (one
+// warp), staging of the scaled pivot row, the old row k and the factors, then one elimination
+// pass in which row k takes the pivot row and the pivot row's slot takes the old row k (the
+// swap).  A zero pivot yields non-finite entries, which the outer iteration reports as
+// divergence.
+__host__ __device__ inline size_t gj_scratch_elems(int m) { return (size_t)2 * m * m + 5 * (size_t)m; }
+
+template <typename C, typename T>
+__global__ void __launch_bounds__(1024) k_gauss_jordan(C *__restrict__ gaug, int m, int smem_ok, T *__restrict__ inv)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int w2 = 2 * m, tid = threadIdx.x, bs = blockDim.x;
+    C *A = smem_ok ? reinterpret_cast<C *>(smem_raw) : gaug;
+    C *prow = A + (size_t)m * w2, *krow = prow + w2, *fct = krow + w2;
+    __shared__ int piv;
+    if (smem_ok)
+        for (int t = tid; t < m * w2; t += bs) A[t] = gaug[t];
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        if (tid < 32) {
+            C best = -1;
+            int bi = m;
+            for (int i = k + tid; i < m; i += 32) {
+                const C v = fabs(A[(size_t)i * w2 + k]);
+                if (v > best) { best = v; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const C ov = __shfl_down_sync(0xffffffffu, best, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (tid == 0) piv = bi;
+        }
+        __syncthreads();
+        const int pr = piv < m ? piv : k;   // an all-NaN column leaves the rows in place
+        const C ip = (C)1 / A[(size_t)pr * w2 + k];
+        for (int j = tid; j < w2; j += bs) {
+            prow[j] = A[(size_t)pr * w2 + j] * ip;
+            krow[j] = A[(size_t)k * w2 + j];
+        }
+        for (int i = tid; i < m; i += bs) fct[i] = A[(size_t)(i == pr ? k : i) * w2 + k];
+        __syncthreads();
+        for (int t = tid; t < m * w2; t += bs) {
+            const int i = t / w2, j = t - i * w2;
+            if (i == k) A[t] = prow[j];
+            else if (i == pr) A[t] = krow[j] - fct[i] * prow[j];
+            else A[t] -= fct[i] * prow[j];
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < m * m; t += bs) {
+        const int i = t / m, j = t - i * m;
+        inv[t] = (T)A[(size_t)i * w2 + m + j];
+    }
+}
+
+// Coarsest-level correction: e_psi = Gpsi[0:N, 0:N] f_psi, e_W = GW[0:3N, 0:3N] f_W (the
+// bordered rows and columns belong to the multipliers; their right-hand side is zero).  One
+// warp per output row; FP32 rows accumulate in FP32, FP64 rows in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_apply(const T *__restrict__ Gpsi, int mpsi, const T *__restrict__ GW,
+                                                     int mw, const T *__restrict__ f, T *__restrict__ e, int N)
+{
+    const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (row >= 4 * N) return;
+    T acc = 0;
+    if (row < N) {
+        const T *g = Gpsi + (size_t)row * mpsi;
+        for (int j = lane; j < N; j += 32) acc = fma(g[j], f[j], acc);
+    } else {
+        const T *g = GW + (size_t)(row - N) * mw;
+        for (int j = lane; j < 3 * N; j += 32) acc = fma(g[j], f[N + j], acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) e[row] = acc;
+}
+
+}  // namespace ctt

@@ -15,6 +15,7 @@
 #include "mg_kernels.cuh"
 #include "mg_tile.cuh"
 #include "mg_outer.cuh"
+#include "mg_coarse.cuh"
 
 namespace ctt {
 
@@ -153,6 +154,12 @@ inline Regions outer_regions(const Geo &g, int order, int *grid)
     return r;
 }
 
+// Dense coarsest-level solve: available when the bordered W system has at most kDenseMaxW rows.
+inline bool dense_eligible(const int nc[3], int periodic)
+{
+    return dense_m_w(nc[0] * nc[1] * nc[2], periodic) <= kDenseMaxW;
+}
+
 inline size_t coarse_smem_bytes(size_t Nc, size_t tb) { return 14 * Nc * tb; }
 constexpr size_t kMaxCoarseSmem = 200 * 1024;
 inline size_t direct_smem_bytes(size_t Nc, int periodic, size_t tb)
@@ -183,6 +190,11 @@ struct mg_ctx {
     double *SRC = nullptr;   // 5N: rho0, rho2, Sx, Sy, Sz
     double *R = nullptr;     // 5N: outer pass-1 output
     double *D = nullptr;     // 4N: q_0, q_1, q_2, div W of the FP64 residual's pass A
+    int dense = 0;           // 1: the coarsest level is solved with the dense inverses below
+    int mpsi = 0, mw = 0;    // orders of the (bordered) psi and W systems
+    void *Gpsi = nullptr;    // mpsi^2 T: inverse of the psi row (per outer iteration)
+    void *GW = nullptr;      // mw^2 T: inverse of the W rows (once, at creation)
+    void *gj = nullptr;      // Gauss-Jordan scratch, gj_scratch_elems(mw) doubles
     double *partial = nullptr;
     ctt::Scalars *scal = nullptr;
     ctt::Scalars *host_scal = nullptr;   // pinned
@@ -200,5 +212,6 @@ template <typename T, int ORDER> mg_status engine_iteration(mg_ctx *x);
 template <typename T, int ORDER> mg_status engine_residual(mg_ctx *x, double *HM);
 template <typename T, int ORDER> mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms);
 template <typename T, int ORDER> mg_status engine_prepare(mg_ctx *x);
+template <typename T, int ORDER> mg_status engine_dense_setup(mg_ctx *x);
 mg_status engine_project_gauge(mg_ctx *x);
 }  // namespace ctt

@@ -96,6 +96,13 @@ mg_status enqueue_coarse(mg_ctx *x, int l)
     LevelBufs &L = x->lev[l];
     const size_t tb = sizeof(T);
     const int periodic = x->cfg.bc == MG_BC_PERIODIC;
+    if (x->dense) {   // exact coarse correction by the precomputed inverses
+        const int N = (int)L.N;
+        k_dense_apply<T><<<(4 * N * 32 + 255) / 256, 256, 0, x->stream>>>(
+            (const T *)x->Gpsi, x->mpsi, (const T *)x->GW, x->mw, (const T *)L.f, (T *)L.eA, N);
+        CK(cudaGetLastError());
+        return MG_OK;
+    }
     Coef<T> cf = make_coef<T>(L.geo, x->cfg.order, x->omega);
     const size_t smem = coarse_smem_bytes(L.N, tb);
     if (smem <= kMaxCoarseSmem) {
@@ -197,6 +204,53 @@ mg_status enqueue_residual(mg_ctx *x, double *HM)
     return MG_OK;
 }
 
+// Shared memory of a one-CTA Gauss-Jordan inversion of order m in type C (0: the matrix stays in
+// global memory, which the kernel then uses in place).
+template <typename C>
+inline size_t gj_smem(int m)
+{
+    const size_t b = gj_scratch_elems(m) * sizeof(C);
+    return b <= kMaxCoarseSmem ? b : 0;
+}
+
+// Inverse of the coarsest psi row for this outer iteration (its coefficients were just restricted).
+template <typename T, int ORDER>
+mg_status enqueue_dense_psi_inverse(mg_ctx *x)
+{
+    LevelBufs &C = x->lev[x->nlev - 1];
+    const int periodic = x->cfg.bc == MG_BC_PERIODIC;
+    Coef<T> cf = make_coef<T>(C.geo, x->cfg.order);
+    const size_t sm = gj_smem<T>(x->mpsi);
+    dispatch_bc(x->cfg.bc, [&](auto B) {
+        k_dense_psi_assemble<T, T, ORDER, decltype(B)::value><<<1, 512, 0, x->stream>>>(C.geo, cf, (const T *)C.c,
+                                                                                      (T *)x->gj, periodic);
+    });
+    k_gauss_jordan<T, T><<<1, 1024, sm, x->stream>>>((T *)x->gj, x->mpsi, sm > 0, (T *)x->Gpsi);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// Inverse of the coarsest W rows, once per context (FP64 elimination, stored as T).
+template <typename T, int ORDER>
+mg_status engine_dense_setup(mg_ctx *x)
+{
+    LevelBufs &C = x->lev[x->nlev - 1];
+    const int periodic = x->cfg.bc == MG_BC_PERIODIC;
+    const int N = (int)C.N;
+    Coef<double> cf = make_coef<double>(C.geo, x->cfg.order);
+    CK(cudaMemsetAsync(x->gj, 0, gj_scratch_elems(x->mw) * sizeof(double), x->stream));
+    dispatch_bc(x->cfg.bc, [&](auto B) {
+        k_dense_w_assemble<double, double, ORDER, decltype(B)::value><<<3 * N + 1, 256, 4 * N * sizeof(double),
+                                                                        x->stream>>>(C.geo, cf, (double *)x->gj,
+                                                                                     periodic);
+    });
+    const size_t sm = gj_smem<double>(x->mw);
+    k_gauss_jordan<double, T><<<1, 1024, sm, x->stream>>>((double *)x->gj, x->mw, sm > 0, (T *)x->GW);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(x->stream));
+    return MG_OK;
+}
+
 template <typename T, int ORDER>
 mg_status enqueue_iteration(mg_ctx *x)
 {
@@ -206,6 +260,7 @@ mg_status enqueue_iteration(mg_ctx *x)
                                                                        (const T *)x->lev[l - 1].c, (T *)C.c, 2, C.split);
     }
     CK(cudaGetLastError());
+    if (x->dense) CKS(enqueue_dense_psi_inverse<T, ORDER>(x));
     for (int cyc = 0; cyc < x->cfg.inner_cycles; ++cyc) CKS(enqueue_vcycle<T, ORDER>(x, cyc == 0));
     int periodic = x->cfg.bc == MG_BC_PERIODIC;
     LevelBufs &L0 = x->lev[0];
@@ -234,6 +289,11 @@ mg_status engine_prepare(mg_ctx *x)
             cudaFuncSetAttribute(k_coarse_psi_direct<T, ORDER, decltype(B)::value>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxCoarseSmem) != cudaSuccess)
             st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(coarse kernels)");
+        if (cudaFuncSetAttribute(k_gauss_jordan<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMaxCoarseSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(k_gauss_jordan<double, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMaxCoarseSmem) != cudaSuccess)
+            st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(k_gauss_jordan)");
         if (cudaFuncSetAttribute(k_smooth_tile<T, ORDER, decltype(B)::value>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_smem_bytes<T, ORDER>()) != cudaSuccess)

@@ -6,4 +6,5 @@ template mg_status engine_iteration<float, 4>(mg_ctx *);
 template mg_status engine_residual<float, 4>(mg_ctx *, double *);
 template mg_status engine_time_kernel<float, 4>(mg_ctx *, int, int, float *);
 template mg_status engine_prepare<float, 4>(mg_ctx *);
+template mg_status engine_dense_setup<float, 4>(mg_ctx *);
 }  // namespace ctt

@@ -6,6 +6,7 @@ template mg_status engine_iteration<double, 2>(mg_ctx *);
 template mg_status engine_residual<double, 2>(mg_ctx *, double *);
 template mg_status engine_time_kernel<double, 2>(mg_ctx *, int, int, float *);
 template mg_status engine_prepare<double, 2>(mg_ctx *);
+template mg_status engine_dense_setup<double, 2>(mg_ctx *);
 
 mg_status engine_project_gauge(mg_ctx *x)
 {

@@ -6,4 +6,5 @@ template mg_status engine_iteration<double, 4>(mg_ctx *);
 template mg_status engine_residual<double, 4>(mg_ctx *, double *);
 template mg_status engine_time_kernel<double, 4>(mg_ctx *, int, int, float *);
 template mg_status engine_prepare<double, 4>(mg_ctx *);
+template mg_status engine_dense_setup<double, 4>(mg_ctx *);
 }  // namespace ctt

@@ -589,9 +589,19 @@ struct Scalars {
     double norms[4];
     double emean[4];
     double sums[8];
-    unsigned int err;   // nonzero: a bounded wait of a pipelined kernel gave up (MG_ERR_TIMEOUT)
-    unsigned int pad;
+    unsigned int err;         // nonzero: a bounded wait of a pipelined kernel gave up (MG_ERR_TIMEOUT)
+    unsigned int nonfinite;   // nonzero: a source value is NaN or infinite (set by k_flag_nonfinite)
 };
+
+// Flags any NaN or infinity among n doubles (exponent field all ones; integer test, no FP64 op).
+static __global__ void __launch_bounds__(256) k_flag_nonfinite(const double *__restrict__ a, size_t n,
+                                                               unsigned int *__restrict__ flag)
+{
+    bool bad = false;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        bad |= ((__double_as_longlong(a[i]) >> 52) & 0x7ff) == 0x7ff;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
 
 // Final single-block reduction of per-block partial sums: partial[b * NV + a].
 template <int NV>

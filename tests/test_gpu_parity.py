@@ -215,6 +215,19 @@ def test_tiled_and_global_smoother_agree(mg, case, precision):
         assert rel(W0, W1) < 1e-10
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_dense_and_iterative_coarse_solves_agree(mg, precision):
+    """The coarsest level is solved by precomputed dense inverses when it is small (4^3 here) and
+    by red-black sweeps plus the direct psi elimination when it is larger (8^3 with 3 levels):
+    both hierarchies converge to the same root."""
+    p = CASES["modes_periodic_o4_n32"]()
+    prec = mg.MG_FP64 if precision == "fp64" else mg.MG_MIXED
+    st0, i0, u0, W0 = gpu_solve(mg, p, prec)
+    st1, i1, u1, W1 = gpu_solve(mg, p, prec, levels=3)
+    assert st0 == mg.MG_OK and st1 == mg.MG_OK
+    assert rel(1.0 + u0, 1.0 + u1) < 1e-10 and rel(W0, W1) < 1e-10
+
+
 def test_graph_and_direct_launch_agree(mg):
     p = fields.puncture_shell(n=32, half=16.0)
     _, i1, u1, W1 = gpu_solve(mg, p, mg.MG_MIXED, use_graph=1)
@@ -236,6 +249,14 @@ def test_error_statuses(mg):
         with pytest.raises(mg.MGError) as e:
             mg.mg_set_sources(ctx, bad, p["rho2"], *[np.ascontiguousarray(s) for s in p["S"]])
         assert e.value.status == mg.MG_ERR_INVALID_ARG
+        bad_dev = [dev(a) for a in (p["rho0"], p["rho2"], *p["S"])]
+        bad_dev[4][0, 0, 1] = float("inf")            # device inputs are checked the same way
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_set_sources(ctx, *bad_dev)
+        assert e.value.status == mg.MG_ERR_INVALID_ARG
+        with pytest.raises(mg.MGError) as e:           # a rejected call leaves no sources behind
+            mg.mg_solve(ctx)
+        assert e.value.status == mg.MG_ERR_STATE
         gt = np.zeros((6,) + p["rho0"].shape)
         gt[0] = gt[3] = gt[5] = 1.0
         mg.mg_set_conformal_metric(ctx, gt)          # flat: accepted
