@@ -353,6 +353,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
                     break;
                 }
                 L.tg = tile_grid(L.geo, x->sms, x->tbytes == 4 ? 2 : 1);
+                L.tgr = tile_grid(L.geo, x->sms, x->tbytes == 4 ? 2 : 1, true);
                 L.tiled = 1;
             }
             if (st != MG_OK) break;

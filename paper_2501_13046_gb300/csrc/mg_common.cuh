@@ -67,8 +67,8 @@ struct LevelBufs {
     void *eA, *eB, *f, *c;   // T arrays: 4N, 4N, 4N, 2N (c holds the psi-row coefficients a, b)
     int split;               // 1: colour-split storage (every level above the coarsest), 0: plain
     int curB;                // enqueue-time bookkeeping: 1 when eB holds the current correction
-    int tiled;               // 1: colour passes run the TMA-tiled kernel (tensor maps below)
-    TileGrid tg;
+    int tiled;               // 1: colour passes and the restriction run the TMA-tiled kernels
+    TileGrid tg, tgr;        // launch shapes of the colour pass and of the residual + restriction
     CUtensorMap tmA, tmB;    // 5-D maps of eA, eB: (pair, row, plane, field, colour half)
     void *cur() const { return curB ? eB : eA; }
     void *alt() const { return curB ? eA : eB; }
@@ -82,13 +82,51 @@ inline bool tile_eligible(const Geo &g, int split)
     return split && g.n[0] % 8 == 0 && g.n[1] % 8 == 0 && g.n[0] >= 16 && g.n[1] >= 16 && g.n[2] >= 8;
 }
 
-inline TileGrid tile_grid(const Geo &g, int sms, int ctas_per_sm)
+// even: chunks of an even number of planes starting at even z (the restriction pairs planes)
+inline TileGrid tile_grid(const Geo &g, int sms, int ctas_per_sm, bool even = false)
 {
     TileGrid t;
     t.ntx = (g.n[0] / 2 + kTileP - 1) / kTileP;
     t.nty = g.n[1] / kTileY;
     int chunks = std::max(1, sms * ctas_per_sm / (t.ntx * t.nty));
     t.zc = std::max(2, (g.n[2] + chunks - 1) / chunks);
+    if (even) t.zc += t.zc & 1;
+    return t;
+}
+
+// Folded inner-operator weights of a level (the discrete operator of apply_J).
+template <typename T>
+TileCoef<T> make_tile_coef(const Geo &g, int order, double omega = 1.0)
+{
+    TileCoef<T> t;
+    const double c1 = order == 2 ? 0.5 : 8.0 / 12.0, c2 = order == 2 ? 0.0 : 1.0 / 12.0;
+    const double k1 = order == 2 ? 1.0 : 16.0 / 12.0, k2 = order == 2 ? 0.0 : -1.0 / 12.0;
+    const double k0 = order == 2 ? -2.0 : -30.0 / 12.0;
+    double lk0 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double ih2 = 1.0 / (g.h[a] * g.h[a]);
+        t.lk1[a] = (T)(k1 * ih2);
+        t.lnk2[a] = (T)(k2 * ih2);
+        lk0 += k0 * ih2;
+    }
+    t.lk0 = (T)lk0;
+    t.dl = (T)lk0;
+    for (int A = 0; A < 3; ++A) {
+        const double ihA2 = 1.0 / (g.h[A] * g.h[A]);
+        const double m0 = lk0 + k0 * ihA2 / 3.0;
+        t.mk0[A] = (T)m0;
+        for (int a = 0; a < 3; ++a) {
+            const double ih2 = 1.0 / (g.h[a] * g.h[a]), s = a == A ? 4.0 / 3.0 : 1.0;
+            t.mk1[A][a] = (T)(s * k1 * ih2);
+            t.mnk2[A][a] = (T)(s * k2 * ih2);
+            const double x = 1.0 / (3.0 * g.h[A] * g.h[a]);
+            t.x11[A][a] = (T)(c1 * c1 * x);
+            t.x12[A][a] = (T)(-c1 * c2 * x);
+            t.x22[A][a] = (T)(c2 * c2 * x);
+        }
+        t.idW[A] = (T)(omega / m0);
+    }
+    t.iom = (T)(1.0 / omega);
     return t;
 }
 

@@ -46,16 +46,45 @@ void dispatch_bc(int bc, Fn &&fn)
 
 // One colour pass of the TMA-tiled kernel (X: old values, O: other colour, Y: output).
 template <typename T, int ORDER>
-mg_status launch_tile(mg_ctx *x, const LevelBufs &L, const Coef<T> &cf, const CUtensorMap &mX,
+mg_status launch_tile(mg_ctx *x, const LevelBufs &L, const TileCoef<T> &tc, const CUtensorMap &mX,
                       const CUtensorMap &mO, const T *X, const T *O, T *Y, int colour)
 {
     const int grid = tile_ctas(L.geo, L.tg);
     const size_t smem = tile_smem_bytes<T, ORDER>();
     dispatch_bc(x->cfg.bc, [&](auto B) {
-        k_smooth_tile<T, ORDER, decltype(B)::value><<<grid, kTileThreads, smem, x->stream>>>(
-            mX, mO, L.geo, cf, X, O, Y, (const T *)L.f, (const T *)L.c, colour, L.tg, &x->scal->err,
-            (long long)x->cfg.spin_limit);
+        constexpr int BC = decltype(B)::value;
+        auto k = colour ? k_smooth_tile<T, ORDER, BC, 1> : k_smooth_tile<T, ORDER, BC, 0>;
+        k<<<grid, kTileThreads, smem, x->stream>>>(mX, mO, L.geo, tc, X, O, Y, (const T *)L.f, (const T *)L.c, L.tg,
+                                                   &x->scal->err, (long long)x->cfg.spin_limit);
     });
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// Residual of level l's current correction, restricted to the right-hand side of level l + 1.
+template <typename T, int ORDER>
+mg_status enqueue_restrict(mg_ctx *x, int l)
+{
+    LevelBufs &L = x->lev[l];
+    LevelBufs &C = x->lev[l + 1];
+    if (L.tiled) {
+        const TileCoef<T> tc = make_tile_coef<T>(L.geo, x->cfg.order);
+        const int grid = tile_ctas(L.geo, L.tgr);
+        const size_t smem = tile_restrict_smem_bytes<T, ORDER>();
+        dispatch_bc(x->cfg.bc, [&](auto B) {
+            k_restrict_tile<T, ORDER, decltype(B)::value><<<grid, kTileThreads, smem, x->stream>>>(
+                L.tm_cur(), L.geo, tc, C.geo, (const T *)L.cur(), (const T *)L.f, (const T *)L.c, (T *)C.f, C.split,
+                L.tgr, &x->scal->err, (long long)x->cfg.spin_limit);
+        });
+    } else {
+        Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
+        int rgrid = 0;
+        Regions rr = restrict_regions(C.geo, &rgrid, x->threads);
+        dispatch_bc(x->cfg.bc, [&](auto B) {
+            k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, x->threads, 0, x->stream>>>(
+                L.geo, cf, C.geo, (const T *)L.cur(), (const T *)L.f, (const T *)L.c, (T *)C.f, C.split, rr);
+        });
+    }
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -67,6 +96,7 @@ mg_status enqueue_sweeps(mg_ctx *x, int l, int sweeps)
 {
     LevelBufs &L = x->lev[l];
     Coef<T> cf = make_coef<T>(L.geo, x->cfg.order, x->omega);
+    const TileCoef<T> tc = make_tile_coef<T>(L.geo, x->cfg.order, x->omega);
     int grid = 0;
     Regions rg = smooth_regions(L.geo, ORDER, &grid, x->threads);
     for (int s = 0; s < sweeps; ++s) {
@@ -76,7 +106,7 @@ mg_status enqueue_sweeps(mg_ctx *x, int l, int sweeps)
             const T *O = colour == 0 ? X : Y;
             if (L.tiled) {
                 const CUtensorMap &mO = colour == 0 ? L.tm_cur() : L.tm_alt();
-                CKS(launch_tile<T, ORDER>(x, L, cf, L.tm_cur(), mO, X, O, Y, colour));
+                CKS(launch_tile<T, ORDER>(x, L, tc, L.tm_cur(), mO, X, O, Y, colour));
             } else {
                 dispatch_bc(x->cfg.bc, [&](auto B) {
                     k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, x->threads, 0, x->stream>>>(
@@ -144,14 +174,7 @@ mg_status enqueue_cycle(mg_ctx *x, int l, bool zero)
     }
     CKS(enqueue_sweeps<T, ORDER>(x, l, x->cfg.nu_pre));
     LevelBufs &C = x->lev[l + 1];
-    Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
-    int rgrid = 0;
-    Regions rr = restrict_regions(C.geo, &rgrid, x->threads);
-    dispatch_bc(x->cfg.bc, [&](auto B) {
-        k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, x->threads, 0, x->stream>>>(
-            L.geo, cf, C.geo, (const T *)L.cur(), (const T *)L.f, (const T *)L.c, (T *)C.f, C.split, rr);
-    });
-    CK(cudaGetLastError());
+    CKS(enqueue_restrict<T, ORDER>(x, l));
     const int visits = l + 1 == Lc ? 1 : x->gamma;
     for (int v = 0; v < visits; ++v) CKS(enqueue_cycle<T, ORDER>(x, l + 1, v == 0));
     dispatch_bc(x->cfg.bc, [&](auto B) {
@@ -294,10 +317,14 @@ mg_status engine_prepare(mg_ctx *x)
             cudaFuncSetAttribute(k_gauss_jordan<double, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kMaxCoarseSmem) != cudaSuccess)
             st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(k_gauss_jordan)");
-        if (cudaFuncSetAttribute(k_smooth_tile<T, ORDER, decltype(B)::value>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile_smem_bytes<T, ORDER>()) != cudaSuccess)
-            st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(k_smooth_tile)");
+        constexpr int BC = decltype(B)::value;
+        if (cudaFuncSetAttribute(k_smooth_tile<T, ORDER, BC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<T, ORDER>()) != cudaSuccess ||
+            cudaFuncSetAttribute(k_smooth_tile<T, ORDER, BC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<T, ORDER>()) != cudaSuccess ||
+            cudaFuncSetAttribute(k_restrict_tile<T, ORDER, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_restrict_smem_bytes<T, ORDER>()) != cudaSuccess)
+            st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(tiled kernels)");
     });
     return st;
 }
@@ -313,7 +340,8 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
         if (which == 0) {
             if (!L.split) return fail(MG_ERR_INVALID_ARG, "one-level hierarchy has no global smoother");
             if (L.tiled) {
-                CKS(launch_tile<T, ORDER>(x, L, cf, L.tmA, L.tmA, (const T *)L.eA, (const T *)L.eA, (T *)L.eB, r & 1));
+                const TileCoef<T> tc = make_tile_coef<T>(L.geo, x->cfg.order, x->omega);
+                CKS(launch_tile<T, ORDER>(x, L, tc, L.tmA, L.tmA, (const T *)L.eA, (const T *)L.eA, (T *)L.eB, r & 1));
                 continue;
             }
             int grid = 0;
@@ -324,13 +352,10 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
             });
         } else if (which == 1) {
             if (x->nlev < 2) return fail(MG_ERR_INVALID_ARG, "one-level hierarchy has no restriction");
-            LevelBufs &Cl = x->lev[1];
-            int rgrid = 0;
-            Regions rr = restrict_regions(Cl.geo, &rgrid, x->threads);
-            dispatch_bc(x->cfg.bc, [&](auto B) {
-                k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, x->threads, 0, x->stream>>>(
-                    L.geo, cf, Cl.geo, (const T *)L.eA, (const T *)L.f, (const T *)L.c, (T *)Cl.f, Cl.split, rr);
-            });
+            const int keep = L.curB;
+            L.curB = 0;   // residual of eA
+            CKS(enqueue_restrict<T, ORDER>(x, 0));
+            L.curB = keep;
         } else {
             CKS(enqueue_outer_pass1<ORDER>(x));
         }

@@ -1,19 +1,23 @@
-// mg_tile.cuh -- shared-memory tiled red-black colour pass for colour-split levels.
+// mg_tile.cuh -- shared-memory tiled kernels of the colour-split levels: the red-black colour
+// pass of the smoother and the fused residual + restriction.
 //
 // A CTA owns a tile of 32 colour pairs (64 cells) in x by 8 rows in y and marches through a
 // chunk of z planes.  Each plane of the 4 correction fields (both colour halves, the tile plus
 // its stencil halo) is brought into a ring of shared-memory slots by two TMA tensor loads
-// (cp.async.bulk.tensor, one per colour half) completing on an mbarrier; the stencil of
-// apply_J then reads only shared memory.  Halo cells outside the box (periodic wrap, or the
-// Robin 1/r ghost value v(clamp(g)) |x_clamp| / |x_g|) are not addressable by the tensor
-// load, which fills them with zeros: the CTA fetches them with plain loads one plane ahead and
-// writes them over the zero fill once the plane's TMA has completed.  The arithmetic per cell
-// is that of k_smooth_colour (same operator, same update, same Jacobi-within-colour reads), so
-// both kernels compute the same iterate up to FP rounding order.
+// (cp.async.bulk.tensor, one per colour half) completing on an mbarrier; the stencils then read
+// only shared memory.  Halo cells outside the box (periodic wrap, or the Robin 1/r ghost value
+// v(clamp(g)) |x_clamp| / |x_g|) are not addressable by the tensor load, which fills them with
+// zeros: the CTA fetches them with plain loads one plane ahead and writes them over the zero
+// fill once the plane's TMA has completed.  One barrier per plane orders everything: before it
+// the plane about to enter the stencil window is completed (TMA wait + halo), after it the slot
+// of the plane that left the window is refilled while the current plane is computed.
+//
+// The operator is that of apply_J (same discrete stencils and reads) with the grid spacing,
+// the 1/3 of the grad-div term and the tensor-product weights folded into per-level constants.
 //
 // Requirements (checked on the host): colour-split level, nx and ny multiples of 8 and >= 16,
-// nz >= 8, so every TMA x coordinate and stride is 16-byte aligned and no tile row is both
-// the first and the last of the box.
+// nz >= 8 (and even chunks for the restriction), so every TMA x coordinate and stride is
+// 16-byte aligned and no tile row is both the first and the last of the box.
 #pragma once
 #include <cuda.h>
 
@@ -38,10 +42,26 @@ template <typename T, int ORDER> __host__ __device__ constexpr size_t tile_smem_
 {
     return (size_t)tile_slots<ORDER>() * tile_slot_elems<ORDER>() * sizeof(T) + 8 * tile_slots<ORDER>();
 }
+// restriction: plus the staging of the odd rows' partial sums (4 warps x 32 lanes x 4 fields)
+template <typename T, int ORDER> __host__ __device__ constexpr size_t tile_restrict_smem_bytes()
+{
+    return tile_smem_bytes<T, ORDER>() + 16 + (size_t)(kTileY / 2) * 32 * 4 * sizeof(T);
+}
 
 struct TileGrid {
     int ntx, nty;   // tiles along x (pairs) and y (rows)
     int zc;         // planes per CTA
+};
+
+// Folded stencil weights of the inner operator on one level.
+template <typename T>
+struct TileCoef {
+    T lk0, lk1[3], lnk2[3];              // Lap f = lk0 f + sum_a lk1 (f+a + f-a) + lnk2 (f+2a + f-2a)
+    T mk0[3], mk1[3][3], mnk2[3][3];     // row A: Lap W_A + (1/3) D_AA W_A, same form
+    T x11[3][3], x12[3][3], x22[3][3];   // (1/3) D_A D_B f = x11 g11 + x12 (g12 + g21) + x22 g22
+    T dl;                                // diagonal of Lap (psi-row update)
+    T idW[3];                            // omega / diagonal of row A
+    T iom;                               // 1 / omega
 };
 
 // ---------------------------------------------------------------- TMA / mbarrier (inline PTX)
@@ -89,7 +109,7 @@ __device__ __forceinline__ bool tile_mbar_wait(uint64_t *mb, uint32_t parity, lo
 // generic-proxy accesses of shared memory are ordered before later async-proxy (TMA) writes
 __device__ __forceinline__ void tile_fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 5-D tiled tensor load into shared memory, completing `bytes` on the mbarrier.
+// 5-D tiled tensor load into shared memory, completing its bytes on the mbarrier.
 __device__ __forceinline__ void tile_tma_load(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                               int c4, uint64_t *mb)
 {
@@ -132,146 +152,168 @@ __device__ __forceinline__ T tile_fetch(const Geo &g, const T *X, const T *O, in
     return v;
 }
 
-// Shared-memory accessor of one field around the active cell: ob[dz + H] is the cell's offset in
-// the same-colour half of plane z + dz; oh moves to the other colour half; pa is the x parity
-// of the active cells of this row (a neighbour at odd dx sits in pair m + pa + (dx-1)/2).
-template <typename T, int ORDER>
-struct AccT {
-    const T *sm;
-    const int *ob;
-    int oh, pa;
-    int fo;   // field offset, F * tile_field_elems
-    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
-    {
-        int o = ob[dz + ORDER / 2] + fo + dy * kTileW;
-        if ((dx + dy + dz) & 1) o += oh;
-        o += (dx & 1) ? pa + ((dx - 1) >> 1) : (dx >> 1);
-        return sm[o];
-    }
-};
-
+// ---------------------------------------------------------------- the plane ring
+// Loading side of a tiled kernel: geometry of the CTA's tile, the TMA ring and the halo fix-ups.
+// Usage: prologue(); then for every plane z of the chunk: advance(z) (false: stop, the CTA
+// failed a bounded wait) followed by the plane's computation; finally finish(failed).
 template <typename T, int ORDER, int BC>
-__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
-    k_smooth_tile(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmO, Geo g,
-                  Coef<T> cf, const T *__restrict__ X, const T *__restrict__ O, T *__restrict__ Y,
-                  const T *__restrict__ f, const T *__restrict__ ab, int colour, TileGrid tg,
-                  unsigned int *__restrict__ err, long long spin)
-{
-    constexpr int H = ORDER / 2, RY = tile_rows<ORDER>(), S = tile_slots<ORDER>();
-    constexpr int FE = tile_field_elems<ORDER>(), HE = tile_half_elems<ORDER>(), SE = tile_slot_elems<ORDER>();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * SE * sizeof(T));
+struct TileRing {
+    static constexpr int H = ORDER / 2, RY = tile_rows<ORDER>(), S = tile_slots<ORDER>();
+    static constexpr int FE = tile_field_elems<ORDER>(), HE = tile_half_elems<ORDER>(), SE = tile_slot_elems<ORDER>();
 
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx >> 1;
-    const unsigned N = (unsigned)nx * ny * nz, Nh = N >> 1;
-    int b = blockIdx.x;
-    const int tx = b % tg.ntx;
-    b /= tg.ntx;
-    const int ty = b % tg.nty;
-    const int tz = b / tg.nty;
-    const int P0 = tx * kTileP, y0 = ty * kTileY, z0 = tz * tg.zc;
-    const int z1 = min(z0 + tg.zc, nz);
-    if (z0 >= z1) return;
-    const int tpt = min(kTileP, nxh - P0);   // pairs in this tile
-    const int zs = z0 - H;                   // first loaded plane; plane p (relative) is zs + p
-    const int NP = (z1 - z0) + 2 * H;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    T *sm;
+    uint64_t *bar;
+    const Geo *g;
+    const T *X, *O;
+    const CUtensorMap *tmX, *tmO;
+    int colour;   // the half loaded from X (tmX); the other half comes from O (tmO)
+    long long spin;
+    int P0, y0, z0, z1, tpt, zs, NP, tid;
+    int npos, done, issued;
+    int fo[kTileFix], fP[kTileFix], fy[kTileFix], fh[kTileFix], ff[kTileFix];
+    T fv[kTileFix];   // halo values of the plane issued last, stored after its TMA completes
 
-    auto ghost_plane = [&](int p) { return BC == BC_ROBIN && (zs + p < 0 || zs + p >= nz); };
-    auto issue = [&](int p) {   // one thread: start the loads of relative plane p
+    __device__ __forceinline__ void setup(unsigned char *smem_raw, const Geo &geo, const T *X_, const T *O_,
+                                          const CUtensorMap *mX, const CUtensorMap *mO, int col, const TileGrid &tg,
+                                          long long spin_)
+    {
+        sm = reinterpret_cast<T *>(smem_raw);
+        bar = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * SE * sizeof(T));
+        g = &geo;
+        X = X_;
+        O = O_;
+        tmX = mX;
+        tmO = mO;
+        colour = col;
+        spin = spin_;
+        const int nxh = geo.n[0] >> 1, ny = geo.n[1], nz = geo.n[2];
+        int b = blockIdx.x;
+        const int tx = b % tg.ntx;
+        b /= tg.ntx;
+        const int ty = b % tg.nty;
+        const int tz = b / tg.nty;
+        P0 = tx * kTileP;
+        y0 = ty * kTileY;
+        z0 = tz * tg.zc;
+        z1 = min(z0 + tg.zc, nz);
+        tpt = min(kTileP, nxh - P0);
+        zs = z0 - H;
+        NP = (z1 - z0) + 2 * H;
+        tid = threadIdx.x;
+        done = -1;
+        issued = -1;
+        // halo elements the tensor load leaves zero: rows outside [0, ny) and pairs outside
+        // [0, nxh), restricted to what the stencil reads (pairs P0-1 .. P0+tpt)
+        npos = tpt + 2;
+        const int top = y0 == 0 ? H : 0, bot = (y0 + kTileY >= ny) ? H : 0;
+        const int ngr = top + bot;
+        const int lcol = P0 == 0 ? 1 : 0, rcol = (P0 + tpt >= nxh) ? 1 : 0, ngc = lcol + rcol;
+        const int nfix = (ngr * npos + (RY - ngr) * ngc) * 8;
+#pragma unroll
+        for (int i = 0; i < kTileFix; ++i) {
+            const int e = tid + i * kTileThreads;
+            fo[i] = -1;
+            fP[i] = fy[i] = fh[i] = ff[i] = 0;
+            fv[i] = 0;
+            if (e < nfix) {
+                const int hf = e & 7, h = hf >> 2, fld = hf & 3;
+                int rest = e >> 3, r, pos;
+                if (rest < ngr * npos) {
+                    const int gr = rest / npos;
+                    pos = kTilePad - 1 + rest % npos;
+                    r = gr < top ? gr : RY - bot + (gr - top);
+                } else {
+                    rest -= ngr * npos;
+                    const int c = rest % ngc;
+                    r = top + rest / ngc;
+                    pos = (c == 0 && lcol) ? kTilePad - 1 : kTilePad + tpt;
+                }
+                fo[i] = h * HE + fld * FE + r * kTileW + pos;
+                fP[i] = P0 - kTilePad + pos;
+                fy[i] = y0 - H + r;
+                fh[i] = h;
+                ff[i] = fld;
+            }
+        }
+    }
+
+    __device__ __forceinline__ bool ghost(int p) const { return BC == BC_ROBIN && (zs + p < 0 || zs + p >= g->n[2]); }
+
+    __device__ __forceinline__ void issue(int p)   // one thread: start the loads of relative plane p
+    {
         uint64_t *mb = bar + p % S;
-        if (ghost_plane(p)) { tile_mbar_arrive(mb); return; }   // filled by plain loads instead
+        if (ghost(p)) { tile_mbar_arrive(mb); return; }   // filled by plain loads instead
         int z = zs + p;
+        const int nz = g->n[2];
         if (BC == BC_PERIODIC) { z += z < 0 ? nz : 0; z -= z >= nz ? nz : 0; }
         T *dst = sm + (p % S) * SE;
         tile_mbar_expect_tx(mb, (uint32_t)(2 * HE * sizeof(T)));
-        tile_tma_load(dst + colour * HE, &tmX, P0 - kTilePad, y0 - H, z, 0, colour, mb);
-        tile_tma_load(dst + (1 - colour) * HE, &tmO, P0 - kTilePad, y0 - H, z, 0, 1 - colour, mb);
-    };
-
-    // Halo elements the tensor load leaves zero: rows outside [0, ny) and pairs outside
-    // [0, nxh), restricted to what the stencil reads (pairs P0-1 .. P0+tpt).
-    const int npos = tpt + 2;
-    const int top = y0 == 0 ? H : 0, bot = (y0 + kTileY >= ny) ? H : 0;
-    const int ngr = top + bot;
-    const int lcol = P0 == 0 ? 1 : 0, rcol = (P0 + tpt >= nxh) ? 1 : 0, ngc = lcol + rcol;
-    const int nfix = (ngr * npos + (RY - ngr) * ngc) * 8;
-    int fo[kTileFix], fP[kTileFix], fy[kTileFix], fh[kTileFix], ff[kTileFix];
-#pragma unroll
-    for (int i = 0; i < kTileFix; ++i) {
-        int e = tid + i * kTileThreads;
-        fo[i] = -1;
-        if (e < nfix) {
-            const int hf = e & 7, h = hf >> 2, fld = hf & 3;
-            int rest = e >> 3, r, pos;
-            if (rest < ngr * npos) {
-                const int gr = rest / npos;
-                pos = kTilePad - 1 + rest % npos;
-                r = gr < top ? gr : RY - bot + (gr - top);
-            } else {
-                rest -= ngr * npos;
-                const int c = rest % ngc;
-                r = top + rest / ngc;
-                pos = (c == 0 && lcol) ? kTilePad - 1 : kTilePad + tpt;
-            }
-            fo[i] = h * HE + fld * FE + r * kTileW + pos;
-            fP[i] = P0 - kTilePad + pos;
-            fy[i] = y0 - H + r;
-            fh[i] = h;
-            ff[i] = fld;
-        }
+        tile_tma_load(dst + colour * HE, tmX, P0 - kTilePad, y0 - H, z, 0, colour, mb);
+        tile_tma_load(dst + (1 - colour) * HE, tmO, P0 - kTilePad, y0 - H, z, 0, 1 - colour, mb);
     }
-    // every element of a Robin ghost plane (no tensor load for it)
-    auto fill_plane = [&](int p) {
+
+    __device__ __forceinline__ void fill_plane(int p)   // every element of a Robin ghost plane
+    {
         T *dst = sm + (p % S) * SE;
         const int tot = 8 * RY * npos;
         for (int e = tid; e < tot; e += kTileThreads) {
             const int hf = e & 7, h = hf >> 2, fld = hf & 3;
             const int rest = e >> 3, r = rest / npos, pos = kTilePad - 1 + rest % npos;
             dst[h * HE + fld * FE + r * kTileW + pos] =
-                tile_fetch<T, BC>(g, X, O, colour, P0 - kTilePad + pos, y0 - H + r, zs + p, h, fld);
+                tile_fetch<T, BC>(*g, X, O, colour, P0 - kTilePad + pos, y0 - H + r, zs + p, h, fld);
         }
-    };
-    auto load_fix = [&](int p, T (&v)[kTileFix]) {
+    }
+
+    __device__ __forceinline__ void load_fix(int p)
+    {
 #pragma unroll
         for (int i = 0; i < kTileFix; ++i)
-            if (fo[i] >= 0) v[i] = tile_fetch<T, BC>(g, X, O, colour, fP[i], fy[i], zs + p, fh[i], ff[i]);
-    };
-    auto store_fix = [&](int p, const T (&v)[kTileFix]) {
+            if (fo[i] >= 0) fv[i] = tile_fetch<T, BC>(*g, X, O, colour, fP[i], fy[i], zs + p, fh[i], ff[i]);
+    }
+
+    __device__ __forceinline__ void store_fix(int p)
+    {
         T *dst = sm + (p % S) * SE;
 #pragma unroll
         for (int i = 0; i < kTileFix; ++i)
-            if (fo[i] >= 0) dst[fo[i]] = v[i];
-    };
-    auto wait_plane = [&](int p) { return tile_mbar_wait(bar + p % S, (uint32_t)((p / S) & 1), spin); };
-
-    if (tid < S) tile_mbar_init(bar + tid, 1);
-    tile_mbar_init_fence();
-    __syncthreads();
-    const int pre = min(2 * H + 1, NP);
-    if (tid == 0)
-        for (int p = 0; p < pre; ++p) issue(p);
-    // prologue: planes 0 .. 2H-1 completed here, plane 2H staged (its halo stored after its wait)
-    bool ok = true;
-    for (int p = 0; p < 2 * H && ok; ++p) {
-        if (ghost_plane(p)) { fill_plane(p); continue; }
-        ok = wait_plane(p);
-        T v[kTileFix];
-        load_fix(p, v);
-        store_fix(p, v);
+            if (fo[i] >= 0) dst[fo[i]] = fv[i];
     }
-    T cur[kTileFix], nxt[kTileFix];
-    if (ghost_plane(2 * H)) fill_plane(2 * H);
-    else load_fix(2 * H, cur);
-    int done = -1;             // planes 0 .. done completed for the whole CTA
-    int issued = pre - 1;      // planes 0 .. issued have loads in flight or completed
-    bool failed = false;       // uniform across the CTA
 
-    for (int z = z0; z < z1; ++z) {
-        const int p = z - zs;   // relative index of the computed plane
-        if (__syncthreads_or(!ok)) { failed = true; break; }   // (A) slot of plane p - H - 1 is free again
-        done = p + H - 1;
+    __device__ __forceinline__ bool wait(int p, long long limit)
+    {
+        return tile_mbar_wait(bar + p % S, (uint32_t)((p / S) & 1), limit);
+    }
+
+    // planes 0 .. 2H: issue all, complete 0 .. 2H-1 here, stage the halo of 2H
+    __device__ __forceinline__ bool prologue()
+    {
+        if (tid < S) tile_mbar_init(bar + tid, 1);
+        tile_mbar_init_fence();
+        __syncthreads();
+        if (tid == 0)
+            for (int p = 0; p <= 2 * H; ++p) issue(p);
+        issued = 2 * H;
+        bool ok = true;
+        for (int p = 0; p < 2 * H; ++p) {
+            if (ghost(p)) { fill_plane(p); continue; }
+            ok = ok && wait(p, spin);
+            load_fix(p);
+            store_fix(p);
+        }
+        if (ghost(2 * H)) fill_plane(2 * H);
+        else load_fix(2 * H);
+        return ok;
+    }
+
+    // Before computing plane z: complete plane z + H, then (after the barrier) refill the slot of
+    // plane z - H - 1 with plane z + H + 1.  Returns false, for every thread, if a wait gave up.
+    __device__ __forceinline__ bool advance(int z, bool ok)
+    {
+        const int p = z - zs;
+        ok = ok && wait(p + H, spin);
+        if (!ghost(p + H)) store_fix(p + H);
+        if (__syncthreads_or(!ok)) return false;
+        done = p + H;
         const int pn = p + H + 1;
         if (pn < NP) {
             if (tid == 0) {
@@ -279,47 +321,235 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
                 issue(pn);
             }
             issued = pn;
-            if (ghost_plane(pn)) fill_plane(pn);
-            else load_fix(pn, nxt);
+            if (ghost(pn)) fill_plane(pn);
+            else load_fix(pn);
         }
-        const int y = y0 + w;
-        const bool act = lane < tpt;
-        const unsigned q = (colour ? Nh : 0u) + (unsigned)(P0 + lane) + (unsigned)nxh * ((unsigned)y + (unsigned)ny * z);
+        return true;
+    }
+
+    __device__ __forceinline__ void finish(bool failed, unsigned int *err)
+    {
+        if (!failed) return;
+        if (tid == 0) atomicOr(err, 1u);
+        // let the loads still in flight land before the CTA's shared memory is released (a
+        // tensor load of an in-bounds box always completes; the bound only guards the poll)
+        for (int p = done + 1; p <= issued; ++p) wait(p, spin > kTileDrain ? spin : kTileDrain);
+    }
+
+    // offset of the cell (lane, warp row w, plane z) in the colour half `half` of each window plane
+    __device__ __forceinline__ void bases(int z, int w, int lane, int half, int (&ob)[2 * H + 1]) const
+    {
+        const int p = z - zs;
+#pragma unroll
+        for (int d = -H; d <= H; ++d) ob[d + H] = ((p + d) % S) * SE + half * HE + (w + H) * kTileW + kTilePad + lane;
+    }
+};
+
+// Shared-memory accessor of one field around a cell: ob[dz + H] is the cell's offset in its
+// colour half of plane z + dz, OH moves to the other colour half, PA is the cell's x parity (a
+// neighbour at odd dx sits in pair m + PA + (dx-1)/2); fo is the field offset.
+template <typename T, int ORDER, int OH, int PA>
+struct AccT {
+    const T *sm;
+    const int *ob;
+    int fo;
+    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
+    {
+        int o = ob[dz + ORDER / 2] + fo + dy * kTileW;
+        if ((dx + dy + dz) & 1) o += OH;
+        o += (dx & 1) ? PA + ((dx - 1) >> 1) : (dx >> 1);
+        return sm[o];
+    }
+};
+
+// ---------------------------------------------------------------- folded operator
+template <int ORDER, typename T, class F>
+__device__ __forceinline__ T lap_fold(const F &f, T c, T k0, const T *k1, const T *nk2)
+{
+    T s = k0 * c;
+    s = fma(k1[0], f(1, 0, 0) + f(-1, 0, 0), s);
+    s = fma(k1[1], f(0, 1, 0) + f(0, -1, 0), s);
+    s = fma(k1[2], f(0, 0, 1) + f(0, 0, -1), s);
+    if constexpr (ORDER == 4) {
+        s = fma(nk2[0], f(2, 0, 0) + f(-2, 0, 0), s);
+        s = fma(nk2[1], f(0, 2, 0) + f(0, -2, 0), s);
+        s = fma(nk2[2], f(0, 0, 2) + f(0, 0, -2), s);
+    }
+    return s;
+}
+
+// (1/3) D_A D_B f from the antisymmetric corner sums g(a, b) = f(a,b) + f(-a,-b) - f(a,-b) - f(-a,b)
+template <int ORDER, int A, int B, typename T, class F>
+__device__ __forceinline__ T dmix_fold(const F &f, T x11, T x12, T x22)
+{
+    auto gq = [&](int a, int b) {
+        return (ax2<A, B>(f, a, b) + ax2<A, B>(f, -a, -b)) - (ax2<A, B>(f, a, -b) + ax2<A, B>(f, -a, b));
+    };
+    T r = x11 * gq(1, 1);
+    if constexpr (ORDER == 4) {
+        r = fma(x12, gq(1, 2) + gq(2, 1), r);
+        r = fma(x22, gq(2, 2), r);
+    }
+    return r;
+}
+
+// out = J e at one cell (the operator of apply_J), centre values in ctr.
+template <int ORDER, typename T, class F>
+__device__ __forceinline__ void apply_J_fold(const F &e0, const F &e1, const F &e2, const F &e3, T ca, T cb,
+                                             const TileCoef<T> &tc, T out[4], T ctr[4])
+{
+    ctr[0] = e0(0, 0, 0);
+    ctr[1] = e1(0, 0, 0);
+    ctr[2] = e2(0, 0, 0);
+    ctr[3] = e3(0, 0, 0);
+    out[0] = fma(ca, lap_fold<ORDER>(e0, ctr[0], tc.lk0, tc.lk1, tc.lnk2), cb * ctr[0]);
+    out[1] = lap_fold<ORDER>(e1, ctr[1], tc.mk0[0], tc.mk1[0], tc.mnk2[0]) +
+             (dmix_fold<ORDER, 0, 1>(e2, tc.x11[0][1], tc.x12[0][1], tc.x22[0][1]) +
+              dmix_fold<ORDER, 0, 2>(e3, tc.x11[0][2], tc.x12[0][2], tc.x22[0][2]));
+    out[2] = lap_fold<ORDER>(e2, ctr[2], tc.mk0[1], tc.mk1[1], tc.mnk2[1]) +
+             (dmix_fold<ORDER, 1, 0>(e1, tc.x11[1][0], tc.x12[1][0], tc.x22[1][0]) +
+              dmix_fold<ORDER, 1, 2>(e3, tc.x11[1][2], tc.x12[1][2], tc.x22[1][2]));
+    out[3] = lap_fold<ORDER>(e3, ctr[3], tc.mk0[2], tc.mk1[2], tc.mnk2[2]) +
+             (dmix_fold<ORDER, 2, 0>(e1, tc.x11[2][0], tc.x12[2][0], tc.x22[2][0]) +
+              dmix_fold<ORDER, 2, 1>(e2, tc.x11[2][1], tc.x12[2][1], tc.x22[2][1]));
+}
+
+// J e of the cell with x parity PA in colour half HALF (both compile-time) from the window.
+template <typename T, int ORDER, int HALF, int PA>
+__device__ __forceinline__ void tile_apply(const T *sm, const int *ob, T ca, T cb, const TileCoef<T> &tc, T Je[4],
+                                           T ctr[4])
+{
+    constexpr int FE = tile_field_elems<ORDER>(), OH = (1 - 2 * HALF) * tile_half_elems<ORDER>();
+    AccT<T, ORDER, OH, PA> a0{sm, ob, 0}, a1{sm, ob, FE}, a2{sm, ob, 2 * FE}, a3{sm, ob, 3 * FE};
+    apply_J_fold<ORDER, T>(a0, a1, a2, a3, ca, cb, tc, Je, ctr);
+}
+
+// ---------------------------------------------------------------- colour pass
+template <typename T, int ORDER, int BC, int COLOUR>
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
+    k_smooth_tile(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmO, Geo g,
+                  TileCoef<T> tc, const T *__restrict__ X, const T *__restrict__ O, T *__restrict__ Y,
+                  const T *__restrict__ f, const T *__restrict__ ab, TileGrid tg, unsigned int *__restrict__ err,
+                  long long spin)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int H = ORDER / 2;
+    TileRing<T, ORDER, BC> ring;
+    ring.setup(smem_raw, g, X, O, &tmX, &tmO, COLOUR, tg, spin);
+    if (ring.z0 >= ring.z1) return;
+    const int nxh = g.n[0] >> 1, ny = g.n[1];
+    const unsigned N = (unsigned)g.n[0] * ny * g.n[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool act = lane < ring.tpt;
+    bool ok = ring.prologue(), failed = false;
+    for (int z = ring.z0; z < ring.z1; ++z) {
+        const int y = ring.y0 + w;
+        const unsigned q = (COLOUR ? N / 2 : 0u) + (unsigned)(ring.P0 + lane) + (unsigned)nxh * ((unsigned)y + (unsigned)ny * z);
         T ca = 0, cb = 0, fq[4] = {0, 0, 0, 0};
-        if (act) {
+        if (act) {   // in flight during the wait and the barrier
             ca = ab[q];
             cb = ab[N + q];
 #pragma unroll
             for (int a = 0; a < 4; ++a) fq[a] = f[a * N + q];
         }
-        ok = wait_plane(p + H);
-        if (!ghost_plane(p + H)) store_fix(p + H, cur);
-#pragma unroll
-        for (int i = 0; i < kTileFix; ++i) cur[i] = nxt[i];
-        if (__syncthreads_or(!ok)) { failed = true; break; }   // (B) plane p + H and its halo are in place
+        if (!ring.advance(z, ok)) { failed = true; break; }
         if (act) {
-            const int pa = (colour + y + z) & 1;
             int ob[2 * H + 1];
-#pragma unroll
-            for (int d = -H; d <= H; ++d)
-                ob[d + H] = ((p + d) % S) * SE + colour * HE + (w + H) * kTileW + kTilePad + lane;
-            const int oh = (1 - 2 * colour) * HE;
-            AccT<T, ORDER> a0{sm, ob, oh, pa, 0}, a1{sm, ob, oh, pa, FE}, a2{sm, ob, oh, pa, 2 * FE},
-                a3{sm, ob, oh, pa, 3 * FE};
+            ring.bases(z, w, lane, COLOUR, ob);
             T Je[4], ctr[4];
-            apply_J<ORDER, T>(a0, a1, a2, a3, ca, cb, cf, Je, ctr);
-            Y[q] = ctr[0] + (fq[0] - Je[0]) / ((ca * cf.dl + cb) * cf.iom);
+            if ((COLOUR + y + z) & 1) tile_apply<T, ORDER, COLOUR, 1>(ring.sm, ob, ca, cb, tc, Je, ctr);
+            else tile_apply<T, ORDER, COLOUR, 0>(ring.sm, ob, ca, cb, tc, Je, ctr);
+            Y[q] = ctr[0] + (fq[0] - Je[0]) / ((ca * tc.dl + cb) * tc.iom);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (fq[1 + a] - Je[1 + a]) * cf.idW[a];
+            for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (fq[1 + a] - Je[1 + a]) * tc.idW[a];
         }
     }
-    if (failed) {
-        if (tid == 0) atomicOr(err, 1u);
-        // let the loads still in flight land before the CTA's shared memory is released (a
-        // tensor load of an in-bounds box always completes; the bound only guards the poll)
-        for (int p = done + 1; p <= issued; ++p)
-            tile_mbar_wait(bar + p % S, (uint32_t)((p / S) & 1), spin > kTileDrain ? spin : kTileDrain);
+    ring.finish(failed, err);
+}
+
+// ---------------------------------------------------------------- residual + restriction
+// r = f - J e at both cells of each thread's pair on every plane, summed over the pair (x), the
+// two planes of a coarse plane (z, in registers) and the two rows of a coarse row (y, odd warps
+// hand their sums to the even ones through shared memory); the 8-child mean goes to the coarse
+// right-hand side fc (colour-split, or plain when the coarse level is the coarsest).
+template <typename T, int ORDER, int BC>
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
+    k_restrict_tile(const __grid_constant__ CUtensorMap tm, Geo g, TileCoef<T> tc, Geo gc, const T *__restrict__ e,
+                    const T *__restrict__ f, const T *__restrict__ ab, T *__restrict__ fc, int csplit, TileGrid tg,
+                    unsigned int *__restrict__ err, long long spin)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int H = ORDER / 2;
+    TileRing<T, ORDER, BC> ring;
+    ring.setup(smem_raw, g, e, e, &tm, &tm, 0, tg, spin);
+    if (ring.z0 >= ring.z1) return;
+    T *stage = reinterpret_cast<T *>(smem_raw + tile_smem_bytes<T, ORDER>() + 16);   // [4 rows][32 lanes][4]
+    const int nxh = g.n[0] >> 1, ny = g.n[1];
+    const unsigned N = (unsigned)g.n[0] * ny * g.n[2];
+    const unsigned Nc = (unsigned)gc.n[0] * gc.n[1] * gc.n[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool act = lane < ring.tpt;
+    T acc[4] = {0, 0, 0, 0};
+    auto flush = [&](int K) {   // even warps: add the odd row's sums and write coarse plane K's cell
+        if ((w & 1) == 0 && act) {
+            const int I = ring.P0 + lane, J = (ring.y0 + w) >> 1;
+            const unsigned linc = (unsigned)I + (unsigned)gc.n[0] * ((unsigned)J + (unsigned)gc.n[1] * (unsigned)K);
+            const unsigned pc = csplit ? (((I + J + K) & 1) ? Nc / 2 : 0u) + (linc >> 1) : linc;
+            const T *st = stage + ((w >> 1) * 32 + lane) * 4;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) fc[a * Nc + pc] = (acc[a] + st[a]) * (T)0.125;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a] = 0;
+    };
+    bool ok = ring.prologue(), failed = false;
+    for (int z = ring.z0; z < ring.z1; ++z) {
+        const int y = ring.y0 + w;
+        const unsigned m = (unsigned)(ring.P0 + lane) + (unsigned)nxh * ((unsigned)y + (unsigned)ny * z);
+        const int c0 = (y + z) & 1;   // colour of the pair's even-x cell
+        const unsigned q0 = (c0 ? N / 2 : 0u) + m, q1 = (c0 ? 0u : N / 2) + m;
+        T a0 = 0, b0 = 0, a1 = 0, b1 = 0, f0[4] = {0, 0, 0, 0}, f1[4] = {0, 0, 0, 0};
+        if (act) {
+            a0 = ab[q0];
+            b0 = ab[N + q0];
+            a1 = ab[q1];
+            b1 = ab[N + q1];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                f0[a] = f[a * N + q0];
+                f1[a] = f[a * N + q1];
+            }
+        }
+        if (!ring.advance(z, ok)) { failed = true; break; }
+        if ((z & 1) == 0 && z > ring.z0) flush((z >> 1) - 1);   // the previous coarse plane
+        if (act) {
+            int obA[2 * H + 1], obB[2 * H + 1];
+            ring.bases(z, w, lane, c0, obA);       // even-x cell, colour c0
+            ring.bases(z, w, lane, 1 - c0, obB);   // odd-x cell, the other colour
+            T Je[4], ctr[4];
+            if (c0 == 0) tile_apply<T, ORDER, 0, 0>(ring.sm, obA, a0, b0, tc, Je, ctr);
+            else tile_apply<T, ORDER, 1, 0>(ring.sm, obA, a0, b0, tc, Je, ctr);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] += f0[a] - Je[a];
+            if (c0 == 0) tile_apply<T, ORDER, 1, 1>(ring.sm, obB, a1, b1, tc, Je, ctr);
+            else tile_apply<T, ORDER, 0, 1>(ring.sm, obB, a1, b1, tc, Je, ctr);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] += f1[a] - Je[a];
+        }
+        if ((z & 1) && (w & 1)) {   // odd row of a coarse row: hand the sums to the even warp
+            T *st = stage + ((w >> 1) * 32 + lane) * 4;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                st[a] = acc[a];
+                acc[a] = 0;
+            }
+        }
     }
+    if (!failed) {
+        __syncthreads();
+        flush((ring.z1 >> 1) - 1);
+    }
+    ring.finish(failed, err);
 }
 
 }  // namespace ctt

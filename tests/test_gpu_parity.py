@@ -207,9 +207,14 @@ def test_tiled_and_global_smoother_agree(mg, case, precision):
     st1, i1, u1, W1 = gpu_solve(mg, p, prec, smoother=1)
     assert st0 == mg.MG_OK and st1 == mg.MG_OK
     assert abs(i0["outer_iters"] - i1["outer_iters"]) <= 1
-    # the first residual reductions agree to the inner precision
+    # the first residual reductions agree, relative to each iteration's largest norm: the two
+    # kernels sum the stencils in different orders, and the FP32 rounding differences (~1e-7),
+    # amplified by the conditioning of the inner solve (the psi row is indefinite and the 4^3
+    # coarsest grid of a Robin box is poorly conditioned), reach ~1e-4 of the largest component
     k = min(3, len(i0["history"]), len(i1["history"]))
-    np.testing.assert_allclose(i0["history"][:k], i1["history"][:k], rtol=1e-3 if precision == "mixed" else 1e-9)
+    h0, h1 = np.asarray(i0["history"][:k]), np.asarray(i1["history"][:k])
+    scale = np.maximum(h0.max(axis=1, keepdims=True), 1e-300)
+    assert (np.abs(h0 - h1) / scale).max() < (1e-2 if precision == "mixed" else 1e-12)
     assert rel(1.0 + u0, 1.0 + u1) < 1e-10
     if np.abs(W1).max() > 1e-12:
         assert rel(W0, W1) < 1e-10
@@ -226,6 +231,34 @@ def test_dense_and_iterative_coarse_solves_agree(mg, precision):
     st1, i1, u1, W1 = gpu_solve(mg, p, prec, levels=3)
     assert st0 == mg.MG_OK and st1 == mg.MG_OK
     assert rel(1.0 + u0, 1.0 + u1) < 1e-10 and rel(W0, W1) < 1e-10
+
+
+ONE_ITER_CASES = {
+    "periodic_o4_n32": lambda: fields.modes_periodic(n=32, a0=5e-5),
+    "periodic_o4_n80_partial_tiles": lambda: fields.modes_periodic(n=80, a0=5e-5),
+    "periodic_o2_n32": lambda: fields.sine_periodic(n=32),
+    "robin_o4_n32": lambda: fields.puncture_shell(n=32, half=16.0),
+    "robin_o4_n48_partial_tile": lambda: fields.puncture_shell(n=48, half=24.0),
+}
+
+
+@pytest.mark.parametrize("case", list(ONE_ITER_CASES))
+def test_tiled_kernels_match_global_kernels_after_one_iteration(mg, case):
+    """Element-wise check of the TMA-tiled colour pass and residual + restriction against the
+    global-memory kernels: one outer iteration with one V(1,1) cycle from psi = 1, W = 0, so the
+    state afterwards is the FP32 correction itself.  The two paths apply the same operator and
+    differ only in FP32 summation order (~1e-7 relative, amplified by the conditioning of the
+    inner solve); a wrong halo value (wrap, Robin ghost, tile edge) would change the cells next to
+    it by a fraction of order one.  Bound: 1e-4 of each field's largest value."""
+    p = ONE_ITER_CASES[case]()
+    over = dict(max_outer=1, tol=1e-30, inner_cycles=1, nu_pre=1, nu_post=1)
+    _, _, u0, W0 = gpu_solve(mg, p, mg.MG_MIXED, smoother=0, **over)
+    _, _, u1, W1 = gpu_solve(mg, p, mg.MG_MIXED, smoother=1, **over)
+    assert np.abs(u1).max() > 0
+    assert np.abs(u0 - u1).max() <= 1e-4 * np.abs(u1).max()
+    for a in range(3):
+        if np.abs(W1[a]).max() > 1e-14:
+            assert np.abs(W0[a] - W1[a]).max() <= 1e-4 * np.abs(W1[a]).max()
 
 
 def test_graph_and_direct_launch_agree(mg):
