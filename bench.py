@@ -159,14 +159,15 @@ def batch_measure(mg, torch, sp, precision, repeats=1):
     sizes = fields.batch_sizes()
     ps = [fields.batch_instance(n, a0, seed, device="cuda") for n, a0, seed in sizes]
     cfgs = [mg.config_for(p, precision, tol=WORKLOAD["tol"], max_outer=60) for p in ps]
-    # one-time tuning per grid size on that size's first instance (untimed)
-    tuned = {}
-    for p, c in zip(ps, cfgs):
-        n = p["n"][0]
-        if n not in tuned:
-            best, tms = mg.mg_autotune(c, p["rho0"], p["rho2"], p["S"][0], p["S"][1], p["S"][2], stream=sp)
-            tuned[n] = tune_summary(best, tms)
-        apply_tuned(c, tuned[n])
+    # one-time tuning (untimed) on the first instance of the largest size, which dominates the
+    # batch; the batch iterates in lock step until its slowest instance converges, so every
+    # instance uses the same setting rather than one tuned on a single instance of its size
+    big = max(range(len(ps)), key=lambda b: ps[b]["n"][0])
+    pb = ps[big]
+    best, tms = mg.mg_autotune(cfgs[big], pb["rho0"], pb["rho2"], pb["S"][0], pb["S"][1], pb["S"][2], stream=sp)
+    tuned = {pb["n"][0]: tune_summary(best, tms)}
+    for c in cfgs:
+        apply_tuned(c, tuned[pb["n"][0]])
     bt = mg.mg_batch_create(cfgs, sp)
     try:
         for b, p in enumerate(ps):

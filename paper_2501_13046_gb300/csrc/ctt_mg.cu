@@ -359,6 +359,9 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
             if (st != MG_OK) break;
         }
         if (cudaStreamCreateWithFlags(&x->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&x->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x->ev_join, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&x->ev_in, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&x->ev_out, cudaEventDisableTiming) != cudaSuccess) {
             st = fail(MG_ERR_CUDA, "stream/event creation");
@@ -606,6 +609,12 @@ void mg_destroy(mg_ctx *x)
         cudaStreamSynchronize(x->stream);
         cudaStreamDestroy(x->stream);
     }
+    if (x->side) {
+        cudaStreamSynchronize(x->side);
+        cudaStreamDestroy(x->side);
+    }
+    if (x->ev_fork) cudaEventDestroy(x->ev_fork);
+    if (x->ev_join) cudaEventDestroy(x->ev_join);
     if (x->ev_in) cudaEventDestroy(x->ev_in);
     if (x->ev_out) cudaEventDestroy(x->ev_out);
     if (x->host_scal) cudaFreeHost(x->host_scal);

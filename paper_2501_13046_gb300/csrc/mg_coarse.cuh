@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(256) k_dense_w_assemble(Geo g, Coef<T> cf, C *
 // matrix: pivot row (2m), old row k (2m), column factors (m), gj_scratch_elems(m) in all; with
 // smem_ok it is all copied into dynamic shared memory first.  Per column: pivot search (one
 // warp), staging of the scaled pivot row, the old row k and the factors, then one elimination
-// pass in which row k takes the pivot row and the pivot row's slot takes the old row k (the
-// swap).  A zero pivot yields non-finite entries, which the outer iteration reports as
+// pass (one warp per row) in which row k takes the pivot row and the pivot row's slot takes
+// the old row k (the swap).  A zero pivot yields non-finite entries, which the outer iteration reports as
 // divergence.
 __host__ __device__ inline size_t gj_scratch_elems(int m) { return (size_t)2 * m * m + 5 * (size_t)m; }
 
@@ -146,17 +146,22 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(C *__restrict__ gaug, int
         __syncthreads();
         const int pr = piv < m ? piv : k;   // an all-NaN column leaves the rows in place
         const C ip = (C)1 / A[(size_t)pr * w2 + k];
-        for (int j = tid; j < w2; j += bs) {
+        // columns left of k are already reduced (zero in rows k and pr), so only j >= k change
+        for (int j = k + tid; j < w2; j += bs) {
             prow[j] = A[(size_t)pr * w2 + j] * ip;
             krow[j] = A[(size_t)k * w2 + j];
         }
         for (int i = tid; i < m; i += bs) fct[i] = A[(size_t)(i == pr ? k : i) * w2 + k];
         __syncthreads();
-        for (int t = tid; t < m * w2; t += bs) {
-            const int i = t / w2, j = t - i * w2;
-            if (i == k) A[t] = prow[j];
-            else if (i == pr) A[t] = krow[j] - fct[i] * prow[j];
-            else A[t] -= fct[i] * prow[j];
+        for (int i = tid >> 5; i < m; i += bs >> 5) {   // one warp per row, lanes along the row
+            C *row = A + (size_t)i * w2;
+            const C fi = fct[i];
+            if (i == k)
+                for (int j = k + (tid & 31); j < w2; j += 32) row[j] = prow[j];
+            else if (i == pr)
+                for (int j = k + (tid & 31); j < w2; j += 32) row[j] = krow[j] - fi * prow[j];
+            else
+                for (int j = k + (tid & 31); j < w2; j += 32) row[j] -= fi * prow[j];
         }
         __syncthreads();
     }

@@ -213,6 +213,9 @@ struct mg_ctx {
     cudaStream_t user_stream = nullptr;   // the caller's stream (may be the legacy default stream)
     cudaStream_t stream = nullptr;        // private non-blocking stream: all library work and captures
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t side = nullptr;           // parallel branch: the per-iteration psi inverse
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool join_pending = false;             // enqueue-time: the next coarse solve waits for ev_join
     int nlev = 0;
     size_t N = 0;
     size_t tbytes = 8;   // sizeof(T) of the inner solve

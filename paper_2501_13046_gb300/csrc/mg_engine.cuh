@@ -127,6 +127,10 @@ mg_status enqueue_coarse(mg_ctx *x, int l)
     const size_t tb = sizeof(T);
     const int periodic = x->cfg.bc == MG_BC_PERIODIC;
     if (x->dense) {   // exact coarse correction by the precomputed inverses
+        if (x->join_pending) {
+            CK(cudaStreamWaitEvent(x->stream, x->ev_join, 0));
+            x->join_pending = false;
+        }
         const int N = (int)L.N;
         k_dense_apply<T><<<(4 * N * 32 + 255) / 256, 256, 0, x->stream>>>(
             (const T *)x->Gpsi, x->mpsi, (const T *)x->GW, x->mw, (const T *)L.f, (T *)L.eA, N);
@@ -178,7 +182,7 @@ mg_status enqueue_cycle(mg_ctx *x, int l, bool zero)
     const int visits = l + 1 == Lc ? 1 : x->gamma;
     for (int v = 0; v < visits; ++v) CKS(enqueue_cycle<T, ORDER>(x, l + 1, v == 0));
     dispatch_bc(x->cfg.bc, [&](auto B) {
-        k_prolong_add<T, decltype(B)::value><<<grid_for(C.N, 1 << 24, x->threads), x->threads, 0, x->stream>>>(
+        k_prolong_add<T, decltype(B)::value><<<grid_for(L.N, 1 << 24, x->threads), x->threads, 0, x->stream>>>(
             L.geo, C.geo, (const T *)C.cur(), (T *)L.cur(), C.split);
     });
     CK(cudaGetLastError());
@@ -236,7 +240,9 @@ inline size_t gj_smem(int m)
     return b <= kMaxCoarseSmem ? b : 0;
 }
 
-// Inverse of the coarsest psi row for this outer iteration (its coefficients were just restricted).
+// Inverse of the coarsest psi row for this outer iteration (its coefficients were just restricted),
+// on a parallel branch: the one-CTA elimination overlaps the first cycle's descent, and the first
+// coarse solve of the iteration waits for it (enqueue_coarse).
 template <typename T, int ORDER>
 mg_status enqueue_dense_psi_inverse(mg_ctx *x)
 {
@@ -244,12 +250,16 @@ mg_status enqueue_dense_psi_inverse(mg_ctx *x)
     const int periodic = x->cfg.bc == MG_BC_PERIODIC;
     Coef<T> cf = make_coef<T>(C.geo, x->cfg.order);
     const size_t sm = gj_smem<T>(x->mpsi);
+    CK(cudaEventRecord(x->ev_fork, x->stream));
+    CK(cudaStreamWaitEvent(x->side, x->ev_fork, 0));
     dispatch_bc(x->cfg.bc, [&](auto B) {
-        k_dense_psi_assemble<T, T, ORDER, decltype(B)::value><<<1, 512, 0, x->stream>>>(C.geo, cf, (const T *)C.c,
-                                                                                      (T *)x->gj, periodic);
+        k_dense_psi_assemble<T, T, ORDER, decltype(B)::value><<<1, 512, 0, x->side>>>(C.geo, cf, (const T *)C.c,
+                                                                                    (T *)x->gj, periodic);
     });
-    k_gauss_jordan<T, T><<<1, 1024, sm, x->stream>>>((T *)x->gj, x->mpsi, sm > 0, (T *)x->Gpsi);
+    k_gauss_jordan<T, T><<<1, 1024, sm, x->side>>>((T *)x->gj, x->mpsi, sm > 0, (T *)x->Gpsi);
     CK(cudaGetLastError());
+    CK(cudaEventRecord(x->ev_join, x->side));
+    x->join_pending = true;
     return MG_OK;
 }
 

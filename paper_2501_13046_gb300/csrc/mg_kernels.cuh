@@ -482,51 +482,60 @@ __global__ void __launch_bounds__(256) k_restrict_mean(Geo g, Geo gc, const T *_
     }
 }
 
-// Fine correction (colour-split) += cell-centred trilinear interpolation of the coarse
-// correction (colour-split or plain; weights 3/4 and 1/4 per axis, boundary values from the BC).
+// Prolongation + add: e_fine += P e_coarse, trilinear in cell-centred coordinates (weights 3/4 for
+// the parent and 1/4 for its neighbour towards the child, per axis).  One thread per fine cell
+// (fine level colour-split, threads in storage order so that the read-modify-write of e_fine is
+// coalesced): the 8 coarse cells and weights are set up once and serve all 4 fields.  Coarse
+// neighbours outside the box take the level's boundary value (periodic wrap, or the Robin ratio
+// |x_clamp| / |x_g| folded into the weight).  Coarse level colour-split or plain (csplit).
 template <typename T, int BC>
 __global__ void __launch_bounds__(256) k_prolong_add(Geo g, Geo gc, const T *__restrict__ ec, T *__restrict__ ef,
                                                      int csplit)
 {
-    const size_t Nc = (size_t)gc.n[0] * gc.n[1] * gc.n[2];
-    const size_t Nf = 8 * Nc;
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < Nc; q += (size_t)gridDim.x * blockDim.x) {
-        int I = (int)(q % gc.n[0]);
-        size_t rest = q / gc.n[0];
-        int J = (int)(rest % gc.n[1]);
-        int K = (int)(rest / gc.n[1]);
-#pragma unroll 1
-        for (int a = 0; a < 4; ++a) {
-            const T *fc = ec + a * Nc;
-            AccB2<T, BC> acc{fc, fc, &gc, Nc, I, J, K, 0};
-            T v[3][3][3];
+    const unsigned nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx >> 1;
+    const unsigned N = nx * ny * nz, Nh = N >> 1;
+    const int ncx = gc.n[0], ncy = gc.n[1], ncz = gc.n[2];
+    const unsigned Nc = (unsigned)ncx * ncy * ncz;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < N; q += gridDim.x * blockDim.x) {
+        const unsigned c = q >= Nh, m = q - (c ? Nh : 0u);
+        const unsigned row = m / nxh, xi = m - row * nxh;
+        const int j = (int)(row % ny), k = (int)(row / ny);
+        const int i = 2 * (int)xi + (int)((c + j + k) & 1);
+        const int I = i >> 1, J = j >> 1, K = k >> 1;
+        const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
+        unsigned idx[8];
+        T w[8];
 #pragma unroll
-            for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if (csplit) {
-                            v[dz + 1][dy + 1][dx + 1] = acc(dx, dy, dz);
-                        } else {
-                            v[dz + 1][dy + 1][dx + 1] = fetch_bc<T, BC>(fc, gc, I + dx, J + dy, K + dz);
-                        }
-                    }
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                int sx = (d & 1) ? 1 : -1, sy = ((d >> 1) & 1) ? 1 : -1, sz = (d >> 2) ? 1 : -1;
-                T s = 0;
-#pragma unroll
-                for (int cz = 0; cz < 2; ++cz)
-#pragma unroll
-                    for (int cy = 0; cy < 2; ++cy)
-#pragma unroll
-                        for (int cx = 0; cx < 2; ++cx) {
-                            T w = (T)((cx ? 0.25 : 0.75) * (cy ? 0.25 : 0.75) * (cz ? 0.25 : 0.75));
-                            s += w * v[1 + cz * sz][1 + cy * sy][1 + cx * sx];
-                        }
-                ef[a * Nf + sidx(g, 2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), Nf, 1)] += s;
+        for (int d = 0; d < 8; ++d) {
+            const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+            int cx = I + dx * sx, cy = J + dy * sy, cz = K + dz * sz;
+            double wd = (dx ? 0.25 : 0.75) * (dy ? 0.25 : 0.75) * (dz ? 0.25 : 0.75);
+            int bx = cx, by = cy, bz = cz;
+            if (BC == BC_PERIODIC) {
+                bx += bx < 0 ? ncx : 0; bx -= bx >= ncx ? ncx : 0;
+                by += by < 0 ? ncy : 0; by -= by >= ncy ? ncy : 0;
+                bz += bz < 0 ? ncz : 0; bz -= bz >= ncz ? ncz : 0;
+            } else {
+                bx = min(max(bx, 0), ncx - 1);
+                by = min(max(by, 0), ncy - 1);
+                bz = min(max(bz, 0), ncz - 1);
+                if (bx != cx || by != cy || bz != cz) {
+                    const double ax = cellx(gc, 0, bx), ay = cellx(gc, 1, by), az = cellx(gc, 2, bz);
+                    const double gx = cellx(gc, 0, cx), gy = cellx(gc, 1, cy), gz = cellx(gc, 2, cz);
+                    wd *= sqrt(ax * ax + ay * ay + az * az) / sqrt(gx * gx + gy * gy + gz * gz);
+                }
             }
+            const unsigned lin = (unsigned)bx + (unsigned)ncx * ((unsigned)by + (unsigned)ncy * (unsigned)bz);
+            idx[d] = csplit ? (((bx + by + bz) & 1) ? Nc / 2 : 0u) + (lin >> 1) : lin;
+            w[d] = (T)wd;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const T *e = ec + (size_t)a * Nc;
+            T s = 0;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) s = fma(w[d], e[idx[d]], s);
+            ef[(size_t)a * N + q] += s;
         }
     }
 }
@@ -639,9 +648,27 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_sum4(const T *__restrict__ x, size_t N, double *__restrict__ partial)
 {
     double v[4] = {0, 0, 0, 0};
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+    if constexpr (sizeof(T) == 4) {
+        // each thread's sum as an unevaluated pair hi + lo of floats, kept exact by Knuth's
+        // two-sum (the rounding error of every addition is carried in lo), then one FP64 sum
+        float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+        for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) v[a] += (double)x[a * N + p];
+            for (int a = 0; a < 4; ++a) {
+                const float b = (float)x[a * N + p];
+                const float s = __fadd_rn(hi[a], b);
+                const float bv = __fsub_rn(s, hi[a]);
+                const float err = __fadd_rn(__fsub_rn(hi[a], __fsub_rn(s, bv)), __fsub_rn(b, bv));
+                hi[a] = s;
+                lo[a] = __fadd_rn(lo[a], err);
+            }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] = (double)hi[a] + (double)lo[a];
+    } else {
+        for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) v[a] += (double)x[a * N + p];
+    }
     double r[4];
     block_sum<4>(v, r);
     if (threadIdx.x == 0)
@@ -669,14 +696,13 @@ __global__ void __launch_bounds__(256) k_update(Geo g, double *__restrict__ x, c
     double m[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) m[a] = periodic ? esums[a] / (double)N : 0.0;
+    const unsigned nx = (unsigned)g.n[0], ny = (unsigned)g.n[1];   // grids hold < 2^31 cells
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
         size_t q = p;
         if (split) {
-            int i = (int)(p % g.n[0]);
-            size_t rest = p / g.n[0];
-            int j = (int)(rest % g.n[1]);
-            int k = (int)(rest / g.n[1]);
-            q = (((i + j + k) & 1) ? N / 2 : 0) + (p >> 1);
+            const unsigned pu = (unsigned)p, rest = pu / nx;
+            const unsigned par = (pu - rest * nx) + (rest % ny) + rest / ny;
+            q = ((par & 1) ? N / 2 : 0) + (p >> 1);
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) x[a * N + p] += (double)e[a * N + q] - m[a];
@@ -775,7 +801,14 @@ static __global__ void k_outer_scalars(Scalars *s, size_t N, int kmode_integrabi
 
 // Pass 2: final residuals, norm partials, inner right-hand side and coefficients in T:
 //   f = (-psi^-5 F_psi, -F_W,i),  a = psi^-5,  b = psi^-5 c,  c = dF_psi/du.
-// Optionally (HM != nullptr) writes H and M (4 FP64 fields) instead of the inner data.
+// F_psi = R0 - (K^2/12) psi^5 and F_W,i = R_i + m_i are always formed in FP64: these are the
+// differences of nearly equal terms.  With an FP32 inner solve (T = float) and no field output,
+// the later products (the psi^-5, psi^-6 scalings of H and M, the inner data) are formed in FP32:
+// each is a product of already-accurate factors, so the norms keep 7 significant digits and the
+// FP64 ALU, at 2 lanes per clock per SM on this GPU, is spared the division and powers.
+// Optionally (HM != nullptr) writes H and M (4 FP64 fields, FP64 throughout) instead.
+__device__ __forceinline__ float absnanf(float x) { return (x == x) ? fabsf(x) : __int_as_float(0x7f800000); }
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__restrict__ x, const double *__restrict__ R,
                                                      const Scalars *__restrict__ s, T *__restrict__ f,
@@ -786,18 +819,38 @@ __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__rest
     const double K2 = s->K2;
     const double m0 = s->msrc[0], m1 = s->msrc[1], m2 = s->msrc[2];
     double mx[4] = {0, 0, 0, 0};
+    float mxf[4] = {0, 0, 0, 0};
+    const bool fast = sizeof(T) == 4 && HM == nullptr;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-        int i = (int)(p % g.n[0]);
-        size_t rest = p / g.n[0];
-        int j = (int)(rest % g.n[1]);
-        int k = (int)(rest / g.n[1]);
-        double psi = psi_background(g, i, j, k) + x[p];
-        double p2 = psi * psi, p4 = p2 * p2, p5 = p4 * psi;
-        double ip = 1.0 / psi, ip2 = ip * ip, ip5 = ip2 * ip2 * ip, ip6 = ip5 * ip;
-        double Fp = R[p] - (K2 / 12.0) * p5;
-        double Fw0 = R[N + p] + m0, Fw1 = R[2 * N + p] + m1, Fw2 = R[3 * N + p] + m2;
-        double H = -8.0 * ip5 * Fp;
-        double M0 = ip6 * Fw0, M1 = ip6 * Fw1, M2 = ip6 * Fw2;
+        const unsigned pu = (unsigned)p, nx = (unsigned)g.n[0], ny = (unsigned)g.n[1];
+        const int i = (int)(pu % nx);
+        const unsigned rest = pu / nx;
+        const int j = (int)(rest % ny);
+        const int k = (int)(rest / ny);
+        const double psi = psi_background(g, i, j, k) + x[p];
+        const double p2 = psi * psi, p4 = p2 * p2, p5 = p4 * psi;
+        const double Fp = fma(-K2 / 12.0, p5, R[p]);
+        const double Fw0 = R[N + p] + m0, Fw1 = R[2 * N + p] + m1, Fw2 = R[3 * N + p] + m2;
+        if (fast) {
+            const float ps = (float)psi, ip = 1.0f / ps, ip2 = ip * ip, ip5 = ip2 * ip2 * ip, ip6 = ip5 * ip;
+            const float fp = (float)Fp, w0 = (float)Fw0, w1 = (float)Fw1, w2 = (float)Fw2;
+            mxf[0] = fmaxf(mxf[0], absnanf(-8.0f * ip5 * fp));
+            mxf[1] = fmaxf(mxf[1], absnanf(ip6 * w0));
+            mxf[2] = fmaxf(mxf[2], absnanf(ip6 * w1));
+            mxf[3] = fmaxf(mxf[3], absnanf(ip6 * w2));
+            const size_t q = split ? (((i + j + k) & 1) ? N / 2 : 0) + (p >> 1) : p;
+            const float ps2 = ps * ps;
+            f[q] = (T)(-ip5 * fp);
+            f[N + q] = (T)(-w0);
+            f[2 * N + q] = (T)(-w1);
+            f[3 * N + q] = (T)(-w2);
+            ab[q] = (T)ip5;
+            ab[N + q] = (T)(ip5 * ((float)R[4 * N + p] - (float)(5.0 / 12.0 * K2) * (ps2 * ps2)));
+            continue;
+        }
+        const double ip = 1.0 / psi, ip2 = ip * ip, ip5 = ip2 * ip2 * ip, ip6 = ip5 * ip;
+        const double H = -8.0 * ip5 * Fp;
+        const double M0 = ip6 * Fw0, M1 = ip6 * Fw1, M2 = ip6 * Fw2;
         mx[0] = fmax(mx[0], absnan(H));
         mx[1] = fmax(mx[1], absnan(M0));
         mx[2] = fmax(mx[2], absnan(M1));
@@ -808,7 +861,7 @@ __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__rest
             HM[2 * N + p] = M1;
             HM[3 * N + p] = M2;
         } else {
-            size_t q = split ? (((i + j + k) & 1) ? N / 2 : 0) + (p >> 1) : p;
+            const size_t q = split ? (((i + j + k) & 1) ? N / 2 : 0) + (p >> 1) : p;
             f[q] = (T)(-ip5 * Fp);
             f[N + q] = (T)(-Fw0);
             f[2 * N + q] = (T)(-Fw1);
@@ -817,6 +870,8 @@ __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__rest
             ab[N + q] = (T)(ip5 * (R[4 * N + p] - (5.0 / 12.0) * K2 * p4));
         }
     }
+    if (fast)
+        for (int a = 0; a < 4; ++a) mx[a] = (double)mxf[a];
     double r[4];
     block_max<4>(mx, r);
     if (threadIdx.x == 0)
