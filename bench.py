@@ -194,6 +194,68 @@ def batch_measure(mg, torch, sp, precision, repeats=1):
             "max_norm": max(float(i["norms"].max()) for i in infos)}
 
 
+# FP64 flops of the residual pass B per interior cell, counted from its source (an FMA is 2):
+# Lap u 19, three momentum rows 75, AtAt 55, nonlinear terms and outputs 38.
+PASSB_FLOPS_PER_CELL = 187
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes of one 128^3 pass-B launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture of the kernel as it stands (profiles/outer_pass1q_128cube_periodic_o4.md); None if none
+PASSB_TRAFFIC_128 = None
+
+
+def kernel_rooflines(mg, ctx, N):
+    """Live CUDA-event timings (library stream) of the dominant kernel and of the colour pass."""
+    pk, src = peaks()
+    msb, bytesb = mg.mg_time_kernel(ctx, 3, 10)   # FP64 residual pass B alone
+    ms0, bytes0 = mg.mg_time_kernel(ctx, 0, 40)   # finest FP32 colour pass
+    ms1, bytes1 = mg.mg_time_kernel(ctx, 1, 20)   # finest residual + restriction
+    ach = PASSB_FLOPS_PER_CELL * N / (msb * 1e-3) / 1e12
+    sm_gbs = bytes0 / (ms0 * 1e-3) / 1e9
+    rr_gbs = bytes1 / (ms1 * 1e-3) / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": PASSB_TRAFFIC_128,
+            "kernel": "k_outer_pass1q<4,periodic> (FP64 residual pass B, 128^3; FP64 pipe bound)",
+            "ms_per_launch": msb, "algorithmic_flops": PASSB_FLOPS_PER_CELL * N, "algorithmic_bytes": bytesb,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz",
+            "colour_pass": {"bound": "hbm", "kernel": "k_smooth_tile<float,4,periodic,c> (finest, one colour)",
+                            "ms_per_launch": ms0, "algorithmic_bytes": bytes0, "achieved": sm_gbs,
+                            "unit": "GB/s", "peak": pk["hbm_gbs"], "frac": sm_gbs / pk["hbm_gbs"],
+                            "peak_source": src + " hbm_gbs (copy test)"},
+            "residual_restrict": {"bound": "hbm", "kernel": "k_restrict_tile<float,4,periodic> (finest)",
+                                  "ms_per_launch": ms1, "algorithmic_bytes": bytes1, "achieved": rr_gbs,
+                                  "unit": "GB/s", "peak": pk["hbm_gbs"], "frac": rr_gbs / pk["hbm_gbs"]}}
+
+
+def run_solve_profile(args):
+    """Only the benchmarked solve: W + K mixed solves of the 128^3 workload from psi = 1 with the
+    settings given (--settings inner,nu,omega; default: autotuned).  The committed launch lists and
+    kernel captures are taken from this command."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_13046_gb300 import mg
+    p = make_problem()
+    sp = torch.cuda.current_stream().cuda_stream
+    src = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (p["rho0"], p["rho2"], *p["S"])]
+    cfg = mg.config_for(p, mg.MG_MIXED, tol=WORKLOAD["tol"], max_outer=60)
+    if args.settings:
+        inner, nu, om = args.settings.split(",")
+        apply_tuned(cfg, {"inner_cycles": int(inner), "nu": int(nu), "omega": float(om)})
+    else:
+        cfg, _ = mg.mg_autotune(cfg, *src, stream=sp)
+    ctx = mg.mg_create(cfg, sp)
+    mg.mg_set_sources(ctx, *src)
+    stream = torch.cuda.current_stream()
+    solve_loop(mg, torch, ctx, args.warmup, stream)
+    secs, info = solve_loop(mg, torch, ctx, args.steps, stream)
+    print(json.dumps({"workload": "solve", "solves_per_s": args.steps / secs, "outer_iters": info["outer_iters"],
+                      "launches_per_solve": info["kernel_launches"], "inner_cycles": cfg.inner_cycles,
+                      "nu": cfg.nu_pre, "omega": cfg.omega}))
+    mg.mg_destroy(ctx)
+    return 0
+
+
 def tune_summary(cfg, ms):
     return {"inner_cycles": cfg.inner_cycles, "nu": cfg.nu_pre, "omega": cfg.omega, "tune_solve_ms": ms}
 
@@ -276,13 +338,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bench", choices=["bench", "warmstart"])
+    ap.add_argument("--workload", default="bench", choices=["bench", "warmstart", "solve"])
+    ap.add_argument("--settings", default="", help="solve workload: inner_cycles,nu,omega (default: autotune)")
     ap.add_argument("--train-samples", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--test-instances", type=int, default=256)
     args = ap.parse_args()
     if args.workload == "warmstart" and args.impl == "ours":
         return run_warmstart(args)
+    if args.workload == "solve" and args.impl == "ours":
+        return run_solve_profile(args)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -342,15 +407,7 @@ def main():
     launches = info["kernel_launches"] * args.steps
 
     # dominant kernel: one finest-level red-black colour pass (timed live on the context stream)
-    pk, src = peaks()
-    ms0, bytes0 = mg.mg_time_kernel(ctx, 0, 40)
-    ms2, bytes2 = mg.mg_time_kernel(ctx, 2, 10)
-    achieved = bytes0 / (ms0 * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                "kernel": "k_smooth_tile<float,4,periodic> (TMA-tiled, finest level, one colour pass)",
-                "ms_per_launch": ms0, "algorithmic_bytes": bytes0, "peak_source": src + " hbm_gbs (copy test)",
-                "fp64_residual_pass1_ms": ms2}
+    roofline = kernel_rooflines(mg, ctx, WORKLOAD["n"] ** 3)
 
     # ---- end to end through the public API with host buffers
     host_src = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (p["rho0"], p["rho2"], *p["S"])]

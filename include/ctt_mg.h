@@ -143,7 +143,8 @@ mg_status mg_constraint_fields(struct mg_ctx *ctx, double *H, double *M, int on_
  * stream, bracketed by CUDA events, at the current state (call after mg_solve or
  * mg_residual_norms).  which: 0 = one red-black colour pass of the finest-level smoother,
  * 1 = residual + restriction of the finest level, 2 = outer FP64 residual pass 1 (its two
- * kernels, q/div W then the residual parts, and the reduction of the integrability sums).
+ * kernels, q/div W then the residual parts, and the reduction of the integrability sums),
+ * 3 = the second of those kernels alone (the residual parts; FP64-ALU bound).
  * Returns the mean device time per launch and the algorithmic DRAM bytes one launch must
  * move (every array it reads once, every array it writes once).  The solver state is not
  * changed except for scratch buffers.

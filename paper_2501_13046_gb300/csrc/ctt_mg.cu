@@ -545,7 +545,7 @@ static mg_status mg_constraint_fields_impl(mg_ctx *x, double *H, double *M, int 
 
 static mg_status mg_time_kernel_impl(mg_ctx *x, int which, int reps, double *ms_per_launch, double *bytes_per_launch)
 {
-    if (!x || reps < 1 || which < 0 || which > 2) return fail(MG_ERR_INVALID_ARG, "bad argument");
+    if (!x || reps < 1 || which < 0 || which > 3) return fail(MG_ERR_INVALID_ARG, "bad argument");
     float ms = 0.f;
     const int O = x->cfg.order;
     if (x->tbytes == 8)
@@ -555,7 +555,8 @@ static mg_status mg_time_kernel_impl(mg_ctx *x, int which, int reps, double *ms_
     double N = (double)x->N, s = (double)x->tbytes, b = 0.0;
     if (which == 0) b = 0.5 * 14.0 * s * N;               // half of a two-colour sweep: (2 F + 6) s per cell (algorithmic)
     else if (which == 1) b = (10.0 * s + 4.0 * s / 8.0) * N; // read e, f, a, b; write the coarse rhs
-    else b = (3.0 + 4.0 + 4.0 + 4.0 + 5.0 + 5.0) * 8.0 * N; // A: read W, write q/div; B: read u, W, q/div, 5 sources, write 5
+    else if (which == 2) b = (3.0 + 4.0 + 4.0 + 4.0 + 5.0 + 5.0) * 8.0 * N; // A: W -> q/div; B: u, W, q/div, 5 sources -> 5
+    else b = (4.0 + 4.0 + 5.0 + 5.0) * 8.0 * N;                   // B: read u, W, q/div, 5 sources; write 5
     if (ms_per_launch) *ms_per_launch = ms / reps;
     if (bytes_per_launch) *bytes_per_launch = b;
     return MG_OK;

@@ -366,8 +366,17 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
             L.curB = 0;   // residual of eA
             CKS(enqueue_restrict<T, ORDER>(x, 0));
             L.curB = keep;
-        } else {
+        } else if (which == 2) {
             CKS(enqueue_outer_pass1<ORDER>(x));
+        } else {   // pass B alone (reads pass A's q, div W from the last residual evaluation)
+            Coef<double> cd = make_coef<double>(L.geo, x->cfg.order);
+            OuterCoef oc = make_outer_coef(L.geo, x->cfg.order);
+            int gb = 0;
+            Regions rg = outer_regions(L.geo, ORDER, &gb);
+            dispatch_bc(x->cfg.bc, [&](auto B) {
+                k_outer_pass1q<ORDER, decltype(B)::value><<<gb, kThreads, 0, x->stream>>>(
+                    L.geo, cd, oc, x->X, x->D, x->SRC, x->R, x->partial, rg);
+            });
         }
     }
     CK(cudaGetLastError());
