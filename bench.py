@@ -195,13 +195,13 @@ def batch_measure(mg, torch, sp, precision, repeats=1):
 
 
 # FP64 flops of the residual pass B per interior cell, counted from its source (an FMA is 2):
-# Lap u 19, three momentum rows 75, AtAt 55, nonlinear terms and outputs 38.
-PASSB_FLOPS_PER_CELL = 187
+# Lap u 19, three momentum rows 75, AtAt 55, nonlinear terms and outputs 30.
+PASSB_FLOPS_PER_CELL = 179
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes of one 128^3 pass-B launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture of the kernel as it stands (profiles/outer_pass1q_128cube_periodic_o4.md); None if none
-PASSB_TRAFFIC_128 = 383739136
+PASSB_TRAFFIC_128 = 374301184
 
 
 def kernel_rooflines(mg, ctx, N):

@@ -223,7 +223,7 @@ mg_status enqueue_residual(mg_ctx *x, double *HM)
     double K2f = x->cfg.K * x->cfg.K;
     k_outer_scalars<<<1, 1, 0, x->stream>>>(x->scal, x->N, x->cfg.k_mode == MG_K_INTEGRABILITY, K2f,
                                            x->cfg.bc == MG_BC_PERIODIC);
-    k_outer_pass2<T><<<g1, kThreads, 0, x->stream>>>(L0.geo, x->X, x->R, x->scal, (T *)L0.f, (T *)L0.c, HM,
+    k_outer_pass2<T><<<g1, kThreads, 0, x->stream>>>(L0.geo, x->X, x->R, x->SRC, x->scal, (T *)L0.f, (T *)L0.c, HM,
                                                      x->partial, L0.split);
     k_finalize_max<4><<<1, 256, 0, x->stream>>>(x->partial, g1, x->scal->norms);
     CK(cudaGetLastError());

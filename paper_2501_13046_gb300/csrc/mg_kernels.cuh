@@ -713,7 +713,7 @@ __global__ void __launch_bounds__(256) k_update(Geo g, double *__restrict__ x, c
 // Outer FP64 residual, pass 1.  Per cell:
 //   R0 = Lap u + (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi)       (F_psi before the K^2 term)
 //   R1..3 = Lap W_i + (1/3) d_i d_j W_j - 8 pi psi^6 S_i                   (F_W before adding m_i)
-//   R4 = -(7/8) psi^-8 AtAt + 2 pi (5 rho0 psi^4 + rho2)                  (c before the K^2 term)
+//   R4 = AtAt (the linearisation coefficient c is formed from it in pass 2)
 // and block partial sums of (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi), psi^5, 8 pi psi^6 S_i.
 template <int ORDER, class F>
 __device__ __forceinline__ void outer_cell(const F &u, const F &w0, const F &w1, const F &w2, const Coef<double> &cf,
@@ -746,51 +746,6 @@ __device__ __forceinline__ void outer_cell(const F &u, const F &w0, const F &w1,
     mom[2] = Je[3];
 }
 
-template <int ORDER, int BC>
-__global__ void __launch_bounds__(256) k_outer_pass1(Geo g, Coef<double> cf, const double *__restrict__ x,
-                                                     const double *__restrict__ src, double *__restrict__ R,
-                                                     double *__restrict__ partial)
-{
-    const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
-    const int sy = g.n[0], sz = g.n[0] * g.n[1];
-    double acc[5] = {0, 0, 0, 0, 0};
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-        int i = (int)(p % g.n[0]);
-        size_t rest = p / g.n[0];
-        int j = (int)(rest % g.n[1]);
-        int k = (int)(rest / g.n[1]);
-        double lu, aa, mom[3];
-        if (is_interior(g, i, j, k, halo<ORDER>())) {
-            AccI<double> a0{x + p, sy, sz}, a1{x + N + p, sy, sz}, a2{x + 2 * N + p, sy, sz}, a3{x + 3 * N + p, sy, sz};
-            outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom);
-        } else {
-            AccB<double, BC> a0{x, &g, i, j, k}, a1{x + N, &g, i, j, k}, a2{x + 2 * N, &g, i, j, k},
-                a3{x + 3 * N, &g, i, j, k};
-            outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom);
-        }
-        double psi = psi_background(g, i, j, k) + x[p];
-        double rho0 = src[p], rho2 = src[N + p];
-        double ip = 1.0 / psi;
-        double p2 = psi * psi, p4 = p2 * p2, p5 = p4 * psi, p6 = p5 * psi;
-        double ip2 = ip * ip, ip4 = ip2 * ip2, ip7 = ip4 * ip2 * ip, ip8 = ip4 * ip4;
-        double nonlin = 0.125 * aa * ip7 + 2.0 * kPi * (rho0 * p5 + rho2 * psi);
-        R[p] = lu + nonlin;
-        R[4 * N + p] = -0.875 * aa * ip8 + 2.0 * kPi * (5.0 * rho0 * p4 + rho2);
-        acc[0] += nonlin;
-        acc[1] += p5;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double s = 8.0 * kPi * p6 * src[(2 + a) * N + p];
-            R[(1 + a) * N + p] = mom[a] - s;
-            acc[2 + a] += s;
-        }
-    }
-    double r[5];
-    block_sum<5>(acc, r);
-    if (threadIdx.x == 0)
-        for (int a = 0; a < 5; ++a) partial[blockIdx.x * 5 + a] = r[a];
-}
-
 // K^2 (integrability or fixed) and the momentum-source means from the pass-1 sums.
 static __global__ void k_outer_scalars(Scalars *s, size_t N, int kmode_integrability, double K2_fixed, int periodic)
 {
@@ -811,8 +766,8 @@ __device__ __forceinline__ float absnanf(float x) { return (x == x) ? fabsf(x) :
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__restrict__ x, const double *__restrict__ R,
-                                                     const Scalars *__restrict__ s, T *__restrict__ f,
-                                                     T *__restrict__ ab, double *__restrict__ HM,
+                                                     const double *__restrict__ src, const Scalars *__restrict__ s,
+                                                     T *__restrict__ f, T *__restrict__ ab, double *__restrict__ HM,
                                                      double *__restrict__ partial, int split)
 {
     const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
@@ -839,13 +794,17 @@ __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__rest
             mxf[2] = fmaxf(mxf[2], absnanf(ip6 * w1));
             mxf[3] = fmaxf(mxf[3], absnanf(ip6 * w2));
             const size_t q = split ? (((i + j + k) & 1) ? N / 2 : 0) + (p >> 1) : p;
-            const float ps2 = ps * ps;
+            // c = dF_psi/du = -(7/8) psi^-8 AtAt + 2 pi (5 rho0 psi^4 + rho2) - (5/12) K^2 psi^4
+            const float ps2 = ps * ps, ps4 = ps2 * ps2, ip4 = ip2 * ip2;
+            const float c = -0.875f * (ip4 * ip4) * (float)R[4 * N + p] +
+                            (float)(2.0 * kPi) * (5.0f * (float)src[p] * ps4 + (float)src[N + p]) -
+                            (float)(5.0 / 12.0 * K2) * ps4;
             f[q] = (T)(-ip5 * fp);
             f[N + q] = (T)(-w0);
             f[2 * N + q] = (T)(-w1);
             f[3 * N + q] = (T)(-w2);
             ab[q] = (T)ip5;
-            ab[N + q] = (T)(ip5 * ((float)R[4 * N + p] - (float)(5.0 / 12.0 * K2) * (ps2 * ps2)));
+            ab[N + q] = (T)(ip5 * c);
             continue;
         }
         const double ip = 1.0 / psi, ip2 = ip * ip, ip5 = ip2 * ip2 * ip, ip6 = ip5 * ip;
@@ -866,8 +825,11 @@ __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__rest
             f[N + q] = (T)(-Fw0);
             f[2 * N + q] = (T)(-Fw1);
             f[3 * N + q] = (T)(-Fw2);
+            const double ip4 = ip2 * ip2;
+            const double c = -0.875 * (ip4 * ip4) * R[4 * N + p] + 2.0 * kPi * (5.0 * src[p] * p4 + src[N + p]) -
+                             (5.0 / 12.0) * K2 * p4;
             ab[q] = (T)ip5;
-            ab[N + q] = (T)(ip5 * (R[4 * N + p] - (5.0 / 12.0) * K2 * p4));
+            ab[N + q] = (T)(ip5 * c);
         }
     }
     if (fast)

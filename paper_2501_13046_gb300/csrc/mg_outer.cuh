@@ -93,19 +93,18 @@ __global__ void __launch_bounds__(256) k_outer_div(Geo g, OuterCoef oc, const do
     }
 }
 
-// Lap u, AtAt and the momentum operator at an interior-box cell from pass A's q, div.
-template <int ORDER>
-__device__ __forceinline__ void outer_cell_q(const double *x, const double *D, size_t N, size_t p, int sy, int sz,
-                                             const OuterCoef &oc, double &lu, double &aa, double mom[3])
+// Lap u, AtAt and the momentum operator at a cell from pass A's q, div W (accessors: interior
+// box, or wrapping on periodic boxes, where q and div W are exact at the wrapped cells).
+template <int ORDER, class F>
+__device__ __forceinline__ void outer_cell_qa(const F &u, const F &w0, const F &w1, const F &w2, const F &q0,
+                                              const F &q1, const F &q2, double dv, const OuterCoef &oc, double &lu,
+                                              double &aa, double mom[3])
 {
-    AccI<double> u{x + p, sy, sz}, w0{x + N + p, sy, sz}, w1{x + 2 * N + p, sy, sz}, w2{x + 3 * N + p, sy, sz};
-    AccI<double> q0{D + p, sy, sz}, q1{D + N + p, sy, sz}, q2{D + 2 * N + p, sy, sz};
     lu = lapw<ORDER>(u, oc.k1, oc.nk2, oc.k0);
     mom[0] = lapw<ORDER>(w0, oc.m1[0], oc.nm2[0], oc.m0[0]) + d1w<ORDER, 0>(q0, oc.q1[0], oc.q2[0]);
     mom[1] = lapw<ORDER>(w1, oc.m1[1], oc.nm2[1], oc.m0[1]) + d1w<ORDER, 1>(q1, oc.q1[1], oc.q2[1]);
     mom[2] = lapw<ORDER>(w2, oc.m1[2], oc.nm2[2], oc.m0[2]) + d1w<ORDER, 2>(q2, oc.q1[2], oc.q2[2]);
     // At_ab = G_ab + G_ba - (2/3) delta_ab div, G_ab = D_a W_b; the diagonal from pass A
-    const double dv = D[3 * N + p];
     const double g00 = dv - q0(0, 0, 0), g11 = dv - q1(0, 0, 0), g22 = dv - q2(0, 0, 0);
     const double s01 = d1w<ORDER, 0>(w1, oc.c1[0], oc.c2[0]) + d1w<ORDER, 1>(w0, oc.c1[1], oc.c2[1]);
     const double s02 = d1w<ORDER, 0>(w2, oc.c1[0], oc.c2[0]) + d1w<ORDER, 2>(w0, oc.c1[2], oc.c2[2]);
@@ -116,9 +115,19 @@ __device__ __forceinline__ void outer_cell_q(const double *x, const double *D, s
     aa = fma(2.0, off, fma(a00, a00, fma(a11, a11, a22 * a22)));
 }
 
+template <int ORDER>
+__device__ __forceinline__ void outer_cell_q(const double *x, const double *D, size_t N, size_t p, int sy, int sz,
+                                             const OuterCoef &oc, double &lu, double &aa, double mom[3])
+{
+    AccI<double> u{x + p, sy, sz}, w0{x + N + p, sy, sz}, w1{x + 2 * N + p, sy, sz}, w2{x + 3 * N + p, sy, sz};
+    AccI<double> q0{D + p, sy, sz}, q1{D + N + p, sy, sz}, q2{D + 2 * N + p, sy, sz};
+    outer_cell_qa<ORDER>(u, w0, w1, w2, q0, q1, q2, D[3 * N + p], oc, lu, aa, mom);
+}
+
 // Nonlinear terms and outputs at cell p (shared by the interior and shell paths):
 //   R0 = Lap u + (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi)
-//   R1..3 = mom_i - 8 pi psi^6 S_i,   R4 = -(7/8) psi^-8 AtAt + 2 pi (5 rho0 psi^4 + rho2)
+//   R1..3 = mom_i - 8 pi psi^6 S_i,   R4 = AtAt (pass 2 forms the linearisation coefficient from it,
+//   in the inner solve's precision)
 __device__ __forceinline__ void outer_tail(const Geo &g, int i, int j, int k, size_t p, size_t N, double lu, double aa,
                                            const double mom[3], const double *x, const double *src, double *R,
                                            double acc[5])
@@ -127,10 +136,10 @@ __device__ __forceinline__ void outer_tail(const Geo &g, int i, int j, int k, si
     const double rho0 = src[p], rho2 = src[N + p];
     const double ip = 1.0 / psi;
     const double p2 = psi * psi, p4 = p2 * p2, p5 = p4 * psi, p6 = p5 * psi;
-    const double ip2 = ip * ip, ip4 = ip2 * ip2, ip7 = ip4 * ip2 * ip, ip8 = ip4 * ip4;
+    const double ip2 = ip * ip, ip4 = ip2 * ip2, ip7 = ip4 * ip2 * ip;
     const double nonlin = fma(0.125 * aa, ip7, (2.0 * kPi) * fma(rho0, p5, rho2 * psi));
     R[p] = lu + nonlin;
-    R[4 * N + p] = fma(-0.875 * aa, ip8, (2.0 * kPi) * fma(5.0 * rho0, p4, rho2));
+    R[4 * N + p] = aa;
     acc[0] += nonlin;
     acc[1] += p5;
     const double s8 = (8.0 * kPi) * p6;
@@ -142,16 +151,23 @@ __device__ __forceinline__ void outer_tail(const Geo &g, int i, int j, int k, si
     }
 }
 
-// Shell cells: the direct tensor-product form with boundary values, out of line so that the
-// interior path keeps its registers.  out = (Lap u, AtAt, mom_0, mom_1, mom_2).
+// Shell cells, out of line so that the interior path keeps its registers.  Periodic boxes: the
+// q form with wrapping accessors; Robin boxes: the direct tensor-product form with boundary
+// values (a ghost value of q is not the Robin value of q).  out = (Lap u, AtAt, mom_0..2).
 template <int ORDER, int BC>
-__device__ __noinline__ void outer_shell_cell(const Geo &g, const Coef<double> &cf, const double *x, int i, int j,
-                                              int k, double *out)
+__device__ __noinline__ void outer_shell_cell(const Geo &g, const Coef<double> &cf, const OuterCoef &oc,
+                                              const double *x, const double *D, int i, int j, int k, double *out)
 {
     const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
     AccB<double, BC> a0{x, &g, i, j, k}, a1{x + N, &g, i, j, k}, a2{x + 2 * N, &g, i, j, k}, a3{x + 3 * N, &g, i, j, k};
     double lu, aa, mom[3];
-    outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom);
+    if constexpr (BC == BC_PERIODIC) {
+        AccB<double, BC> q0{D, &g, i, j, k}, q1{D + N, &g, i, j, k}, q2{D + 2 * N, &g, i, j, k};
+        const size_t p = (size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k);
+        outer_cell_qa<ORDER>(a0, a1, a2, a3, q0, q1, q2, D[3 * N + p], oc, lu, aa, mom);
+    } else {
+        outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom);
+    }
     out[0] = lu;
     out[1] = aa;
     out[2] = mom[0];
@@ -185,7 +201,7 @@ __global__ void __launch_bounds__(256, 2) k_outer_pass1q(Geo g, Coef<double> cf,
         for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; shell_cell(g, rg.G, t, i, j, k); t += stride) {
             const size_t p = (size_t)i + (size_t)sy * j + (size_t)sz * k;
             double o[5];
-            outer_shell_cell<ORDER, BC>(g, cf, x, i, j, k, o);
+            outer_shell_cell<ORDER, BC>(g, cf, oc, x, D, i, j, k, o);
             const double mom[3] = {o[2], o[3], o[4]};
             outer_tail(g, i, j, k, p, N, o[0], o[1], mom, x, src, R, acc);
         }
