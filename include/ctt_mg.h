@@ -77,8 +77,10 @@ typedef struct {
     long long spin_limit; /* bound on any device-side wait, in polls (default 1<<24)              */
     int inner_cycles;     /* V-cycles per outer iteration, 0 = auto (1 for MG_FP64, 2 for MG_MIXED) */
     int block_threads;    /* threads per block of the global-memory stencil kernels: 0 = 256, else 64, 128 or 256 */
-    int smoother;         /* 0 = auto: the TMA-tiled colour pass on FP32 levels with nx, ny multiples of 8,
-                             >= 16 and nz >= 8, the global-memory pass elsewhere; 1 = global-memory pass on every level */
+    int smoother;         /* 0 = auto: the TMA-tiled colour pass and restriction on FP32 levels with nx, ny
+                             multiples of 8, >= 16 and nz >= 8, the next-to-coarsest level and the coarsest in one
+                             CTA when small, global-memory kernels elsewhere; 1 = one global-memory kernel per
+                             step on every level */
     int cycle;            /* coarse-level visits per cycle: 0 or 1 = V-cycle (default), 2 = W-cycle           */
     double omega;         /* red-black relaxation weight in (0, 2); 0 = 1.0 (plain Gauss-Seidel per colour)   */
 } mg_config;

@@ -382,6 +382,11 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         if ((st = enter(x)) != MG_OK) break;
         e = cudaMemsetAsync(x->ws, 0, lay.total, x->stream);
         if (e != cudaSuccess) { st = fail(MG_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e)); break; }
+        if (x->dense && x->nlev >= 2) {
+            const LevelBufs &L1 = x->lev[x->nlev - 2], &Lc = x->lev[x->nlev - 1];
+            x->fused = cfg->smoother == 0 && L1.N <= (size_t)kFusedMaxCells &&
+                       fused_smem_bytes((int)L1.N, (int)Lc.N, x->tbytes) <= kMaxCoarseSmem;
+        }
         if (x->dense) {
             const int O = cfg->order;
             st = x->tbytes == 8 ? (O == 2 ? engine_dense_setup<double, 2>(x) : engine_dense_setup<double, 4>(x))

@@ -192,4 +192,154 @@ __global__ void __launch_bounds__(256) k_dense_apply(const T *__restrict__ Gpsi,
     if (lane == 0) e[row] = acc;
 }
 
+// ---------------------------------------------------------------------------------------
+// The bottom of a cycle in one CTA: when the next-to-coarsest level (l = Lc - 1) is small, its
+// pre-smoothing, the residual's 8-child restriction, the coarsest solve by the dense inverses,
+// the trilinear prolongation and the post-smoothing run in shared memory in one launch (the same
+// operator, colour passes and Jacobi-within-colour reads as the per-kernel path).  Level l is
+// colour-split in global memory and plain in shared memory; the coarsest level is plain.
+constexpr int kFusedMaxCells = 1728;   // next-to-coarsest level up to 12^3 cells
+
+__host__ __device__ inline size_t fused_smem_bytes(int N1, int Nc, size_t tb)
+{
+    return (14 * (size_t)N1 + 8 * (size_t)Nc) * tb;
+}
+
+template <typename T, int ORDER, int BC>
+__global__ void __launch_bounds__(1024) k_coarse_cycle(Geo g, Coef<T> cf, Geo gc, const T *__restrict__ f,
+                                                       const T *__restrict__ ab, const T *__restrict__ e_in,
+                                                       T *__restrict__ e_out, int zero, int nu_pre, int nu_post,
+                                                       const T *__restrict__ Gpsi, int mpsi,
+                                                       const T *__restrict__ GW, int mw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int N = g.n[0] * g.n[1] * g.n[2], Nc = gc.n[0] * gc.n[1] * gc.n[2];
+    const int tid = threadIdx.x, bs = blockDim.x;
+    T *cur = reinterpret_cast<T *>(smem_raw);
+    T *alt = cur + 4 * N;
+    T *fs = alt + 4 * N;
+    T *cs = fs + 4 * N;
+    T *fc = cs + 2 * N;
+    T *ec = fc + 4 * Nc;
+    auto ijk = [&](int q, int &i, int &j, int &k) {
+        i = q % g.n[0];
+        j = (q / g.n[0]) % g.n[1];
+        k = q / (g.n[0] * g.n[1]);
+    };
+    auto split_idx = [&](int q) {
+        int i, j, k;
+        ijk(q, i, j, k);
+        return (((i + j + k) & 1) ? N / 2 : 0) + (q >> 1);
+    };
+    for (int q = tid; q < N; q += bs) {
+        const int sq = split_idx(q);
+        for (int a = 0; a < 4; ++a) {
+            fs[a * N + q] = f[a * N + sq];
+            cur[a * N + q] = zero ? (T)0 : e_in[a * N + sq];
+        }
+        cs[q] = ab[sq];
+        cs[N + q] = ab[N + sq];
+    }
+    __syncthreads();
+    auto sweeps = [&](int n) {
+        for (int s = 0; s < n; ++s)
+            for (int colour = 0; colour < 2; ++colour) {
+                for (int q = tid; q < N; q += bs) {
+                    int i, j, k;
+                    ijk(q, i, j, k);
+                    if (((i + j + k) & 1) == colour) {
+                        T Je[4], ctr[4];
+                        AccB<T, BC> a0{cur, &g, i, j, k}, a1{cur + N, &g, i, j, k}, a2{cur + 2 * N, &g, i, j, k},
+                            a3{cur + 3 * N, &g, i, j, k};
+                        apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
+                        alt[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * cf.dl + cs[N + q]) * cf.iom);
+                        for (int a = 0; a < 3; ++a)
+                            alt[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
+                    } else {
+                        for (int a = 0; a < 4; ++a) alt[a * N + q] = cur[a * N + q];
+                    }
+                }
+                __syncthreads();
+                T *t = cur;
+                cur = alt;
+                alt = t;
+            }
+    };
+    sweeps(nu_pre);
+    // residual r = f - J e at every cell (into alt), then the 8-child means
+    for (int q = tid; q < N; q += bs) {
+        int i, j, k;
+        ijk(q, i, j, k);
+        T Je[4], ctr[4];
+        AccB<T, BC> a0{cur, &g, i, j, k}, a1{cur + N, &g, i, j, k}, a2{cur + 2 * N, &g, i, j, k},
+            a3{cur + 3 * N, &g, i, j, k};
+        apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
+        for (int a = 0; a < 4; ++a) alt[a * N + q] = fs[a * N + q] - Je[a];
+    }
+    __syncthreads();
+    for (int t = tid; t < 4 * Nc; t += bs) {
+        const int a = t / Nc, c = t - a * Nc;
+        const int I = c % gc.n[0], J = (c / gc.n[0]) % gc.n[1], K = c / (gc.n[0] * gc.n[1]);
+        T sum = 0;
+        for (int d = 0; d < 8; ++d) {
+            const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
+            sum += alt[a * N + i + g.n[0] * (j + g.n[1] * k)];
+        }
+        fc[t] = sum * (T)0.125;
+    }
+    __syncthreads();
+    // coarsest level: e_c = G f_c (psi rows: Gpsi, W rows: GW), one warp per row
+    for (int r = tid >> 5; r < 4 * Nc; r += bs >> 5) {
+        T acc = 0;
+        if (r < Nc) {
+            const T *gr = Gpsi + (size_t)r * mpsi;
+            for (int j = tid & 31; j < Nc; j += 32) acc = fma(gr[j], fc[j], acc);
+        } else {
+            const T *gr = GW + (size_t)(r - Nc) * mw;
+            for (int j = tid & 31; j < 3 * Nc; j += 32) acc = fma(gr[j], fc[Nc + j], acc);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if ((tid & 31) == 0) ec[r] = acc;
+    }
+    __syncthreads();
+    // trilinear prolongation (3/4, 1/4 per axis; coarse boundary values from the BC) into e
+    const int ncx = gc.n[0], ncy = gc.n[1], ncz = gc.n[2];
+    for (int q = tid; q < N; q += bs) {
+        int i, j, k;
+        ijk(q, i, j, k);
+        const int I = i >> 1, J = j >> 1, K = k >> 1;
+        const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
+        T s4[4] = {0, 0, 0, 0};
+        for (int d = 0; d < 8; ++d) {
+            const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
+            const int cx = I + dx * sx, cy = J + dy * sy, cz = K + dz * sz;
+            double w = (dx ? 0.25 : 0.75) * (dy ? 0.25 : 0.75) * (dz ? 0.25 : 0.75);
+            int bx = cx, by = cy, bz = cz;
+            if (BC == BC_PERIODIC) {
+                bx += bx < 0 ? ncx : 0; bx -= bx >= ncx ? ncx : 0;
+                by += by < 0 ? ncy : 0; by -= by >= ncy ? ncy : 0;
+                bz += bz < 0 ? ncz : 0; bz -= bz >= ncz ? ncz : 0;
+            } else {
+                bx = min(max(bx, 0), ncx - 1);
+                by = min(max(by, 0), ncy - 1);
+                bz = min(max(bz, 0), ncz - 1);
+                if (bx != cx || by != cy || bz != cz) {
+                    const double ax = cellx(gc, 0, bx), ay = cellx(gc, 1, by), az = cellx(gc, 2, bz);
+                    const double gx = cellx(gc, 0, cx), gy = cellx(gc, 1, cy), gz = cellx(gc, 2, cz);
+                    w *= sqrt(ax * ax + ay * ay + az * az) / sqrt(gx * gx + gy * gy + gz * gz);
+                }
+            }
+            const int c = bx + ncx * (by + ncy * bz);
+            for (int a = 0; a < 4; ++a) s4[a] = fma((T)w, ec[a * Nc + c], s4[a]);
+        }
+        for (int a = 0; a < 4; ++a) cur[a * N + q] += s4[a];
+    }
+    __syncthreads();
+    sweeps(nu_post);
+    for (int q = tid; q < N; q += bs) {
+        const int sq = split_idx(q);
+        for (int a = 0; a < 4; ++a) e_out[a * N + sq] = cur[a * N + q];
+    }
+}
+
 }  // namespace ctt

@@ -232,6 +232,7 @@ struct mg_ctx {
     double *R = nullptr;     // 5N: outer pass-1 output
     double *D = nullptr;     // 4N: q_0, q_1, q_2, div W of the FP64 residual's pass A
     int dense = 0;           // 1: the coarsest level is solved with the dense inverses below
+    int fused = 0;           // 1: the next-to-coarsest level's cycle runs in one CTA (k_coarse_cycle)
     int mpsi = 0, mw = 0;    // orders of the (bordered) psi and W systems
     void *Gpsi = nullptr;    // mpsi^2 T: inverse of the psi row (per outer iteration)
     void *GW = nullptr;      // mw^2 T: inverse of the W rows (once, at creation)

@@ -172,6 +172,24 @@ mg_status enqueue_cycle(mg_ctx *x, int l, bool zero)
         L.curB = 0;
         return enqueue_coarse<T, ORDER>(x, Lc);
     }
+    if (x->fused && l == Lc - 1) {   // this level and the coarsest in one CTA
+        LevelBufs &C = x->lev[Lc];
+        if (x->join_pending) {
+            CK(cudaStreamWaitEvent(x->stream, x->ev_join, 0));
+            x->join_pending = false;
+        }
+        const T *ein = zero ? (const T *)L.eA : (const T *)L.cur();
+        const size_t smem = fused_smem_bytes((int)L.N, (int)C.N, sizeof(T));
+        dispatch_bc(x->cfg.bc, [&](auto B) {
+            k_coarse_cycle<T, ORDER, decltype(B)::value><<<1, 1024, smem, x->stream>>>(
+                L.geo, make_coef<T>(L.geo, x->cfg.order, x->omega), C.geo, (const T *)L.f, (const T *)L.c, ein,
+                (T *)L.eA, zero ? 1 : 0, x->cfg.nu_pre, x->cfg.nu_post, (const T *)x->Gpsi, x->mpsi,
+                (const T *)x->GW, x->mw);
+        });
+        CK(cudaGetLastError());
+        L.curB = 0;
+        return MG_OK;
+    }
     if (zero) {
         L.curB = 0;
         CK(cudaMemsetAsync(L.eA, 0, 4 * L.N * sizeof(T), x->stream));
@@ -322,6 +340,9 @@ mg_status engine_prepare(mg_ctx *x)
             cudaFuncSetAttribute(k_coarse_psi_direct<T, ORDER, decltype(B)::value>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxCoarseSmem) != cudaSuccess)
             st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(coarse kernels)");
+        if (cudaFuncSetAttribute(k_coarse_cycle<T, ORDER, decltype(B)::value>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxCoarseSmem) != cudaSuccess)
+            st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(k_coarse_cycle)");
         if (cudaFuncSetAttribute(k_gauss_jordan<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kMaxCoarseSmem) != cudaSuccess ||
             cudaFuncSetAttribute(k_gauss_jordan<double, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
