@@ -227,6 +227,47 @@ def kernel_rooflines(mg, ctx, N):
                                   "unit": "GB/s", "peak": pk["hbm_gbs"], "frac": rr_gbs / pk["hbm_gbs"]}}
 
 
+def unet_fwd_flops(n_net):
+    """Algorithmic flops of one forward pass of the warm-start U-Net at n_net^3 (3x3x3 convs:
+    2 x 27 x Cin x Cout per voxel at the level's resolution; the 1x1 head and glue are ignored)."""
+    from paper_2501_13046_gb300 import warmstart as WS
+    level = {"e0a": 0, "e0": 0, "e1a": 1, "e1": 1, "e2a": 2, "e2": 2, "ba": 3, "b": 3, "d2a": 2, "d2": 2,
+             "d1a": 1, "d1": 1, "d0a": 0, "d0": 0}
+    return sum(2 * 27 * cin * cout * (n_net >> level[name]) ** 3 for name, cin, cout in WS.CONVS)
+
+
+def run_infer(args):
+    """Warm-start inference alone (random weights; the cost does not depend on them): the captured
+    graph (restriction 128^3 -> 64^3, U-Net, prolongation) replayed per instance."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_13046_gb300 import fields
+    from paper_2501_13046_gb300 import warmstart as WS
+    sc = WS.Scales(s_rho=1e3, s_S=1e6, s_K=1 / 6.0, s_u=0.05, s_W=1e-5)
+    pred = WS.Predictor(WS.Params(seed=1), 128, 64, sc)
+    pred.capture()
+    p = fields.batch_instance(128, 5e-5, 20000, device="cuda")
+    u = torch.empty((128,) * 3, dtype=torch.float64, device="cuda")
+    W = torch.empty((3,) + (128,) * 3, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        pred.predict_graph(p, u, W)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        pred.predict_graph(p, u, W)
+    ev1.record()
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    pk, src = peaks()
+    tflops = unet_fwd_flops(64) / (ms * 1e-3) / 1e12
+    print(json.dumps({"workload": "infer", "ms_per_instance": ms, "instances_per_s": 1e3 / ms,
+                      "unet_fwd_gflop": unet_fwd_flops(64) / 1e9, "achieved_tflops": tflops,
+                      "bf16_peak_tflops": pk["bf16_tflops"], "frac": tflops / pk["bf16_tflops"],
+                      "peak_source": src}))
+    return 0
+
+
 def run_solve_profile(args):
     """Only the benchmarked solve: W + K mixed solves of the 128^3 workload from psi = 1 with the
     settings given (--settings inner,nu,omega; default: autotuned).  The committed launch lists and
@@ -338,7 +379,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bench", choices=["bench", "warmstart", "solve"])
+    ap.add_argument("--workload", default="bench", choices=["bench", "warmstart", "solve", "infer"])
     ap.add_argument("--settings", default="", help="solve workload: inner_cycles,nu,omega (default: autotune)")
     ap.add_argument("--train-samples", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=12)
@@ -348,6 +389,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "solve" and args.impl == "ours":
         return run_solve_profile(args)
+    if args.workload == "infer" and args.impl == "ours":
+        return run_infer(args)
     if args.impl == "reference":
         return run_reference(args)
 

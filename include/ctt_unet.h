@@ -67,7 +67,9 @@ int unet_adam(float *p, const float *g, float *m, float *v, long long n, float l
               int t, void *stream);
 
 /* Network input, 16 BF16 channels: [(rho - <rho>) s_rho, S_x s_S, S_y s_S, S_z s_S, K s_K, 0 ...],
- * rho = rho0 + rho2 (FP64 device arrays, rho2 may be NULL).  <rho> is computed on the device. */
+ * rho = rho0 + rho2 (FP64 device arrays, rho2 may be NULL).  <rho> is computed on the device.
+ * K = NaN: the value known before solving, K = -sqrt(24 pi <rho>) (periodic integrability at
+ * psi = 1, W = 0), also computed on the device. */
 int unet_pack_input(const double *rho0, const double *rho2, const double *S, double K, float s_rho, float s_S,
                     float s_K, void *x16, long long nvox, double *scratch_mean, void *stream);
 /* Network output (FP32, 4 channels) to the solver's initial guess: u = out0 s_u (zero mean on

@@ -145,6 +145,133 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(ConvArgs a)
     if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
+// Forward / input gradient on a block tile (k_conv3d_blk): one CTA = 8 (x) x 16 (y) x ZT (z)
+// output voxels, i.e. ZT M-tiles of 128 rows (row r: x = x0 + (r & 7), y = y0 + (r >> 3)).  The
+// CTA loads its input block with a one-voxel halo (wrapped) into shared memory once, in three
+// copies shifted by dx = -1, 0, +1: copy s holds, for every 8-channel chunk, z and y of the
+// halo'd block, the 8 voxels x0 + s - 1 .. x0 + s + 6 as one 128-byte row (a core matrix of the
+// K-major layout: 8 rows of 16 bytes).  For a tap (dx, dy, dz) the A operand of an M-tile is copy
+// dx + 1 seen through a descriptor that starts dy + 1 rows and zt + dz + 1 planes in: the next y
+// is the next 128-byte row (stride between 8-row groups), the next channel chunk is one chunk
+// plane further (stride between K-adjacent core matrices).  Every core matrix stays 128-byte
+// aligned and no data moves per tap: thread 0 issues all 27 x CIN/16 MMAs of every M-tile back
+// to back into TMEM, with all 27 taps' weights resident, and one commit ends the CTA's work.
+constexpr int kBlkX = 8, kBlkY = 16;
+
+template <int CIN, int COUT, int ZT>
+__host__ __device__ constexpr size_t blk_in_bytes() { return (size_t)3 * (CIN / 8) * (kBlkY + 2) * (ZT + 2) * 128; }
+template <int CIN, int COUT, int ZT>
+__host__ __device__ constexpr size_t blk_smem_bytes() { return blk_in_bytes<CIN, COUT, ZT>() + (size_t)27 * COUT * CIN * 2; }
+
+template <int CIN, int COUT, int ZT>
+__global__ void __launch_bounds__(128) k_conv3d_blk(ConvArgs a)
+{
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && ZT * COUT <= 256, "channel counts");
+    constexpr int CH = CIN / 8;
+    constexpr int BX = kBlkX + 2, BY = kBlkY + 2, BZ = ZT + 2;
+    constexpr uint32_t PLANE = BY * 128;             // one z plane of one chunk of one copy
+    constexpr uint32_t CHUNK = BZ * PLANE;           // one chunk of one copy (K-adjacent core matrices)
+    constexpr uint32_t COPY = CH * CHUNK;            // one shifted copy
+    constexpr uint32_t W_TAP = COUT * CIN * 2;       // bytes of one tap's weights
+    constexpr uint32_t SBO_B = (CIN / 8) * 128;
+    constexpr int NCOLS = ZT * COUT <= 32 ? 32 : (ZT * COUT <= 64 ? 64 : (ZT * COUT <= 128 ? 128 : 256));
+    constexpr uint32_t IDESC = idesc_bf16(kTile, COUT);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *In = smem;
+    unsigned char *Wt = smem + blk_in_bytes<CIN, COUT, ZT>();
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nx = a.n0, ny = a.n1, nz = a.n2;
+    const int ntx = nx / kBlkX, nty = ny / kBlkY;
+    int b = blockIdx.x;
+    const int x0 = (b % ntx) * kBlkX;
+    b /= ntx;
+    const int y0 = (b % nty) * kBlkY;
+    const int z0 = (b / nty) * ZT;
+    if (warp == 0) tmem_alloc(&tmem_slot, NCOLS);
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    // halo'd input block: one global load per (voxel, chunk), chunks fastest (coalesced), stored
+    // into every shifted copy that contains the voxel (block x = bx is row position bx - s of copy s)
+    for (int idx = tid; idx < BX * BY * BZ * CH; idx += 128) {
+        const int vb = idx / CH, c = idx - vb * CH;
+        const int bx = vb % BX, by = (vb / BX) % BY, bz = vb / (BX * BY);
+        const int nb = wrapi(x0 - 1 + bx, nx) + nx * (wrapi(y0 - 1 + by, ny) + ny * wrapi(z0 - 1 + bz, nz));
+        const uint4 val = *reinterpret_cast<const uint4 *>(a.x + (size_t)nb * a.xcs + a.xc0 + c * 8);
+#pragma unroll
+        for (int sft = 0; sft < 3; ++sft) {
+            const int xr = bx - sft;
+            if (xr >= 0 && xr < kBlkX)
+                *reinterpret_cast<uint4 *>(In + sft * COPY + c * CHUNK + bz * PLANE + by * 128 + xr * 16) = val;
+        }
+    }
+    // weights of the 27 taps, each in the K-major core-matrix layout of the B operand
+    for (int idx = tid; idx < 27 * COUT * CH; idx += 128) {
+        const int t = idx / (COUT * CH), rem = idx - t * (COUT * CH), r = rem / CH, c = rem - r * CH;
+        const uint4 val = *reinterpret_cast<const uint4 *>(a.w + ((size_t)t * COUT + r) * CIN + c * 8);
+        *reinterpret_cast<uint4 *>(Wt + t * W_TAP + (r >> 3) * SBO_B + c * 128 + (r & 7) * 16) = val;
+    }
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    if (tid == 0) {
+        const uint32_t in0 = smem_u32(In), w0 = smem_u32(Wt);
+        for (int zt = 0; zt < ZT; ++zt)
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                const uint32_t ab = in0 + (uint32_t)(dx + 1) * COPY + (uint32_t)(zt + dz + 1) * PLANE +
+                                    (uint32_t)(dy + 1) * 128;
+                const uint32_t bb = w0 + tap * W_TAP;
+#pragma unroll
+                for (int kk = 0; kk < CIN / 16; ++kk)
+                    mma_bf16(tmem + zt * COUT, smem_desc(ab + kk * 2 * CHUNK, CHUNK, 128),
+                             smem_desc(bb + kk * 256, 128, SBO_B), IDESC, (tap > 0 || kk > 0) ? 1u : 0u);
+            }
+        mma_commit(&mbar);
+        if (!mbar_wait_bounded(&mbar, 0, a.spin_limit)) {
+            failed = 1;
+            mbar_wait_bounded(&mbar, 0, a.spin_limit);   // a second bounded wait before smem goes away
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (!failed) {
+        const int row = warp * 32 + lane;
+        for (int zt = 0; zt < ZT; ++zt) {
+            const size_t v = (size_t)(x0 + (row & 7)) + (size_t)nx * ((y0 + (row >> 3)) + (size_t)ny * (z0 + zt));
+#pragma unroll
+            for (int cc = 0; cc < COUT / 16; ++cc) {
+                float acc[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + zt * COUT + cc * 16, acc);
+                __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    float t = acc[q] + (a.bias ? a.bias[cc * 16 + q] : 0.f);
+                    if (a.relu) t = fmaxf(t, 0.f);
+                    o[q] = __float2bfloat16_rn(t);
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(a.y + v * a.ycs + a.yc0 + cc * 16);
+                dst[0] = reinterpret_cast<uint4 *>(o)[0];
+                dst[1] = reinterpret_cast<uint4 *>(o)[1];
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(a.err, 1);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
 struct WgradArgs {
     const __nv_bfloat16 *x;
     int xcs, xc0;
@@ -292,6 +419,23 @@ namespace {
 template <int CIN, int COUT>
 int launch_fwd(const ConvArgs &a, int nvox, cudaStream_t st)
 {
+    // block-tile kernel where the grid tiles evenly and the block and all weights fit in shared memory
+    constexpr int ZT = 2;
+    constexpr size_t bsm = blk_smem_bytes<CIN, COUT, ZT>();
+    if constexpr (bsm <= 220 * 1024) {
+        if (a.n0 % kBlkX == 0 && a.n1 % kBlkY == 0 && a.n2 % ZT == 0) {
+            static bool attr_blk = false;
+            if (!attr_blk) {
+                if (cudaFuncSetAttribute(k_conv3d_blk<CIN, COUT, ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bsm) != cudaSuccess)
+                    return 2;
+                attr_blk = true;
+            }
+            const int grid = (a.n0 / kBlkX) * (a.n1 / kBlkY) * (a.n2 / ZT);
+            k_conv3d_blk<CIN, COUT, ZT><<<grid, 128, bsm, st>>>(a);
+            return cudaGetLastError() == cudaSuccess ? 0 : 3;
+        }
+    }
     constexpr size_t smem = 2 * (kTile * CIN * 2) + 2 * (COUT * CIN * 2);
     static bool attr = false;
     if (!attr) {

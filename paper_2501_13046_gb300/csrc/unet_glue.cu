@@ -217,12 +217,14 @@ __global__ void k_pack_input(const double *rho0, const double *rho2, const doubl
                              float s_S, float s_K, __nv_bfloat16 *x16, long long nvox, const double *mean)
 {
     const double mu = *mean;
+    // K given, or (NaN) its value at psi = 1 from the discrete integrability condition, K^2 = 24 pi <rho>
+    const double Kv = (K == K) ? K : -sqrt(24.0 * 3.14159265358979323846 * fmax(mu, 0.0));
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
         __align__(16) __nv_bfloat16 o[16];
         double r = rho0[v] + (rho2 ? rho2[v] : 0.0);
         o[0] = __float2bfloat16_rn((float)((r - mu) * s_rho));
         for (int a = 0; a < 3; ++a) o[1 + a] = __float2bfloat16_rn((float)(S[a * nvox + v] * s_S));
-        o[4] = __float2bfloat16_rn((float)(K * s_K));
+        o[4] = __float2bfloat16_rn((float)(Kv * s_K));
         for (int c = 5; c < 16; ++c) o[c] = __float2bfloat16_rn(0.f);
         uint4 *d = reinterpret_cast<uint4 *>(x16 + v * 16);
         d[0] = reinterpret_cast<uint4 *>(o)[0];

@@ -109,3 +109,63 @@ def test_conv_weight_gradient(U, cin, cout):
     assert int(err.item()) == 0
     scale = R.conv_wgrad(np.abs(x), np.abs(dy))   # FP32 accumulation over 1024 voxels
     np.testing.assert_array_less(np.abs(dw.cpu().numpy() - ref), 1e-5 * scale + 1e-6)
+
+
+BLOCK_SHAPES = [(16, 16, 4), (8, 32, 6)]   # nx % 8 == 0, ny % 16 == 0, nz even: the block-tile kernel
+BLOCK_PAIRS = [(16, 16), (16, 32), (16, 48), (32, 16), (32, 32), (32, 64), (48, 16)]
+
+
+@pytest.mark.parametrize("cin,cout", BLOCK_PAIRS)
+@pytest.mark.parametrize("shape", BLOCK_SHAPES)
+def test_conv_forward_block_tiles(U, cin, cout, shape):
+    """Volumes the block-tile kernel takes (8 x 16 x 2 voxel tiles, input block and all weights in
+    shared memory, shifted descriptors per tap), against the FP64 oracle with the same bound."""
+    nz, ny, nx = shape[2], shape[1], shape[0]
+    rng = np.random.default_rng(cin * 977 + cout + nx)
+    x = R.bf16_round(rng.standard_normal((nz, ny, nx, cin)))
+    w = R.bf16_round(rng.standard_normal((27, cout, cin)) / np.sqrt(27 * cin))
+    b = rng.standard_normal(cout).astype(np.float32)
+    wp = torch.empty(w.shape, dtype=torch.bfloat16, device="cuda")
+    U.pack_weights(torch.from_numpy(w.astype(np.float32)).cuda(), cin, cout, 0, wp)
+    for relu in (False, True):
+        ref = R.conv_fwd(x, w, b.astype(np.float64), relu=relu)
+        y = torch.zeros((nz, ny, nx, cout), dtype=torch.bfloat16, device="cuda")
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        U.conv3d_fwd(bf16(x), wp, torch.from_numpy(b).cuda(), y, (nx, ny, nz), cin, cout, relu, err)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        scale = R.conv_fwd(np.abs(x), np.abs(w))
+        assert np.all(np.abs(tohost(y) - ref) <= 2 ** -8 * np.abs(ref) + 1e-5 * scale + 1e-6)
+
+
+def test_conv_block_tiles_on_channel_slices_and_input_gradient(U):
+    """Block-tile kernel reading channels [16, 64) of a 64-channel buffer into channels [16, 32) of
+    a 32-channel one, and the input gradient (flipped, transposed weights) of a (16 -> 48) layer."""
+    nx, ny, nz = 16, 16, 4
+    rng = np.random.default_rng(21)
+    big = R.bf16_round(rng.standard_normal((nz, ny, nx, 64)))
+    w = R.bf16_round(rng.standard_normal((27, 16, 48)) / 30)
+    ref = R.conv_fwd(big[..., 16:64], w)
+    from paper_2501_13046_gb300.unet import Slice
+    wp = torch.empty(w.shape, dtype=torch.bfloat16, device="cuda")
+    U.pack_weights(torch.from_numpy(w.astype(np.float32)).cuda(), 48, 16, 0, wp)
+    ybuf = torch.full((nz, ny, nx, 32), 7.0, dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U.conv3d_fwd(Slice(bf16(big), 16, 48), wp, None, Slice(ybuf, 16, 16), (nx, ny, nz), 48, 16, False, err)
+    torch.cuda.synchronize()
+    out = tohost(ybuf)
+    assert np.all(out[..., :16] == 7.0)
+    scale = R.conv_fwd(np.abs(big[..., 16:64]), np.abs(w))
+    assert np.all(np.abs(out[..., 16:32] - ref) <= 2 ** -8 * np.abs(ref) + 1e-5 * scale + 1e-6)
+    # input gradient of a 16 -> 48 convolution: the forward kernel with 48 -> 16 packed weights
+    dy = R.bf16_round(rng.standard_normal((nz, ny, nx, 48)))
+    w2 = R.bf16_round(rng.standard_normal((27, 48, 16)) / 10)
+    ref2 = R.conv_dgrad(dy, w2)
+    wp2 = torch.empty((27, 16, 48), dtype=torch.bfloat16, device="cuda")
+    U.pack_weights(torch.from_numpy(w2.astype(np.float32)).cuda(), 16, 48, 1, wp2)
+    dx = torch.zeros((nz, ny, nx, 16), dtype=torch.bfloat16, device="cuda")
+    U.conv3d_fwd(bf16(dy), wp2, None, dx, (nx, ny, nz), 48, 16, False, err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    scale2 = R.conv_dgrad(np.abs(dy), np.abs(w2))
+    assert np.all(np.abs(tohost(dx) - ref2) <= 2 ** -8 * np.abs(ref2) + 1e-5 * scale2 + 1e-6)

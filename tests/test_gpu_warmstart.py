@@ -165,3 +165,32 @@ def test_training_lowers_the_loss(mods):
     torch.cuda.synchronize()
     assert int(net.err.item()) == 0
     assert max(losses) < 3 * losses[0] and np.mean(losses[-5:]) < 0.7 * losses[0], losses
+
+
+def test_captured_inference_matches_eager(mods):
+    """The warm-start inference captured once as a CUDA graph (restriction 128^3 -> 64^3, network,
+    prolongation; K channel derived on the device from <rho>) gives the eager result bit for bit
+    on two different instances replayed one after the other, and K = None equals the explicit
+    pre-solve value -sqrt(24 pi <rho>)."""
+    U, WS, fields, mg = mods
+    P = WS.Params(seed=7)
+    sc = WS.Scales(s_rho=1e3, s_S=1e6, s_K=1 / 6.0, s_u=0.05, s_W=1e-5)
+    pred = WS.Predictor(P, 128, 64, sc)
+    pred.capture()
+    for seed in (20000, 20001):
+        p = fields.batch_instance(128, 5e-5, seed, device="cuda")
+        u0, W0 = torch.empty((128,) * 3, dtype=torch.float64, device="cuda"), \
+            torch.empty((3,) + (128,) * 3, dtype=torch.float64, device="cuda")
+        u1, W1 = torch.empty_like(u0), torch.empty_like(W0)
+        pred.predict(p, None, u0, W0)
+        pred.predict_graph(p, u1, W1)
+        torch.cuda.synchronize()
+        assert int(pred.net.err.item()) == 0
+        assert torch.equal(u0, u1) and torch.equal(W0, W1)
+        assert float(u0.abs().max()) > 0
+        rho_mean = float((p["rho0"] + p["rho2"]).mean())
+        u2, W2 = torch.empty_like(u0), torch.empty_like(W0)
+        pred.predict(p, -np.sqrt(24 * np.pi * rho_mean), u2, W2)
+        torch.cuda.synchronize()
+        # the explicit value goes through the same BF16 channel; equal up to its FP64 mean order
+        assert float((u2 - u0).abs().max()) <= 1e-6 * float(u0.abs().max()) + 1e-300
