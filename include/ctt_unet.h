@@ -69,11 +69,12 @@ int unet_adam(float *p, const float *g, float *m, float *v, long long n, float l
 /* Network input, 16 BF16 channels: [(rho - <rho>) s_rho, S_x s_S, S_y s_S, S_z s_S, K s_K, 0 ...],
  * rho = rho0 + rho2 (FP64 device arrays, rho2 may be NULL).  <rho> is computed on the device.
  * K = NaN: the value known before solving, K = -sqrt(24 pi <rho>) (periodic integrability at
- * psi = 1, W = 0), also computed on the device. */
+ * psi = 1, W = 0), also computed on the device.  scratch_mean: device array of at least 264
+ * doubles (means and the block partials of their deterministic reduction). */
 int unet_pack_input(const double *rho0, const double *rho2, const double *S, double K, float s_rho, float s_S,
                     float s_K, void *x16, long long nvox, double *scratch_mean, void *stream);
 /* Network output (FP32, 4 channels) to the solver's initial guess: u = out0 s_u (zero mean on
- * periodic boxes), W_i = out_i s_W (zero mean), FP64. */
+ * periodic boxes), W_i = out_i s_W (zero mean), FP64.  scratch_mean as for unet_pack_input. */
 int unet_unpack_output(const float *out4, float s_u, float s_W, double *u, double *W, long long nvox,
                        double *scratch_mean, void *stream);
 /* Mean of the 8 children of nfields contiguous FP64 fields, (2 m)^3 -> m^3 (m = m0 x m1 x m2). */

@@ -198,19 +198,44 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, long long n
     }
 }
 
-// mean of one FP64 field (one block; small problems) -> *mean
-__global__ void k_mean(const double *a, const double *b, long long n, double *mean)
+// Mean of one FP64 field (a + b when b is given), deterministic: kMeanBlocks blocks each sum a
+// fixed grid-stride subset into partial[block], then one block adds the partials in order.
+constexpr int kMeanBlocks = 256;
+
+__device__ __forceinline__ double block_reduce_sum(double s)
 {
     __shared__ double sh[kT];
-    double s = 0.0;
-    for (long long q = threadIdx.x; q < n; q += blockDim.x) s += a[q] + (b ? b[q] : 0.0);
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *mean = sh[0] / (double)n;
+    return sh[0];
+}
+
+__global__ void k_mean_partial(const double *a, const double *b, long long n, double *partial)
+{
+    double s = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        s += a[q] + (b ? b[q] : 0.0);
+    const double t = block_reduce_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void k_mean_finish(const double *partial, int np, long long n, double *mean)
+{
+    double s = 0.0;
+    for (int q = threadIdx.x; q < np; q += blockDim.x) s += partial[q];
+    const double t = block_reduce_sum(s);
+    if (threadIdx.x == 0) *mean = t / (double)n;
+}
+
+// scratch: means in [0, 8), block partials in [8, 8 + kMeanBlocks)
+void launch_mean(const double *a, const double *b, long long n, double *scratch, int slot, cudaStream_t st)
+{
+    k_mean_partial<<<kMeanBlocks, kT, 0, st>>>(a, b, n, scratch + 8);
+    k_mean_finish<<<1, kT, 0, st>>>(scratch + 8, kMeanBlocks, n, scratch + slot);
 }
 
 __global__ void k_pack_input(const double *rho0, const double *rho2, const double *S, double K, float s_rho,
@@ -396,7 +421,7 @@ int unet_pack_input(const double *rho0, const double *rho2, const double *S, dou
 {
     if (!rho0 || !S || !x16 || !scratch_mean) return 1;
     cudaStream_t st = (cudaStream_t)stream;
-    k_mean<<<1, kT, 0, st>>>(rho0, rho2, nvox, scratch_mean);
+    launch_mean(rho0, rho2, nvox, scratch_mean, 0, st);
     k_pack_input<<<blocks(nvox), kT, 0, st>>>(rho0, rho2, S, K, s_rho, s_S, s_K, (__nv_bfloat16 *)x16, nvox,
                                                scratch_mean);
     return ok();
@@ -410,7 +435,7 @@ int unet_unpack_output(const float *out4, float s_u, float s_W, double *u, doubl
     k_unpack_output<<<blocks(nvox), kT, 0, st>>>(out4, s_u, s_W, u, W, nvox);
     for (int a = 0; a < 4; ++a) {
         double *f = a == 0 ? u : W + (a - 1) * nvox;
-        k_mean<<<1, kT, 0, st>>>(f, nullptr, nvox, scratch_mean + a);
+        launch_mean(f, nullptr, nvox, scratch_mean, a, st);
         k_sub_mean<<<blocks(nvox), kT, 0, st>>>(f, nvox, scratch_mean + a);
     }
     return ok();

@@ -98,7 +98,7 @@ class Net:
         self.cat2 = bf(sz[2], CH[3] + CH[2])
         self.out = torch.zeros((sz[0], sz[0], sz[0], COUT), dtype=torch.float32, device=device)
         self.err = torch.zeros(1, dtype=torch.int32, device=device)
-        self.mean = torch.zeros(8, dtype=torch.float64, device=device)
+        self.mean = torch.zeros(264, dtype=torch.float64, device=device)   # means + reduction partials
         if train:
             self.g = {k: torch.zeros_like(v) for k, v in self.a.items()}
             self.gcat0, self.gcat1, self.gcat2 = (torch.zeros_like(self.cat0), torch.zeros_like(self.cat1),
