@@ -279,7 +279,7 @@ def run_solve_profile(args):
     p = make_problem()
     sp = torch.cuda.current_stream().cuda_stream
     src = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (p["rho0"], p["rho2"], *p["S"])]
-    cfg = mg.config_for(p, mg.MG_MIXED, tol=WORKLOAD["tol"], max_outer=60)
+    cfg = mg.config_for(p, mg.MG_MIXED, tol=WORKLOAD["tol"], max_outer=60, nested=args.nested)
     if args.settings:
         inner, nu, om = args.settings.split(",")
         apply_tuned(cfg, {"inner_cycles": int(inner), "nu": int(nu), "omega": float(om)})
@@ -292,7 +292,8 @@ def run_solve_profile(args):
     secs, info = solve_loop(mg, torch, ctx, args.steps, stream)
     print(json.dumps({"workload": "solve", "solves_per_s": args.steps / secs, "outer_iters": info["outer_iters"],
                       "launches_per_solve": info["kernel_launches"], "inner_cycles": cfg.inner_cycles,
-                      "nu": cfg.nu_pre, "omega": cfg.omega}))
+                      "nu": cfg.nu_pre, "omega": cfg.omega, "nested": cfg.nested,
+                      "nested_iters": info["nested_iters"]}))
     mg.mg_destroy(ctx)
     return 0
 
@@ -381,6 +382,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="bench", choices=["bench", "warmstart", "solve", "infer"])
     ap.add_argument("--settings", default="", help="solve workload: inner_cycles,nu,omega (default: autotune)")
+    ap.add_argument("--nested", type=int, default=1, choices=(0, 1),
+                    help="nested start of each single-context solve (half-size solve, tricubic start)")
     ap.add_argument("--train-samples", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--test-instances", type=int, default=256)
@@ -418,7 +421,7 @@ def main():
 
     def context(precision):
         # one-time launch-parameter tuning (untimed): V-cycles per outer iteration, sweeps, omega
-        base = mg.config_for(p, precision, tol=WORKLOAD["tol"], max_outer=60)
+        base = mg.config_for(p, precision, tol=WORKLOAD["tol"], max_outer=60, nested=args.nested)
         cfg, tms = mg.mg_autotune(base, *src_dev, stream=sp)
         tuned_params[precision] = tune_summary(cfg, tms)
         wsz = mg.mg_workspace_size(cfg)
@@ -481,7 +484,7 @@ def main():
         # the 128^3 periodic tuning of the same precision (a 256^3 FP64 tuning would take minutes);
         # the default settings if that does not converge here
         for params in (tuned_params[prec], None):
-            cfgq = mg.config_for(q, prec, tol=WORKLOAD["tol"], max_outer=60)
+            cfgq = mg.config_for(q, prec, tol=WORKLOAD["tol"], max_outer=60, nested=args.nested)
             if params:
                 apply_tuned(cfgq, params)
             cq = mg.mg_create(cfgq, sp)
@@ -513,6 +516,8 @@ def main():
         v, det = oracle_sample(p)
         cpu = {"value": v, "unit": UNIT, "cores": det["cores"], "kind": "oracle", "sample": det["sample"]}
     cfgd = dict(WORKLOAD, outer_iters=info["outer_iters"], final_norms=list(info["norms"]), K=info["K"],
+                start="nested: half-size solve, tricubic start" if args.nested else "psi = 1, W = 0",
+                nested_outer_iters=info["nested_iters"],
                 fp64_plain_solves_per_s=fp64_solves_per_s, fp64_plain_outer_iters=info64["outer_iters"],
                 tuned={"mixed": tuned_params[mg.MG_MIXED], "fp64_plain": tuned_params[mg.MG_FP64],
                        "note": "mg_autotune before the timed region (inner V-cycles, sweeps, omega)"},

@@ -83,6 +83,16 @@ typedef struct {
                              step on every level */
     int cycle;            /* coarse-level visits per cycle: 0 or 1 = V-cycle (default), 2 = W-cycle           */
     double omega;         /* red-black relaxation weight in (0, 2); 0 = 1.0 (plain Gauss-Seidel per colour)   */
+    int nested;           /* 1 = nested start: when every size is even and its half at least nested_min, a solve
+                             that was given no initial guess (mg_set_initial_guess with a non-NULL u or W) since
+                             the previous solve first solves the same problem on the grid of half the size
+                             (sources: means over 2^3 cells; tolerance max(tol, nested_tol); nested in turn while
+                             it stays eligible) and starts the outer iteration from its solution, interpolated
+                             tricubically.  Only the starting state changes: the stopping test and the discrete
+                             root are the same.  The half-size context lives in this context's workspace.
+                             Ignored by mg_batch_*.  0 = off (default).                                         */
+    int nested_min;       /* smallest half size per axis that is solved first; 0 = 64, else >= 3             */
+    double nested_tol;    /* tolerance of the half-size solve (raised to tol); 0 = 1e-5                      */
 } mg_config;
 
 typedef struct {
@@ -94,14 +104,16 @@ typedef struct {
     double mom_mean[3];   /* m_i removed from the momentum source (periodic), else 0              */
     const double *history;/* 4 norms per outer iteration, owned by the context, valid until the next solve */
     int history_len;      /* rows in history                                                     */
-    double device_ms;     /* device time of the solve (CUDA events on the context's stream)       */
+    double device_ms;     /* device time of the solve, nested start included (CUDA events)        */
     long long kernel_launches; /* library kernels launched by this solve (0 if use_graph == 0)    */
+    int nested_iters;     /* outer iterations of the nested start's half-size solve, 0 without one    */
 } mg_solve_info;
 
 /* Fill *cfg with defaults: order 2, periodic, integrability K, MG_MIXED, tol 1e-10, ... */
 mg_status mg_config_default(mg_config *cfg);
 
-/* Device bytes the context needs for cfg (states, sources, all levels, reduction scratch). */
+/* Device bytes the context needs for cfg (states, sources, all levels, reduction scratch, and the
+ * half-size contexts of a nested start, recursively). */
 mg_status mg_workspace_size(const mg_config *cfg, size_t *bytes);
 
 /*
@@ -125,7 +137,9 @@ mg_status mg_set_sources(struct mg_ctx *ctx, const double *rho0, const double *r
                          const double *Sy, const double *Sz, int on_device);
 
 /* Initial guess for u (N) and W (3N); either may be NULL (zero).  Default: u = 0, W = 0.
- * On periodic boxes the means are projected out at the start of mg_solve. */
+ * On periodic boxes the means are projected out at the start of mg_solve.  With cfg.nested, a
+ * non-NULL u or W replaces the next solve's nested start; (NULL, NULL) keeps it (a half-size solve
+ * that diverges leaves the zero state as the start). */
 mg_status mg_set_initial_guess(struct mg_ctx *ctx, const double *u, const double *W, int on_device);
 
 /* Iterate until max(|H|, |M_i|) <= tol.  info may be NULL. */
@@ -185,7 +199,7 @@ mg_status mg_residual_norms_noalloc(const mg_config *cfg, const double *u, const
  * given problem (sources as for mg_set_sources; each candidate runs one untimed and one timed solve
  * from psi = 1 on a private context) and writes the fastest setting that meets base->tol into
  * *best (the other fields copied from *base), with its solve time in *best_ms.  Results are cached
- * per (grid size, order, bc, precision, k_mode) for the process, and, when cache_path is not NULL,
+ * per (grid size, order, bc, precision, k_mode, nested) for the process, and, when cache_path is not NULL,
  * in that text file (one line per key; read before tuning, rewritten after).  A cache hit runs no
  * solve.  Returns MG_ERR_NOT_CONVERGED if no candidate met the tolerance.
  */

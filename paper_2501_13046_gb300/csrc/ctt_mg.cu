@@ -9,6 +9,7 @@
 // Each outer iteration after the first is one replay of a captured CUDA graph; the only
 // host synchronisation per iteration is the read of K^2 and the four norms.
 #include "mg_common.cuh"
+#include "mg_nested.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -56,6 +57,9 @@ mg_status validate(const mg_config *c)
     if (c->cycle < 0 || c->cycle > 2) return fail(MG_ERR_INVALID_ARG, "cycle must be 0, 1 (V) or 2 (W)");
     if (!(c->omega == 0.0 || (c->omega > 0.0 && c->omega < 2.0)))
         return fail(MG_ERR_INVALID_ARG, "omega must be 0 (default 1) or in (0, 2)");
+    if (c->nested != 0 && c->nested != 1) return fail(MG_ERR_INVALID_ARG, "nested must be 0 or 1");
+    if (c->nested_min != 0 && c->nested_min < 3) return fail(MG_ERR_INVALID_ARG, "nested_min must be 0 or >= 3");
+    if (!(c->nested_tol >= 0.0) || !std::isfinite(c->nested_tol)) return fail(MG_ERR_INVALID_ARG, "bad nested_tol");
     int lv = c->levels > 0 ? c->levels : auto_levels(c->n);
     for (int l = 0; l + 1 < lv; ++l)
         for (int a = 0; a < 3; ++a) {
@@ -66,9 +70,31 @@ mg_status validate(const mg_config *c)
     return MG_OK;
 }
 
+// Nested start defaults.  Half sizes below kNestedMinN are not worth solving first: their outer
+// iterations cost launch latency, not bandwidth, and save little fine work.  Below kNestedTol the
+// half-size solve's own discretisation error against the fine root dominates the fine residual of
+// the interpolated start, so solving it further buys no fine iteration.
+constexpr int kNestedMinN = 64;
+constexpr double kNestedTol = 1e-5;
+
+// Configuration of the half-size problem of c's nested start; false when c has none.  A valid c gives a
+// valid child: its level l is c's level l + 1.
+bool nested_child_config(const mg_config *c, mg_config *cc)
+{
+    if (c->nested != 1) return false;
+    const int nmin = c->nested_min > 0 ? c->nested_min : kNestedMinN;
+    for (int a = 0; a < 3; ++a)
+        if (c->n[a] % 2 != 0 || c->n[a] / 2 < nmin) return false;
+    *cc = *c;
+    for (int a = 0; a < 3; ++a) cc->n[a] = c->n[a] / 2;
+    cc->levels = c->levels > 1 ? c->levels - 1 : 0;
+    cc->tol = std::max(c->tol, c->nested_tol > 0.0 ? c->nested_tol : kNestedTol);
+    return true;
+}
+
 struct Layout {
-    size_t X, SRC, R, D, partial, scal, Gpsi, GW, gj, total;
-    int dense, mpsi, mw;
+    size_t X, SRC, R, D, partial, scal, Gpsi, GW, gj, own, child, total;
+    int dense, mpsi, mw, has_child;
     std::vector<size_t> eA, eB, f, c;
 };
 
@@ -107,6 +133,10 @@ Layout layout_for(const mg_config *c)
             L.gj = take(gj_scratch_elems(L.mw) * 8);
         }
     }
+    L.own = off;
+    mg_config cc;
+    L.has_child = nested_child_config(c, &cc) ? 1 : 0;
+    if (L.has_child) L.child = take(layout_for(&cc).total);
     L.total = off;
     return L;
 }
@@ -380,7 +410,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
             if (st != MG_OK) break;
         }
         if ((st = enter(x)) != MG_OK) break;
-        e = cudaMemsetAsync(x->ws, 0, lay.total, x->stream);
+        e = cudaMemsetAsync(x->ws, 0, lay.own, x->stream);
         if (e != cudaSuccess) { st = fail(MG_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e)); break; }
         if (x->dense && x->nlev >= 2) {
             const LevelBufs &L1 = x->lev[x->nlev - 2], &Lc = x->lev[x->nlev - 1];
@@ -394,6 +424,11 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
             if (st != MG_OK) break;
         }
         if ((st = leave(x, MG_OK)) != MG_OK) break;
+        if (lay.has_child) {
+            mg_config cc;
+            nested_child_config(cfg, &cc);
+            if ((st = mg_create(&cc, x->stream, b + lay.child, lay.total - lay.child, &x->child)) != MG_OK) break;
+        }
     } while (0);
     if (st != MG_OK) {
         mg_destroy(x);
@@ -426,7 +461,7 @@ static mg_status mg_set_sources_impl(mg_ctx *x, const double *rho0, const double
 {
     if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");
     if (!rho0 || !Sx || !Sy || !Sz) return fail(MG_ERR_INVALID_ARG, "rho0 and S must be given");
-    x->have_sources = false;
+    for (mg_ctx *p = x; p; p = p->child) p->have_sources = false;
     CKS(copy_in(x->SRC, rho0, x->N, on_device, x->stream));
     CKS(copy_in(x->SRC + x->N, rho2, x->N, on_device, x->stream));
     CKS(copy_in(x->SRC + 2 * x->N, Sx, x->N, on_device, x->stream));
@@ -440,6 +475,14 @@ static mg_status mg_set_sources_impl(mg_ctx *x, const double *rho0, const double
                        x->stream));
     CK(cudaStreamSynchronize(x->stream));
     if (x->host_scal->nonfinite) return fail(MG_ERR_INVALID_ARG, "non-finite source value");
+    // the nested start's sources, level by level: means over the 2^3 cells of each half-size cell
+    for (mg_ctx *p = x; p->child; p = p->child) {
+        mg_ctx *c = p->child;
+        k_restrict_fields_f64<<<grid_for(5 * c->N), kThreads, 0, x->stream>>>(p->lev[0].geo, c->lev[0].geo, p->SRC,
+                                                                             c->SRC, 5);
+        CK(cudaGetLastError());
+        c->have_sources = true;
+    }
     x->have_sources = true;
     return MG_OK;
 }
@@ -449,6 +492,7 @@ static mg_status mg_set_initial_guess_impl(mg_ctx *x, const double *u, const dou
     if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");
     CKS(copy_in(x->X, u, x->N, on_device, x->stream));
     CKS(copy_in(x->X + x->N, W, 3 * x->N, on_device, x->stream));
+    x->guess_set = u != nullptr || W != nullptr;
     return MG_OK;
 }
 
@@ -458,7 +502,29 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
     if (!x->have_sources) return fail(MG_ERR_STATE, "mg_set_sources must come before mg_solve");
     x->history.clear();
     long long launches = 0;
+    int nested_iters = 0;
     CK(cudaEventRecord(x->ev0, x->stream));
+    if (x->child && !x->guess_set) {
+        // nested start: solve the half-size problem from zero (nesting in turn), interpolate its solution
+        mg_ctx *c = x->child;
+        mg_solve_info ci{};
+        CKS(mg_set_initial_guess(c, nullptr, nullptr, 1));
+        mg_status cs = mg_solve(c, &ci);
+        if (cs != MG_OK && cs != MG_ERR_NOT_CONVERGED && cs != MG_ERR_DIVERGED) return cs;
+        if (cs == MG_ERR_DIVERGED) {
+            CK(cudaMemsetAsync(x->X, 0, 4 * x->N * 8, x->stream));   // no usable start: the zero state
+        } else {
+            const dim3 nb = prolong_cubic_grid(c->lev[0].geo);
+            if (x->cfg.bc == MG_BC_PERIODIC)
+                k_prolong_cubic<BC_PERIODIC><<<nb, 256, 0, x->stream>>>(c->lev[0].geo, x->lev[0].geo, c->X, x->X);
+            else
+                k_prolong_cubic<BC_ROBIN><<<nb, 256, 0, x->stream>>>(c->lev[0].geo, x->lev[0].geo, c->X, x->X);
+            CK(cudaGetLastError());
+            launches += ci.kernel_launches + 1;
+        }
+        nested_iters = ci.outer_iters;
+    }
+    x->guess_set = false;
     if (x->cfg.use_graph) {
         if (!x->graph_start) CKS(capture(x, start_any, &x->graph_start, &x->launches_start));
         CK(cudaGraphLaunch(x->graph_start, x->stream));
@@ -512,6 +578,7 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
         cudaEventElapsedTime(&ms, x->ev0, x->ev1);
         info->device_ms = ms;
         info->kernel_launches = x->cfg.use_graph ? launches : 0;
+        info->nested_iters = nested_iters;
     }
     return result;
 }
@@ -607,6 +674,7 @@ mg_status mg_time_kernel(mg_ctx *x, int which, int reps, double *ms_per_launch, 
 void mg_destroy(mg_ctx *x)
 {
     if (!x) return;
+    if (x->child) mg_destroy(x->child);
     if (x->graph_exec) cudaGraphExecDestroy(x->graph_exec);
     if (x->graph_start) cudaGraphExecDestroy(x->graph_start);
     if (x->ev0) cudaEventDestroy(x->ev0);
@@ -759,7 +827,9 @@ mg_status mg_batch_create(int count, const mg_config *cfgs, void *cuda_stream, m
         st = fail(MG_ERR_CUDA, "stream/event creation");
     for (int b = 0; b < count && st == MG_OK; ++b) {
         mg_ctx *x = nullptr;
-        st = mg_create(&cfgs[b], cuda_stream, nullptr, 0, &x);
+        mg_config cb = cfgs[b];
+        cb.nested = 0;   // the batch replays one graph per round: no per-instance nested start
+        st = mg_create(&cb, cuda_stream, nullptr, 0, &x);
         if (st == MG_OK) bt->ctx.push_back(x);
         cudaEvent_t e;
         if (st == MG_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) bt->ev_join.push_back(e);
@@ -914,7 +984,7 @@ std::string tune_key(const mg_config *c)
 {
     std::ostringstream k;
     k << c->n[0] << ' ' << c->n[1] << ' ' << c->n[2] << ' ' << c->order << ' ' << c->bc << ' ' << c->precision << ' '
-      << c->k_mode;
+      << c->k_mode << ' ' << c->nested;
     return k.str();
 }
 
@@ -925,11 +995,14 @@ void tune_load(const char *path)
     std::string line;
     while (std::getline(f, line)) {
         std::istringstream in(line);
-        int n0, n1, n2, order, bc, prec, km;
+        int n0, n1, n2, order, bc, prec, km, nested;
         TuneResult r;
-        if (in >> n0 >> n1 >> n2 >> order >> bc >> prec >> km >> r.inner >> r.nu >> r.threads >> r.omega >> r.ms) {
+        std::string extra;
+        if (in >> n0 >> n1 >> n2 >> order >> bc >> prec >> km >> nested >> r.inner >> r.nu >> r.threads >> r.omega >>
+                r.ms &&
+            !(in >> extra)) {
             std::ostringstream k;
-            k << n0 << ' ' << n1 << ' ' << n2 << ' ' << order << ' ' << bc << ' ' << prec << ' ' << km;
+            k << n0 << ' ' << n1 << ' ' << n2 << ' ' << order << ' ' << bc << ' ' << prec << ' ' << km << ' ' << nested;
             g_tune_cache.emplace(k.str(), r);
         }
     }

@@ -246,6 +246,8 @@ struct mg_ctx {
     long long launches_iter = 0, launches_start = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<double> history;
+    mg_ctx *child = nullptr;   // half-size problem of the nested start (its workspace is carved from ws)
+    bool guess_set = false;    // the caller gave an initial guess since the previous solve
 };
 
 namespace ctt {

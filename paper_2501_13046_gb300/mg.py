@@ -36,7 +36,8 @@ class mg_config(C.Structure):
         ("punct_m", C.c_double * 2), ("punct_x", (C.c_double * 3) * 2), ("tol", C.c_double), ("max_outer", C.c_int),
         ("nu_pre", C.c_int), ("nu_post", C.c_int), ("coarse_sweeps", C.c_int), ("use_graph", C.c_int),
         ("spin_limit", C.c_longlong), ("inner_cycles", C.c_int), ("block_threads", C.c_int),
-        ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double),
+        ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double), ("nested", C.c_int),
+        ("nested_min", C.c_int), ("nested_tol", C.c_double),
     ]
 
 
@@ -45,6 +46,7 @@ class mg_solve_info(C.Structure):
         ("outer_iters", C.c_int), ("converged", C.c_int), ("K", C.c_double), ("K2", C.c_double),
         ("norms", C.c_double * 4), ("mom_mean", C.c_double * 3), ("history", C.POINTER(C.c_double)),
         ("history_len", C.c_int), ("device_ms", C.c_double), ("kernel_launches", C.c_longlong),
+        ("nested_iters", C.c_int),
     ]
 
 
@@ -161,7 +163,8 @@ def mg_solve(ctx, allow=(MG_ERR_NOT_CONVERGED,)):
         if info.history_len > 0 else np.zeros((0, 4))
     return st, dict(outer_iters=info.outer_iters, converged=bool(info.converged), K=info.K, K2=info.K2,
                     norms=np.array(info.norms[:]), mom_mean=np.array(info.mom_mean[:]), history=hist,
-                    device_ms=info.device_ms, kernel_launches=info.kernel_launches)
+                    device_ms=info.device_ms, kernel_launches=info.kernel_launches,
+                    nested_iters=info.nested_iters)
 
 
 def mg_get_solution(ctx, u=None, W=None):

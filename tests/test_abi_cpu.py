@@ -46,8 +46,27 @@ def test_config_defaults_and_workspace_size(lib):
     assert cfg.smoother == 0 and cfg.block_threads == 0
 
 
+def test_nested_workspace_holds_the_half_size_contexts(lib):
+    """nested = 1 adds the half-size problem's workspace, recursively, while every size stays
+    even and the half size >= nested_min (default 64): 256^3 nests 128^3, which nests 64^3."""
+    def ws(n, nested, nmin=0, order=4):
+        cfg = lib.mg_config_default()
+        cfg.n[0] = cfg.n[1] = cfg.n[2] = n
+        cfg.order, cfg.nested, cfg.nested_min = order, nested, nmin
+        return lib.mg_workspace_size(cfg)
+    assert ws(64, 1) == ws(64, 0)
+    assert ws(128, 1) == ws(128, 0) + ws(64, 0)
+    assert ws(256, 1) == ws(256, 0) + ws(128, 1)
+    assert ws(40, 1, 24) == ws(40, 0)      # half size 20 < 24: not eligible
+    assert ws(48, 1, 24) == ws(48, 0) + ws(24, 0)
+    assert ws(128, 1, 24) == ws(128, 0) + ws(64, 1, 24)
+    assert ws(64, 1, 24) == ws(64, 0) + ws(32, 1, 24) and ws(32, 1, 24) == ws(32, 0)
+    assert ws(128, 1, 24) - ws(128, 0) < ws(128, 0) // 6   # about 1/8 + 1/64, plus the coarse inverses
+
+
 @pytest.mark.parametrize("field,value,status", [
     ("order", 3, 1), ("bc", 7, 1), ("precision", 5, 1), ("levels", 6, 1), ("coarse_sweeps", 0, 1),
+    ("nested", 2, 1), ("nested_min", 2, 1), ("nested_tol", -1.0, 1),
 ])
 def test_invalid_configs_are_rejected_on_the_host(lib, field, value, status):
     cfg = lib.mg_config_default()
