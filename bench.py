@@ -270,13 +270,14 @@ def run_infer(args):
 
 def run_solve_profile(args):
     """Only the benchmarked solve: W + K mixed solves of the 128^3 workload from psi = 1 with the
-    settings given (--settings inner,nu,omega; default: autotuned).  The committed launch lists and
-    kernel captures are taken from this command."""
+    settings given (--settings inner,nu,omega; default: autotuned); --workload shell solves the
+    256^3 Robin puncture shell instead.  The committed launch lists and kernel captures are taken
+    from this command."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2501_13046_gb300 import mg
-    p = make_problem()
+    p = make_problem() if args.workload == "solve" else fields_mod().puncture_shell(n=args.shell_n)
     sp = torch.cuda.current_stream().cuda_stream
     src = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (p["rho0"], p["rho2"], *p["S"])]
     cfg = mg.config_for(p, mg.MG_MIXED, tol=WORKLOAD["tol"], max_outer=60, nested=args.nested)
@@ -290,7 +291,7 @@ def run_solve_profile(args):
     stream = torch.cuda.current_stream()
     solve_loop(mg, torch, ctx, args.warmup, stream)
     secs, info = solve_loop(mg, torch, ctx, args.steps, stream)
-    print(json.dumps({"workload": "solve", "solves_per_s": args.steps / secs, "outer_iters": info["outer_iters"],
+    print(json.dumps({"workload": args.workload, "solves_per_s": args.steps / secs, "outer_iters": info["outer_iters"],
                       "launches_per_solve": info["kernel_launches"], "inner_cycles": cfg.inner_cycles,
                       "nu": cfg.nu_pre, "omega": cfg.omega, "nested": cfg.nested,
                       "nested_iters": info["nested_iters"]}))
@@ -380,7 +381,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bench", choices=["bench", "warmstart", "solve", "infer"])
+    ap.add_argument("--workload", default="bench", choices=["bench", "warmstart", "solve", "shell", "infer"])
+    ap.add_argument("--shell-n", type=int, default=256, help="shell workload: cells per axis")
     ap.add_argument("--settings", default="", help="solve workload: inner_cycles,nu,omega (default: autotune)")
     ap.add_argument("--nested", type=int, default=1, choices=(0, 1),
                     help="nested start of each single-context solve (half-size solve, tricubic start)")
@@ -390,7 +392,7 @@ def main():
     args = ap.parse_args()
     if args.workload == "warmstart" and args.impl == "ours":
         return run_warmstart(args)
-    if args.workload == "solve" and args.impl == "ours":
+    if args.workload in ("solve", "shell") and args.impl == "ours":
         return run_solve_profile(args)
     if args.workload == "infer" and args.impl == "ours":
         return run_infer(args)

@@ -93,7 +93,7 @@ bool nested_child_config(const mg_config *c, mg_config *cc)
 }
 
 struct Layout {
-    size_t X, SRC, R, D, partial, scal, Gpsi, GW, gj, own, child, total;
+    size_t X, SRC, R, D, PB, RT, partial, scal, Gpsi, GW, gj, own, child, total;
     int dense, mpsi, mw, has_child;
     std::vector<size_t> eA, eB, f, c;
 };
@@ -110,6 +110,8 @@ Layout layout_for(const mg_config *c)
     L.SRC = take(5 * N * 8);
     L.R = take(5 * N * 8);
     L.D = take(4 * N * 8);
+    if (c->npunct > 0) L.PB = take(N * 8);
+    if (c->bc == MG_BC_ROBIN) L.RT = take((size_t)(c->n[0] + 4) * (c->n[1] + 4) * (c->n[2] + 4) * 8);
     for (int l = 0; l < lv; ++l) {
         size_t Nl = ((size_t)(c->n[0] >> l)) * (c->n[1] >> l) * (c->n[2] >> l);
         L.eA.push_back(take(4 * Nl * tb));
@@ -412,6 +414,19 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         if ((st = enter(x)) != MG_OK) break;
         e = cudaMemsetAsync(x->ws, 0, lay.own, x->stream);
         if (e != cudaSuccess) { st = fail(MG_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e)); break; }
+        if (cfg->npunct > 0) {
+            double *pb = (double *)(b + lay.PB);
+            k_fill_psibg<<<grid_for(x->N), kThreads, 0, x->stream>>>(x->lev[0].geo, pb);
+            if ((e = cudaGetLastError()) != cudaSuccess) { st = fail(MG_ERR_CUDA, cudaGetErrorString(e)); break; }
+            x->lev[0].geo.psibg = pb;
+        }
+        if (cfg->bc == MG_BC_ROBIN) {
+            double *rt = (double *)(b + lay.RT);
+            const size_t M = (size_t)(cfg->n[0] + 4) * (cfg->n[1] + 4) * (cfg->n[2] + 4);
+            k_fill_robin_table<<<grid_for(M), kThreads, 0, x->stream>>>(x->lev[0].geo, rt);
+            if ((e = cudaGetLastError()) != cudaSuccess) { st = fail(MG_ERR_CUDA, cudaGetErrorString(e)); break; }
+            x->lev[0].geo.rtab = rt;
+        }
         if (x->dense && x->nlev >= 2) {
             const LevelBufs &L1 = x->lev[x->nlev - 2], &Lc = x->lev[x->nlev - 1];
             x->fused = cfg->smoother == 0 && L1.N <= (size_t)kFusedMaxCells &&

@@ -51,11 +51,7 @@ __global__ void __launch_bounds__(512) k_dense_psi_assemble(Geo g, Coef<T> cf, c
                     const int bc[3] = {min(max(c[0], 0), g.n[0] - 1), min(max(c[1], 0), g.n[1] - 1),
                                        min(max(c[2], 0), g.n[2] - 1)};
                     double ratio = 1.0;
-                    if (bc[ax] != c[ax]) {
-                        const double xb = cellx(g, 0, bc[0]), yb = cellx(g, 1, bc[1]), zb = cellx(g, 2, bc[2]);
-                        const double xg = cellx(g, 0, c[0]), yg = cellx(g, 1, c[1]), zg = cellx(g, 2, c[2]);
-                        ratio = sqrt(xb * xb + yb * yb + zb * zb) / sqrt(xg * xg + yg * yg + zg * zg);
-                    }
+                    if (bc[ax] != c[ax]) ratio = robin_ratio<double>(g, bc[0], bc[1], bc[2], c[0], c[1], c[2]);
                     row[bc[0] + g.n[0] * (bc[1] + g.n[1] * bc[2])] += (C)(w * ratio);
                 }
             }
@@ -313,7 +309,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(Geo g, Coef<T> cf, Geo gc
         for (int d = 0; d < 8; ++d) {
             const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
             const int cx = I + dx * sx, cy = J + dy * sy, cz = K + dz * sz;
-            double w = (dx ? 0.25 : 0.75) * (dy ? 0.25 : 0.75) * (dz ? 0.25 : 0.75);
+            T w = (T)((dx ? 0.25 : 0.75) * (dy ? 0.25 : 0.75) * (dz ? 0.25 : 0.75));
             int bx = cx, by = cy, bz = cz;
             if (BC == BC_PERIODIC) {
                 bx += bx < 0 ? ncx : 0; bx -= bx >= ncx ? ncx : 0;
@@ -323,11 +319,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(Geo g, Coef<T> cf, Geo gc
                 bx = min(max(bx, 0), ncx - 1);
                 by = min(max(by, 0), ncy - 1);
                 bz = min(max(bz, 0), ncz - 1);
-                if (bx != cx || by != cy || bz != cz) {
-                    const double ax = cellx(gc, 0, bx), ay = cellx(gc, 1, by), az = cellx(gc, 2, bz);
-                    const double gx = cellx(gc, 0, cx), gy = cellx(gc, 1, cy), gz = cellx(gc, 2, cz);
-                    w *= sqrt(ax * ax + ay * ay + az * az) / sqrt(gx * gx + gy * gy + gz * gz);
-                }
+                if (bx != cx || by != cy || bz != cz) w *= robin_ratio<T>(gc, bx, by, bz, cx, cy, cz);
             }
             const int c = bx + ncx * (by + ncy * bz);
             for (int a = 0; a < 4; ++a) s4[a] = fma((T)w, ec[a * Nc + c], s4[a]);

@@ -177,15 +177,17 @@ inline OuterCoef make_outer_coef(const Geo &g, int order)
 }
 
 // Block split of the FP64 residual pass B: shell blocks first, then interior-box blocks; at most
-// kRedBlocks blocks in all (one reduction partial each).
-inline Regions outer_regions(const Geo &g, int order, int *grid)
+// kRedBlocks blocks in all (one reduction partial each).  A periodic shell cell costs about an
+// interior cell (q form, wrapped); a Robin shell cell takes the tensor-product form with boundary
+// values, several times the arithmetic, so Robin boxes give the shell up to half the blocks.
+inline Regions outer_regions(const Geo &g, int order, int robin, int *grid)
 {
     Regions r;
     r.G = order / 2;
     long long ix = g.n[0] - 2 * r.G, iy = g.n[1] - 2 * r.G, iz = g.n[2] - 2 * r.G;
     size_t nint = (ix > 0 && iy > 0 && iz > 0) ? (size_t)ix * iy * iz : 0;
     size_t nsh = shell_count(g.n, r.G);
-    int bs = nsh ? grid_for(nsh, 152, kThreads) : 0;
+    int bs = nsh ? grid_for(nsh, robin ? kRedBlocks / 2 : 152, kThreads) : 0;
     int bi = nint ? grid_for(nint, kRedBlocks - bs, kThreads) : 0;
     r.nblk_sh = bs;
     *grid = std::max(1, bi + bs);

@@ -219,7 +219,7 @@ mg_status enqueue_outer_pass1(mg_ctx *x)
     Coef<double> cf = make_coef<double>(L0.geo, x->cfg.order);
     OuterCoef oc = make_outer_coef(L0.geo, x->cfg.order);
     int gb = 0;
-    Regions rg = outer_regions(L0.geo, ORDER, &gb);
+    Regions rg = outer_regions(L0.geo, ORDER, x->cfg.bc == MG_BC_ROBIN, &gb);
     dispatch_bc(x->cfg.bc, [&](auto B) {
         k_outer_div<ORDER, decltype(B)::value><<<grid_for(x->N, 1 << 24), kThreads, 0, x->stream>>>(L0.geo, oc, x->X,
                                                                                                       x->D);
@@ -393,7 +393,7 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
             Coef<double> cd = make_coef<double>(L.geo, x->cfg.order);
             OuterCoef oc = make_outer_coef(L.geo, x->cfg.order);
             int gb = 0;
-            Regions rg = outer_regions(L.geo, ORDER, &gb);
+            Regions rg = outer_regions(L.geo, ORDER, x->cfg.bc == MG_BC_ROBIN, &gb);
             dispatch_bc(x->cfg.bc, [&](auto B) {
                 k_outer_pass1q<ORDER, decltype(B)::value><<<gb, kThreads, 0, x->stream>>>(
                     L.geo, cd, oc, x->X, x->D, x->SRC, x->R, x->partial, rg);

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace ctt {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -30,6 +32,9 @@ struct Geo {
     int npunct;
     double pm[2];
     double px[2][3];
+    const double *psibg;   // finest level with punctures: psi_background per cell (N doubles), else null
+    const double *rtab;    // finest level of a Robin box: the FP64 ratio |x_b| / |x_g| on the box padded by
+                           // 2 cells per side (1 inside), (n0+4)(n1+4)(n2+4) doubles, else null
 };
 
 template <typename T>
@@ -47,6 +52,41 @@ template <> struct Vec2<double> { using type = double2; };
 
 __device__ __forceinline__ double cellx(const Geo &g, int a, int i) { return g.lo[a] + (i + 0.5) * g.h[a]; }
 
+// Robin 1/r boundary: a cell g outside the box takes the value of its clamped cell b times |x_b| / |x_g|.
+// The ratio is formed in the level's precision T: FP32 levels (the inner solve's preconditioner)
+// take A rsqrt(A B) = sqrt(A / B) with the hardware reciprocal square root and no FP64 arithmetic,
+// whose rate is 1/64 of FP32 here; FP64 takes one division and one square root.
+template <typename T>
+__device__ __forceinline__ T robin_ratio(const Geo &g, int bi, int bj, int bk, int gi, int gj, int gk)
+{
+    auto c = [&](int a, int i) { return (T)g.lo[a] + ((T)i + (T)0.5) * (T)g.h[a]; };
+    const T xb = c(0, bi), yb = c(1, bj), zb = c(2, bk), xg = c(0, gi), yg = c(1, gj), zg = c(2, gk);
+    const T A = xb * xb + yb * yb + zb * zb, B = xg * xg + yg * yg + zg * zg;
+    if constexpr (std::is_same<T, float>::value) return A * rsqrtf(A * B);
+    else return sqrt(A / B);
+}
+
+// FP64 Robin ratio of the ghost cell (i, j, k) (at most 2 cells outside) onto its clamped cell b:
+// the stored table when there is one (the division and square root run at the FP64 rate).
+__device__ __forceinline__ double robin_ratio_f64(const Geo &g, int bi, int bj, int bk, int i, int j, int k)
+{
+    if (g.rtab)
+        return g.rtab[(size_t)(i + 2) + (size_t)(g.n[0] + 4) * ((size_t)(j + 2) + (size_t)(g.n[1] + 4) * (k + 2))];
+    return robin_ratio<double>(g, bi, bj, bk, i, j, k);
+}
+
+// rt[(i+2) + (n0+4)((j+2) + (n1+4)(k+2))] = |x_clamp| / |x_(i,j,k)| (1 inside the box), -2 <= i < n0 + 2, ...
+static __global__ void __launch_bounds__(256) k_fill_robin_table(Geo g, double *__restrict__ rt)
+{
+    const int m0 = g.n[0] + 4, m1 = g.n[1] + 4;
+    const size_t M = (size_t)m0 * m1 * (g.n[2] + 4);
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < M; p += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % m0) - 2, j = (int)((p / m0) % m1) - 2, k = (int)(p / ((size_t)m0 * m1)) - 2;
+        const int bi = min(max(i, 0), g.n[0] - 1), bj = min(max(j, 0), g.n[1] - 1), bk = min(max(k, 0), g.n[2] - 1);
+        rt[p] = (bi == i && bj == j && bk == k) ? 1.0 : robin_ratio<double>(g, bi, bj, bk, i, j, k);
+    }
+}
+
 __device__ __forceinline__ double psi_background(const Geo &g, int i, int j, int k)
 {
     double v = 1.0;
@@ -57,6 +97,22 @@ __device__ __forceinline__ double psi_background(const Geo &g, int i, int j, int
         v += g.pm[p] / (2.0 * sqrt(dx * dx + dy * dy + dz * dz));
     }
     return v;
+}
+
+// psi_background at cell p = (i, j, k): the stored table when there is one (a FP64 square root and
+// division per puncture and cell cost more than the 8-byte read), else formed in place.
+__device__ __forceinline__ double psi_bg(const Geo &g, int i, int j, int k, size_t p)
+{
+    return g.psibg ? g.psibg[p] : psi_background(g, i, j, k);
+}
+
+static __global__ void __launch_bounds__(256) k_fill_psibg(Geo g, double *__restrict__ pb)
+{
+    const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % g.n[0]), j = (int)((p / g.n[0]) % g.n[1]), k = (int)(p / ((size_t)g.n[0] * g.n[1]));
+        pb[p] = psi_background(g, i, j, k);
+    }
 }
 
 // value of f at a cell that may lie outside the box (offsets are at most +-2 per axis)
@@ -74,10 +130,8 @@ __device__ __forceinline__ T fetch_bc(const T *f, const Geo &g, int i, int j, in
         int bk = min(max(k, 0), g.n[2] - 1);
         T v = f[bi + g.n[0] * (bj + g.n[1] * bk)];
         if (bi == i && bj == j && bk == k) return v;
-        double xb = cellx(g, 0, bi), yb = cellx(g, 1, bj), zb = cellx(g, 2, bk);
-        double xg = cellx(g, 0, i), yg = cellx(g, 1, j), zg = cellx(g, 2, k);
-        double rb = sqrt(xb * xb + yb * yb + zb * zb), rg = sqrt(xg * xg + yg * yg + zg * zg);
-        return (T)((double)v * rb / rg);
+        if constexpr (std::is_same<T, double>::value) return v * robin_ratio_f64(g, bi, bj, bk, i, j, k);
+        else return v * robin_ratio<T>(g, bi, bj, bk, i, j, k);
     }
 }
 
@@ -247,9 +301,10 @@ struct AccB2 {
         size_t lin = (size_t)q[0] + (size_t)g->n[0] * ((size_t)q[1] + (size_t)g->n[1] * q[2]);
         T v = (c2 == c ? same : other)[(c2 ? N / 2 : 0) + (lin >> 1)];
         if (BC == BC_ROBIN && outside) {
-            double xb = cellx(*g, 0, q[0]), yb = cellx(*g, 1, q[1]), zb = cellx(*g, 2, q[2]);
-            double xg = cellx(*g, 0, p[0]), yg = cellx(*g, 1, p[1]), zg = cellx(*g, 2, p[2]);
-            return (T)((double)v * sqrt(xb * xb + yb * yb + zb * zb) / sqrt(xg * xg + yg * yg + zg * zg));
+            if constexpr (std::is_same<T, double>::value)
+                return v * robin_ratio_f64(*g, q[0], q[1], q[2], p[0], p[1], p[2]);
+            else
+                return v * robin_ratio<T>(*g, q[0], q[1], q[2], p[0], p[1], p[2]);
         }
         return v;
     }
@@ -509,7 +564,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(Geo g, Geo gc, const T *__r
         for (int d = 0; d < 8; ++d) {
             const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
             int cx = I + dx * sx, cy = J + dy * sy, cz = K + dz * sz;
-            double wd = (dx ? 0.25 : 0.75) * (dy ? 0.25 : 0.75) * (dz ? 0.25 : 0.75);
+            T wd = (T)((dx ? 0.25 : 0.75) * (dy ? 0.25 : 0.75) * (dz ? 0.25 : 0.75));
             int bx = cx, by = cy, bz = cz;
             if (BC == BC_PERIODIC) {
                 bx += bx < 0 ? ncx : 0; bx -= bx >= ncx ? ncx : 0;
@@ -519,15 +574,11 @@ __global__ void __launch_bounds__(256) k_prolong_add(Geo g, Geo gc, const T *__r
                 bx = min(max(bx, 0), ncx - 1);
                 by = min(max(by, 0), ncy - 1);
                 bz = min(max(bz, 0), ncz - 1);
-                if (bx != cx || by != cy || bz != cz) {
-                    const double ax = cellx(gc, 0, bx), ay = cellx(gc, 1, by), az = cellx(gc, 2, bz);
-                    const double gx = cellx(gc, 0, cx), gy = cellx(gc, 1, cy), gz = cellx(gc, 2, cz);
-                    wd *= sqrt(ax * ax + ay * ay + az * az) / sqrt(gx * gx + gy * gy + gz * gz);
-                }
+                if (bx != cx || by != cy || bz != cz) wd *= robin_ratio<T>(gc, bx, by, bz, cx, cy, cz);
             }
             const unsigned lin = (unsigned)bx + (unsigned)ncx * ((unsigned)by + (unsigned)ncy * (unsigned)bz);
             idx[d] = csplit ? (((bx + by + bz) & 1) ? Nc / 2 : 0u) + (lin >> 1) : lin;
-            w[d] = (T)wd;
+            w[d] = wd;
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -782,7 +833,7 @@ __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__rest
         const unsigned rest = pu / nx;
         const int j = (int)(rest % ny);
         const int k = (int)(rest / ny);
-        const double psi = psi_background(g, i, j, k) + x[p];
+        const double psi = psi_bg(g, i, j, k, p) + x[p];
         const double p2 = psi * psi, p4 = p2 * p2, p5 = p4 * psi;
         const double Fp = fma(-K2 / 12.0, p5, R[p]);
         const double Fw0 = R[N + p] + m0, Fw1 = R[2 * N + p] + m1, Fw2 = R[3 * N + p] + m2;
@@ -941,11 +992,7 @@ __global__ void __launch_bounds__(512) k_coarse_psi_direct(Geo g, Coef<T> cf, co
                     int bc[3] = {min(max(c[0], 0), g.n[0] - 1), min(max(c[1], 0), g.n[1] - 1),
                                  min(max(c[2], 0), g.n[2] - 1)};
                     double ratio = 1.0;
-                    if (bc[ax] != c[ax]) {
-                        double xb = cellx(g, 0, bc[0]), yb = cellx(g, 1, bc[1]), zb = cellx(g, 2, bc[2]);
-                        double xg = cellx(g, 0, c[0]), yg = cellx(g, 1, c[1]), zg = cellx(g, 2, c[2]);
-                        ratio = sqrt(xb * xb + yb * yb + zb * zb) / sqrt(xg * xg + yg * yg + zg * zg);
-                    }
+                    if (bc[ax] != c[ax]) ratio = robin_ratio<double>(g, bc[0], bc[1], bc[2], c[0], c[1], c[2]);
                     row[bc[0] + g.n[0] * (bc[1] + g.n[1] * bc[2])] += (T)((double)w * ratio);
                 }
             }

@@ -132,7 +132,7 @@ __device__ __forceinline__ void outer_tail(const Geo &g, int i, int j, int k, si
                                            const double mom[3], const double *x, const double *src, double *R,
                                            double acc[5])
 {
-    const double psi = psi_background(g, i, j, k) + x[p];
+    const double psi = psi_bg(g, i, j, k, p) + x[p];
     const double rho0 = src[p], rho2 = src[N + p];
     const double ip = 1.0 / psi;
     const double p2 = psi * psi, p4 = p2 * p2, p5 = p4 * psi, p6 = p5 * psi;

@@ -144,11 +144,7 @@ __device__ __forceinline__ T tile_fetch(const Geo &g, const T *X, const T *O, in
     const size_t N = (size_t)nx * ny * nz;
     const size_t idx = (size_t)f * N + (hb ? N / 2 : 0) + (size_t)(xb >> 1) + (size_t)(nx >> 1) * (yb + (size_t)ny * zb);
     T v = (hb == colour ? X : O)[idx];
-    if (BC == BC_ROBIN && (xb != x || yb != y || zb != z)) {
-        double ax = cellx(g, 0, xb), ay = cellx(g, 1, yb), az = cellx(g, 2, zb);
-        double gx = cellx(g, 0, x), gy = cellx(g, 1, y), gz = cellx(g, 2, z);
-        v = (T)((double)v * sqrt(ax * ax + ay * ay + az * az) / sqrt(gx * gx + gy * gy + gz * gz));
-    }
+    if (BC == BC_ROBIN && (xb != x || yb != y || zb != z)) v *= robin_ratio<T>(g, xb, yb, zb, x, y, z);
     return v;
 }
 

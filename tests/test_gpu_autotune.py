@@ -73,7 +73,8 @@ def test_autotune_reads_cache_file(mg, tmp_path):
     p = fields.modes_periodic(n=24)
     base = mg.config_for(p, mg.MG_MIXED, tol=1e-10, max_outer=40)
     cache = tmp_path / "tune.txt"
-    cache.write_text("24 24 24 4 0 %d %d 3 1 128 1.15 1.5\n" % (mg.MG_MIXED, base.k_mode))
+    # key (n, order, bc, precision, k_mode, nested), then inner, nu, threads, omega, ms
+    cache.write_text("24 24 24 4 0 %d %d 0 3 1 128 1.15 1.5\n" % (mg.MG_MIXED, base.k_mode))
     best, ms = mg.mg_autotune(base, *sources(p), stream=torch.cuda.current_stream().cuda_stream,
                               cache_path=str(cache))
     assert (best.inner_cycles, best.nu_pre, best.nu_post, best.block_threads) == (3, 1, 1, 128)
