@@ -212,6 +212,12 @@ mg_status enqueue_vcycle(mg_ctx *x, bool first) { return enqueue_cycle<T, ORDER>
 
 // FP64 residual pass 1 (pass A: q, div W; pass B: R and the integrability sums), then the
 // final reduction of the sums.
+// Pass B finishes the outer scalars in its last block (sums, K^2, m_i).
+inline OuterFin outer_fin(mg_ctx *x)
+{
+    return OuterFin{x->scal, x->cfg.k_mode == MG_K_INTEGRABILITY, x->cfg.bc == MG_BC_PERIODIC, x->cfg.K * x->cfg.K};
+}
+
 template <int ORDER>
 mg_status enqueue_outer_pass1(mg_ctx *x)
 {
@@ -224,9 +230,8 @@ mg_status enqueue_outer_pass1(mg_ctx *x)
         k_outer_div<ORDER, decltype(B)::value><<<grid_for(x->N, 1 << 24), kThreads, 0, x->stream>>>(L0.geo, oc, x->X,
                                                                                                       x->D);
         k_outer_pass1q<ORDER, decltype(B)::value><<<gb, kThreads, 0, x->stream>>>(L0.geo, cf, oc, x->X, x->D, x->SRC,
-                                                                                  x->R, x->partial, rg);
+                                                                                  x->R, x->partial, rg, outer_fin(x));
     });
-    k_finalize_sum<5><<<1, 256, 0, x->stream>>>(x->partial, gb, x->scal->sums);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -238,12 +243,8 @@ mg_status enqueue_residual(mg_ctx *x, double *HM)
     LevelBufs &L0 = x->lev[0];
     CKS(enqueue_outer_pass1<ORDER>(x));
     int g1 = grid_for(x->N, kRedBlocks);
-    double K2f = x->cfg.K * x->cfg.K;
-    k_outer_scalars<<<1, 1, 0, x->stream>>>(x->scal, x->N, x->cfg.k_mode == MG_K_INTEGRABILITY, K2f,
-                                           x->cfg.bc == MG_BC_PERIODIC);
     k_outer_pass2<T><<<g1, kThreads, 0, x->stream>>>(L0.geo, x->X, x->R, x->SRC, x->scal, (T *)L0.f, (T *)L0.c, HM,
-                                                     x->partial, L0.split);
-    k_finalize_max<4><<<1, 256, 0, x->stream>>>(x->partial, g1, x->scal->norms);
+                                                     x->partial, L0.split, 1);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(x->host_scal, x->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, x->stream));
     return MG_OK;
@@ -317,11 +318,11 @@ mg_status enqueue_iteration(mg_ctx *x)
     LevelBufs &L0 = x->lev[0];
     if (periodic) {
         int g = grid_for(x->N, kRedBlocks);
-        k_sum4<T><<<g, kThreads, 0, x->stream>>>((const T *)L0.cur(), x->N, x->partial);
-        k_finalize_sum<4><<<1, 256, 0, x->stream>>>(x->partial, g, x->scal->emean);
+        k_sum4<T><<<g, kThreads, 0, x->stream>>>((const T *)L0.cur(), x->N, x->partial, x->scal->emean,
+                                                 &x->scal->ticket[2]);
     }
-    k_update<T><<<grid_for(x->N), kThreads, 0, x->stream>>>(L0.geo, x->X, (const T *)L0.cur(), x->N, x->scal->emean,
-                                                            periodic, L0.split);
+    k_update<T><<<grid_for(x->N), kThreads, 0, x->stream>>>(L0.geo, x->X, (const T *)L0.cur(), x->N,
+                                                            periodic ? x->scal->emean : nullptr, L0.split);
     CK(cudaGetLastError());
     return enqueue_residual<T, ORDER>(x, nullptr);
 }
@@ -396,7 +397,7 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
             Regions rg = outer_regions(L.geo, ORDER, x->cfg.bc == MG_BC_ROBIN, &gb);
             dispatch_bc(x->cfg.bc, [&](auto B) {
                 k_outer_pass1q<ORDER, decltype(B)::value><<<gb, kThreads, 0, x->stream>>>(
-                    L.geo, cd, oc, x->X, x->D, x->SRC, x->R, x->partial, rg);
+                    L.geo, cd, oc, x->X, x->D, x->SRC, x->R, x->partial, rg, OuterFin{nullptr, 0, 0, 0.0});
             });
         }
     }

@@ -12,8 +12,7 @@ mg_status engine_project_gauge(mg_ctx *x)
 {
     if (x->cfg.bc != MG_BC_PERIODIC) return MG_OK;
     int g = grid_for(x->N, kRedBlocks);
-    k_sum4<double><<<g, kThreads, 0, x->stream>>>(x->X, x->N, x->partial);
-    k_finalize_sum<4><<<1, 256, 0, x->stream>>>(x->partial, g, x->scal->emean);
+    k_sum4<double><<<g, kThreads, 0, x->stream>>>(x->X, x->N, x->partial, x->scal->emean, &x->scal->ticket[2]);
     k_sub_mean4<double><<<grid_for(x->N), kThreads, 0, x->stream>>>(x->X, x->N, x->scal->emean);
     CK(cudaGetLastError());
     return MG_OK;

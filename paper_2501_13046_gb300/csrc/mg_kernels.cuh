@@ -639,6 +639,37 @@ __device__ __forceinline__ void block_max(double (&v)[NV], double *out)
     __syncthreads();
 }
 
+// Last-block finalisation of a grid reduction: every block has stored its row of NV partials; the
+// block whose ticket comes last reduces all rows in the order and tree of k_finalize_sum /
+// k_finalize_max (blockDim.x = 256 there and here, so the result is the same) into out, and
+// returns true in all its threads.  atomicInc wraps the ticket back to 0 for the next launch.
+template <int NV, bool MAX>
+__device__ __forceinline__ bool finalize_last(const double *partial, int nblocks, double *out, unsigned int *ticket)
+{
+    __shared__ unsigned int last;
+    __threadfence();   // this block's row is visible before its ticket is
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicInc(ticket, gridDim.x - 1) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double v[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            const double p = __ldcg(partial + b * NV + a);
+            v[a] = MAX ? fmax(v[a], p) : v[a] + p;
+        }
+    double r[NV];
+    if constexpr (MAX) block_max<NV>(v, r);
+    else block_sum<NV>(v, r);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < NV; ++a) out[a] = r[a];
+    return true;
+}
+
 // |x| with NaN mapped to +inf, so that a max-reduction cannot hide it
 __device__ __forceinline__ double absnan(double x) { return (x == x) ? fabs(x) : __longlong_as_double(0x7ff0000000000000ULL); }
 
@@ -651,6 +682,22 @@ struct Scalars {
     double sums[8];
     unsigned int err;         // nonzero: a bounded wait of a pipelined kernel gave up (MG_ERR_TIMEOUT)
     unsigned int nonfinite;   // nonzero: a source value is NaN or infinite (set by k_flag_nonfinite)
+    unsigned int ticket[3];   // last-block counters: pass-B sums, pass-2 norms, means of e (finalize_last)
+};
+
+// K^2 (integrability or fixed) and the momentum-source means from the pass-1 sums.
+__device__ __forceinline__ void outer_scalars(Scalars *s, size_t N, int kmode_integrability, double K2_fixed,
+                                              int periodic)
+{
+    s->K2 = kmode_integrability ? 12.0 * s->sums[0] / s->sums[1] : K2_fixed;
+    for (int a = 0; a < 3; ++a) s->msrc[a] = periodic ? s->sums[2 + a] / (double)N : 0.0;
+}
+
+// What the last block of pass B finishes when s is set: the sums, then K^2 and m_i.
+struct OuterFin {
+    Scalars *s;
+    int kmode_integrability, periodic;
+    double K2_fixed;
 };
 
 // Flags any NaN or infinity among n doubles (exponent field all ones; integer test, no FP64 op).
@@ -694,9 +741,11 @@ __global__ void k_finalize_max(const double *__restrict__ partial, int nblocks, 
         for (int a = 0; a < NV; ++a) out[a] = r[a];
 }
 
-// Sums of 4 contiguous fields (block partials).
+// Sums of 4 contiguous fields (block partials); with means != nullptr the last block also forms
+// means[a] = sum_a / N (ticket: its finalize_last counter).
 template <typename T>
-__global__ void __launch_bounds__(256) k_sum4(const T *__restrict__ x, size_t N, double *__restrict__ partial)
+__global__ void __launch_bounds__(256) k_sum4(const T *__restrict__ x, size_t N, double *__restrict__ partial,
+                                              double *__restrict__ means, unsigned int *ticket)
 {
     double v[4] = {0, 0, 0, 0};
     if constexpr (sizeof(T) == 4) {
@@ -724,15 +773,17 @@ __global__ void __launch_bounds__(256) k_sum4(const T *__restrict__ x, size_t N,
     block_sum<4>(v, r);
     if (threadIdx.x == 0)
         for (int a = 0; a < 4; ++a) partial[blockIdx.x * 4 + a] = r[a];
+    if (means && finalize_last<4, false>(partial, gridDim.x, means, ticket) && threadIdx.x == 0)
+        for (int a = 0; a < 4; ++a) means[a] = means[a] / (double)N;
 }
 
-// x_a -= sums_a / N for 4 contiguous fields (periodic gauge)
+// x_a -= means_a for 4 contiguous fields (periodic gauge)
 template <typename T>
-__global__ void __launch_bounds__(256) k_sub_mean4(T *__restrict__ x, size_t N, const double *__restrict__ sums)
+__global__ void __launch_bounds__(256) k_sub_mean4(T *__restrict__ x, size_t N, const double *__restrict__ means)
 {
     double m[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) m[a] = sums[a] / (double)N;
+    for (int a = 0; a < 4; ++a) m[a] = means[a];
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
 #pragma unroll
         for (int a = 0; a < 4; ++a) x[a * N + p] -= (T)m[a];
@@ -742,11 +793,11 @@ __global__ void __launch_bounds__(256) k_sub_mean4(T *__restrict__ x, size_t N, 
 // the finest level's layout (colour-split when split != 0).
 template <typename T>
 __global__ void __launch_bounds__(256) k_update(Geo g, double *__restrict__ x, const T *__restrict__ e, size_t N,
-                                                const double *__restrict__ esums, int periodic, int split)
+                                                const double *__restrict__ means, int split)
 {
     double m[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) m[a] = periodic ? esums[a] / (double)N : 0.0;
+    for (int a = 0; a < 4; ++a) m[a] = means ? means[a] : 0.0;
     const unsigned nx = (unsigned)g.n[0], ny = (unsigned)g.n[1];   // grids hold < 2^31 cells
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
         size_t q = p;
@@ -801,8 +852,7 @@ __device__ __forceinline__ void outer_cell(const F &u, const F &w0, const F &w1,
 static __global__ void k_outer_scalars(Scalars *s, size_t N, int kmode_integrability, double K2_fixed, int periodic)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    s->K2 = kmode_integrability ? 12.0 * s->sums[0] / s->sums[1] : K2_fixed;
-    for (int a = 0; a < 3; ++a) s->msrc[a] = periodic ? s->sums[2 + a] / (double)N : 0.0;
+    outer_scalars(s, N, kmode_integrability, K2_fixed, periodic);
 }
 
 // Pass 2: final residuals, norm partials, inner right-hand side and coefficients in T:
@@ -817,9 +867,9 @@ __device__ __forceinline__ float absnanf(float x) { return (x == x) ? fabsf(x) :
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__restrict__ x, const double *__restrict__ R,
-                                                     const double *__restrict__ src, const Scalars *__restrict__ s,
+                                                     const double *__restrict__ src, Scalars *s,
                                                      T *__restrict__ f, T *__restrict__ ab, double *__restrict__ HM,
-                                                     double *__restrict__ partial, int split)
+                                                     double *__restrict__ partial, int split, int fuse)
 {
     const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
     const double K2 = s->K2;
@@ -889,6 +939,7 @@ __global__ void __launch_bounds__(256) k_outer_pass2(Geo g, const double *__rest
     block_max<4>(mx, r);
     if (threadIdx.x == 0)
         for (int a = 0; a < 4; ++a) partial[blockIdx.x * 4 + a] = r[a];
+    if (fuse) finalize_last<4, true>(partial, gridDim.x, s->norms, &s->ticket[1]);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -181,7 +181,7 @@ template <int ORDER, int BC>
 __global__ void __launch_bounds__(256, 2) k_outer_pass1q(Geo g, Coef<double> cf, OuterCoef oc,
                                                       const double *__restrict__ x, const double *__restrict__ D,
                                                       const double *__restrict__ src, double *__restrict__ R,
-                                                      double *__restrict__ partial, Regions rg)
+                                                      double *__restrict__ partial, Regions rg, OuterFin fin)
 {
     const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
     const int sy = g.n[0], sz = g.n[0] * g.n[1];
@@ -210,6 +210,8 @@ __global__ void __launch_bounds__(256, 2) k_outer_pass1q(Geo g, Coef<double> cf,
     block_sum<5>(acc, r);
     if (threadIdx.x == 0)
         for (int a = 0; a < 5; ++a) partial[blockIdx.x * 5 + a] = r[a];
+    if (fin.s && finalize_last<5, false>(partial, gridDim.x, fin.s->sums, &fin.s->ticket[0]) && threadIdx.x == 0)
+        outer_scalars(fin.s, N, fin.kmode_integrability, fin.K2_fixed, fin.periodic);
 }
 
 }  // namespace ctt
