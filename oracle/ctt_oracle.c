@@ -21,6 +21,12 @@
  *     F_W,i = Lap W_i + (1/3) d_i d_j W_j - 8 pi (psi^6 S_i - m_i),  M_i = psi^-6 F_W,i
  *   with m_i = <8 pi psi^6 S_i> on periodic boxes (0 otherwise).
  *   psi = 1 + sum_p m_p / (2 |x - x_p|) + u; the Laplacian acts on u only.
+ *   Punctures may carry Bowen-York momentum P and spin S (Key features, "Flexibility": boosted
+ *   and/or spinning black holes): their analytic conformal extrinsic curvature
+ *     Ab_ij = 3/(2 r^2) [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n] + 3/r^3 [(S x n)_i n_j + (S x n)_j n_i]
+ *   (n the unit vector from the puncture, r the distance; a vacuum solution of the momentum
+ *   constraint, traceless and divergence-free away from the puncture, whose ADM momentum is P and
+ *   ADM angular momentum S) is added to At_ij before AtAt is formed; F_W is unchanged.
  *   On periodic boxes K^2 is set by the exact discrete integrability
  *   sum_cells F_psi = 0, and the gauge is <u> = 0, <W_i> = 0.
  *
@@ -56,9 +62,11 @@ typedef struct {
     double h[3];
     int order;       /* 2 or 4 */
     int bc;          /* 0 = periodic, 1 = Robin 1/r */
-    int npunct;      /* 0, 1 or 2 bare punctures (Robin boxes only) */
+    int npunct;      /* 0, 1 or 2 punctures (Robin boxes only) */
     double pm[2];
     double px[2][3];
+    double pP[2][3]; /* Bowen-York linear momentum of each puncture (0: bare) */
+    double pS[2][3]; /* Bowen-York spin of each puncture (0: bare) */
 } ora_grid;
 
 static long ncells(const ora_grid *g) { return (long)g->n[0] * g->n[1] * g->n[2]; }
@@ -177,18 +185,45 @@ static double momop_at(const ora_grid *g, const double *W, int comp, int i, int 
     return v;
 }
 
-/* AtAt = sum_ij At_ij^2 with At built from first derivatives of W */
+/* Bowen-York conformal extrinsic curvature of all punctures at the point x (the formula in the
+ * header, summed over punctures) */
+static void by_point(const ora_grid *g, const double x[3], double A[3][3])
+{
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) A[a][b] = 0.0;
+    for (int p = 0; p < g->npunct; ++p) {
+        const double *P = g->pP[p], *S = g->pS[p];
+        double d[3], r2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            d[a] = x[a] - g->px[p][a];
+            r2 += d[a] * d[a];
+        }
+        double r = sqrt(r2), n[3] = {d[0] / r, d[1] / r, d[2] / r};
+        double Pn = P[0] * n[0] + P[1] * n[1] + P[2] * n[2];
+        double Sxn[3] = {S[1] * n[2] - S[2] * n[1], S[2] * n[0] - S[0] * n[2], S[0] * n[1] - S[1] * n[0]};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double delta = a == b ? 1.0 : 0.0;
+                A[a][b] += 3.0 / (2.0 * r2) * (P[a] * n[b] + P[b] * n[a] - (delta - n[a] * n[b]) * Pn) +
+                           3.0 / (r2 * r) * (Sxn[a] * n[b] + Sxn[b] * n[a]);
+            }
+    }
+}
+
+/* AtAt = sum_ij At_ij^2 with At built from first derivatives of W, plus the Bowen-York part */
 static double atat_at(const ora_grid *g, const double *W, int i, int j, int k)
 {
     long N = ncells(g);
     double G[3][3]; /* G[a][b] = D_a W_b */
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) G[a][b] = d1_at(g, W + b * N, a, i, j, k);
+    double x[3] = {cellx(g, 0, i), cellx(g, 1, j), cellx(g, 2, k)}, B[3][3];
+    by_point(g, x, B);
     double div = G[0][0] + G[1][1] + G[2][2];
     double s = 0.0;
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
-            double A = G[a][b] + G[b][a] - (a == b ? 2.0 / 3.0 * div : 0.0);
+            double A = G[a][b] + G[b][a] - (a == b ? 2.0 / 3.0 * div : 0.0) + B[a][b];
             s += A * A;
         }
     return s;
@@ -249,6 +284,15 @@ void ora_atat(const ora_grid *g, const double *W, double *out)
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
             for (int i = 0; i < g->n[0]; ++i) out[lin(g, i, j, k)] = atat_at(g, W, i, j, k);
+}
+
+/* The 9 components (row-major) of the Bowen-York curvature at the point x */
+void ora_by_point(const ora_grid *g, const double *x, double *out)
+{
+    double A[3][3];
+    by_point(g, x, A);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) out[3 * a + b] = A[a][b];
 }
 
 /* out = value at the out-of-box cell (i,j,k) under the boundary condition */

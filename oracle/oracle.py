@@ -34,6 +34,8 @@ class Grid(C.Structure):
         ("npunct", C.c_int),
         ("pm", C.c_double * 2),
         ("px", (C.c_double * 3) * 2),
+        ("pP", (C.c_double * 3) * 2),
+        ("pS", (C.c_double * 3) * 2),
     ]
 
 
@@ -63,6 +65,7 @@ def lib():
         L.ora_atat.argtypes = [gp, dp, dp]
         L.ora_boundary_value.argtypes = [gp, dp, C.c_int, C.c_int, C.c_int]
         L.ora_boundary_value.restype = C.c_double
+        L.ora_by_point.argtypes = [gp, dp, dp]
         L.ora_restrict.argtypes = [gp, dp, dp]
         L.ora_prolong_add.argtypes = [gp, dp, dp]
         L.ora_residual.argtypes = [gp, dp, dp, dp, dp, dp, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -77,7 +80,8 @@ def lib():
 
 
 def make_grid(n, lo, hi, order, bc, punctures=()):
-    """n: int or 3 ints; lo/hi: float or 3 floats; punctures: [(mass, (x, y, z)), ...]."""
+    """n: int or 3 ints; lo/hi: float or 3 floats; punctures: [(mass, (x, y, z)), ...] or, with
+    Bowen-York momentum and spin, [(mass, (x, y, z), (Px, Py, Pz), (Sx, Sy, Sz)), ...]."""
     n = [n] * 3 if np.isscalar(n) else list(n)
     lo = [lo] * 3 if np.isscalar(lo) else list(lo)
     hi = [hi] * 3 if np.isscalar(hi) else list(hi)
@@ -87,11 +91,24 @@ def make_grid(n, lo, hi, order, bc, punctures=()):
         g.lo[a] = float(lo[a])
         g.h[a] = (float(hi[a]) - float(lo[a])) / int(n[a])
     g.order, g.bc, g.npunct = int(order), int(bc), len(punctures)
-    for p, (m, x) in enumerate(punctures):
+    for p, pun in enumerate(punctures):
+        m, x = pun[0], pun[1]
+        P = pun[2] if len(pun) > 2 else (0.0, 0.0, 0.0)
+        S = pun[3] if len(pun) > 3 else (0.0, 0.0, 0.0)
         g.pm[p] = float(m)
         for a in range(3):
             g.px[p][a] = float(x[a])
+            g.pP[p][a] = float(P[a])
+            g.pS[p][a] = float(S[a])
     return g
+
+
+def by_point(g, x):
+    """3x3 Bowen-York conformal extrinsic curvature of g's punctures at the point x."""
+    out = np.empty(9)
+    xs = np.ascontiguousarray(x, dtype=np.float64)
+    lib().ora_by_point(C.byref(g), _p(xs), _p(out))
+    return out.reshape(3, 3)
 
 
 def coarse(g, level=1):
