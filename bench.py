@@ -277,7 +277,12 @@ def run_solve_profile(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2501_13046_gb300 import mg
-    p = make_problem() if args.workload == "solve" else fields_mod().puncture_shell(n=args.shell_n)
+    if args.workload == "solve":
+        p = make_problem()
+    elif args.workload == "shell":
+        p = fields_mod().puncture_shell(n=args.shell_n)
+    else:
+        p = fields_mod().bowen_york_binary(n=args.binary_n)
     sp = torch.cuda.current_stream().cuda_stream
     src = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (p["rho0"], p["rho2"], *p["S"])]
     cfg = mg.config_for(p, mg.MG_MIXED, tol=WORKLOAD["tol"], max_outer=60, nested=args.nested)
@@ -381,7 +386,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bench", choices=["bench", "warmstart", "solve", "shell", "infer"])
+    ap.add_argument("--workload", default="bench", choices=["bench", "warmstart", "solve", "shell", "binary", "infer"])
+    ap.add_argument("--binary-n", type=int, default=128, help="binary workload: cells per axis")
     ap.add_argument("--shell-n", type=int, default=256, help="shell workload: cells per axis")
     ap.add_argument("--settings", default="", help="solve workload: inner_cycles,nu,omega (default: autotune)")
     ap.add_argument("--nested", type=int, default=1, choices=(0, 1),
@@ -392,7 +398,7 @@ def main():
     args = ap.parse_args()
     if args.workload == "warmstart" and args.impl == "ours":
         return run_warmstart(args)
-    if args.workload in ("solve", "shell") and args.impl == "ours":
+    if args.workload in ("solve", "shell", "binary") and args.impl == "ours":
         return run_solve_profile(args)
     if args.workload == "infer" and args.impl == "ours":
         return run_infer(args)
@@ -503,6 +509,28 @@ def main():
             break
     del qsrc
     torch.cuda.empty_cache()
+    # Bowen-York binary (two boosted, spinning punctures and a scalar shell), 128^3, nested start
+    bq = fields_mod().bowen_york_binary(n=128)
+    bsrc = [dev(a) for a in (bq["rho0"], bq["rho2"], *bq["S"])]
+    binary = {}
+    for params in (tuned_params[mg.MG_MIXED], None):
+        cfgb = mg.config_for(bq, mg.MG_MIXED, tol=WORKLOAD["tol"], max_outer=60, nested=args.nested)
+        if params:
+            apply_tuned(cfgb, params)
+        cb = mg.mg_create(cfgb, sp)
+        mg.mg_set_sources(cb, *bsrc)
+        try:
+            solve_loop(mg, torch, cb, 2, stream)
+            tb, ib = solve_loop(mg, torch, cb, 5, stream)
+        except (mg.MGError, AssertionError):
+            mg.mg_destroy(cb)
+            continue
+        binary = {"solves_per_s": 5 / tb, "outer_iters": ib["outer_iters"], "nested_outer_iters": ib["nested_iters"],
+                  "max_norm": float(ib["norms"].max()), "settings": "tuned" if params else "default"}
+        mg.mg_destroy(cb)
+        break
+    del bsrc
+    torch.cuda.empty_cache()
     batch_mixed = batch_measure(mg, torch, sp, mg.MG_MIXED, repeats=2)
     torch.cuda.empty_cache()
     batch_fp64 = batch_measure(mg, torch, sp, mg.MG_FP64, repeats=1)
@@ -526,6 +554,9 @@ def main():
                 mixed_over_fp64=value / ws / fp64_solves_per_s,
                 puncture_shell_256={**shell, "workload": "M=1 puncture, [-64,64]^3, 256^3, 4th order, Robin 1/r, "
                                                           "phi=0.02 exp(-(r-10)^2/4), Pi=0.01 phi, K=0"},
+                bowen_york_binary_128={**binary, "workload": "two Bowen-York punctures m=0.5 at (+-3,0,0), P=(0,+-0.2,0), "
+                                                             "S=(0,0,0.1), scalar shell A=0.01 at r=8, [-16,16]^3, "
+                                                             "128^3, 4th order, Robin, K=0, mixed"},
                 batch_64_uneven={"mixed": batch_mixed, "fp64_plain": batch_fp64,
                                  "mixed_over_fp64": batch_mixed["solves_per_s"] / batch_fp64["solves_per_s"],
                                  "workload": "64 periodic instances, n ~ U{48,64,96,128,160}, L=32, 4th order, "

@@ -93,6 +93,11 @@ typedef struct {
                              Ignored by mg_batch_*.  0 = off (default).                                         */
     int nested_min;       /* smallest half size per axis that is solved first; 0 = 64, else >= 3             */
     double nested_tol;    /* tolerance of the half-size solve (raised to tol); 0 = 1e-5                      */
+    double punct_P[2][3]; /* Bowen-York linear momentum of puncture p (0 = bare).  With P or S set, the
+                             analytic curvature 3/(2r^2)[P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n]
+                             + 3/r^3 [(S x n)_i n_j + (S x n)_j n_i] (n, r from the puncture; ADM momentum P,
+                             ADM angular momentum S) is added to At_ij before AtAt; F_W is unchanged     */
+    double punct_S[2][3]; /* Bowen-York spin of puncture p (0 = bare)                                    */
 } mg_config;
 
 typedef struct {
@@ -174,8 +179,9 @@ mg_status mg_time_kernel(struct mg_ctx *ctx, int which, int reps, double *ms_per
  * process whose device memory belongs to a fixed arena or another framework's allocator, or a
  * loop that must not allocate after start-up.  It takes no context.
  *
- *   cfg         grid, order, bc, k_mode, K and punctures (the iteration fields are ignored);
- *               at most 262144 cells (64^3), larger grids return MG_ERR_INVALID_ARG.
+ *   cfg         grid, order, bc, k_mode, K and bare punctures (the iteration fields are ignored);
+ *               at most 262144 cells (64^3), larger grids return MG_ERR_INVALID_ARG; punctures with a
+ *               Bowen-York momentum or spin return MG_ERR_UNSUPPORTED.
  *   u, W        device arrays, N and 3N doubles (layout as above); psi = 1 + punctures + u.
  *   rho0, S     device arrays, N and 3N doubles; rho2 device array or NULL (zero).
  *   out         host array of 4 doubles: max |H|, max |M_x|, max |M_y|, max |M_z|.

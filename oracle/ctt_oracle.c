@@ -295,6 +295,20 @@ void ora_by_point(const ora_grid *g, const double *x, double *out)
         for (int b = 0; b < 3; ++b) out[3 * a + b] = A[a][b];
 }
 
+/* The Bowen-York curvature at every cell centre: 9 fields of N (component 3a + b) */
+void ora_by_cells(const ora_grid *g, double *out)
+{
+    long N = ncells(g);
+#pragma omp parallel for
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                double x[3] = {cellx(g, 0, i), cellx(g, 1, j), cellx(g, 2, k)}, A[3][3];
+                by_point(g, x, A);
+                for (int c = 0; c < 9; ++c) out[c * N + lin(g, i, j, k)] = A[c / 3][c % 3];
+            }
+}
+
 /* out = value at the out-of-box cell (i,j,k) under the boundary condition */
 double ora_boundary_value(const ora_grid *g, const double *f, int i, int j, int k)
 {

@@ -66,6 +66,7 @@ def lib():
         L.ora_boundary_value.argtypes = [gp, dp, C.c_int, C.c_int, C.c_int]
         L.ora_boundary_value.restype = C.c_double
         L.ora_by_point.argtypes = [gp, dp, dp]
+        L.ora_by_cells.argtypes = [gp, dp]
         L.ora_restrict.argtypes = [gp, dp, dp]
         L.ora_prolong_add.argtypes = [gp, dp, dp]
         L.ora_residual.argtypes = [gp, dp, dp, dp, dp, dp, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -109,6 +110,13 @@ def by_point(g, x):
     xs = np.ascontiguousarray(x, dtype=np.float64)
     lib().ora_by_point(C.byref(g), _p(xs), _p(out))
     return out.reshape(3, 3)
+
+
+def by_cells(g):
+    """Bowen-York curvature at every cell centre, shape (3, 3, nz, ny, nx)."""
+    out = np.empty(9 * ncells(g))
+    lib().ora_by_cells(C.byref(g), _p(out))
+    return out.reshape((3, 3) + shape3(g))
 
 
 def coarse(g, level=1):

@@ -57,6 +57,10 @@ mg_status validate(const mg_config *c)
     if (c->cycle < 0 || c->cycle > 2) return fail(MG_ERR_INVALID_ARG, "cycle must be 0, 1 (V) or 2 (W)");
     if (!(c->omega == 0.0 || (c->omega > 0.0 && c->omega < 2.0)))
         return fail(MG_ERR_INVALID_ARG, "omega must be 0 (default 1) or in (0, 2)");
+    for (int p = 0; p < 2; ++p)
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(c->punct_P[p][a]) || !std::isfinite(c->punct_S[p][a]))
+                return fail(MG_ERR_INVALID_ARG, "puncture momentum or spin not finite");
     if (c->nested != 0 && c->nested != 1) return fail(MG_ERR_INVALID_ARG, "nested must be 0 or 1");
     if (c->nested_min != 0 && c->nested_min < 3) return fail(MG_ERR_INVALID_ARG, "nested_min must be 0 or >= 3");
     if (!(c->nested_tol >= 0.0) || !std::isfinite(c->nested_tol)) return fail(MG_ERR_INVALID_ARG, "bad nested_tol");
@@ -68,6 +72,15 @@ mg_status validate(const mg_config *c)
                 return fail(MG_ERR_INVALID_ARG, "levels: every level above the coarsest needs even sizes >= 6");
         }
     return MG_OK;
+}
+
+// Punctures with a Bowen-York momentum or spin (only the first npunct count).
+bool has_bowen_york(const mg_config *c)
+{
+    for (int p = 0; p < c->npunct; ++p)
+        for (int a = 0; a < 3; ++a)
+            if (c->punct_P[p][a] != 0.0 || c->punct_S[p][a] != 0.0) return true;
+    return false;
 }
 
 // Nested start defaults.  Half sizes below kNestedMinN are not worth solving first: their outer
@@ -93,7 +106,7 @@ bool nested_child_config(const mg_config *c, mg_config *cc)
 }
 
 struct Layout {
-    size_t X, SRC, R, D, PB, RT, partial, scal, Gpsi, GW, gj, own, child, total;
+    size_t X, SRC, R, D, PB, RT, BY, partial, scal, Gpsi, GW, gj, own, child, total;
     int dense, mpsi, mw, has_child;
     std::vector<size_t> eA, eB, f, c;
 };
@@ -112,6 +125,7 @@ Layout layout_for(const mg_config *c)
     L.D = take(4 * N * 8);
     if (c->npunct > 0) L.PB = take(N * 8);
     if (c->bc == MG_BC_ROBIN) L.RT = take((size_t)(c->n[0] + 4) * (c->n[1] + 4) * (c->n[2] + 4) * 8);
+    if (has_bowen_york(c)) L.BY = take(6 * N * 8);
     for (int l = 0; l < lv; ++l) {
         size_t Nl = ((size_t)(c->n[0] >> l)) * (c->n[1] >> l) * (c->n[2] >> l);
         L.eA.push_back(take(4 * Nl * tb));
@@ -426,6 +440,21 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
             k_fill_robin_table<<<grid_for(M), kThreads, 0, x->stream>>>(x->lev[0].geo, rt);
             if ((e = cudaGetLastError()) != cudaSuccess) { st = fail(MG_ERR_CUDA, cudaGetErrorString(e)); break; }
             x->lev[0].geo.rtab = rt;
+        }
+        if (has_bowen_york(cfg)) {
+            ByPunct bp;
+            std::memset(&bp, 0, sizeof(bp));
+            bp.n = cfg->npunct;
+            for (int p = 0; p < cfg->npunct; ++p)
+                for (int a = 0; a < 3; ++a) {
+                    bp.x[p][a] = cfg->punct_x[p][a];
+                    bp.P[p][a] = cfg->punct_P[p][a];
+                    bp.S[p][a] = cfg->punct_S[p][a];
+                }
+            double *by = (double *)(b + lay.BY);
+            k_fill_by<<<grid_for(x->N), kThreads, 0, x->stream>>>(x->lev[0].geo, bp, by);
+            if ((e = cudaGetLastError()) != cudaSuccess) { st = fail(MG_ERR_CUDA, cudaGetErrorString(e)); break; }
+            x->lev[0].geo.by = by;
         }
         if (x->dense && x->nlev >= 2) {
             const LevelBufs &L1 = x->lev[x->nlev - 2], &Lc = x->lev[x->nlev - 1];

@@ -35,7 +35,49 @@ struct Geo {
     const double *psibg;   // finest level with punctures: psi_background per cell (N doubles), else null
     const double *rtab;    // finest level of a Robin box: the FP64 ratio |x_b| / |x_g| on the box padded by
                            // 2 cells per side (1 inside), (n0+4)(n1+4)(n2+4) doubles, else null
+    const double *by;      // finest level with Bowen-York punctures: their curvature per cell, 6 fields of N
+                           // (A_00, A_11, A_22, A_01, A_02, A_12), else null
 };
+
+// Bowen-York punctures (boosted and/or spinning black holes): positions, momenta and spins.
+struct ByPunct {
+    int n;
+    double x[2][3], P[2][3], S[2][3];
+};
+
+// by = sum over punctures of the analytic conformal extrinsic curvature
+//   A_ij = 3/(2 r^2) [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n] + 3/r^3 [(S x n)_i n_j + (S x n)_j n_i]
+// (n the unit vector from the puncture to the cell centre, r the distance), once per context.
+static __global__ void __launch_bounds__(256) k_fill_by(Geo g, ByPunct bp, double *__restrict__ by)
+{
+    const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        const int c[3] = {(int)(p % g.n[0]), (int)((p / g.n[0]) % g.n[1]), (int)(p / ((size_t)g.n[0] * g.n[1]))};
+        double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int q = 0; q < bp.n; ++q) {
+            double d[3], r2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                d[a] = g.lo[a] + (c[a] + 0.5) * g.h[a] - bp.x[q][a];
+                r2 += d[a] * d[a];
+            }
+            const double r = sqrt(r2), n[3] = {d[0] / r, d[1] / r, d[2] / r};
+            const double *P = bp.P[q], *S = bp.S[q];
+            const double Pn = P[0] * n[0] + P[1] * n[1] + P[2] * n[2];
+            const double Sxn[3] = {S[1] * n[2] - S[2] * n[1], S[2] * n[0] - S[0] * n[2], S[0] * n[1] - S[1] * n[0]};
+            const double cp = 1.5 / r2, cs = 3.0 / (r2 * r);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    A[a][b] += cp * (P[a] * n[b] + P[b] * n[a] - ((a == b ? 1.0 : 0.0) - n[a] * n[b]) * Pn) +
+                               cs * (Sxn[a] * n[b] + Sxn[b] * n[a]);
+        }
+        by[p] = A[0][0];
+        by[N + p] = A[1][1];
+        by[2 * N + p] = A[2][2];
+        by[3 * N + p] = A[0][1];
+        by[4 * N + p] = A[0][2];
+        by[5 * N + p] = A[1][2];
+    }
+}
 
 template <typename T>
 struct Coef {
@@ -819,7 +861,8 @@ __global__ void __launch_bounds__(256) k_update(Geo g, double *__restrict__ x, c
 // and block partial sums of (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi), psi^5, 8 pi psi^6 S_i.
 template <int ORDER, class F>
 __device__ __forceinline__ void outer_cell(const F &u, const F &w0, const F &w1, const F &w2, const Coef<double> &cf,
-                                           double &lu, double &aa, double mom[3])
+                                           double &lu, double &aa, double mom[3], const double *by = nullptr,
+                                           size_t N = 0)
 {
     double G[3][3];   // G[a][b] = D_a W_b
     G[0][0] = d1<ORDER, 0, double>(w0) * cf.ih[0];
@@ -832,12 +875,21 @@ __device__ __forceinline__ void outer_cell(const F &u, const F &w0, const F &w1,
     G[1][2] = d1<ORDER, 1, double>(w2) * cf.ih[1];
     G[2][2] = d1<ORDER, 2, double>(w2) * cf.ih[2];
     double div = G[0][0] + G[1][1] + G[2][2];
+    double B[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // Bowen-York part (by: the cell's first component)
+    if (by) {
+        B[0][0] = by[0];
+        B[1][1] = by[N];
+        B[2][2] = by[2 * N];
+        B[0][1] = B[1][0] = by[3 * N];
+        B[0][2] = B[2][0] = by[4 * N];
+        B[1][2] = B[2][1] = by[5 * N];
+    }
     aa = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            double A = G[a][b] + G[b][a] - (a == b ? (2.0 / 3.0) * div : 0.0);
+            double A = G[a][b] + G[b][a] - (a == b ? (2.0 / 3.0) * div : 0.0) + B[a][b];
             aa += A * A;
         }
     double Je[4], ctr[4];

@@ -127,6 +127,10 @@ mg_status check_config(const mg_config *c)
         return fail(MG_ERR_INVALID_ARG, "integrability K needs a periodic box");
     if (c->npunct < 0 || c->npunct > 2) return fail(MG_ERR_INVALID_ARG, "npunct must be 0..2");
     if (c->npunct > 0 && c->bc == MG_BC_PERIODIC) return fail(MG_ERR_UNSUPPORTED, "punctures need Robin boundaries");
+    for (int p = 0; p < c->npunct; ++p)
+        for (int a = 0; a < 3; ++a)
+            if (c->punct_P[p][a] != 0.0 || c->punct_S[p][a] != 0.0)
+                return fail(MG_ERR_UNSUPPORTED, "Bowen-York punctures are not supported by the allocation-free norms");
     if (!std::isfinite(c->K)) return fail(MG_ERR_INVALID_ARG, "K not finite");
     size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
     if (N > kNoallocMaxCells)

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_outer_div(Geo g, OuterCoef oc, const do
 template <int ORDER, class F>
 __device__ __forceinline__ void outer_cell_qa(const F &u, const F &w0, const F &w1, const F &w2, const F &q0,
                                               const F &q1, const F &q2, double dv, const OuterCoef &oc, double &lu,
-                                              double &aa, double mom[3])
+                                              double &aa, double mom[3], const double *by = nullptr, size_t N = 0)
 {
     lu = lapw<ORDER>(u, oc.k1, oc.nk2, oc.k0);
     mom[0] = lapw<ORDER>(w0, oc.m1[0], oc.nm2[0], oc.m0[0]) + d1w<ORDER, 0>(q0, oc.q1[0], oc.q2[0]);
@@ -110,18 +110,28 @@ __device__ __forceinline__ void outer_cell_qa(const F &u, const F &w0, const F &
     const double s02 = d1w<ORDER, 0>(w2, oc.c1[0], oc.c2[0]) + d1w<ORDER, 2>(w0, oc.c1[2], oc.c2[2]);
     const double s12 = d1w<ORDER, 1>(w2, oc.c1[1], oc.c2[1]) + d1w<ORDER, 2>(w1, oc.c1[2], oc.c2[2]);
     const double t = (-2.0 / 3.0) * dv;
-    const double a00 = fma(2.0, g00, t), a11 = fma(2.0, g11, t), a22 = fma(2.0, g22, t);
-    const double off = fma(s01, s01, fma(s02, s02, s12 * s12));
+    double a00 = fma(2.0, g00, t), a11 = fma(2.0, g11, t), a22 = fma(2.0, g22, t);
+    double b01 = s01, b02 = s02, b12 = s12;
+    if (by) {   // Bowen-York part (by: the cell's first component, stride N)
+        a00 += by[0];
+        a11 += by[N];
+        a22 += by[2 * N];
+        b01 += by[3 * N];
+        b02 += by[4 * N];
+        b12 += by[5 * N];
+    }
+    const double off = fma(b01, b01, fma(b02, b02, b12 * b12));
     aa = fma(2.0, off, fma(a00, a00, fma(a11, a11, a22 * a22)));
 }
 
 template <int ORDER>
 __device__ __forceinline__ void outer_cell_q(const double *x, const double *D, size_t N, size_t p, int sy, int sz,
-                                             const OuterCoef &oc, double &lu, double &aa, double mom[3])
+                                             const OuterCoef &oc, double &lu, double &aa, double mom[3],
+                                             const double *by)
 {
     AccI<double> u{x + p, sy, sz}, w0{x + N + p, sy, sz}, w1{x + 2 * N + p, sy, sz}, w2{x + 3 * N + p, sy, sz};
     AccI<double> q0{D + p, sy, sz}, q1{D + N + p, sy, sz}, q2{D + 2 * N + p, sy, sz};
-    outer_cell_qa<ORDER>(u, w0, w1, w2, q0, q1, q2, D[3 * N + p], oc, lu, aa, mom);
+    outer_cell_qa<ORDER>(u, w0, w1, w2, q0, q1, q2, D[3 * N + p], oc, lu, aa, mom, by ? by + p : nullptr, N);
 }
 
 // Nonlinear terms and outputs at cell p (shared by the interior and shell paths):
@@ -166,7 +176,8 @@ __device__ __noinline__ void outer_shell_cell(const Geo &g, const Coef<double> &
         const size_t p = (size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k);
         outer_cell_qa<ORDER>(a0, a1, a2, a3, q0, q1, q2, D[3 * N + p], oc, lu, aa, mom);
     } else {
-        outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom);
+        const size_t p = (size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k);
+        outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom, g.by ? g.by + p : nullptr, N);
     }
     out[0] = lu;
     out[1] = aa;
@@ -193,7 +204,7 @@ __global__ void __launch_bounds__(256, 2) k_outer_pass1q(Geo g, Coef<double> cf,
              t += stride) {
             const size_t p = (size_t)i + (size_t)sy * j + (size_t)sz * k;
             double lu, aa, mom[3];
-            outer_cell_q<ORDER>(x, D, N, p, sy, sz, oc, lu, aa, mom);
+            outer_cell_q<ORDER>(x, D, N, p, sy, sz, oc, lu, aa, mom, g.by);
             outer_tail(g, i, j, k, p, N, lu, aa, mom, x, src, R, acc);
         }
     } else {

@@ -136,6 +136,24 @@ def puncture_shell(n=256, half=64.0, A=0.02, mass=1.0, order=4):
                     rho0, rho2, S, A=A)
 
 
+def bowen_york_binary(n=128, half=16.0, d=3.0, mass=0.5, P=0.2, S=0.1, A=0.01, order=4):
+    """Two Bowen-York punctures (Key features, "Flexibility": boosted and/or spinning black holes)
+    of bare mass `mass` at (+-d, 0, 0) with momenta (0, +-P, 0) (an orbiting pair) and equal spins
+    (0, 0, S), in [-half, half]^3 with Robin boundaries and K = 0, plus a scalar shell
+    phi = A exp(-(r - 8)^2 / 4), Pi = 0.01 phi around the origin so that the momentum sources are
+    not zero.  The punctures sit on cell faces when d / h is an integer (never on a cell centre)."""
+    X, Y, Z = cell_centres(n, -half, half)
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    phi = A * np.exp(-((r - 8.0) ** 2) / 4.0)
+    dphidr = -phi * (r - 8.0) / 2.0
+    dphi = [dphidr * X / r, dphidr * Y / r, dphidr * Z / r]
+    Pi = 0.01 * phi
+    rho0, rho2, Ssrc = scalar_sources(phi, dphi, Pi)
+    punct = [(mass, (d, 0.0, 0.0), (0.0, P, 0.0), (0.0, 0.0, S)),
+             (mass, (-d, 0.0, 0.0), (0.0, -P, 0.0), (0.0, 0.0, S))]
+    return _problem("bowen_york_binary", n, -half, half, order, ROBIN, K_FIXED, 0.0, punct, rho0, rho2, Ssrc, A=A)
+
+
 def batch_sizes(count=64, sizes=(48, 64, 96, 128, 160), base_seed=4000, a_lo=2e-5, a_hi=8e-5):
     """[(n_b, a0_b, seed_b)]: n_b uniform over `sizes`, a0_b uniform in [a_lo, a_hi]."""
     out = []

@@ -38,6 +38,7 @@ class mg_config(C.Structure):
         ("spin_limit", C.c_longlong), ("inner_cycles", C.c_int), ("block_threads", C.c_int),
         ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double), ("nested", C.c_int),
         ("nested_min", C.c_int), ("nested_tol", C.c_double),
+        ("punct_P", (C.c_double * 3) * 2), ("punct_S", (C.c_double * 3) * 2),
     ]
 
 
@@ -278,10 +279,15 @@ def config_for(problem, precision=MG_MIXED, **overrides):
     cfg.K = problem["K"]
     cfg.precision = precision
     cfg.npunct = len(problem["punctures"])
-    for p, (m, x) in enumerate(problem["punctures"]):
+    for p, pun in enumerate(problem["punctures"]):
+        m, x = pun[0], pun[1]
         cfg.punct_m[p] = m
         for a in range(3):
             cfg.punct_x[p][a] = x[a]
+            if len(pun) > 2:
+                cfg.punct_P[p][a] = pun[2][a]
+            if len(pun) > 3:
+                cfg.punct_S[p][a] = pun[3][a]
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg

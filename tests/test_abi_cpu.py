@@ -64,6 +64,24 @@ def test_nested_workspace_holds_the_half_size_contexts(lib):
     assert ws(128, 1, 24) - ws(128, 0) < ws(128, 0) // 6   # about 1/8 + 1/64, plus the coarse inverses
 
 
+def test_bowen_york_workspace_and_validation(lib):
+    """A puncture with a momentum or spin adds its curvature table (6 FP64 fields) to the
+    workspace; a non-finite momentum is rejected on the host."""
+    def cfg_for(P=(0.0, 0.0, 0.0), S=(0.0, 0.0, 0.0)):
+        cfg = lib.mg_config_default()
+        cfg.n[0] = cfg.n[1] = cfg.n[2] = 32
+        cfg.bc, cfg.k_mode, cfg.npunct, cfg.punct_m[0] = lib.MG_BC_ROBIN, lib.MG_K_FIXED, 1, 1.0
+        for a in range(3):
+            cfg.punct_P[0][a], cfg.punct_S[0][a] = P[a], S[a]
+        return cfg
+    bare = lib.mg_workspace_size(cfg_for())
+    assert lib.mg_workspace_size(cfg_for(P=(0.1, 0.0, 0.0))) == bare + 6 * 32 ** 3 * 8
+    assert lib.mg_workspace_size(cfg_for(S=(0.0, 0.0, 0.2))) == bare + 6 * 32 ** 3 * 8
+    with pytest.raises(lib.MGError) as e:
+        lib.mg_workspace_size(cfg_for(P=(float("nan"), 0.0, 0.0)))
+    assert e.value.status == lib.MG_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("field,value,status", [
     ("order", 3, 1), ("bc", 7, 1), ("precision", 5, 1), ("levels", 6, 1), ("coarse_sweeps", 0, 1),
     ("nested", 2, 1), ("nested_min", 2, 1), ("nested_tol", -1.0, 1),
