@@ -92,7 +92,7 @@ typedef struct {
                              root are the same.  The half-size context lives in this context's workspace.
                              Ignored by mg_batch_*.  0 = off (default).                                         */
     int nested_min;       /* smallest half size per axis that is solved first; 0 = 64, else >= 3             */
-    double nested_tol;    /* tolerance of the half-size solve (raised to tol); 0 = 1e-5                      */
+    double nested_tol;    /* tolerance of the half-size solve (raised to tol); 0 = 3e-4                      */
     double punct_P[2][3]; /* Bowen-York linear momentum of puncture p (0 = bare).  With P or S set, the
                              analytic curvature 3/(2r^2)[P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n]
                              + 3/r^3 [(S x n)_i n_j + (S x n)_j n_i] (n, r from the puncture; ADM momentum P,

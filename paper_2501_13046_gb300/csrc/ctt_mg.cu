@@ -84,11 +84,13 @@ bool has_bowen_york(const mg_config *c)
 }
 
 // Nested start defaults.  Half sizes below kNestedMinN are not worth solving first: their outer
-// iterations cost launch latency, not bandwidth, and save little fine work.  Below kNestedTol the
-// half-size solve's own discretisation error against the fine root dominates the fine residual of
-// the interpolated start, so solving it further buys no fine iteration.
+// iterations cost launch latency, not bandwidth, and save little fine work.  The fine residual of
+// the interpolated start is set by the half-size root's own discretisation error (about 1.5e-4 at
+// 128^3 from 64^3) once the half-size solve is below it, so kNestedTol stops it near that level
+// (measured: 128^3 periodic and 256^3 Robin shell both fastest at 1e-4..3e-4; 1e-3 costs a fine
+// iteration on the shell).
 constexpr int kNestedMinN = 64;
-constexpr double kNestedTol = 1e-5;
+constexpr double kNestedTol = 3e-4;
 
 // Configuration of the half-size problem of c's nested start; false when c has none.  A valid c gives a
 // valid child: its level l is c's level l + 1.
@@ -367,6 +369,8 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
                 g.n[a] = cfg->n[a] >> l;
                 g.lo[a] = cfg->lo[a];
                 g.h[a] = (cfg->hi[a] - cfg->lo[a]) / cfg->n[a] * (double)(1 << l);
+                g.lof[a] = (float)g.lo[a];
+                g.hf[a] = (float)g.h[a];
             }
             g.npunct = cfg->npunct;
             for (int p = 0; p < cfg->npunct; ++p) {
@@ -459,7 +463,8 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         if (x->dense && x->nlev >= 2) {
             const LevelBufs &L1 = x->lev[x->nlev - 2], &Lc = x->lev[x->nlev - 1];
             x->fused = cfg->smoother == 0 && L1.N <= (size_t)kFusedMaxCells &&
-                       fused_smem_bytes((int)L1.N, (int)Lc.N, x->tbytes) <= kMaxCoarseSmem;
+                       fused_smem_bytes((int)L1.N, (int)Lc.N, x->tbytes,
+                                        fused_ratio_cells(L1.geo, cfg->bc == MG_BC_ROBIN)) <= kMaxCoarseSmem;
         }
         if (x->dense) {
             const int O = cfg->order;

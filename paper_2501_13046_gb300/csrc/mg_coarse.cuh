@@ -195,14 +195,41 @@ __global__ void __launch_bounds__(256) k_dense_apply(const T *__restrict__ Gpsi,
 // operator, colour passes and Jacobi-within-colour reads as the per-kernel path).  Level l is
 // colour-split in global memory and plain in shared memory; the coarsest level is plain.
 constexpr int kFusedMaxCells = 1728;   // next-to-coarsest level up to 12^3 cells
+// threads of k_coarse_cycle: 128 registers per thread for FP32 (255 for FP64), which the 4th-order
+// stencil with Robin ratios needs without spilling
+template <typename T> constexpr int fused_threads() { return sizeof(T) == 8 ? 256 : 512; }
 
-__host__ __device__ inline size_t fused_smem_bytes(int N1, int Nc, size_t tb)
+// Shared memory of k_coarse_cycle: the level's state, ping-pong copy, rhs and coefficients, the
+// coarsest level's rhs and solution, and on Robin boxes the level's ghost ratios (rt_cells =
+// (n0+4)(n1+4)(n2+4), else 0).
+__host__ __device__ inline size_t fused_smem_bytes(int N1, int Nc, size_t tb, size_t rt_cells)
 {
-    return (14 * (size_t)N1 + 8 * (size_t)Nc) * tb;
+    return (14 * (size_t)N1 + 8 * (size_t)Nc + rt_cells) * tb;
 }
 
+inline size_t fused_ratio_cells(const Geo &g, int robin)
+{
+    return robin ? (size_t)(g.n[0] + 4) * (g.n[1] + 4) * (g.n[2] + 4) : 0;
+}
+
+// Robin accessor of the fused cycle: the clamped cell's value times the level's ghost ratio, read
+// from the table rt over the box padded by 2 (1 inside), so no branch and no square root.
+template <typename T>
+struct AccRT {
+    const T *f, *rt;
+    const Geo *g;
+    int i, j, k;
+    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
+    {
+        const int p0 = i + dx, p1 = j + dy, p2 = k + dz;
+        const int n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
+        const int b0 = min(max(p0, 0), n0 - 1), b1 = min(max(p1, 0), n1 - 1), b2 = min(max(p2, 0), n2 - 1);
+        return f[b0 + n0 * (b1 + n1 * b2)] * rt[(p0 + 2) + (n0 + 4) * ((p1 + 2) + (n1 + 4) * (p2 + 2))];
+    }
+};
+
 template <typename T, int ORDER, int BC>
-__global__ void __launch_bounds__(1024) k_coarse_cycle(Geo g, Coef<T> cf, Geo gc, const T *__restrict__ f,
+__global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef<T> cf, Geo gc, const T *__restrict__ f,
                                                        const T *__restrict__ ab, const T *__restrict__ e_in,
                                                        T *__restrict__ e_out, int zero, int nu_pre, int nu_post,
                                                        const T *__restrict__ Gpsi, int mpsi,
@@ -217,6 +244,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(Geo g, Coef<T> cf, Geo gc
     T *cs = fs + 4 * N;
     T *fc = cs + 2 * N;
     T *ec = fc + 4 * Nc;
+    T *rt = ec + 4 * Nc;   // Robin: ghost ratios of the level over its box padded by 2
     auto ijk = [&](int q, int &i, int &j, int &k) {
         i = q % g.n[0];
         j = (q / g.n[0]) % g.n[1];
@@ -236,29 +264,50 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(Geo g, Coef<T> cf, Geo gc
         cs[q] = ab[sq];
         cs[N + q] = ab[N + sq];
     }
+    if constexpr (BC == BC_ROBIN) {
+        const int m0 = g.n[0] + 4, m1 = g.n[1] + 4, M = m0 * m1 * (g.n[2] + 4);
+        for (int e = tid; e < M; e += bs) {
+            const int i = e % m0 - 2, j = (e / m0) % m1 - 2, k = e / (m0 * m1) - 2;
+            const int bi = min(max(i, 0), g.n[0] - 1), bj = min(max(j, 0), g.n[1] - 1), bk = min(max(k, 0), g.n[2] - 1);
+            rt[e] = (bi == i && bj == j && bk == k) ? (T)1 : robin_ratio<T>(g, bi, bj, bk, i, j, k);
+        }
+    }
     __syncthreads();
+    // J e at cell (i, j, k) of the level held in e
+    auto apply = [&](const T *e, int i, int j, int k, T a, T b, T Je[4], T ctr[4]) {
+        if constexpr (BC == BC_ROBIN) {
+            AccRT<T> a0{e, rt, &g, i, j, k}, a1{e + N, rt, &g, i, j, k}, a2{e + 2 * N, rt, &g, i, j, k},
+                a3{e + 3 * N, rt, &g, i, j, k};
+            apply_J<ORDER, T>(a0, a1, a2, a3, a, b, cf, Je, ctr);
+        } else {
+            AccB<T, BC> a0{e, &g, i, j, k}, a1{e + N, &g, i, j, k}, a2{e + 2 * N, &g, i, j, k}, a3{e + 3 * N, &g, i, j, k};
+            apply_J<ORDER, T>(a0, a1, a2, a3, a, b, cf, Je, ctr);
+        }
+    };
+    // one colour pass: the cells of the colour (thread t: pair t % (nx/2) of row t / (nx/2); nx is
+    // even on every level above the coarsest) write their new values into alt (Jacobi within the
+    // colour: all reads see cur), then copy them back into cur
+    const int nxh = g.n[0] >> 1, Nh = N >> 1;
     auto sweeps = [&](int n) {
         for (int s = 0; s < n; ++s)
             for (int colour = 0; colour < 2; ++colour) {
-                for (int q = tid; q < N; q += bs) {
-                    int i, j, k;
-                    ijk(q, i, j, k);
-                    if (((i + j + k) & 1) == colour) {
-                        T Je[4], ctr[4];
-                        AccB<T, BC> a0{cur, &g, i, j, k}, a1{cur + N, &g, i, j, k}, a2{cur + 2 * N, &g, i, j, k},
-                            a3{cur + 3 * N, &g, i, j, k};
-                        apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
-                        alt[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * cf.dl + cs[N + q]) * cf.iom);
-                        for (int a = 0; a < 3; ++a)
-                            alt[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
-                    } else {
-                        for (int a = 0; a < 4; ++a) alt[a * N + q] = cur[a * N + q];
-                    }
+                for (int t = tid; t < Nh; t += bs) {
+                    const int row = t / nxh, j = row % g.n[1], k = row / g.n[1];
+                    const int i = 2 * (t - row * nxh) + ((colour + j + k) & 1);
+                    const int q = i + g.n[0] * row;
+                    T Je[4], ctr[4];
+                    apply(cur, i, j, k, cs[q], cs[N + q], Je, ctr);
+                    alt[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * cf.dl + cs[N + q]) * cf.iom);
+                    for (int a = 0; a < 3; ++a)
+                        alt[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
                 }
                 __syncthreads();
-                T *t = cur;
-                cur = alt;
-                alt = t;
+                for (int t = tid; t < Nh; t += bs) {
+                    const int row = t / nxh, j = row % g.n[1], k = row / g.n[1];
+                    const int q = 2 * (t - row * nxh) + ((colour + j + k) & 1) + g.n[0] * row;
+                    for (int a = 0; a < 4; ++a) cur[a * N + q] = alt[a * N + q];
+                }
+                __syncthreads();
             }
     };
     sweeps(nu_pre);
@@ -267,9 +316,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(Geo g, Coef<T> cf, Geo gc
         int i, j, k;
         ijk(q, i, j, k);
         T Je[4], ctr[4];
-        AccB<T, BC> a0{cur, &g, i, j, k}, a1{cur + N, &g, i, j, k}, a2{cur + 2 * N, &g, i, j, k},
-            a3{cur + 3 * N, &g, i, j, k};
-        apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
+        apply(cur, i, j, k, cs[q], cs[N + q], Je, ctr);
         for (int a = 0; a < 4; ++a) alt[a * N + q] = fs[a * N + q] - Je[a];
     }
     __syncthreads();

@@ -179,9 +179,10 @@ mg_status enqueue_cycle(mg_ctx *x, int l, bool zero)
             x->join_pending = false;
         }
         const T *ein = zero ? (const T *)L.eA : (const T *)L.cur();
-        const size_t smem = fused_smem_bytes((int)L.N, (int)C.N, sizeof(T));
+        const size_t smem =
+            fused_smem_bytes((int)L.N, (int)C.N, sizeof(T), fused_ratio_cells(L.geo, x->cfg.bc == MG_BC_ROBIN));
         dispatch_bc(x->cfg.bc, [&](auto B) {
-            k_coarse_cycle<T, ORDER, decltype(B)::value><<<1, 1024, smem, x->stream>>>(
+            k_coarse_cycle<T, ORDER, decltype(B)::value><<<1, fused_threads<T>(), smem, x->stream>>>(
                 L.geo, make_coef<T>(L.geo, x->cfg.order, x->omega), C.geo, (const T *)L.f, (const T *)L.c, ein,
                 (T *)L.eA, zero ? 1 : 0, x->cfg.nu_pre, x->cfg.nu_post, (const T *)x->Gpsi, x->mpsi,
                 (const T *)x->GW, x->mw);

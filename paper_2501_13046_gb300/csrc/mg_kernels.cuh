@@ -29,6 +29,7 @@ struct Geo {
     int n[3];
     double lo[3];
     double h[3];
+    float lof[3], hf[3];   // lo and h rounded to FP32 (FP32 Robin ratios; set with lo and h)
     int npunct;
     double pm[2];
     double px[2][3];
@@ -101,7 +102,10 @@ __device__ __forceinline__ double cellx(const Geo &g, int a, int i) { return g.l
 template <typename T>
 __device__ __forceinline__ T robin_ratio(const Geo &g, int bi, int bj, int bk, int gi, int gj, int gk)
 {
-    auto c = [&](int a, int i) { return (T)g.lo[a] + ((T)i + (T)0.5) * (T)g.h[a]; };
+    auto c = [&](int a, int i) {
+        if constexpr (std::is_same<T, float>::value) return g.lof[a] + ((float)i + 0.5f) * g.hf[a];
+        else return g.lo[a] + (i + 0.5) * g.h[a];
+    };
     const T xb = c(0, bi), yb = c(1, bj), zb = c(2, bk), xg = c(0, gi), yg = c(1, gj), zg = c(2, gk);
     const T A = xb * xb + yb * yb + zb * zb, B = xg * xg + yg * yg + zg * zg;
     if constexpr (std::is_same<T, float>::value) return A * rsqrtf(A * B);

@@ -159,6 +159,8 @@ extern "C" mg_status mg_residual_norms_noalloc(const mg_config *cfg, const doubl
         g.n[a] = cfg->n[a];
         g.lo[a] = cfg->lo[a];
         g.h[a] = (cfg->hi[a] - cfg->lo[a]) / cfg->n[a];
+        g.lof[a] = (float)g.lo[a];
+        g.hf[a] = (float)g.h[a];
     }
     g.npunct = cfg->npunct;
     for (int p = 0; p < cfg->npunct; ++p) {
