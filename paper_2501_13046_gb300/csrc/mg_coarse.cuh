@@ -284,30 +284,29 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
             apply_J<ORDER, T>(a0, a1, a2, a3, a, b, cf, Je, ctr);
         }
     };
-    // one colour pass: the cells of the colour (thread t: pair t % (nx/2) of row t / (nx/2); nx is
-    // even on every level above the coarsest) write their new values into alt (Jacobi within the
-    // colour: all reads see cur), then copy them back into cur
+    // one colour pass, ping-pong: thread t takes pair t % (nx/2) of row t / (nx/2) (nx is even on
+    // every level above the coarsest); the pair's cell of the colour gets its new value in alt
+    // (Jacobi within the colour: all reads see cur), the other cell is copied; then swap
     const int nxh = g.n[0] >> 1, Nh = N >> 1;
     auto sweeps = [&](int n) {
         for (int s = 0; s < n; ++s)
             for (int colour = 0; colour < 2; ++colour) {
                 for (int t = tid; t < Nh; t += bs) {
                     const int row = t / nxh, j = row % g.n[1], k = row / g.n[1];
-                    const int i = 2 * (t - row * nxh) + ((colour + j + k) & 1);
-                    const int q = i + g.n[0] * row;
+                    const int par = (colour + j + k) & 1;
+                    const int i = 2 * (t - row * nxh) + par;
+                    const int q = i + g.n[0] * row, qo = q + 1 - 2 * par;   // the pair's other cell
                     T Je[4], ctr[4];
                     apply(cur, i, j, k, cs[q], cs[N + q], Je, ctr);
                     alt[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * cf.dl + cs[N + q]) * cf.iom);
                     for (int a = 0; a < 3; ++a)
                         alt[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
+                    for (int a = 0; a < 4; ++a) alt[a * N + qo] = cur[a * N + qo];
                 }
                 __syncthreads();
-                for (int t = tid; t < Nh; t += bs) {
-                    const int row = t / nxh, j = row % g.n[1], k = row / g.n[1];
-                    const int q = 2 * (t - row * nxh) + ((colour + j + k) & 1) + g.n[0] * row;
-                    for (int a = 0; a < 4; ++a) cur[a * N + q] = alt[a * N + q];
-                }
-                __syncthreads();
+                T *tmp = cur;
+                cur = alt;
+                alt = tmp;
             }
     };
     sweeps(nu_pre);
