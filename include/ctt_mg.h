@@ -153,6 +153,18 @@ mg_status mg_solve(struct mg_ctx *ctx, mg_solve_info *info);
 /* Copy out u (N doubles), W (3N doubles) and K; any pointer may be NULL. */
 mg_status mg_get_solution(struct mg_ctx *ctx, double *u, double *W, double *K, int on_device);
 
+/*
+ * Checkpoint / resume.  mg_checkpoint_save writes the context's state to `path` as a raw
+ * little-endian file: the 8 bytes "CTTMGCK1", int32 n[3], order, bc, 0, the last K^2 (double),
+ * then u (N doubles) and W (3N doubles), x fastest, no ghost cells.  mg_checkpoint_load reads such
+ * a file written for the same n, order and bc and makes its (u, W) the next solve's initial guess
+ * (as mg_set_initial_guess with non-NULL u and W: a nested start is skipped).  Both return
+ * MG_ERR_INVALID_ARG for a file that cannot be opened, read or written, a bad header or another
+ * grid, and MG_ERR_UNSUPPORTED on a big-endian host; both synchronise the context's stream.
+ */
+mg_status mg_checkpoint_save(struct mg_ctx *ctx, const char *path);
+mg_status mg_checkpoint_load(struct mg_ctx *ctx, const char *path);
+
 /* Evaluate the constraints at the current state: out = max |H|, max |M_x|, |M_y|, |M_z|. */
 mg_status mg_residual_norms(struct mg_ctx *ctx, double out[4]);
 

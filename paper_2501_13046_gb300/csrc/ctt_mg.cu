@@ -12,7 +12,10 @@
 #include "mg_nested.cuh"
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
+#include <cstdint>
+#include <cstdio>
 #include <mutex>
 
 namespace ctt {
@@ -24,6 +27,12 @@ mg_status fail(mg_status s, const std::string &msg)
     g_last_error = msg;
     return s;
 }
+
+// NVTX range for the duration of a scope (host-side phases of a solve; free when no tool listens)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 }  // namespace ctt
 
@@ -549,11 +558,13 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
 {
     if (!x) return fail(MG_ERR_INVALID_ARG, "null ctx");
     if (!x->have_sources) return fail(MG_ERR_STATE, "mg_set_sources must come before mg_solve");
+    NvtxRange solve_range(x->child ? "mg_solve (nested)" : "mg_solve");
     x->history.clear();
     long long launches = 0;
     int nested_iters = 0;
     CK(cudaEventRecord(x->ev0, x->stream));
     if (x->child && !x->guess_set) {
+        NvtxRange nested_range("nested start: half-size solve + tricubic interpolation");
         // nested start: solve the half-size problem from zero (nesting in turn), interpolate its solution
         mg_ctx *c = x->child;
         mg_solve_info ci{};
@@ -601,6 +612,7 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
         if (grow >= 3) { result = fail(MG_ERR_DIVERGED, "constraint norm grew for 3 outer iterations"); break; }
         prev = mx;
         if (it >= x->cfg.max_outer) { result = fail(MG_ERR_NOT_CONVERGED, "max_outer reached"); break; }
+        NvtxRange iter_range("outer iteration");
         if (x->cfg.use_graph) {
             if (!x->graph_exec) CKS(capture(x, iteration_any, &x->graph_exec, &x->launches_iter));
             CK(cudaGraphLaunch(x->graph_exec, x->stream));
@@ -639,6 +651,59 @@ static mg_status mg_get_solution_impl(mg_ctx *x, double *u, double *W, double *K
     CKS(copy_out(W, x->X + x->N, 3 * x->N, on_device, x->stream));
     CK(cudaStreamSynchronize(x->stream));
     if (K) *K = -std::sqrt(std::max(0.0, x->host_scal->K2));
+    return MG_OK;
+}
+
+// ---- checkpoint / resume
+static const char kCkptMagic[8] = {'C', 'T', 'T', 'M', 'G', 'C', 'K', '1'};
+
+static bool host_little_endian()
+{
+    const uint32_t one = 1;
+    unsigned char b;
+    std::memcpy(&b, &one, 1);
+    return b == 1;
+}
+
+static mg_status mg_checkpoint_save_impl(mg_ctx *x, const char *path)
+{
+    if (!x || !path) return fail(MG_ERR_INVALID_ARG, "null argument");
+    if (!host_little_endian()) return fail(MG_ERR_UNSUPPORTED, "checkpoint files are little-endian");
+    std::vector<double> h(4 * x->N);
+    CK(cudaMemcpyAsync(h.data(), x->X, 4 * x->N * 8, cudaMemcpyDeviceToHost, x->stream));
+    CK(cudaStreamSynchronize(x->stream));
+    const int32_t hdr[6] = {x->cfg.n[0], x->cfg.n[1], x->cfg.n[2], x->cfg.order, x->cfg.bc, 0};
+    const double K2 = x->host_scal->K2;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(MG_ERR_INVALID_ARG, std::string("cannot open for writing: ") + path);
+    bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int32_t), 6, f) == 6 &&
+              std::fwrite(&K2, sizeof(double), 1, f) == 1 && std::fwrite(h.data(), 8, h.size(), f) == h.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MG_OK : fail(MG_ERR_INVALID_ARG, std::string("write failed: ") + path);
+}
+
+static mg_status mg_checkpoint_load_impl(mg_ctx *x, const char *path)
+{
+    if (!x || !path) return fail(MG_ERR_INVALID_ARG, "null argument");
+    if (!host_little_endian()) return fail(MG_ERR_UNSUPPORTED, "checkpoint files are little-endian");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(MG_ERR_INVALID_ARG, std::string("cannot open: ") + path);
+    char magic[8];
+    int32_t hdr[6];
+    double K2 = 0.0;
+    std::vector<double> h(4 * x->N);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+              std::fread(hdr, sizeof(int32_t), 6, f) == 6;
+    ok = ok && hdr[0] == x->cfg.n[0] && hdr[1] == x->cfg.n[1] && hdr[2] == x->cfg.n[2] && hdr[3] == x->cfg.order &&
+         hdr[4] == x->cfg.bc;
+    ok = ok && std::fread(&K2, sizeof(double), 1, f) == 1 && std::fread(h.data(), 8, h.size(), f) == h.size();
+    char extra;
+    ok = ok && std::fread(&extra, 1, 1, f) == 0;   // nothing after the state
+    std::fclose(f);
+    if (!ok) return fail(MG_ERR_INVALID_ARG, std::string("not a checkpoint of this grid: ") + path);
+    CK(cudaMemcpyAsync(x->X, h.data(), 4 * x->N * 8, cudaMemcpyHostToDevice, x->stream));
+    CK(cudaStreamSynchronize(x->stream));
+    x->guess_set = true;
     return MG_OK;
 }
 
@@ -711,6 +776,8 @@ mg_status mg_get_solution(mg_ctx *x, double *u, double *W, double *K, int on_dev
     MG_WRAP(mg_get_solution_impl(x, u, W, K, on_device));
 }
 mg_status mg_residual_norms(mg_ctx *x, double out[4]) { MG_WRAP(mg_residual_norms_impl(x, out)); }
+mg_status mg_checkpoint_save(mg_ctx *x, const char *path) { MG_WRAP(mg_checkpoint_save_impl(x, path)); }
+mg_status mg_checkpoint_load(mg_ctx *x, const char *path) { MG_WRAP(mg_checkpoint_load_impl(x, path)); }
 mg_status mg_constraint_fields(mg_ctx *x, double *H, double *M, int on_device)
 {
     MG_WRAP(mg_constraint_fields_impl(x, H, M, on_device));
@@ -914,6 +981,7 @@ mg_status mg_batch_get_solution(mg_batch *bt, int b, double *u, double *W, doubl
 mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms)
 {
     if (!bt) return fail(MG_ERR_INVALID_ARG, "null batch");
+    NvtxRange range("mg_batch_solve");
     const int nb = (int)bt->ctx.size();
     for (mg_ctx *x : bt->ctx)
         if (!x->have_sources) return fail(MG_ERR_STATE, "every instance needs mg_batch_set_sources first");
@@ -1074,6 +1142,7 @@ extern "C" mg_status mg_autotune(const mg_config *base, const double *rho0, cons
 {
     CKS(validate(base));
     if (!best) return fail(MG_ERR_INVALID_ARG, "null best");
+    NvtxRange range("mg_autotune");
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_load(cache_path);
     const std::string key = tune_key(base);

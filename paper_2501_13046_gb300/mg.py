@@ -26,7 +26,7 @@ EXPORTS = ("mg_config_default", "mg_workspace_size", "mg_create", "mg_set_confor
            "mg_set_initial_guess", "mg_solve", "mg_get_solution", "mg_residual_norms", "mg_constraint_fields",
            "mg_time_kernel", "mg_residual_norms_noalloc", "mg_destroy", "mg_status_string", "mg_last_error",
            "mg_batch_create", "mg_batch_set_sources", "mg_batch_set_initial_guess", "mg_batch_solve",
-           "mg_batch_get_solution", "mg_batch_destroy", "mg_autotune")
+           "mg_batch_get_solution", "mg_batch_destroy", "mg_autotune", "mg_checkpoint_save", "mg_checkpoint_load")
 
 
 class mg_config(C.Structure):
@@ -75,6 +75,8 @@ def _load():
     L.mg_time_kernel.argtypes = [vp, C.c_int, C.c_int, dp, dp]
     L.mg_residual_norms_noalloc.argtypes = [C.POINTER(mg_config), vp, vp, vp, vp, vp, dp, dp, vp]
     L.mg_destroy.argtypes = [vp]
+    L.mg_checkpoint_save.argtypes = [vp, C.c_char_p]
+    L.mg_checkpoint_load.argtypes = [vp, C.c_char_p]
     L.mg_destroy.restype = None
     L.mg_batch_create.argtypes = [C.c_int, C.POINTER(mg_config), vp, C.POINTER(vp)]
     L.mg_batch_set_sources.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, C.c_int]
@@ -202,6 +204,14 @@ def mg_residual_norms_noalloc(cfg, u, W, rho0, rho2, S, stream=0):
     _check(_lib.mg_residual_norms_noalloc(C.byref(cfg), ptr(u), ptr(W), ptr(rho0), ptr(rho2), ptr(S), out,
                                           C.byref(k2), C.c_void_p(stream or None)), "mg_residual_norms_noalloc")
     return np.array(out[:]), k2.value
+
+
+def mg_checkpoint_save(ctx, path):
+    _check(_lib.mg_checkpoint_save(ctx, os.fsencode(path)), "mg_checkpoint_save")
+
+
+def mg_checkpoint_load(ctx, path):
+    _check(_lib.mg_checkpoint_load(ctx, os.fsencode(path)), "mg_checkpoint_load")
 
 
 def mg_destroy(ctx):
