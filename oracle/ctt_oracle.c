@@ -35,7 +35,10 @@
  *   D_aa  : (f+1 - 2f + f-1)/h^2      | (-f+2 + 16f+1 - 30f + 16f-1 - f-2)/12h^2
  *   D_ab  : D_a applied to D_b (a != b);  Lap = sum_a D_aa
  *   Boundary values outside the box: periodic wrap, or Robin 1/r falloff
- *   v(g) = v(b) |x_b| / |x_g| with b the cell obtained by clamping g into the box.
+ *   v(g) = v(b) |x_b| / |x_g| with b the cell obtained by clamping g into the box.  On a Robin box
+ *   a lower face x_a = 0 may instead be a reflection-symmetry plane (Key features, "Boundary
+ *   conditions": reflective): below it g_a -> -1 - g_a (the mirror cell), with the sign of W_a,
+ *   the component normal to the plane, flipped and every other field kept.
  *
  * Solver (any convergent method reaches the same discrete solution): an outer
  * defect-correction loop in FP64 (residual, integrability K^2, norms), with an
@@ -67,6 +70,7 @@ typedef struct {
     double px[2][3];
     double pP[2][3]; /* Bowen-York linear momentum of each puncture (0: bare) */
     double pS[2][3]; /* Bowen-York spin of each puncture (0: bare) */
+    int reflect;     /* Robin boxes: bit a = the lower face of axis a (x_a = 0) is a symmetry plane */
 } ora_grid;
 
 static long ncells(const ora_grid *g) { return (long)g->n[0] * g->n[1] * g->n[2]; }
@@ -78,22 +82,27 @@ static long lin(const ora_grid *g, int i, int j, int k)
 
 static double cellx(const ora_grid *g, int a, int i) { return g->lo[a] + (i + 0.5) * g->h[a]; }
 
-/* Value of f at integer cell (i,j,k), which may lie outside the box. */
-static double at(const ora_grid *g, const double *f, int i, int j, int k)
+/* Value of field f (fi: 0 = u, 1..3 = W_x..W_z) at integer cell (i,j,k), which may lie outside
+ * the box. */
+static double at(const ora_grid *g, int fi, const double *f, int i, int j, int k)
 {
     int p[3] = {i, j, k};
     int b[3];
     int outside = 0;
+    double sign = 1.0;
     for (int a = 0; a < 3; ++a) {
         int n = g->n[a];
         if (g->bc == 0) {
             b[a] = ((p[a] % n) + n) % n;
+        } else if (p[a] < 0 && ((g->reflect >> a) & 1)) {
+            b[a] = -1 - p[a];              /* mirror image across the plane x_a = 0 */
+            if (fi == 1 + a) sign = -sign; /* the normal component of W is odd */
         } else {
             b[a] = p[a] < 0 ? 0 : (p[a] >= n ? n - 1 : p[a]);
             if (b[a] != p[a]) outside = 1;
         }
     }
-    double v = f[lin(g, b[0], b[1], b[2])];
+    double v = sign * f[lin(g, b[0], b[1], b[2])];
     if (!outside) return v;
     double rb2 = 0.0, rg2 = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -105,12 +114,12 @@ static double at(const ora_grid *g, const double *f, int i, int j, int k)
 }
 
 /* f at (i,j,k) shifted by s along axis a and t along axis b */
-static double at2(const ora_grid *g, const double *f, int i, int j, int k, int a, int s, int b, int t)
+static double at2(const ora_grid *g, int fi, const double *f, int i, int j, int k, int a, int s, int b, int t)
 {
     int o[3] = {0, 0, 0};
     o[a] += s;
     o[b] += t;
-    return at(g, f, i + o[0], j + o[1], k + o[2]);
+    return at(g, fi, f, i + o[0], j + o[1], k + o[2]);
 }
 
 /* first-derivative weights w[s] for offsets s = -2..2 (index s+2), times 1/h */
@@ -137,26 +146,26 @@ static void d2_weights(int order, double w[5])
     }
 }
 
-static double d1_at(const ora_grid *g, const double *f, int a, int i, int j, int k)
+static double d1_at(const ora_grid *g, int fi, const double *f, int a, int i, int j, int k)
 {
     double w[5], s = 0.0;
     d1_weights(g->order, w);
     for (int t = -2; t <= 2; ++t)
-        if (w[t + 2] != 0.0) s += w[t + 2] * at2(g, f, i, j, k, a, t, a, 0);
+        if (w[t + 2] != 0.0) s += w[t + 2] * at2(g, fi, f, i, j, k, a, t, a, 0);
     return s / g->h[a];
 }
 
-static double d2_at(const ora_grid *g, const double *f, int a, int i, int j, int k)
+static double d2_at(const ora_grid *g, int fi, const double *f, int a, int i, int j, int k)
 {
     double w[5], s = 0.0;
     d2_weights(g->order, w);
     for (int t = -2; t <= 2; ++t)
-        if (w[t + 2] != 0.0) s += w[t + 2] * at2(g, f, i, j, k, a, t, a, 0);
+        if (w[t + 2] != 0.0) s += w[t + 2] * at2(g, fi, f, i, j, k, a, t, a, 0);
     return s / (g->h[a] * g->h[a]);
 }
 
 /* D_a D_b f for a != b: tensor product of the two first-derivative stencils */
-static double dmix_at(const ora_grid *g, const double *f, int a, int b, int i, int j, int k)
+static double dmix_at(const ora_grid *g, int fi, const double *f, int a, int b, int i, int j, int k)
 {
     double w[5], s = 0.0;
     d1_weights(g->order, w);
@@ -164,24 +173,24 @@ static double dmix_at(const ora_grid *g, const double *f, int a, int b, int i, i
         if (w[p + 2] == 0.0) continue;
         double inner = 0.0;
         for (int q = -2; q <= 2; ++q)
-            if (w[q + 2] != 0.0) inner += w[q + 2] * at2(g, f, i, j, k, a, p, b, q);
+            if (w[q + 2] != 0.0) inner += w[q + 2] * at2(g, fi, f, i, j, k, a, p, b, q);
         s += w[p + 2] * inner;
     }
     return s / (g->h[a] * g->h[b]);
 }
 
-static double lap_at(const ora_grid *g, const double *f, int i, int j, int k)
+static double lap_at(const ora_grid *g, int fi, const double *f, int i, int j, int k)
 {
-    return d2_at(g, f, 0, i, j, k) + d2_at(g, f, 1, i, j, k) + d2_at(g, f, 2, i, j, k);
+    return d2_at(g, fi, f, 0, i, j, k) + d2_at(g, fi, f, 1, i, j, k) + d2_at(g, fi, f, 2, i, j, k);
 }
 
 /* (Lap + (1/3) d_i d_j) W at a cell, component i; W holds 3 contiguous fields */
 static double momop_at(const ora_grid *g, const double *W, int comp, int i, int j, int k)
 {
     long N = ncells(g);
-    double v = lap_at(g, W + comp * N, i, j, k) + d2_at(g, W + comp * N, comp, i, j, k) / 3.0;
+    double v = lap_at(g, 1 + comp, W + comp * N, i, j, k) + d2_at(g, 1 + comp, W + comp * N, comp, i, j, k) / 3.0;
     for (int b = 0; b < 3; ++b)
-        if (b != comp) v += dmix_at(g, W + b * N, comp, b, i, j, k) / 3.0;
+        if (b != comp) v += dmix_at(g, 1 + b, W + b * N, comp, b, i, j, k) / 3.0;
     return v;
 }
 
@@ -216,7 +225,7 @@ static double atat_at(const ora_grid *g, const double *W, int i, int j, int k)
     long N = ncells(g);
     double G[3][3]; /* G[a][b] = D_a W_b */
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) G[a][b] = d1_at(g, W + b * N, a, i, j, k);
+        for (int b = 0; b < 3; ++b) G[a][b] = d1_at(g, 1 + b, W + b * N, a, i, j, k);
     double x[3] = {cellx(g, 0, i), cellx(g, 1, j), cellx(g, 2, k)}, B[3][3];
     by_point(g, x, B);
     double div = G[0][0] + G[1][1] + G[2][2];
@@ -251,7 +260,7 @@ void ora_d1(const ora_grid *g, int a, const double *f, double *out)
 #pragma omp parallel for
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
-            for (int i = 0; i < g->n[0]; ++i) out[lin(g, i, j, k)] = d1_at(g, f, a, i, j, k);
+            for (int i = 0; i < g->n[0]; ++i) out[lin(g, i, j, k)] = d1_at(g, 0, f, a, i, j, k);
 }
 
 void ora_d2(const ora_grid *g, int a, const double *f, double *out)
@@ -259,7 +268,7 @@ void ora_d2(const ora_grid *g, int a, const double *f, double *out)
 #pragma omp parallel for
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
-            for (int i = 0; i < g->n[0]; ++i) out[lin(g, i, j, k)] = d2_at(g, f, a, i, j, k);
+            for (int i = 0; i < g->n[0]; ++i) out[lin(g, i, j, k)] = d2_at(g, 0, f, a, i, j, k);
 }
 
 void ora_dmix(const ora_grid *g, int a, int b, const double *f, double *out)
@@ -267,7 +276,7 @@ void ora_dmix(const ora_grid *g, int a, int b, const double *f, double *out)
 #pragma omp parallel for
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
-            for (int i = 0; i < g->n[0]; ++i) out[lin(g, i, j, k)] = dmix_at(g, f, a, b, i, j, k);
+            for (int i = 0; i < g->n[0]; ++i) out[lin(g, i, j, k)] = dmix_at(g, 0, f, a, b, i, j, k);
 }
 
 void ora_lap(const ora_grid *g, const double *f, double *out)
@@ -275,7 +284,7 @@ void ora_lap(const ora_grid *g, const double *f, double *out)
 #pragma omp parallel for
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
-            for (int i = 0; i < g->n[0]; ++i) out[lin(g, i, j, k)] = lap_at(g, f, i, j, k);
+            for (int i = 0; i < g->n[0]; ++i) out[lin(g, i, j, k)] = lap_at(g, 0, f, i, j, k);
 }
 
 void ora_atat(const ora_grid *g, const double *W, double *out)
@@ -309,10 +318,11 @@ void ora_by_cells(const ora_grid *g, double *out)
             }
 }
 
-/* out = value at the out-of-box cell (i,j,k) under the boundary condition */
-double ora_boundary_value(const ora_grid *g, const double *f, int i, int j, int k)
+/* value of field f (fi: 0 = u, 1..3 = W_x..W_z) at the out-of-box cell (i,j,k) under the
+ * boundary condition */
+double ora_boundary_value(const ora_grid *g, int fi, const double *f, int i, int j, int k)
 {
-    return at(g, f, i, j, k);
+    return at(g, fi, f, i, j, k);
 }
 
 /* mean of the 8 children; gc is the coarse grid */
@@ -331,8 +341,8 @@ void ora_restrict(const ora_grid *gc, const double *fine, double *coarse)
             }
 }
 
-/* fine += trilinear interpolation of coarse; gc is the coarse grid */
-void ora_prolong_add(const ora_grid *gc, const double *coarse, double *fine)
+/* fine += trilinear interpolation of coarse field fi; gc is the coarse grid */
+void ora_prolong_add(const ora_grid *gc, int fi, const double *coarse, double *fine)
 {
     int nf0 = 2 * gc->n[0], nf1 = 2 * gc->n[1];
     for (int K = 0; K < gc->n[2]; ++K)
@@ -347,7 +357,7 @@ void ora_prolong_add(const ora_grid *gc, const double *coarse, double *fine)
                                 for (int b = 0; b < 2; ++b)
                                     for (int c = 0; c < 2; ++c) {
                                         double w = (a ? 0.25 : 0.75) * (b ? 0.25 : 0.75) * (c ? 0.25 : 0.75);
-                                        v += w * at(gc, coarse, I + a * sx, J + b * sy, K + c * sz);
+                                        v += w * at(gc, fi, coarse, I + a * sx, J + b * sy, K + c * sz);
                                     }
                             fine[(2 * I + di) + (long)nf0 * ((2 * J + dj) + (long)nf1 * (2 * K + dk))] += v;
                         }
@@ -380,7 +390,7 @@ int ora_residual(const ora_grid *g, const double *u, const double *W, const doub
                 long p = lin(g, i, j, k);
                 psi[p] = psibg_at(g, i, j, k) + u[p];
                 aa[p] = atat_at(g, W, i, j, k);
-                lu[p] = lap_at(g, u, i, j, k);
+                lu[p] = lap_at(g, 0, u, i, j, k);
             }
     double k2 = *K2;
     if (kmode == 1) {
@@ -469,7 +479,7 @@ static void gs_sweeps(ora_level *L, int sweeps)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i) {
                     long p = lin(g, i, j, k);
-                    double rp = L->f[p] - (L->a[p] * lap_at(g, L->e, i, j, k) + L->c[p] * L->e[p]);
+                    double rp = L->f[p] - (L->a[p] * lap_at(g, 0, L->e, i, j, k) + L->c[p] * L->e[p]);
                     L->e[p] += rp / (L->a[p] * dl + L->c[p]);
                     for (int a = 0; a < 3; ++a) {
                         double ra = L->f[(1 + a) * N + p] - momop_at(g, L->e + N, a, i, j, k);
@@ -486,7 +496,7 @@ static void linear_residual(ora_level *L)
         for (int j = 0; j < g->n[1]; ++j)
             for (int i = 0; i < g->n[0]; ++i) {
                 long p = lin(g, i, j, k);
-                L->r[p] = L->f[p] - (L->a[p] * lap_at(g, L->e, i, j, k) + L->c[p] * L->e[p]);
+                L->r[p] = L->f[p] - (L->a[p] * lap_at(g, 0, L->e, i, j, k) + L->c[p] * L->e[p]);
                 for (int a = 0; a < 3; ++a)
                     L->r[(1 + a) * N + p] = L->f[(1 + a) * N + p] - momop_at(g, L->e + N, a, i, j, k);
             }
@@ -525,7 +535,7 @@ static int coarse_psi_direct(ora_level *L)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i) {
                     long p = lin(g, i, j, k);
-                    A[p * m + q] = L->a[p] * lap_at(g, unit, i, j, k) + L->c[p] * unit[p];
+                    A[p * m + q] = L->a[p] * lap_at(g, 0, unit, i, j, k) + L->c[p] * unit[p];
                 }
         unit[q] = 0.0;
     }
@@ -578,7 +588,7 @@ static void vcycle(ora_level *lv, int l, int nlev, int nu1, int nu2, int csweeps
     ora_level *C = &lv[l + 1];
     for (int a = 0; a < 4; ++a) ora_restrict(&C->g, L->r + a * N, C->f + a * C->N);
     vcycle(lv, l + 1, nlev, nu1, nu2, csweeps);
-    for (int a = 0; a < 4; ++a) ora_prolong_add(&C->g, C->e + a * C->N, L->e + a * N);
+    for (int a = 0; a < 4; ++a) ora_prolong_add(&C->g, a, C->e + a * C->N, L->e + a * N);
     gs_sweeps(L, nu2);
 }
 

@@ -36,6 +36,7 @@ class Grid(C.Structure):
         ("px", (C.c_double * 3) * 2),
         ("pP", (C.c_double * 3) * 2),
         ("pS", (C.c_double * 3) * 2),
+        ("reflect", C.c_int),
     ]
 
 
@@ -63,12 +64,12 @@ def lib():
         L.ora_dmix.argtypes = [gp, C.c_int, C.c_int, dp, dp]
         L.ora_lap.argtypes = [gp, dp, dp]
         L.ora_atat.argtypes = [gp, dp, dp]
-        L.ora_boundary_value.argtypes = [gp, dp, C.c_int, C.c_int, C.c_int]
+        L.ora_boundary_value.argtypes = [gp, C.c_int, dp, C.c_int, C.c_int, C.c_int]
         L.ora_boundary_value.restype = C.c_double
         L.ora_by_point.argtypes = [gp, dp, dp]
         L.ora_by_cells.argtypes = [gp, dp]
         L.ora_restrict.argtypes = [gp, dp, dp]
-        L.ora_prolong_add.argtypes = [gp, dp, dp]
+        L.ora_prolong_add.argtypes = [gp, C.c_int, dp, dp]
         L.ora_residual.argtypes = [gp, dp, dp, dp, dp, dp, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp]
         L.ora_residual.restype = C.c_int
         L.ora_auto_levels.argtypes = [C.POINTER(C.c_int)]
@@ -80,9 +81,10 @@ def lib():
     return _lib
 
 
-def make_grid(n, lo, hi, order, bc, punctures=()):
+def make_grid(n, lo, hi, order, bc, punctures=(), reflect=0):
     """n: int or 3 ints; lo/hi: float or 3 floats; punctures: [(mass, (x, y, z)), ...] or, with
-    Bowen-York momentum and spin, [(mass, (x, y, z), (Px, Py, Pz), (Sx, Sy, Sz)), ...]."""
+    Bowen-York momentum and spin, [(mass, (x, y, z), (Px, Py, Pz), (Sx, Sy, Sz)), ...];
+    reflect (Robin boxes): bit a makes the lower face x_a = 0 a reflection-symmetry plane."""
     n = [n] * 3 if np.isscalar(n) else list(n)
     lo = [lo] * 3 if np.isscalar(lo) else list(lo)
     hi = [hi] * 3 if np.isscalar(hi) else list(hi)
@@ -91,7 +93,7 @@ def make_grid(n, lo, hi, order, bc, punctures=()):
         g.n[a] = int(n[a])
         g.lo[a] = float(lo[a])
         g.h[a] = (float(hi[a]) - float(lo[a])) / int(n[a])
-    g.order, g.bc, g.npunct = int(order), int(bc), len(punctures)
+    g.order, g.bc, g.npunct, g.reflect = int(order), int(bc), len(punctures), int(reflect)
     for p, pun in enumerate(punctures):
         m, x = pun[0], pun[1]
         P = pun[2] if len(pun) > 2 else (0.0, 0.0, 0.0)
@@ -176,9 +178,10 @@ def atat(g, W):
     return out.reshape(shape3(g))
 
 
-def boundary_value(g, f, i, j, k):
+def boundary_value(g, f, i, j, k, fi=0):
+    """Value of field f (fi: 0 = u, 1..3 = W_x..W_z) at the cell (i, j, k), which may lie outside the box."""
     f = _arr(f, ncells(g))
-    return lib().ora_boundary_value(C.byref(g), _p(f), i, j, k)
+    return lib().ora_boundary_value(C.byref(g), fi, _p(f), i, j, k)
 
 
 def restrict(gc, fine):
@@ -187,11 +190,12 @@ def restrict(gc, fine):
     return out.reshape(shape3(gc))
 
 
-def prolong_add(gc, coarse_f, fine):
+def prolong_add(gc, coarse_f, fine, fi=0):
+    """fine + trilinear interpolation of coarse field fi (0 = u, 1..3 = W_x..W_z)."""
     coarse_f = _arr(coarse_f, ncells(gc))
     fine = np.array(fine, dtype=np.float64, copy=True).reshape(-1)
     assert fine.size == 8 * ncells(gc)
-    lib().ora_prolong_add(C.byref(gc), _p(coarse_f), _p(fine))
+    lib().ora_prolong_add(C.byref(gc), fi, _p(coarse_f), _p(fine))
     return fine
 
 
