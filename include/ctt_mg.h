@@ -98,6 +98,10 @@ typedef struct {
                              + 3/r^3 [(S x n)_i n_j + (S x n)_j n_i] (n, r from the puncture; ADM momentum P,
                              ADM angular momentum S) is added to At_ij before AtAt; F_W is unchanged     */
     double punct_S[2][3]; /* Bowen-York spin of puncture p (0 = bare)                                    */
+    int reflect;          /* Robin boxes: bit a (a = 0, 1, 2) makes the lower face of axis a a reflection-
+                             symmetry plane (lo[a] must be 0): a cell below it takes the value of its mirror
+                             image, with the sign flipped for W_a (the component normal to the plane) and kept
+                             for u and the other components.  7 = octant symmetry.  0 = all faces Robin.    */
 } mg_config;
 
 typedef struct {

@@ -70,6 +70,11 @@ mg_status validate(const mg_config *c)
         for (int a = 0; a < 3; ++a)
             if (!std::isfinite(c->punct_P[p][a]) || !std::isfinite(c->punct_S[p][a]))
                 return fail(MG_ERR_INVALID_ARG, "puncture momentum or spin not finite");
+    if (c->reflect < 0 || c->reflect > 7) return fail(MG_ERR_INVALID_ARG, "reflect must be a mask of 3 bits");
+    if (c->reflect != 0 && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "symmetry planes need a Robin box");
+    for (int a = 0; a < 3; ++a)
+        if (((c->reflect >> a) & 1) && c->lo[a] != 0.0)
+            return fail(MG_ERR_INVALID_ARG, "a symmetry plane must be the face x_a = 0 (lo[a] = 0)");
     if (c->nested != 0 && c->nested != 1) return fail(MG_ERR_INVALID_ARG, "nested must be 0 or 1");
     if (c->nested_min != 0 && c->nested_min < 3) return fail(MG_ERR_INVALID_ARG, "nested_min must be 0 or >= 3");
     if (!(c->nested_tol >= 0.0) || !std::isfinite(c->nested_tol)) return fail(MG_ERR_INVALID_ARG, "bad nested_tol");
@@ -381,6 +386,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
                 g.lof[a] = (float)g.lo[a];
                 g.hf[a] = (float)g.h[a];
             }
+            g.reflect = cfg->bc == MG_BC_ROBIN ? cfg->reflect : 0;
             g.npunct = cfg->npunct;
             for (int p = 0; p < cfg->npunct; ++p) {
                 g.pm[p] = cfg->punct_m[p];

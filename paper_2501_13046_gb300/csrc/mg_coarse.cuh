@@ -47,11 +47,10 @@ __global__ void __launch_bounds__(512) k_dense_psi_assemble(Geo g, Coef<T> cf, c
                     c[ax] += c[ax] < 0 ? g.n[ax] : 0;
                     c[ax] -= c[ax] >= g.n[ax] ? g.n[ax] : 0;
                     row[c[0] + g.n[0] * (c[1] + g.n[1] * c[2])] += (C)w;
-                } else {
-                    const int bc[3] = {min(max(c[0], 0), g.n[0] - 1), min(max(c[1], 0), g.n[1] - 1),
-                                       min(max(c[2], 0), g.n[2] - 1)};
+                } else {   // psi is even across symmetry planes: mirror, or clamp with the 1/r ratio
+                    int bc[3], mirror;
                     double ratio = 1.0;
-                    if (bc[ax] != c[ax]) ratio = robin_ratio<double>(g, bc[0], bc[1], bc[2], c[0], c[1], c[2]);
+                    if (bc_cell<BC>(g, c, bc, mirror)) ratio = robin_ratio<double>(g, bc[0], bc[1], bc[2], c[0], c[1], c[2]);
                     row[bc[0] + g.n[0] * (bc[1] + g.n[1] * bc[2])] += (C)(w * ratio);
                 }
             }
@@ -89,7 +88,8 @@ __global__ void __launch_bounds__(256) k_dense_w_assemble(Geo g, Coef<T> cf, C *
     __syncthreads();
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
         const int i = p % g.n[0], j = (p / g.n[0]) % g.n[1], k = p / (g.n[0] * g.n[1]);
-        AccB<T, BC> a0{e, &g, i, j, k}, a1{e + N, &g, i, j, k}, a2{e + 2 * N, &g, i, j, k}, a3{e + 3 * N, &g, i, j, k};
+        AccB<T, BC> a0{e, 0, &g, i, j, k}, a1{e + N, 1, &g, i, j, k}, a2{e + 2 * N, 2, &g, i, j, k},
+            a3{e + 3 * N, 3, &g, i, j, k};
         T Je[4], ctr[4];
         apply_J<ORDER, T>(a0, a1, a2, a3, (T)1, (T)0, cf, Je, ctr);
         for (int A = 0; A < 3; ++A) aug[(size_t)(A * N + p) * w2 + col] = (C)Je[1 + A];
@@ -212,19 +212,25 @@ inline size_t fused_ratio_cells(const Geo &g, int robin)
     return robin ? (size_t)(g.n[0] + 4) * (g.n[1] + 4) * (g.n[2] + 4) : 0;
 }
 
-// Robin accessor of the fused cycle: the clamped cell's value times the level's ghost ratio, read
-// from the table rt over the box padded by 2 (1 inside), so no branch and no square root.
+// Robin accessor of the fused cycle: the value of the cell bc_cell maps to, times the level's
+// ghost ratio read from the table rt over the box padded by 2 (1 inside or only mirrored), so no
+// square root per access; fi is the field (0 = u, 1..3 = W_x..W_z) for the sign across symmetry
+// planes.
 template <typename T>
 struct AccRT {
-    const T *f, *rt;
+    const T *f;
+    int fi;
+    const T *rt;
     const Geo *g;
     int i, j, k;
     __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
     {
-        const int p0 = i + dx, p1 = j + dy, p2 = k + dz;
-        const int n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
-        const int b0 = min(max(p0, 0), n0 - 1), b1 = min(max(p1, 0), n1 - 1), b2 = min(max(p2, 0), n2 - 1);
-        return f[b0 + n0 * (b1 + n1 * b2)] * rt[(p0 + 2) + (n0 + 4) * ((p1 + 2) + (n1 + 4) * (p2 + 2))];
+        const int p[3] = {i + dx, j + dy, k + dz};
+        int b[3], mirror;
+        bc_cell<BC_ROBIN>(*g, p, b, mirror);
+        const T v = f[b[0] + g->n[0] * (b[1] + g->n[1] * b[2])] *
+                    rt[(p[0] + 2) + (g->n[0] + 4) * ((p[1] + 2) + (g->n[1] + 4) * (p[2] + 2))];
+        return bc_sign(mirror, fi) < 0 ? -v : v;
     }
 };
 
@@ -267,20 +273,21 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
     if constexpr (BC == BC_ROBIN) {
         const int m0 = g.n[0] + 4, m1 = g.n[1] + 4, M = m0 * m1 * (g.n[2] + 4);
         for (int e = tid; e < M; e += bs) {
-            const int i = e % m0 - 2, j = (e / m0) % m1 - 2, k = e / (m0 * m1) - 2;
-            const int bi = min(max(i, 0), g.n[0] - 1), bj = min(max(j, 0), g.n[1] - 1), bk = min(max(k, 0), g.n[2] - 1);
-            rt[e] = (bi == i && bj == j && bk == k) ? (T)1 : robin_ratio<T>(g, bi, bj, bk, i, j, k);
+            const int c[3] = {e % m0 - 2, (e / m0) % m1 - 2, e / (m0 * m1) - 2};
+            int b[3], mirror;
+            rt[e] = bc_cell<BC>(g, c, b, mirror) ? robin_ratio<T>(g, b[0], b[1], b[2], c[0], c[1], c[2]) : (T)1;
         }
     }
     __syncthreads();
     // J e at cell (i, j, k) of the level held in e
     auto apply = [&](const T *e, int i, int j, int k, T a, T b, T Je[4], T ctr[4]) {
         if constexpr (BC == BC_ROBIN) {
-            AccRT<T> a0{e, rt, &g, i, j, k}, a1{e + N, rt, &g, i, j, k}, a2{e + 2 * N, rt, &g, i, j, k},
-                a3{e + 3 * N, rt, &g, i, j, k};
+            AccRT<T> a0{e, 0, rt, &g, i, j, k}, a1{e + N, 1, rt, &g, i, j, k}, a2{e + 2 * N, 2, rt, &g, i, j, k},
+                a3{e + 3 * N, 3, rt, &g, i, j, k};
             apply_J<ORDER, T>(a0, a1, a2, a3, a, b, cf, Je, ctr);
         } else {
-            AccB<T, BC> a0{e, &g, i, j, k}, a1{e + N, &g, i, j, k}, a2{e + 2 * N, &g, i, j, k}, a3{e + 3 * N, &g, i, j, k};
+            AccB<T, BC> a0{e, 0, &g, i, j, k}, a1{e + N, 1, &g, i, j, k}, a2{e + 2 * N, 2, &g, i, j, k},
+                a3{e + 3 * N, 3, &g, i, j, k};
             apply_J<ORDER, T>(a0, a1, a2, a3, a, b, cf, Je, ctr);
         }
     };
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
     }
     __syncthreads();
     // trilinear prolongation (3/4, 1/4 per axis; coarse boundary values from the BC) into e
-    const int ncx = gc.n[0], ncy = gc.n[1], ncz = gc.n[2];
+    const int ncx = gc.n[0], ncy = gc.n[1];
     for (int q = tid; q < N; q += bs) {
         int i, j, k;
         ijk(q, i, j, k);
@@ -354,21 +361,12 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
         T s4[4] = {0, 0, 0, 0};
         for (int d = 0; d < 8; ++d) {
             const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
-            const int cx = I + dx * sx, cy = J + dy * sy, cz = K + dz * sz;
+            const int cc[3] = {I + dx * sx, J + dy * sy, K + dz * sz};
             T w = (T)((dx ? 0.25 : 0.75) * (dy ? 0.25 : 0.75) * (dz ? 0.25 : 0.75));
-            int bx = cx, by = cy, bz = cz;
-            if (BC == BC_PERIODIC) {
-                bx += bx < 0 ? ncx : 0; bx -= bx >= ncx ? ncx : 0;
-                by += by < 0 ? ncy : 0; by -= by >= ncy ? ncy : 0;
-                bz += bz < 0 ? ncz : 0; bz -= bz >= ncz ? ncz : 0;
-            } else {
-                bx = min(max(bx, 0), ncx - 1);
-                by = min(max(by, 0), ncy - 1);
-                bz = min(max(bz, 0), ncz - 1);
-                if (bx != cx || by != cy || bz != cz) w *= robin_ratio<T>(gc, bx, by, bz, cx, cy, cz);
-            }
-            const int c = bx + ncx * (by + ncy * bz);
-            for (int a = 0; a < 4; ++a) s4[a] = fma((T)w, ec[a * Nc + c], s4[a]);
+            int b[3], mirror;
+            if (bc_cell<BC>(gc, cc, b, mirror)) w *= robin_ratio<T>(gc, b[0], b[1], b[2], cc[0], cc[1], cc[2]);
+            const int c = b[0] + ncx * (b[1] + ncy * b[2]);
+            for (int a = 0; a < 4; ++a) s4[a] = fma(bc_sign(mirror, a) < 0 ? -w : w, ec[a * Nc + c], s4[a]);
         }
         for (int a = 0; a < 4; ++a) cur[a * N + q] += s4[a];
     }

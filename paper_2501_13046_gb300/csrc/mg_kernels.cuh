@@ -30,6 +30,8 @@ struct Geo {
     double lo[3];
     double h[3];
     float lof[3], hf[3];   // lo and h rounded to FP32 (FP32 Robin ratios; set with lo and h)
+    int reflect;           // Robin boxes: bit a set = the lower face of axis a (at x_a = 0) is a
+                           // reflection-symmetry plane instead of a Robin face
     int npunct;
     double pm[2];
     double px[2][3];
@@ -112,6 +114,38 @@ __device__ __forceinline__ T robin_ratio(const Geo &g, int bi, int bj, int bk, i
     else return sqrt(A / B);
 }
 
+// The in-box cell b that supplies the value at a cell p at most 2 cells outside the box.
+// Periodic boxes wrap.  Robin boxes mirror p_a -> -1 - p_a below a lower face marked in g.reflect
+// (a symmetry plane; bit a of `mirror` is set) and clamp every other out-of-box coordinate; the
+// return value says whether a coordinate was clamped, in which case the value is scaled by the
+// 1/r ratio |x_b| / |x_p| (mirroring keeps |x|, the planes passing through the origin).
+template <int BC>
+__device__ __forceinline__ bool bc_cell(const Geo &g, const int p[3], int b[3], int &mirror)
+{
+    mirror = 0;
+    bool clamped = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int n = g.n[a];
+        if constexpr (BC == BC_PERIODIC) {
+            b[a] = p[a] + (p[a] < 0 ? n : 0) - (p[a] >= n ? n : 0);
+        } else {
+            if (p[a] < 0 && ((g.reflect >> a) & 1)) {
+                b[a] = -1 - p[a];
+                mirror |= 1 << a;
+            } else {
+                b[a] = min(max(p[a], 0), n - 1);
+                clamped |= b[a] != p[a];
+            }
+        }
+    }
+    return clamped;
+}
+
+// Sign of field fi (0 = u, 1..3 = W_x..W_z) at a cell mirrored across the planes in `mirror`:
+// the component of W normal to a symmetry plane is odd across it, everything else even.
+__device__ __forceinline__ int bc_sign(int mirror, int fi) { return (fi >= 1 && ((mirror >> (fi - 1)) & 1)) ? -1 : 1; }
+
 // FP64 Robin ratio of the ghost cell (i, j, k) (at most 2 cells outside) onto its clamped cell b:
 // the stored table when there is one (the division and square root run at the FP64 rate).
 __device__ __forceinline__ double robin_ratio_f64(const Geo &g, int bi, int bj, int bk, int i, int j, int k)
@@ -121,15 +155,17 @@ __device__ __forceinline__ double robin_ratio_f64(const Geo &g, int bi, int bj, 
     return robin_ratio<double>(g, bi, bj, bk, i, j, k);
 }
 
-// rt[(i+2) + (n0+4)((j+2) + (n1+4)(k+2))] = |x_clamp| / |x_(i,j,k)| (1 inside the box), -2 <= i < n0 + 2, ...
+// rt[(i+2) + (n0+4)((j+2) + (n1+4)(k+2))] = |x_b| / |x_(i,j,k)| with b = bc_cell (1 when no
+// coordinate is clamped: inside the box, or only mirrored), -2 <= i < n0 + 2, ...
 static __global__ void __launch_bounds__(256) k_fill_robin_table(Geo g, double *__restrict__ rt)
 {
     const int m0 = g.n[0] + 4, m1 = g.n[1] + 4;
     const size_t M = (size_t)m0 * m1 * (g.n[2] + 4);
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < M; p += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(p % m0) - 2, j = (int)((p / m0) % m1) - 2, k = (int)(p / ((size_t)m0 * m1)) - 2;
-        const int bi = min(max(i, 0), g.n[0] - 1), bj = min(max(j, 0), g.n[1] - 1), bk = min(max(k, 0), g.n[2] - 1);
-        rt[p] = (bi == i && bj == j && bk == k) ? 1.0 : robin_ratio<double>(g, bi, bj, bk, i, j, k);
+        const int c[3] = {(int)(p % m0) - 2, (int)((p / m0) % m1) - 2, (int)(p / ((size_t)m0 * m1)) - 2};
+        int b[3], mirror;
+        const bool clamped = bc_cell<BC_ROBIN>(g, c, b, mirror);
+        rt[p] = clamped ? robin_ratio<double>(g, b[0], b[1], b[2], c[0], c[1], c[2]) : 1.0;
     }
 }
 
@@ -161,9 +197,10 @@ static __global__ void __launch_bounds__(256) k_fill_psibg(Geo g, double *__rest
     }
 }
 
-// value of f at a cell that may lie outside the box (offsets are at most +-2 per axis)
+// value of field f (index fi, see bc_sign) at a cell that may lie outside the box (offsets are at
+// most +-2 per axis)
 template <typename T, int BC>
-__device__ __forceinline__ T fetch_bc(const T *f, const Geo &g, int i, int j, int k)
+__device__ __forceinline__ T fetch_bc(const T *f, int fi, const Geo &g, int i, int j, int k)
 {
     if constexpr (BC == BC_PERIODIC) {
         i += (i < 0) ? g.n[0] : 0; i -= (i >= g.n[0]) ? g.n[0] : 0;
@@ -171,13 +208,14 @@ __device__ __forceinline__ T fetch_bc(const T *f, const Geo &g, int i, int j, in
         k += (k < 0) ? g.n[2] : 0; k -= (k >= g.n[2]) ? g.n[2] : 0;
         return f[i + g.n[0] * (j + g.n[1] * k)];
     } else {
-        int bi = min(max(i, 0), g.n[0] - 1);
-        int bj = min(max(j, 0), g.n[1] - 1);
-        int bk = min(max(k, 0), g.n[2] - 1);
-        T v = f[bi + g.n[0] * (bj + g.n[1] * bk)];
-        if (bi == i && bj == j && bk == k) return v;
-        if constexpr (std::is_same<T, double>::value) return v * robin_ratio_f64(g, bi, bj, bk, i, j, k);
-        else return v * robin_ratio<T>(g, bi, bj, bk, i, j, k);
+        const int p[3] = {i, j, k};
+        int b[3], mirror;
+        const bool clamped = bc_cell<BC>(g, p, b, mirror);
+        T v = f[b[0] + g.n[0] * (b[1] + g.n[1] * b[2])];
+        if (bc_sign(mirror, fi) < 0) v = -v;
+        if (!clamped) return v;
+        if constexpr (std::is_same<T, double>::value) return v * robin_ratio_f64(g, b[0], b[1], b[2], i, j, k);
+        else return v * robin_ratio<T>(g, b[0], b[1], b[2], i, j, k);
     }
 }
 
@@ -190,13 +228,14 @@ struct AccI {   // every offset of the stencil stays inside the box
 };
 
 template <typename T, int BC>
-struct AccB {   // near the boundary
+struct AccB {   // near the boundary; fi: the field (0 = u, 1..3 = W_x..W_z), for symmetry planes
     const T *f;
+    int fi;
     const Geo *g;
     int i, j, k;
     __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
     {
-        return fetch_bc<T, BC>(f, *g, i + dx, j + dy, k + dz);
+        return fetch_bc<T, BC>(f, fi, *g, i + dx, j + dy, k + dz);
     }
 };
 
@@ -325,27 +364,19 @@ struct AccS {
 template <typename T, int BC>
 struct AccB2 {
     const T *same, *other;
+    int fi;   // the field (0 = u, 1..3 = W_x..W_z), for symmetry planes
     const Geo *g;
     size_t N;
     int i, j, k, c;
     __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
     {
         int p[3] = {i + dx, j + dy, k + dz};
-        int q[3];
-        bool outside = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            int n = g->n[a];
-            if (BC == BC_PERIODIC) {
-                q[a] = p[a] + (p[a] < 0 ? n : 0) - (p[a] >= n ? n : 0);
-            } else {
-                q[a] = min(max(p[a], 0), n - 1);
-                outside |= q[a] != p[a];
-            }
-        }
+        int q[3], mirror;
+        const bool outside = bc_cell<BC>(*g, p, q, mirror);
         int c2 = (q[0] + q[1] + q[2]) & 1;
         size_t lin = (size_t)q[0] + (size_t)g->n[0] * ((size_t)q[1] + (size_t)g->n[1] * q[2]);
         T v = (c2 == c ? same : other)[(c2 ? N / 2 : 0) + (lin >> 1)];
+        if (BC == BC_ROBIN && bc_sign(mirror, fi) < 0) v = -v;
         if (BC == BC_ROBIN && outside) {
             if constexpr (std::is_same<T, double>::value)
                 return v * robin_ratio_f64(*g, q[0], q[1], q[2], p[0], p[1], p[2]);
@@ -375,8 +406,8 @@ __device__ __forceinline__ void apply_J_split(const T *X, const T *O, size_t N, 
         AccS<T> a3{Xs + 3 * N, Xs + 3 * N + sel, Oo + 3 * N, Oo + 3 * N + sel, nxh, plane};
         apply_J<ORDER, T>(a0, a1, a2, a3, ca, cb, cf, out, centre);
     } else {
-        AccB2<T, BC> a0{X, O, &g, N, i, j, k, c}, a1{X + N, O + N, &g, N, i, j, k, c},
-            a2{X + 2 * N, O + 2 * N, &g, N, i, j, k, c}, a3{X + 3 * N, O + 3 * N, &g, N, i, j, k, c};
+        AccB2<T, BC> a0{X, O, 0, &g, N, i, j, k, c}, a1{X + N, O + N, 1, &g, N, i, j, k, c},
+            a2{X + 2 * N, O + 2 * N, 2, &g, N, i, j, k, c}, a3{X + 3 * N, O + 3 * N, 3, &g, N, i, j, k, c};
         apply_J<ORDER, T>(a0, a1, a2, a3, ca, cb, cf, out, centre);
     }
 }
@@ -587,16 +618,17 @@ __global__ void __launch_bounds__(256) k_restrict_mean(Geo g, Geo gc, const T *_
 // the parent and 1/4 for its neighbour towards the child, per axis).  One thread per fine cell
 // (fine level colour-split, threads in storage order so that the read-modify-write of e_fine is
 // coalesced): the 8 coarse cells and weights are set up once and serve all 4 fields.  Coarse
-// neighbours outside the box take the level's boundary value (periodic wrap, or the Robin ratio
-// |x_clamp| / |x_g| folded into the weight).  Coarse level colour-split or plain (csplit).
+// neighbours outside the box take the level's boundary value (periodic wrap, the mirror image
+// across a symmetry plane with W's normal component negated, or the Robin ratio |x_clamp| / |x_g|
+// folded into the weight).  Coarse level colour-split or plain (csplit).
 template <typename T, int BC>
 __global__ void __launch_bounds__(256) k_prolong_add(Geo g, Geo gc, const T *__restrict__ ec, T *__restrict__ ef,
                                                      int csplit)
 {
     const unsigned nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx >> 1;
     const unsigned N = nx * ny * nz, Nh = N >> 1;
-    const int ncx = gc.n[0], ncy = gc.n[1], ncz = gc.n[2];
-    const unsigned Nc = (unsigned)ncx * ncy * ncz;
+    const int ncx = gc.n[0], ncy = gc.n[1];
+    const unsigned Nc = (unsigned)ncx * ncy * gc.n[2];
     for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < N; q += gridDim.x * blockDim.x) {
         const unsigned c = q >= Nh, m = q - (c ? Nh : 0u);
         const unsigned row = m / nxh, xi = m - row * nxh;
@@ -606,24 +638,16 @@ __global__ void __launch_bounds__(256) k_prolong_add(Geo g, Geo gc, const T *__r
         const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
         unsigned idx[8];
         T w[8];
+        int mir[8];   // symmetry planes crossed to reach parent d (signs per field: bc_sign)
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
-            int cx = I + dx * sx, cy = J + dy * sy, cz = K + dz * sz;
+            const int c[3] = {I + dx * sx, J + dy * sy, K + dz * sz};
             T wd = (T)((dx ? 0.25 : 0.75) * (dy ? 0.25 : 0.75) * (dz ? 0.25 : 0.75));
-            int bx = cx, by = cy, bz = cz;
-            if (BC == BC_PERIODIC) {
-                bx += bx < 0 ? ncx : 0; bx -= bx >= ncx ? ncx : 0;
-                by += by < 0 ? ncy : 0; by -= by >= ncy ? ncy : 0;
-                bz += bz < 0 ? ncz : 0; bz -= bz >= ncz ? ncz : 0;
-            } else {
-                bx = min(max(bx, 0), ncx - 1);
-                by = min(max(by, 0), ncy - 1);
-                bz = min(max(bz, 0), ncz - 1);
-                if (bx != cx || by != cy || bz != cz) wd *= robin_ratio<T>(gc, bx, by, bz, cx, cy, cz);
-            }
-            const unsigned lin = (unsigned)bx + (unsigned)ncx * ((unsigned)by + (unsigned)ncy * (unsigned)bz);
-            idx[d] = csplit ? (((bx + by + bz) & 1) ? Nc / 2 : 0u) + (lin >> 1) : lin;
+            int b[3];
+            if (bc_cell<BC>(gc, c, b, mir[d])) wd *= robin_ratio<T>(gc, b[0], b[1], b[2], c[0], c[1], c[2]);
+            const unsigned lin = (unsigned)b[0] + (unsigned)ncx * ((unsigned)b[1] + (unsigned)ncy * (unsigned)b[2]);
+            idx[d] = csplit ? (((b[0] + b[1] + b[2]) & 1) ? Nc / 2 : 0u) + (lin >> 1) : lin;
             w[d] = wd;
         }
 #pragma unroll
@@ -631,7 +655,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(Geo g, Geo gc, const T *__r
             const T *e = ec + (size_t)a * Nc;
             T s = 0;
 #pragma unroll
-            for (int d = 0; d < 8; ++d) s = fma(w[d], e[idx[d]], s);
+            for (int d = 0; d < 8; ++d) s = fma(bc_sign(mir[d], a) < 0 ? -w[d] : w[d], e[idx[d]], s);
             ef[(size_t)a * N + q] += s;
         }
     }
@@ -1027,8 +1051,8 @@ __global__ void __launch_bounds__(512) k_coarse_solve(Geo g, Coef<T> cf, const T
                 int i = q % g.n[0], j = (q / g.n[0]) % g.n[1], k = q / (g.n[0] * g.n[1]);
                 if (((i + j + k) & 1) == colour) {
                     T Je[4], ctr[4];
-                    AccB<T, BC> a0{eA, &g, i, j, k}, a1{eA + N, &g, i, j, k}, a2{eA + 2 * N, &g, i, j, k},
-                        a3{eA + 3 * N, &g, i, j, k};
+                    AccB<T, BC> a0{eA, 0, &g, i, j, k}, a1{eA + N, 1, &g, i, j, k}, a2{eA + 2 * N, 2, &g, i, j, k},
+                        a3{eA + 3 * N, 3, &g, i, j, k};
                     apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
                     eB[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * cf.dl + cs[N + q]) * cf.iom);
                     for (int a = 0; a < 3; ++a) eB[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
@@ -1095,11 +1119,10 @@ __global__ void __launch_bounds__(512) k_coarse_psi_direct(Geo g, Coef<T> cf, co
                     c[ax] += c[ax] < 0 ? g.n[ax] : 0;
                     c[ax] -= c[ax] >= g.n[ax] ? g.n[ax] : 0;
                     row[c[0] + g.n[0] * (c[1] + g.n[1] * c[2])] += w;
-                } else {
-                    int bc[3] = {min(max(c[0], 0), g.n[0] - 1), min(max(c[1], 0), g.n[1] - 1),
-                                 min(max(c[2], 0), g.n[2] - 1)};
+                } else {   // psi is even across symmetry planes: mirror, or clamp with the 1/r ratio
+                    int bc[3], mirror;
                     double ratio = 1.0;
-                    if (bc[ax] != c[ax]) ratio = robin_ratio<double>(g, bc[0], bc[1], bc[2], c[0], c[1], c[2]);
+                    if (bc_cell<BC>(g, c, bc, mirror)) ratio = robin_ratio<double>(g, bc[0], bc[1], bc[2], c[0], c[1], c[2]);
                     row[bc[0] + g.n[0] * (bc[1] + g.n[1] * bc[2])] += (T)((double)w * ratio);
                 }
             }

@@ -61,16 +61,14 @@ __global__ void __launch_bounds__(256) k_prolong_cubic(Geo gc, Geo g, const doub
             const int p[3] = {I0 - 2 + lx, J0 - 2 + ly, K0 - 2 + lz};
             int b[3];
             bool outside = false;
-            for (int a = 0; a < 3; ++a) {
-                const int n = gc.n[a];
-                if (BC == BC_PERIODIC) {
-                    b[a] = ((p[a] % n) + n) % n;
-                } else {
-                    b[a] = min(max(p[a], 0), n - 1);
-                    outside |= b[a] != p[a];
-                }
+            int mirror = 0;
+            if (BC == BC_PERIODIC) {
+                for (int a = 0; a < 3; ++a) b[a] = ((p[a] % gc.n[a]) + gc.n[a]) % gc.n[a];
+            } else {   // the halo reaches at most 2 cells below the box, where the mirror applies
+                outside = bc_cell<BC>(gc, p, b, mirror);
             }
             double v = src[(size_t)b[0] + (size_t)nc0 * ((size_t)b[1] + (size_t)nc1 * b[2])];
+            if (bc_sign(mirror, f) < 0) v = -v;
             if (BC == BC_ROBIN && outside) v *= (double)robin_ratio<float>(gc, b[0], b[1], b[2], p[0], p[1], p[2]);
             tin[lz][ly][lx] = (float)v;
         }

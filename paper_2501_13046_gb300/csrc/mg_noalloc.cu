@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(256) k_noalloc_pass1(Geo g, Coef<double> cf, c
             AccI<double> a0{u + p, sy, sz}, a1{W + p, sy, sz}, a2{W + N + p, sy, sz}, a3{W + 2 * N + p, sy, sz};
             outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom);
         } else {
-            AccB<double, BC> a0{u, &g, i, j, k}, a1{W, &g, i, j, k}, a2{W + N, &g, i, j, k}, a3{W + 2 * N, &g, i, j, k};
+            AccB<double, BC> a0{u, 0, &g, i, j, k}, a1{W, 1, &g, i, j, k}, a2{W + N, 2, &g, i, j, k},
+                a3{W + 2 * N, 3, &g, i, j, k};
             outer_cell<ORDER>(a0, a1, a2, a3, cf, lu, aa, mom);
         }
         double psi = psi_background(g, i, j, k) + u[p];
@@ -131,6 +132,7 @@ mg_status check_config(const mg_config *c)
         for (int a = 0; a < 3; ++a)
             if (c->punct_P[p][a] != 0.0 || c->punct_S[p][a] != 0.0)
                 return fail(MG_ERR_UNSUPPORTED, "Bowen-York punctures are not supported by the allocation-free norms");
+    if (c->reflect != 0) return fail(MG_ERR_UNSUPPORTED, "symmetry planes are not supported by the allocation-free norms");
     if (!std::isfinite(c->K)) return fail(MG_ERR_INVALID_ARG, "K not finite");
     size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
     if (N > kNoallocMaxCells)

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) k_outer_div(Geo g, OuterCoef oc, const do
             h1 = d1w<ORDER, 1>(a2, oc.c1[1], oc.c2[1]);
             h2 = d1w<ORDER, 2>(a3, oc.c1[2], oc.c2[2]);
         } else {
-            AccB<double, BC> a1{x + N, &g, i, j, k}, a2{x + 2 * N, &g, i, j, k}, a3{x + 3 * N, &g, i, j, k};
+            AccB<double, BC> a1{x + N, 1, &g, i, j, k}, a2{x + 2 * N, 2, &g, i, j, k}, a3{x + 3 * N, 3, &g, i, j, k};
             h0 = d1w<ORDER, 0>(a1, oc.c1[0], oc.c2[0]);
             h1 = d1w<ORDER, 1>(a2, oc.c1[1], oc.c2[1]);
             h2 = d1w<ORDER, 2>(a3, oc.c1[2], oc.c2[2]);
@@ -169,10 +169,11 @@ __device__ __noinline__ void outer_shell_cell(const Geo &g, const Coef<double> &
                                               const double *x, const double *D, int i, int j, int k, double *out)
 {
     const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
-    AccB<double, BC> a0{x, &g, i, j, k}, a1{x + N, &g, i, j, k}, a2{x + 2 * N, &g, i, j, k}, a3{x + 3 * N, &g, i, j, k};
+    AccB<double, BC> a0{x, 0, &g, i, j, k}, a1{x + N, 1, &g, i, j, k}, a2{x + 2 * N, 2, &g, i, j, k},
+        a3{x + 3 * N, 3, &g, i, j, k};
     double lu, aa, mom[3];
     if constexpr (BC == BC_PERIODIC) {
-        AccB<double, BC> q0{D, &g, i, j, k}, q1{D + N, &g, i, j, k}, q2{D + 2 * N, &g, i, j, k};
+        AccB<double, BC> q0{D, 0, &g, i, j, k}, q1{D + N, 0, &g, i, j, k}, q2{D + 2 * N, 0, &g, i, j, k};   // periodic
         const size_t p = (size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k);
         outer_cell_qa<ORDER>(a0, a1, a2, a3, q0, q1, q2, D[3 * N + p], oc, lu, aa, mom);
     } else {

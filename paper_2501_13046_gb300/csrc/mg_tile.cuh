@@ -129,22 +129,15 @@ __device__ __forceinline__ T tile_fetch(const Geo &g, const T *X, const T *O, in
                                         int f)
 {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int x = 2 * P + ((h + y + z) & 1);
-    int xb = x, yb = y, zb = z;
-    if (BC == BC_PERIODIC) {
-        xb += xb < 0 ? nx : 0; xb -= xb >= nx ? nx : 0;
-        yb += yb < 0 ? ny : 0; yb -= yb >= ny ? ny : 0;
-        zb += zb < 0 ? nz : 0; zb -= zb >= nz ? nz : 0;
-    } else {
-        xb = min(max(xb, 0), nx - 1);
-        yb = min(max(yb, 0), ny - 1);
-        zb = min(max(zb, 0), nz - 1);
-    }
-    const int hb = (xb + yb + zb) & 1;
+    const int p[3] = {2 * P + ((h + y + z) & 1), y, z};
+    int b[3], mirror;
+    const bool clamped = bc_cell<BC>(g, p, b, mirror);   // wrap; or mirror / clamp (field f's sign)
+    const int hb = (b[0] + b[1] + b[2]) & 1;
     const size_t N = (size_t)nx * ny * nz;
-    const size_t idx = (size_t)f * N + (hb ? N / 2 : 0) + (size_t)(xb >> 1) + (size_t)(nx >> 1) * (yb + (size_t)ny * zb);
+    const size_t idx = (size_t)f * N + (hb ? N / 2 : 0) + (size_t)(b[0] >> 1) + (size_t)(nx >> 1) * (b[1] + (size_t)ny * b[2]);
     T v = (hb == colour ? X : O)[idx];
-    if (BC == BC_ROBIN && (xb != x || yb != y || zb != z)) v *= robin_ratio<T>(g, xb, yb, zb, x, y, z);
+    if (BC == BC_ROBIN && bc_sign(mirror, f) < 0) v = -v;
+    if (BC == BC_ROBIN && clamped) v *= robin_ratio<T>(g, b[0], b[1], b[2], p[0], p[1], p[2]);
     return v;
 }
 

@@ -154,6 +154,21 @@ def bowen_york_binary(n=128, half=16.0, d=3.0, mass=0.5, P=0.2, S=0.1, A=0.01, o
     return _problem("bowen_york_binary", n, -half, half, order, ROBIN, K_FIXED, 0.0, punct, rho0, rho2, Ssrc, A=A)
 
 
+def octant(problem):
+    """The upper octant x, y, z > 0 of a problem on a box [-L, L]^3 (n even) that is symmetric
+    under the three reflections (u, rho even; S_i odd in x_i): the same sources on [0, L]^3 at n/2
+    cells per axis, with the three lower faces marked as symmetry planes (reflect = 7)."""
+    n = problem["n"]
+    assert all(m % 2 == 0 for m in n) and problem["bc"] == ROBIN
+    hi = problem["hi"]
+    cut = lambda a: np.ascontiguousarray(a[..., n[2] // 2:, n[1] // 2:, n[0] // 2:])
+    out = _problem(problem["name"] + "_octant", [m // 2 for m in n], 0.0, hi, problem["order"], ROBIN,
+                   problem["kmode"], problem["K"], problem["punctures"], cut(problem["rho0"]), cut(problem["rho2"]),
+                   cut(problem["S"]), **problem["meta"])
+    out["reflect"] = 7
+    return out
+
+
 def batch_sizes(count=64, sizes=(48, 64, 96, 128, 160), base_seed=4000, a_lo=2e-5, a_hi=8e-5):
     """[(n_b, a0_b, seed_b)]: n_b uniform over `sizes`, a0_b uniform in [a_lo, a_hi]."""
     out = []

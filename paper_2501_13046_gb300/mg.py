@@ -38,7 +38,7 @@ class mg_config(C.Structure):
         ("spin_limit", C.c_longlong), ("inner_cycles", C.c_int), ("block_threads", C.c_int),
         ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double), ("nested", C.c_int),
         ("nested_min", C.c_int), ("nested_tol", C.c_double),
-        ("punct_P", (C.c_double * 3) * 2), ("punct_S", (C.c_double * 3) * 2),
+        ("punct_P", (C.c_double * 3) * 2), ("punct_S", (C.c_double * 3) * 2), ("reflect", C.c_int),
     ]
 
 
@@ -289,6 +289,7 @@ def config_for(problem, precision=MG_MIXED, **overrides):
     cfg.K = problem["K"]
     cfg.precision = precision
     cfg.npunct = len(problem["punctures"])
+    cfg.reflect = problem.get("reflect", 0)
     for p, pun in enumerate(problem["punctures"]):
         m, x = pun[0], pun[1]
         cfg.punct_m[p] = m

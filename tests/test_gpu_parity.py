@@ -239,6 +239,7 @@ ONE_ITER_CASES = {
     "periodic_o2_n32": lambda: fields.sine_periodic(n=32),
     "robin_o4_n32": lambda: fields.puncture_shell(n=32, half=16.0),
     "robin_o4_n48_partial_tile": lambda: fields.puncture_shell(n=48, half=24.0),
+    "octant_o4_n32_symmetry_planes": lambda: fields.octant(fields.puncture_shell(n=64, half=16.0)),
 }
 
 
