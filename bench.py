@@ -507,6 +507,28 @@ def main():
                            "max_norm": float(iq["norms"].max()), "settings": "tuned" if params else "default"}
             mg.mg_destroy(cq)
             break
+    # the same problem on its octant (128^3, three symmetry planes), mixed
+    qo = fields_mod().octant(q)
+    qosrc = [dev(a) for a in (qo["rho0"], qo["rho2"], *qo["S"])]
+    for params in (tuned_params[mg.MG_MIXED], None):
+        cfgo = mg.config_for(qo, mg.MG_MIXED, tol=WORKLOAD["tol"], max_outer=60, nested=args.nested)
+        if params:
+            apply_tuned(cfgo, params)
+        co = mg.mg_create(cfgo, sp)
+        mg.mg_set_sources(co, *qosrc)
+        try:
+            solve_loop(mg, torch, co, 2, stream)
+            to, io = solve_loop(mg, torch, co, 5, stream)
+        except (mg.MGError, AssertionError):
+            mg.mg_destroy(co)
+            continue
+        shell["mixed_octant_128"] = {"solves_per_s": 5 / to, "outer_iters": io["outer_iters"],
+                                     "max_norm": float(io["norms"].max()),
+                                     "settings": "tuned" if params else "default",
+                                     "workload": "the octant [0,64]^3 at 128^3, symmetry planes x,y,z=0 (reflect=7)"}
+        mg.mg_destroy(co)
+        break
+    del qosrc
     del qsrc
     torch.cuda.empty_cache()
     # Bowen-York binary (two boosted, spinning punctures and a scalar shell), 128^3, nested start
