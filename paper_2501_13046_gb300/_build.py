@@ -15,7 +15,9 @@ LIB = os.path.join(HERE, "libctt_mg.so")
 OBJDIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["ctt_mg.cu", "mg_engine_f32_o2.cu", "mg_engine_f32_o4.cu", "mg_engine_f64_o2.cu", "mg_engine_f64_o4.cu", "mg_noalloc.cu", "unet_conv.cu", "unet_glue.cu"]
+# one engine unit per (precision, order, boundary variant): they compile in parallel
+ENGINE = ["mg_engine_f32_o2_periodic.cu", "mg_engine_f32_o2_robin.cu", "mg_engine_f32_o2_sym.cu", "mg_engine_f32_o4_periodic.cu", "mg_engine_f32_o4_robin.cu", "mg_engine_f32_o4_sym.cu", "mg_engine_f64_o2_periodic.cu", "mg_engine_f64_o2_robin.cu", "mg_engine_f64_o2_sym.cu", "mg_engine_f64_o4_periodic.cu", "mg_engine_f64_o4_robin.cu", "mg_engine_f64_o4_sym.cu"]
+SOURCES = ["ctt_mg.cu", *ENGINE, "mg_noalloc.cu", "unet_conv.cu", "unet_glue.cu"]
 
 
 def nvcc():

@@ -207,19 +207,41 @@ bool encode_level_map(CUtensorMap *m, void *base, const Geo &g, size_t N, size_t
     return r == CUDA_SUCCESS;
 }
 
-mg_status residual_any(mg_ctx *x, double *HM)
+// Calls fn(T{}, ORDER tag, BC tag) for the context's inner precision, stencil order and boundary
+// variant (periodic; Robin; Robin with symmetry planes), the engine instantiation to use.
+template <class Fn>
+mg_status with_engine(const mg_ctx *x, Fn &&fn)
 {
-    if (x->tbytes == 8) return x->cfg.order == 2 ? engine_residual<double, 2>(x, HM) : engine_residual<double, 4>(x, HM);
-    return x->cfg.order == 2 ? engine_residual<float, 2>(x, HM) : engine_residual<float, 4>(x, HM);
+    auto by_bc = [&](auto t, auto o) -> mg_status {
+        if (x->cfg.bc == MG_BC_PERIODIC) return fn(t, o, std::integral_constant<int, BC_PERIODIC>());
+        if (x->cfg.reflect == 0) return fn(t, o, std::integral_constant<int, BC_ROBIN>());
+        return fn(t, o, std::integral_constant<int, BC_SYM>());
+    };
+    using O2 = std::integral_constant<int, 2>;
+    using O4 = std::integral_constant<int, 4>;
+    if (x->tbytes == 8) return x->cfg.order == 2 ? by_bc(double{}, O2{}) : by_bc(double{}, O4{});
+    return x->cfg.order == 2 ? by_bc(float{}, O2{}) : by_bc(float{}, O4{});
 }
 
-mg_status iteration_any(mg_ctx *x)
-{
-    if (x->tbytes == 8) return x->cfg.order == 2 ? engine_iteration<double, 2>(x) : engine_iteration<double, 4>(x);
-    return x->cfg.order == 2 ? engine_iteration<float, 2>(x) : engine_iteration<float, 4>(x);
-}
+#define ENGINE_CALL(name, ...)                                                                          \
+    with_engine(x, [&](auto t, auto o, auto b) {                                                      \
+        return name<decltype(t), decltype(o)::value, decltype(b)::value>(__VA_ARGS__);                \
+    })
 
-mg_status project_gauge(mg_ctx *x) { return engine_project_gauge(x); }
+mg_status residual_any(mg_ctx *x, double *HM) { return ENGINE_CALL(engine_residual, x, HM); }
+
+mg_status iteration_any(mg_ctx *x) { return ENGINE_CALL(engine_iteration, x); }
+
+// Periodic gauge <u> = <W_i> = 0: the means (one grid reduction, finished in its last block) removed.
+mg_status project_gauge(mg_ctx *x)
+{
+    if (x->cfg.bc != MG_BC_PERIODIC) return MG_OK;
+    int g = grid_for(x->N, kRedBlocks);
+    k_sum4<double><<<g, kThreads, 0, x->stream>>>(x->X, x->N, x->partial, x->scal->emean, &x->scal->ticket[2]);
+    k_sub_mean4<double><<<grid_for(x->N), kThreads, 0, x->stream>>>(x->X, x->N, x->scal->emean);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
 
 mg_status start_any(mg_ctx *x)
 {
@@ -438,12 +460,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
             st = fail(MG_ERR_CUDA, "cudaEventCreate");
             break;
         }
-        {
-            const int O = cfg->order;
-            st = x->tbytes == 8 ? (O == 2 ? engine_prepare<double, 2>(x) : engine_prepare<double, 4>(x))
-                                : (O == 2 ? engine_prepare<float, 2>(x) : engine_prepare<float, 4>(x));
-            if (st != MG_OK) break;
-        }
+        if ((st = ENGINE_CALL(engine_prepare, x)) != MG_OK) break;
         if ((st = enter(x)) != MG_OK) break;
         e = cudaMemsetAsync(x->ws, 0, lay.own, x->stream);
         if (e != cudaSuccess) { st = fail(MG_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e)); break; }
@@ -456,7 +473,10 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         if (cfg->bc == MG_BC_ROBIN) {
             double *rt = (double *)(b + lay.RT);
             const size_t M = (size_t)(cfg->n[0] + 4) * (cfg->n[1] + 4) * (cfg->n[2] + 4);
-            k_fill_robin_table<<<grid_for(M), kThreads, 0, x->stream>>>(x->lev[0].geo, rt);
+            if (cfg->reflect)
+                k_fill_robin_table<BC_SYM><<<grid_for(M), kThreads, 0, x->stream>>>(x->lev[0].geo, rt);
+            else
+                k_fill_robin_table<BC_ROBIN><<<grid_for(M), kThreads, 0, x->stream>>>(x->lev[0].geo, rt);
             if ((e = cudaGetLastError()) != cudaSuccess) { st = fail(MG_ERR_CUDA, cudaGetErrorString(e)); break; }
             x->lev[0].geo.rtab = rt;
         }
@@ -481,12 +501,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
                        fused_smem_bytes((int)L1.N, (int)Lc.N, x->tbytes,
                                         fused_ratio_cells(L1.geo, cfg->bc == MG_BC_ROBIN)) <= kMaxCoarseSmem;
         }
-        if (x->dense) {
-            const int O = cfg->order;
-            st = x->tbytes == 8 ? (O == 2 ? engine_dense_setup<double, 2>(x) : engine_dense_setup<double, 4>(x))
-                                : (O == 2 ? engine_dense_setup<float, 2>(x) : engine_dense_setup<float, 4>(x));
-            if (st != MG_OK) break;
-        }
+        if (x->dense && (st = ENGINE_CALL(engine_dense_setup, x)) != MG_OK) break;
         if ((st = leave(x, MG_OK)) != MG_OK) break;
         if (lay.has_child) {
             mg_config cc;
@@ -583,6 +598,8 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
             const dim3 nb = prolong_cubic_grid(c->lev[0].geo);
             if (x->cfg.bc == MG_BC_PERIODIC)
                 k_prolong_cubic<BC_PERIODIC><<<nb, 256, 0, x->stream>>>(c->lev[0].geo, x->lev[0].geo, c->X, x->X);
+            else if (x->cfg.reflect)
+                k_prolong_cubic<BC_SYM><<<nb, 256, 0, x->stream>>>(c->lev[0].geo, x->lev[0].geo, c->X, x->X);
             else
                 k_prolong_cubic<BC_ROBIN><<<nb, 256, 0, x->stream>>>(c->lev[0].geo, x->lev[0].geo, c->X, x->X);
             CK(cudaGetLastError());
@@ -739,11 +756,7 @@ static mg_status mg_time_kernel_impl(mg_ctx *x, int which, int reps, double *ms_
 {
     if (!x || reps < 1 || which < 0 || which > 3) return fail(MG_ERR_INVALID_ARG, "bad argument");
     float ms = 0.f;
-    const int O = x->cfg.order;
-    if (x->tbytes == 8)
-        CKS(O == 2 ? engine_time_kernel<double, 2>(x, which, reps, &ms) : engine_time_kernel<double, 4>(x, which, reps, &ms));
-    else
-        CKS(O == 2 ? engine_time_kernel<float, 2>(x, which, reps, &ms) : engine_time_kernel<float, 4>(x, which, reps, &ms));
+    CKS(ENGINE_CALL(engine_time_kernel, x, which, reps, &ms));
     double N = (double)x->N, s = (double)x->tbytes, b = 0.0;
     if (which == 0) b = 0.5 * 14.0 * s * N;               // half of a two-colour sweep: (2 F + 6) s per cell (algorithmic)
     else if (which == 1) b = (10.0 * s + 4.0 * s / 8.0) * N; // read e, f, a, b; write the coarse rhs

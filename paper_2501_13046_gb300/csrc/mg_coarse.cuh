@@ -216,7 +216,7 @@ inline size_t fused_ratio_cells(const Geo &g, int robin)
 // ghost ratio read from the table rt over the box padded by 2 (1 inside or only mirrored), so no
 // square root per access; fi is the field (0 = u, 1..3 = W_x..W_z) for the sign across symmetry
 // planes.
-template <typename T>
+template <typename T, int BC>
 struct AccRT {
     const T *f;
     int fi;
@@ -227,10 +227,10 @@ struct AccRT {
     {
         const int p[3] = {i + dx, j + dy, k + dz};
         int b[3], mirror;
-        bc_cell<BC_ROBIN>(*g, p, b, mirror);
+        bc_cell<BC>(*g, p, b, mirror);
         const T v = f[b[0] + g->n[0] * (b[1] + g->n[1] * b[2])] *
                     rt[(p[0] + 2) + (g->n[0] + 4) * ((p[1] + 2) + (g->n[1] + 4) * (p[2] + 2))];
-        return bc_sign(mirror, fi) < 0 ? -v : v;
+        return bc_signed<BC>(v, mirror, fi);
     }
 };
 
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
         cs[q] = ab[sq];
         cs[N + q] = ab[N + sq];
     }
-    if constexpr (BC == BC_ROBIN) {
+    if constexpr (BC != BC_PERIODIC) {
         const int m0 = g.n[0] + 4, m1 = g.n[1] + 4, M = m0 * m1 * (g.n[2] + 4);
         for (int e = tid; e < M; e += bs) {
             const int c[3] = {e % m0 - 2, (e / m0) % m1 - 2, e / (m0 * m1) - 2};
@@ -281,8 +281,8 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
     __syncthreads();
     // J e at cell (i, j, k) of the level held in e
     auto apply = [&](const T *e, int i, int j, int k, T a, T b, T Je[4], T ctr[4]) {
-        if constexpr (BC == BC_ROBIN) {
-            AccRT<T> a0{e, 0, rt, &g, i, j, k}, a1{e + N, 1, rt, &g, i, j, k}, a2{e + 2 * N, 2, rt, &g, i, j, k},
+        if constexpr (BC != BC_PERIODIC) {
+            AccRT<T, BC> a0{e, 0, rt, &g, i, j, k}, a1{e + N, 1, rt, &g, i, j, k}, a2{e + 2 * N, 2, rt, &g, i, j, k},
                 a3{e + 3 * N, 3, rt, &g, i, j, k};
             apply_J<ORDER, T>(a0, a1, a2, a3, a, b, cf, Je, ctr);
         } else {
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
             int b[3], mirror;
             if (bc_cell<BC>(gc, cc, b, mirror)) w *= robin_ratio<T>(gc, b[0], b[1], b[2], cc[0], cc[1], cc[2]);
             const int c = b[0] + ncx * (b[1] + ncy * b[2]);
-            for (int a = 0; a < 4; ++a) s4[a] = fma(bc_sign(mirror, a) < 0 ? -w : w, ec[a * Nc + c], s4[a]);
+            for (int a = 0; a < 4; ++a) s4[a] = fma(bc_signed<BC>(w, mirror, a), ec[a * Nc + c], s4[a]);
         }
         for (int a = 0; a < 4; ++a) cur[a * N + q] += s4[a];
     }

@@ -253,11 +253,10 @@ struct mg_ctx {
 };
 
 namespace ctt {
-// Per-(precision, order) engine entry points, instantiated in mg_engine_*.cu.
-template <typename T, int ORDER> mg_status engine_iteration(mg_ctx *x);
-template <typename T, int ORDER> mg_status engine_residual(mg_ctx *x, double *HM);
-template <typename T, int ORDER> mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms);
-template <typename T, int ORDER> mg_status engine_prepare(mg_ctx *x);
-template <typename T, int ORDER> mg_status engine_dense_setup(mg_ctx *x);
-mg_status engine_project_gauge(mg_ctx *x);
+// Per-(precision, order, boundary variant) engine entry points, instantiated in mg_engine_*.cu.
+template <typename T, int ORDER, int BC> mg_status engine_iteration(mg_ctx *x);
+template <typename T, int ORDER, int BC> mg_status engine_residual(mg_ctx *x, double *HM);
+template <typename T, int ORDER, int BC> mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms);
+template <typename T, int ORDER, int BC> mg_status engine_prepare(mg_ctx *x);
+template <typename T, int ORDER, int BC> mg_status engine_dense_setup(mg_ctx *x);
 }  // namespace ctt

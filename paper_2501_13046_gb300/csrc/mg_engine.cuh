@@ -37,22 +37,22 @@ inline Regions restrict_regions(const Geo &gc, int *grid, int threads)
     return r;
 }
 
-template <class Fn>
-void dispatch_bc(int bc, Fn &&fn)
+// The engine is instantiated per boundary variant BC (periodic, Robin, Robin with symmetry planes;
+// one translation unit each, so they compile in parallel); kernels take it as a type tag.
+template <int BC, class Fn>
+void with_bc(Fn &&fn)
 {
-    if (bc == MG_BC_PERIODIC) fn(std::integral_constant<int, BC_PERIODIC>());
-    else fn(std::integral_constant<int, BC_ROBIN>());
+    fn(std::integral_constant<int, BC>());
 }
 
 // One colour pass of the TMA-tiled kernel (X: old values, O: other colour, Y: output).
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status launch_tile(mg_ctx *x, const LevelBufs &L, const TileCoef<T> &tc, const CUtensorMap &mX,
                       const CUtensorMap &mO, const T *X, const T *O, T *Y, int colour)
 {
     const int grid = tile_ctas(L.geo, L.tg);
     const size_t smem = tile_smem_bytes<T, ORDER>();
-    dispatch_bc(x->cfg.bc, [&](auto B) {
-        constexpr int BC = decltype(B)::value;
+    with_bc<BC>([&](auto B) {
         auto k = colour ? k_smooth_tile<T, ORDER, BC, 1> : k_smooth_tile<T, ORDER, BC, 0>;
         k<<<grid, kTileThreads, smem, x->stream>>>(mX, mO, L.geo, tc, X, O, Y, (const T *)L.f, (const T *)L.c, L.tg,
                                                    &x->scal->err, (long long)x->cfg.spin_limit);
@@ -62,7 +62,7 @@ mg_status launch_tile(mg_ctx *x, const LevelBufs &L, const TileCoef<T> &tc, cons
 }
 
 // Residual of level l's current correction, restricted to the right-hand side of level l + 1.
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status enqueue_restrict(mg_ctx *x, int l)
 {
     LevelBufs &L = x->lev[l];
@@ -71,7 +71,7 @@ mg_status enqueue_restrict(mg_ctx *x, int l)
         const TileCoef<T> tc = make_tile_coef<T>(L.geo, x->cfg.order);
         const int grid = tile_ctas(L.geo, L.tgr);
         const size_t smem = tile_restrict_smem_bytes<T, ORDER>();
-        dispatch_bc(x->cfg.bc, [&](auto B) {
+        with_bc<BC>([&](auto B) {
             k_restrict_tile<T, ORDER, decltype(B)::value><<<grid, kTileThreads, smem, x->stream>>>(
                 L.tm_cur(), L.geo, tc, C.geo, (const T *)L.cur(), (const T *)L.f, (const T *)L.c, (T *)C.f, C.split,
                 L.tgr, &x->scal->err, (long long)x->cfg.spin_limit);
@@ -80,7 +80,7 @@ mg_status enqueue_restrict(mg_ctx *x, int l)
         Coef<T> cf = make_coef<T>(L.geo, x->cfg.order);
         int rgrid = 0;
         Regions rr = restrict_regions(C.geo, &rgrid, x->threads);
-        dispatch_bc(x->cfg.bc, [&](auto B) {
+        with_bc<BC>([&](auto B) {
             k_residual_restrict<T, ORDER, decltype(B)::value><<<rgrid, x->threads, 0, x->stream>>>(
                 L.geo, cf, C.geo, (const T *)L.cur(), (const T *)L.f, (const T *)L.c, (T *)C.f, C.split, rr);
         });
@@ -91,7 +91,7 @@ mg_status enqueue_restrict(mg_ctx *x, int l)
 
 // `sweeps` red-black sweeps on a colour-split level.  Each sweep reads the current buffer and
 // writes the alternate one (red half, then black half), then the two swap roles.
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status enqueue_sweeps(mg_ctx *x, int l, int sweeps)
 {
     LevelBufs &L = x->lev[l];
@@ -106,9 +106,9 @@ mg_status enqueue_sweeps(mg_ctx *x, int l, int sweeps)
             const T *O = colour == 0 ? X : Y;
             if (L.tiled) {
                 const CUtensorMap &mO = colour == 0 ? L.tm_cur() : L.tm_alt();
-                CKS(launch_tile<T, ORDER>(x, L, tc, L.tm_cur(), mO, X, O, Y, colour));
+                CKS(launch_tile<T, ORDER, BC>(x, L, tc, L.tm_cur(), mO, X, O, Y, colour));
             } else {
-                dispatch_bc(x->cfg.bc, [&](auto B) {
+                with_bc<BC>([&](auto B) {
                     k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, x->threads, 0, x->stream>>>(
                         L.geo, cf, X, O, Y, (const T *)L.f, (const T *)L.c, colour, rg);
                 });
@@ -120,7 +120,7 @@ mg_status enqueue_sweeps(mg_ctx *x, int l, int sweeps)
     return MG_OK;
 }
 
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status enqueue_coarse(mg_ctx *x, int l)
 {
     LevelBufs &L = x->lev[l];
@@ -140,14 +140,14 @@ mg_status enqueue_coarse(mg_ctx *x, int l)
     Coef<T> cf = make_coef<T>(L.geo, x->cfg.order, x->omega);
     const size_t smem = coarse_smem_bytes(L.N, tb);
     if (smem <= kMaxCoarseSmem) {
-        dispatch_bc(x->cfg.bc, [&](auto B) {
+        with_bc<BC>([&](auto B) {
             k_coarse_solve<T, ORDER, decltype(B)::value><<<1, 512, smem, x->stream>>>(
                 L.geo, cf, (const T *)L.f, (const T *)L.c, (T *)L.eA, x->cfg.coarse_sweeps, periodic);
         });
         CK(cudaGetLastError());
         const size_t dsm = direct_smem_bytes(L.N, periodic, tb);
         if (dsm <= kMaxCoarseSmem) {
-            dispatch_bc(x->cfg.bc, [&](auto B) {
+            with_bc<BC>([&](auto B) {
                 k_coarse_psi_direct<T, ORDER, decltype(B)::value><<<1, 512, dsm, x->stream>>>(
                     L.geo, cf, (const T *)L.f, (const T *)L.c, (T *)L.eA, periodic);
             });
@@ -163,14 +163,14 @@ mg_status enqueue_coarse(mg_ctx *x, int l)
 // the residual is restricted once; the coarser level is then cycled gamma times on that right-
 // hand side (1: V-cycle, 2: W-cycle), the later visits continuing from its correction, and the
 // result is prolongated and post-smoothed.  The coarsest level is visited once (exact solve).
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status enqueue_cycle(mg_ctx *x, int l, bool zero)
 {
     const int Lc = x->nlev - 1;
     LevelBufs &L = x->lev[l];
     if (l == Lc) {   // the coarse solve writes the whole correction
         L.curB = 0;
-        return enqueue_coarse<T, ORDER>(x, Lc);
+        return enqueue_coarse<T, ORDER, BC>(x, Lc);
     }
     if (x->fused && l == Lc - 1) {   // this level and the coarsest in one CTA
         LevelBufs &C = x->lev[Lc];
@@ -181,7 +181,7 @@ mg_status enqueue_cycle(mg_ctx *x, int l, bool zero)
         const T *ein = zero ? (const T *)L.eA : (const T *)L.cur();
         const size_t smem =
             fused_smem_bytes((int)L.N, (int)C.N, sizeof(T), fused_ratio_cells(L.geo, x->cfg.bc == MG_BC_ROBIN));
-        dispatch_bc(x->cfg.bc, [&](auto B) {
+        with_bc<BC>([&](auto B) {
             k_coarse_cycle<T, ORDER, decltype(B)::value><<<1, fused_threads<T>(), smem, x->stream>>>(
                 L.geo, make_coef<T>(L.geo, x->cfg.order, x->omega), C.geo, (const T *)L.f, (const T *)L.c, ein,
                 (T *)L.eA, zero ? 1 : 0, x->cfg.nu_pre, x->cfg.nu_post, (const T *)x->Gpsi, x->mpsi,
@@ -195,21 +195,21 @@ mg_status enqueue_cycle(mg_ctx *x, int l, bool zero)
         L.curB = 0;
         CK(cudaMemsetAsync(L.eA, 0, 4 * L.N * sizeof(T), x->stream));
     }
-    CKS(enqueue_sweeps<T, ORDER>(x, l, x->cfg.nu_pre));
+    CKS(enqueue_sweeps<T, ORDER, BC>(x, l, x->cfg.nu_pre));
     LevelBufs &C = x->lev[l + 1];
-    CKS(enqueue_restrict<T, ORDER>(x, l));
+    CKS(enqueue_restrict<T, ORDER, BC>(x, l));
     const int visits = l + 1 == Lc ? 1 : x->gamma;
-    for (int v = 0; v < visits; ++v) CKS(enqueue_cycle<T, ORDER>(x, l + 1, v == 0));
-    dispatch_bc(x->cfg.bc, [&](auto B) {
+    for (int v = 0; v < visits; ++v) CKS(enqueue_cycle<T, ORDER, BC>(x, l + 1, v == 0));
+    with_bc<BC>([&](auto B) {
         k_prolong_add<T, decltype(B)::value><<<grid_for(L.N, 1 << 24, x->threads), x->threads, 0, x->stream>>>(
             L.geo, C.geo, (const T *)C.cur(), (T *)L.cur(), C.split);
     });
     CK(cudaGetLastError());
-    return enqueue_sweeps<T, ORDER>(x, l, x->cfg.nu_post);
+    return enqueue_sweeps<T, ORDER, BC>(x, l, x->cfg.nu_post);
 }
 
-template <typename T, int ORDER>
-mg_status enqueue_vcycle(mg_ctx *x, bool first) { return enqueue_cycle<T, ORDER>(x, 0, first); }
+template <typename T, int ORDER, int BC>
+mg_status enqueue_vcycle(mg_ctx *x, bool first) { return enqueue_cycle<T, ORDER, BC>(x, 0, first); }
 
 // FP64 residual pass 1 (pass A: q, div W; pass B: R and the integrability sums), then the
 // final reduction of the sums.
@@ -219,7 +219,7 @@ inline OuterFin outer_fin(mg_ctx *x)
     return OuterFin{x->scal, x->cfg.k_mode == MG_K_INTEGRABILITY, x->cfg.bc == MG_BC_PERIODIC, x->cfg.K * x->cfg.K};
 }
 
-template <int ORDER>
+template <int ORDER, int BC>
 mg_status enqueue_outer_pass1(mg_ctx *x)
 {
     LevelBufs &L0 = x->lev[0];
@@ -227,7 +227,7 @@ mg_status enqueue_outer_pass1(mg_ctx *x)
     OuterCoef oc = make_outer_coef(L0.geo, x->cfg.order);
     int gb = 0;
     Regions rg = outer_regions(L0.geo, ORDER, x->cfg.bc == MG_BC_ROBIN, &gb);
-    dispatch_bc(x->cfg.bc, [&](auto B) {
+    with_bc<BC>([&](auto B) {
         k_outer_div<ORDER, decltype(B)::value><<<grid_for(x->N, 1 << 24), kThreads, 0, x->stream>>>(L0.geo, oc, x->X,
                                                                                                       x->D);
         k_outer_pass1q<ORDER, decltype(B)::value><<<gb, kThreads, 0, x->stream>>>(L0.geo, cf, oc, x->X, x->D, x->SRC,
@@ -238,11 +238,11 @@ mg_status enqueue_outer_pass1(mg_ctx *x)
 }
 
 // Outer residual.  HM != nullptr: write H, M instead of the inner rhs/coefficient.
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status enqueue_residual(mg_ctx *x, double *HM)
 {
     LevelBufs &L0 = x->lev[0];
-    CKS(enqueue_outer_pass1<ORDER>(x));
+    CKS(enqueue_outer_pass1<ORDER, BC>(x));
     int g1 = grid_for(x->N, kRedBlocks);
     k_outer_pass2<T><<<g1, kThreads, 0, x->stream>>>(L0.geo, x->X, x->R, x->SRC, x->scal, (T *)L0.f, (T *)L0.c, HM,
                                                      x->partial, L0.split, 1);
@@ -263,7 +263,7 @@ inline size_t gj_smem(int m)
 // Inverse of the coarsest psi row for this outer iteration (its coefficients were just restricted),
 // on a parallel branch: the one-CTA elimination overlaps the first cycle's descent, and the first
 // coarse solve of the iteration waits for it (enqueue_coarse).
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status enqueue_dense_psi_inverse(mg_ctx *x)
 {
     LevelBufs &C = x->lev[x->nlev - 1];
@@ -272,7 +272,7 @@ mg_status enqueue_dense_psi_inverse(mg_ctx *x)
     const size_t sm = gj_smem<T>(x->mpsi);
     CK(cudaEventRecord(x->ev_fork, x->stream));
     CK(cudaStreamWaitEvent(x->side, x->ev_fork, 0));
-    dispatch_bc(x->cfg.bc, [&](auto B) {
+    with_bc<BC>([&](auto B) {
         k_dense_psi_assemble<T, T, ORDER, decltype(B)::value><<<1, 512, 0, x->side>>>(C.geo, cf, (const T *)C.c,
                                                                                     (T *)x->gj, periodic);
     });
@@ -284,7 +284,7 @@ mg_status enqueue_dense_psi_inverse(mg_ctx *x)
 }
 
 // Inverse of the coarsest W rows, once per context (FP64 elimination, stored as T).
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status engine_dense_setup(mg_ctx *x)
 {
     LevelBufs &C = x->lev[x->nlev - 1];
@@ -292,7 +292,7 @@ mg_status engine_dense_setup(mg_ctx *x)
     const int N = (int)C.N;
     Coef<double> cf = make_coef<double>(C.geo, x->cfg.order);
     CK(cudaMemsetAsync(x->gj, 0, gj_scratch_elems(x->mw) * sizeof(double), x->stream));
-    dispatch_bc(x->cfg.bc, [&](auto B) {
+    with_bc<BC>([&](auto B) {
         k_dense_w_assemble<double, double, ORDER, decltype(B)::value><<<3 * N + 1, 256, 4 * N * sizeof(double),
                                                                         x->stream>>>(C.geo, cf, (double *)x->gj,
                                                                                      periodic);
@@ -304,7 +304,7 @@ mg_status engine_dense_setup(mg_ctx *x)
     return MG_OK;
 }
 
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status enqueue_iteration(mg_ctx *x)
 {
     for (int l = 1; l < x->nlev; ++l) {
@@ -313,8 +313,8 @@ mg_status enqueue_iteration(mg_ctx *x)
                                                                        (const T *)x->lev[l - 1].c, (T *)C.c, 2, C.split);
     }
     CK(cudaGetLastError());
-    if (x->dense) CKS(enqueue_dense_psi_inverse<T, ORDER>(x));
-    for (int cyc = 0; cyc < x->cfg.inner_cycles; ++cyc) CKS(enqueue_vcycle<T, ORDER>(x, cyc == 0));
+    if (x->dense) CKS(enqueue_dense_psi_inverse<T, ORDER, BC>(x));
+    for (int cyc = 0; cyc < x->cfg.inner_cycles; ++cyc) CKS(enqueue_vcycle<T, ORDER, BC>(x, cyc == 0));
     int periodic = x->cfg.bc == MG_BC_PERIODIC;
     LevelBufs &L0 = x->lev[0];
     if (periodic) {
@@ -325,18 +325,18 @@ mg_status enqueue_iteration(mg_ctx *x)
     k_update<T><<<grid_for(x->N), kThreads, 0, x->stream>>>(L0.geo, x->X, (const T *)L0.cur(), x->N,
                                                             periodic ? x->scal->emean : nullptr, L0.split);
     CK(cudaGetLastError());
-    return enqueue_residual<T, ORDER>(x, nullptr);
+    return enqueue_residual<T, ORDER, BC>(x, nullptr);
 }
 
-template <typename T, int ORDER>
-mg_status engine_iteration(mg_ctx *x) { return enqueue_iteration<T, ORDER>(x); }
+template <typename T, int ORDER, int BC>
+mg_status engine_iteration(mg_ctx *x) { return enqueue_iteration<T, ORDER, BC>(x); }
 
 // Kernel attributes, set once at context creation (never inside a stream capture).
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status engine_prepare(mg_ctx *x)
 {
     mg_status st = MG_OK;
-    dispatch_bc(x->cfg.bc, [&](auto B) {
+    with_bc<BC>([&](auto B) {
         if (cudaFuncSetAttribute(k_coarse_solve<T, ORDER, decltype(B)::value>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxCoarseSmem) != cudaSuccess ||
             cudaFuncSetAttribute(k_coarse_psi_direct<T, ORDER, decltype(B)::value>,
@@ -350,7 +350,6 @@ mg_status engine_prepare(mg_ctx *x)
             cudaFuncSetAttribute(k_gauss_jordan<double, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kMaxCoarseSmem) != cudaSuccess)
             st = fail(MG_ERR_CUDA, "cudaFuncSetAttribute(k_gauss_jordan)");
-        constexpr int BC = decltype(B)::value;
         if (cudaFuncSetAttribute(k_smooth_tile<T, ORDER, BC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_smem_bytes<T, ORDER>()) != cudaSuccess ||
             cudaFuncSetAttribute(k_smooth_tile<T, ORDER, BC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -363,7 +362,7 @@ mg_status engine_prepare(mg_ctx *x)
 }
 
 // Back-to-back launches of one kernel between events (measurement aid).
-template <typename T, int ORDER>
+template <typename T, int ORDER, int BC>
 mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
 {
     LevelBufs &L = x->lev[0];
@@ -374,12 +373,12 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
             if (!L.split) return fail(MG_ERR_INVALID_ARG, "one-level hierarchy has no global smoother");
             if (L.tiled) {
                 const TileCoef<T> tc = make_tile_coef<T>(L.geo, x->cfg.order, x->omega);
-                CKS(launch_tile<T, ORDER>(x, L, tc, L.tmA, L.tmA, (const T *)L.eA, (const T *)L.eA, (T *)L.eB, r & 1));
+                CKS(launch_tile<T, ORDER, BC>(x, L, tc, L.tmA, L.tmA, (const T *)L.eA, (const T *)L.eA, (T *)L.eB, r & 1));
                 continue;
             }
             int grid = 0;
             Regions rg = smooth_regions(L.geo, ORDER, &grid, x->threads);
-            dispatch_bc(x->cfg.bc, [&](auto B) {
+            with_bc<BC>([&](auto B) {
                 k_smooth_colour<T, ORDER, decltype(B)::value><<<grid, x->threads, 0, x->stream>>>(
                     L.geo, cf, (const T *)L.eA, (const T *)L.eA, (T *)L.eB, (const T *)L.f, (const T *)L.c, r & 1, rg);
             });
@@ -387,16 +386,16 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
             if (x->nlev < 2) return fail(MG_ERR_INVALID_ARG, "one-level hierarchy has no restriction");
             const int keep = L.curB;
             L.curB = 0;   // residual of eA
-            CKS(enqueue_restrict<T, ORDER>(x, 0));
+            CKS(enqueue_restrict<T, ORDER, BC>(x, 0));
             L.curB = keep;
         } else if (which == 2) {
-            CKS(enqueue_outer_pass1<ORDER>(x));
+            CKS(enqueue_outer_pass1<ORDER, BC>(x));
         } else {   // pass B alone (reads pass A's q, div W from the last residual evaluation)
             Coef<double> cd = make_coef<double>(L.geo, x->cfg.order);
             OuterCoef oc = make_outer_coef(L.geo, x->cfg.order);
             int gb = 0;
             Regions rg = outer_regions(L.geo, ORDER, x->cfg.bc == MG_BC_ROBIN, &gb);
-            dispatch_bc(x->cfg.bc, [&](auto B) {
+            with_bc<BC>([&](auto B) {
                 k_outer_pass1q<ORDER, decltype(B)::value><<<gb, kThreads, 0, x->stream>>>(
                     L.geo, cd, oc, x->X, x->D, x->SRC, x->R, x->partial, rg, OuterFin{nullptr, 0, 0, 0.0});
             });
@@ -409,7 +408,7 @@ mg_status engine_time_kernel(mg_ctx *x, int which, int reps, float *ms)
     return MG_OK;
 }
 
-template <typename T, int ORDER>
-mg_status engine_residual(mg_ctx *x, double *HM) { return enqueue_residual<T, ORDER>(x, HM); }
+template <typename T, int ORDER, int BC>
+mg_status engine_residual(mg_ctx *x, double *HM) { return enqueue_residual<T, ORDER, BC>(x, HM); }
 
 }  // namespace ctt

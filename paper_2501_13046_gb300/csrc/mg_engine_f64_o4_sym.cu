@@ -1,0 +1,10 @@
+// Instantiation of the multigrid engine for inner precision double, stencil order 4, Robin boxes with symmetry planes.
+#include "mg_engine.cuh"
+
+namespace ctt {
+template mg_status engine_iteration<double, 4, BC_SYM>(mg_ctx *);
+template mg_status engine_residual<double, 4, BC_SYM>(mg_ctx *, double *);
+template mg_status engine_time_kernel<double, 4, BC_SYM>(mg_ctx *, int, int, float *);
+template mg_status engine_prepare<double, 4, BC_SYM>(mg_ctx *);
+template mg_status engine_dense_setup<double, 4, BC_SYM>(mg_ctx *);
+}  // namespace ctt

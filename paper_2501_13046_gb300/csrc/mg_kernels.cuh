@@ -23,7 +23,8 @@
 namespace ctt {
 
 constexpr double kPi = 3.14159265358979323846;
-enum { BC_PERIODIC = 0, BC_ROBIN = 1 };
+// Kernel boundary variants: periodic; Robin on every face; Robin with symmetry planes (g.reflect)
+enum { BC_PERIODIC = 0, BC_ROBIN = 1, BC_SYM = 2 };
 
 struct Geo {
     int n[3];
@@ -129,6 +130,9 @@ __device__ __forceinline__ bool bc_cell(const Geo &g, const int p[3], int b[3], 
         const int n = g.n[a];
         if constexpr (BC == BC_PERIODIC) {
             b[a] = p[a] + (p[a] < 0 ? n : 0) - (p[a] >= n ? n : 0);
+        } else if constexpr (BC == BC_ROBIN) {
+            b[a] = min(max(p[a], 0), n - 1);
+            clamped |= b[a] != p[a];
         } else {
             if (p[a] < 0 && ((g.reflect >> a) & 1)) {
                 b[a] = -1 - p[a];
@@ -146,6 +150,14 @@ __device__ __forceinline__ bool bc_cell(const Geo &g, const int p[3], int b[3], 
 // the component of W normal to a symmetry plane is odd across it, everything else even.
 __device__ __forceinline__ int bc_sign(int mirror, int fi) { return (fi >= 1 && ((mirror >> (fi - 1)) & 1)) ? -1 : 1; }
 
+// v, negated when field fi changes sign across the planes in `mirror` (symmetry-plane variant only)
+template <int BC, typename T>
+__device__ __forceinline__ T bc_signed(T v, int mirror, int fi)
+{
+    if constexpr (BC == BC_SYM) return bc_sign(mirror, fi) < 0 ? -v : v;
+    else return v;
+}
+
 // FP64 Robin ratio of the ghost cell (i, j, k) (at most 2 cells outside) onto its clamped cell b:
 // the stored table when there is one (the division and square root run at the FP64 rate).
 __device__ __forceinline__ double robin_ratio_f64(const Geo &g, int bi, int bj, int bk, int i, int j, int k)
@@ -157,14 +169,15 @@ __device__ __forceinline__ double robin_ratio_f64(const Geo &g, int bi, int bj, 
 
 // rt[(i+2) + (n0+4)((j+2) + (n1+4)(k+2))] = |x_b| / |x_(i,j,k)| with b = bc_cell (1 when no
 // coordinate is clamped: inside the box, or only mirrored), -2 <= i < n0 + 2, ...
-static __global__ void __launch_bounds__(256) k_fill_robin_table(Geo g, double *__restrict__ rt)
+template <int BC>
+__global__ void __launch_bounds__(256) k_fill_robin_table(Geo g, double *__restrict__ rt)
 {
     const int m0 = g.n[0] + 4, m1 = g.n[1] + 4;
     const size_t M = (size_t)m0 * m1 * (g.n[2] + 4);
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < M; p += (size_t)gridDim.x * blockDim.x) {
         const int c[3] = {(int)(p % m0) - 2, (int)((p / m0) % m1) - 2, (int)(p / ((size_t)m0 * m1)) - 2};
         int b[3], mirror;
-        const bool clamped = bc_cell<BC_ROBIN>(g, c, b, mirror);
+        const bool clamped = bc_cell<BC>(g, c, b, mirror);
         rt[p] = clamped ? robin_ratio<double>(g, b[0], b[1], b[2], c[0], c[1], c[2]) : 1.0;
     }
 }
@@ -211,8 +224,7 @@ __device__ __forceinline__ T fetch_bc(const T *f, int fi, const Geo &g, int i, i
         const int p[3] = {i, j, k};
         int b[3], mirror;
         const bool clamped = bc_cell<BC>(g, p, b, mirror);
-        T v = f[b[0] + g.n[0] * (b[1] + g.n[1] * b[2])];
-        if (bc_sign(mirror, fi) < 0) v = -v;
+        const T v = bc_signed<BC>(f[b[0] + g.n[0] * (b[1] + g.n[1] * b[2])], mirror, fi);
         if (!clamped) return v;
         if constexpr (std::is_same<T, double>::value) return v * robin_ratio_f64(g, b[0], b[1], b[2], i, j, k);
         else return v * robin_ratio<T>(g, b[0], b[1], b[2], i, j, k);
@@ -376,8 +388,8 @@ struct AccB2 {
         int c2 = (q[0] + q[1] + q[2]) & 1;
         size_t lin = (size_t)q[0] + (size_t)g->n[0] * ((size_t)q[1] + (size_t)g->n[1] * q[2]);
         T v = (c2 == c ? same : other)[(c2 ? N / 2 : 0) + (lin >> 1)];
-        if (BC == BC_ROBIN && bc_sign(mirror, fi) < 0) v = -v;
-        if (BC == BC_ROBIN && outside) {
+        v = bc_signed<BC>(v, mirror, fi);
+        if (BC != BC_PERIODIC && outside) {
             if constexpr (std::is_same<T, double>::value)
                 return v * robin_ratio_f64(*g, q[0], q[1], q[2], p[0], p[1], p[2]);
             else
@@ -655,7 +667,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(Geo g, Geo gc, const T *__r
             const T *e = ec + (size_t)a * Nc;
             T s = 0;
 #pragma unroll
-            for (int d = 0; d < 8; ++d) s = fma(bc_sign(mir[d], a) < 0 ? -w[d] : w[d], e[idx[d]], s);
+            for (int d = 0; d < 8; ++d) s = fma(bc_signed<BC>(w[d], mir[d], a), e[idx[d]], s);
             ef[(size_t)a * N + q] += s;
         }
     }

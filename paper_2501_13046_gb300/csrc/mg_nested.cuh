@@ -68,8 +68,8 @@ __global__ void __launch_bounds__(256) k_prolong_cubic(Geo gc, Geo g, const doub
                 outside = bc_cell<BC>(gc, p, b, mirror);
             }
             double v = src[(size_t)b[0] + (size_t)nc0 * ((size_t)b[1] + (size_t)nc1 * b[2])];
-            if (bc_sign(mirror, f) < 0) v = -v;
-            if (BC == BC_ROBIN && outside) v *= (double)robin_ratio<float>(gc, b[0], b[1], b[2], p[0], p[1], p[2]);
+            v = bc_signed<BC>(v, mirror, f);
+            if (BC != BC_PERIODIC && outside) v *= (double)robin_ratio<float>(gc, b[0], b[1], b[2], p[0], p[1], p[2]);
             tin[lz][ly][lx] = (float)v;
         }
         __syncthreads();

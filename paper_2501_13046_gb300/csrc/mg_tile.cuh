@@ -136,8 +136,8 @@ __device__ __forceinline__ T tile_fetch(const Geo &g, const T *X, const T *O, in
     const size_t N = (size_t)nx * ny * nz;
     const size_t idx = (size_t)f * N + (hb ? N / 2 : 0) + (size_t)(b[0] >> 1) + (size_t)(nx >> 1) * (b[1] + (size_t)ny * b[2]);
     T v = (hb == colour ? X : O)[idx];
-    if (BC == BC_ROBIN && bc_sign(mirror, f) < 0) v = -v;
-    if (BC == BC_ROBIN && clamped) v *= robin_ratio<T>(g, b[0], b[1], b[2], p[0], p[1], p[2]);
+    v = bc_signed<BC>(v, mirror, f);
+    if (BC != BC_PERIODIC && clamped) v *= robin_ratio<T>(g, b[0], b[1], b[2], p[0], p[1], p[2]);
     return v;
 }
 
@@ -226,7 +226,7 @@ struct TileRing {
         }
     }
 
-    __device__ __forceinline__ bool ghost(int p) const { return BC == BC_ROBIN && (zs + p < 0 || zs + p >= g->n[2]); }
+    __device__ __forceinline__ bool ghost(int p) const { return BC != BC_PERIODIC && (zs + p < 0 || zs + p >= g->n[2]); }
 
     __device__ __forceinline__ void issue(int p)   // one thread: start the loads of relative plane p
     {
