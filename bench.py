@@ -201,7 +201,7 @@ PASSB_FLOPS_PER_CELL = 179
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes of one 128^3 pass-B launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture of the kernel as it stands (profiles/outer_pass1q_128cube_periodic_o4.md); None if none
-PASSB_TRAFFIC_128 = 375336448
+PASSB_TRAFFIC_128 = 374079744
 
 
 def kernel_rooflines(mg, ctx, N):
