@@ -82,6 +82,22 @@ def test_bowen_york_workspace_and_validation(lib):
     assert e.value.status == lib.MG_ERR_INVALID_ARG
 
 
+def test_symmetry_plane_validation(lib):
+    """reflect needs a Robin box whose marked lower faces are x_a = 0; it adds no workspace."""
+    def cfg_for(bc, reflect, lo=0.0):
+        cfg = lib.mg_config_default()
+        cfg.n[0] = cfg.n[1] = cfg.n[2] = 32
+        cfg.bc, cfg.k_mode, cfg.reflect = bc, lib.MG_K_FIXED, reflect
+        for a in range(3):
+            cfg.lo[a], cfg.hi[a] = lo, lo + 16.0
+        return cfg
+    assert lib.mg_workspace_size(cfg_for(lib.MG_BC_ROBIN, 7)) == lib.mg_workspace_size(cfg_for(lib.MG_BC_ROBIN, 0))
+    for bad in (cfg_for(lib.MG_BC_PERIODIC, 1), cfg_for(lib.MG_BC_ROBIN, 8), cfg_for(lib.MG_BC_ROBIN, 2, lo=-8.0)):
+        with pytest.raises(lib.MGError) as e:
+            lib.mg_workspace_size(bad)
+        assert e.value.status == lib.MG_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("field,value,status", [
     ("order", 3, 1), ("bc", 7, 1), ("precision", 5, 1), ("levels", 6, 1), ("coarse_sweeps", 0, 1),
     ("nested", 2, 1), ("nested_min", 2, 1), ("nested_tol", -1.0, 1),
