@@ -5,8 +5,9 @@
 //   F_psi = Lap u - (K^2/12) psi^5 + (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi)
 //   F_W,i = Lap W_i + (1/3) d_i d_j W_j - 8 pi (psi^6 S_i - m_i)
 // Centred cell stencils of order 2 or 4; boundary values are produced on the fly by
-// every kernel (periodic wrap, or Robin 1/r: v(g) = v(clamp(g)) |x_clamp| / |x_g|),
-// so arrays carry no ghost cells and no fill pass exists.
+// every kernel (periodic wrap, or Robin 1/r: v(g) = v(clamp(g)) |x_clamp| / |x_g|, or, below a
+// symmetry plane x_a = 0 of a Robin box, the mirror image with W_a negated; see bc_cell), so
+// arrays carry no ghost cells and no fill pass exists.
 //
 // Inner problem (defect correction): the block-diagonal linearisation
 //   (Lap + c) e_psi = f_psi,   (Lap + (1/3) grad div) e_W = f_W,
@@ -1094,7 +1095,8 @@ __global__ void __launch_bounds__(512) k_coarse_solve(Geo g, Coef<T> cf, const T
 }
 
 // Coarsest level, psi row only: assemble the dense matrix of a Lap + b (boundary values folded
-// into the columns: periodic wrap, or the Robin ratio |x_b|/|x_g| onto the clamped cell),
+// into the columns: periodic wrap, the mirror cell across a symmetry plane, or the Robin ratio
+// |x_b|/|x_g| onto the clamped cell),
 // bordered on periodic boxes by a constant Lagrange multiplier with the constraint <e> = 0,
 // and solve it by Gaussian elimination with partial pivoting in shared memory.  The exact
 // solve keeps the V-cycle contracting when the psi operator is indefinite on its lowest

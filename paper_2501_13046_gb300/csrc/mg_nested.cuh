@@ -8,7 +8,8 @@
 // cells at offsets (-1, 0, 1, 2) from the parent toward the fine cell, (-7, 105, 35, -5)/128
 // (O(h^4), against O(h^2) for trilinear weights, whose interpolation error the fine Laplacian
 // amplifies into a large starting residual).  Coarse cells outside the box take the level's
-// boundary values (periodic wrap, or the Robin 1/r value).  The arithmetic is FP32: the result
+// boundary values (periodic wrap, the mirror image across a symmetry plane, or the Robin 1/r
+// value).  The arithmetic is FP32: the result
 // is only a starting state.  The weights factor per axis, so the interpolation runs as three
 // one-dimensional passes over a shared-memory tile.
 #pragma once

@@ -5,8 +5,9 @@
 // chunk of z planes.  Each plane of the 4 correction fields (both colour halves, the tile plus
 // its stencil halo) is brought into a ring of shared-memory slots by two TMA tensor loads
 // (cp.async.bulk.tensor, one per colour half) completing on an mbarrier; the stencils then read
-// only shared memory.  Halo cells outside the box (periodic wrap, or the Robin 1/r ghost value
-// v(clamp(g)) |x_clamp| / |x_g|) are not addressable by the tensor load, which fills them with
+// only shared memory.  Halo cells outside the box (periodic wrap, the Robin 1/r ghost value
+// v(clamp(g)) |x_clamp| / |x_g|, or a mirror image across a symmetry plane with W's normal component
+// negated) are not addressable by the tensor load, which fills them with
 // zeros: the CTA fetches them with plain loads one plane ahead and writes them over the zero
 // fill once the plane's TMA has completed.  One barrier per plane orders everything: before it
 // the plane about to enter the stencil window is completed (TMA wait + halo), after it the slot
