@@ -9,12 +9,13 @@
  *   F_psi  = Lap u - (K^2/12) psi^5 + (1/8) psi^-7 AtAt + 2 pi (rho0 psi^5 + rho2 psi)
  *   F_W,i  = Lap W_i + (1/3) d_i d_j W_j - 8 pi (psi^6 S_i - m_i)
  *   H = -8 psi^-5 F_psi,  M_i = psi^-6 F_W,i,
- *   psi = 1 + sum_p m_p / (2 |x - x_p|) + u,   At_ij = d_i W_j + d_j W_i - (2/3) delta_ij d_k W_k,
+ *   psi = 1 + sum_p m_p / (2 |x - x_p|) + u,   At_ij = d_i W_j + d_j W_i - (2/3) delta_ij d_k W_k
+ *           (+ the analytic Bowen-York curvature of punctures that carry momentum or spin),
  *
  * with rho = rho0 + psi^-4 rho2 (rho2 = gradient energy of a scalar field), on a
  * cell-centred uniform grid (x_i = lo + (i + 1/2) h) with 2nd- or 4th-order
- * centred stencils, periodic or Robin 1/r boundaries (Key features, "Boundary
- * conditions"), by multigrid (Key features, "Fast").  On periodic boxes K^2 is
+ * centred stencils, periodic or Robin 1/r boundaries, optionally with reflection-symmetry
+ * planes (Key features, "Boundary conditions"), by multigrid (Key features, "Fast").  On periodic boxes K^2 is
  * set every outer iteration by the discrete integrability condition
  * sum_cells F_psi = 0, the gauge is <u> = <W_i> = 0, and m_i = <8 pi psi^6 S_i>;
  * elsewhere K is the configured constant and m_i = 0.  The constraint norms
