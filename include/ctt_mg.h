@@ -205,10 +205,10 @@ mg_status mg_time_kernel(struct mg_ctx *ctx, int which, int reps, double *ms_per
  *   K2          host pointer or NULL: the K^2 used (integrability value on periodic boxes).
  *   cuda_stream stream for all work (NULL = legacy default stream); the call synchronises it.
  *
- * Scratch: one file-scope device array of 10.54 MB, which every GPU that loads the library
+ * Scratch: one file-scope device array of 8.47 MB, which every GPU that loads the library
  * holds until the process exits.  The first call on a device looks up that device's address of
- * the array (with the device current) and caches it, so make the first call on each device
- * before any stream capture.  All calls share the array and it keeps the last call's contents;
+ * the array (with the device current) and caches it: that first call on each device should come
+ * before any stream capture begins.  All calls share the array and it keeps the last call's contents;
  * two calls whose work overlaps on the GPU (different streams, or different threads) race on
  * it and give undefined results, so serialise them.  The call allocates no device or host memory.
  */

@@ -1,7 +1,7 @@
 // mg_noalloc.cu -- constraint norms of a caller-held state without any device allocation.
 //
 // For callers that must not allocate device memory: the scratch of this entry point (the
-// five FP64 pass-1 fields, the per-block reduction partials and the reduced scalars) lives in
+// four FP64 pass-1 fields, the per-block reduction partials and the reduced scalars) lives in
 // one file-scope device array, sized for grids of at most kNoallocMaxCells cells, that every
 // GPU loading the library holds until the process exits.  The arithmetic is that of the
 // context path (mg_residual_norms): the same per-cell residual, integrability K^2 and
@@ -14,10 +14,10 @@ namespace ctt {
 namespace {
 
 constexpr size_t kNoallocMaxCells = 64 * 64 * 64;                 // 262,144 cells
-constexpr size_t kNoallocR = 5 * kNoallocMaxCells;                // pass-1 output, 5 FP64 fields
+constexpr size_t kNoallocR = 4 * kNoallocMaxCells;                // pass-1 output, 4 FP64 fields
 constexpr size_t kNoallocPartials = (size_t)kRedBlocks * 8;       // block partials
 constexpr size_t kNoallocScalars = 64;                            // >= sizeof(Scalars) / 8
-constexpr size_t kNoallocDoubles = kNoallocR + kNoallocPartials + kNoallocScalars;   // 10.54 MB
+constexpr size_t kNoallocDoubles = kNoallocR + kNoallocPartials + kNoallocScalars;   // 8.47 MB
 static_assert(sizeof(Scalars) <= kNoallocScalars * sizeof(double), "scalar slot too small");
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
@@ -70,11 +70,10 @@ __global__ void __launch_bounds__(256) k_noalloc_pass1(Geo g, Coef<double> cf, c
         double psi = psi_background(g, i, j, k) + u[p];
         double r0 = rho0[p], r2 = rho2 ? rho2[p] : 0.0;
         double ip = 1.0 / psi;
-        double p2 = psi * psi, p4 = p2 * p2, p5 = p4 * psi, p6 = p5 * psi;
-        double ip2 = ip * ip, ip4 = ip2 * ip2, ip7 = ip4 * ip2 * ip, ip8 = ip4 * ip4;
+        double p2 = psi * psi, p5 = p2 * p2 * psi, p6 = p5 * psi;
+        double ip2 = ip * ip, ip4 = ip2 * ip2, ip7 = ip4 * ip2 * ip;
         double nonlin = 0.125 * aa * ip7 + 2.0 * kPi * (r0 * p5 + r2 * psi);
         R[p] = lu + nonlin;
-        R[4 * N + p] = -0.875 * aa * ip8 + 2.0 * kPi * (5.0 * r0 * p4 + r2);
         acc[0] += nonlin;
         acc[1] += p5;
 #pragma unroll
@@ -134,10 +133,12 @@ mg_status check_config(const mg_config *c)
                 return fail(MG_ERR_UNSUPPORTED, "Bowen-York punctures are not supported by the allocation-free norms");
     if (c->reflect != 0) return fail(MG_ERR_UNSUPPORTED, "symmetry planes are not supported by the allocation-free norms");
     if (!std::isfinite(c->K)) return fail(MG_ERR_INVALID_ARG, "K not finite");
-    size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
-    if (N > kNoallocMaxCells)
-        return fail(MG_ERR_INVALID_ARG, "mg_residual_norms_noalloc: grid of " + std::to_string(N) +
-                                            " cells exceeds the static scratch limit of 262144 cells (64^3)");
+    // each product is checked before the next one is formed, so no cell count wraps around
+    const char *msg = "mg_residual_norms_noalloc: the grid exceeds the static scratch limit of 262144 cells (64^3)";
+    for (int a = 0; a < 3; ++a)
+        if ((size_t)c->n[a] > kNoallocMaxCells) return fail(MG_ERR_INVALID_ARG, msg);
+    const size_t n01 = (size_t)c->n[0] * c->n[1];
+    if (n01 > kNoallocMaxCells || n01 * c->n[2] > kNoallocMaxCells) return fail(MG_ERR_INVALID_ARG, msg);
     return MG_OK;
 }
 

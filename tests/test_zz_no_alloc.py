@@ -75,11 +75,28 @@ def test_noalloc_norms_match_context_path_twice(mg, case):
         assert np.isfinite(K2) and K2 >= 0.0
 
 
-def test_noalloc_rejects_grids_beyond_the_static_limit(mg):
+def test_noalloc_without_rho2_matches_a_context_with_zero_rho2(mg):
+    """rho2 = NULL means rho2 = 0 (no gradient energy): compare with a context given zeros."""
+    p = fields.modes_periodic(n=32, a0=1e-3)
+    p["rho2"] = np.zeros_like(p["rho2"])
+    cfg = mg.config_for(p, mg.MG_FP64)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    for seed in (3, 4):
+        u, W = state(p, seed)
+        want = context_norms(mg, p, u, W)
+        got, _ = mg.mg_residual_norms_noalloc(cfg, dev(u), dev(W), dev(p["rho0"]), None, dev(p["S"]),
+                                              torch.cuda.current_stream().cuda_stream)
+        np.testing.assert_allclose(got, want, rtol=RTOL)
+
+
+@pytest.mark.parametrize("n", [(64, 64, 65), (1 << 21, 1 << 21, 1 << 22), (1 << 30, 4, 4), (3, 3, 1 << 29)])
+def test_noalloc_rejects_grids_beyond_the_static_limit(mg, n):
+    """Larger grids are rejected before any work, including sizes whose cell count would wrap
+    around 64 bits (2^21 x 2^21 x 2^22 = 2^64)."""
     p = fields.uniform(n=16)
     cfg = mg.config_for(p, mg.MG_FP64)
-    cfg.n[0] = cfg.n[1] = 64
-    cfg.n[2] = 65     # 64*64*65 cells > 64^3
+    for a in range(3):
+        cfg.n[a] = n[a]
     z = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(mg.MGError) as e:
         mg.mg_residual_norms_noalloc(cfg, z, z, z, None, z)
