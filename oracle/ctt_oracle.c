@@ -56,6 +56,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORA_PI 3.14159265358979323846
 
@@ -251,6 +254,19 @@ static double psibg_at(const ora_grid *g, int i, int j, int k)
         v += g->pm[p] / (2.0 * sqrt(r2));
     }
     return v;
+}
+
+/* Threads of the OpenMP loops (the pointwise residual and operator loops; the Gauss-Seidel
+ * sweeps are sequential).  Returns the count now in effect (1 without OpenMP). */
+int ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* ---------------- exported operator entry points (used by the pins) ---------------- */

@@ -77,6 +77,8 @@ def lib():
         L.ora_solve.argtypes = [gp, dp, dp, dp, C.c_int, dp, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
                                 C.c_int, dp, dp, dp, C.POINTER(C.c_int)]
         L.ora_solve.restype = C.c_int
+        L.ora_set_threads.argtypes = [C.c_int]
+        L.ora_set_threads.restype = C.c_int
         _lib = L
     return _lib
 
@@ -104,6 +106,11 @@ def make_grid(n, lo, hi, order, bc, punctures=(), reflect=0):
             g.pP[p][a] = float(P[a])
             g.pS[p][a] = float(S[a])
     return g
+
+
+def set_threads(n=0):
+    """Threads of the oracle's OpenMP loops (n <= 0 leaves the count); returns the count in effect."""
+    return lib().ora_set_threads(int(n))
 
 
 def by_point(g, x):
