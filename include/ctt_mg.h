@@ -74,7 +74,8 @@ typedef struct {
     int max_outer;        /* outer (defect-correction) iterations (default 60)                    */
     int nu_pre, nu_post;  /* red-black sweeps before / after the coarse correction (default 2, 2) */
     int coarse_sweeps;    /* red-black sweeps on the coarsest level (default 60)                  */
-    int use_graph;        /* 1 = replay each outer iteration as a captured CUDA graph (default 1) */
+    int use_graph;        /* 1 = replay each outer iteration as a captured CUDA graph (default 1); 0 = direct
+                             launches; 2 = as 1, and a batch (mg_batch_solve) is paced from the host     */
     long long spin_limit; /* bound on any device-side wait, in polls (default 1<<24)              */
     int inner_cycles;     /* V-cycles per outer iteration, 0 = auto (1 for MG_FP64, 2 for MG_MIXED) */
     int block_threads;    /* threads per block of the global-memory stencil kernels: 0 = 256, else 64, 128 or 256 */
@@ -103,6 +104,24 @@ typedef struct {
                              symmetry plane (lo[a] must be 0): a cell below it takes the value of its mirror
                              image, with the sign flipped for W_a (the component normal to the plane) and kept
                              for u and the other components.  7 = octant symmetry.  0 = all faces Robin.    */
+    double field_tol;     /* > 0: a solve stops only when, besides max(|H|, |M_i|) <= tol, the last outer update
+                             changed every field by at most field_tol times its size (max |e_u| <= field_tol
+                             max |psi|, max |e_W_i| <= field_tol max |W_i|); with the outer iteration's
+                             contraction rho, the remaining error per field is then about rho / (1 - rho) of
+                             that.  A residual bound alone fixes each field only to |J^-1| tol in absolute
+                             terms, which for a small W_i can be far from tol relative to W_i.  Needs at least
+                             one outer update.  The half-size solve of a nested start ignores it.  0 = off.  */
+    int extrap;           /* Robin boxes: bit 2a (lower) / 2a + 1 (upper) makes that face of axis a extrapolating
+                             (the paper lists extrapolating, reflective and periodic boundaries, Key features,
+                             "Boundary conditions"): a cell beyond it at distance d along its normal takes the
+                             linear extrapolation (1 + d) v(b) - d v(b') through the boundary cell b of its line
+                             and the next one in, for u and every W_i; beyond several such faces the rule applies
+                             axis by axis, and the Robin or mirror rule then handles the remaining coordinates.
+                             Linear fields are reproduced exactly.  Such a face leaves the field's normal
+                             behaviour free, so whether the problem stays well posed depends on the faces
+                             chosen: at least one face must stay Robin (MG_ERR_UNSUPPORTED otherwise), and some
+                             sets (e.g. the three lower faces) give a nearly singular system that does not
+                             converge.  A lower face cannot be both extrapolating and a symmetry plane.  0 = none. */
 } mg_config;
 
 typedef struct {
@@ -117,6 +136,13 @@ typedef struct {
     double device_ms;     /* device time of the solve, nested start included (CUDA events)        */
     long long kernel_launches; /* library kernels launched by this solve (0 if use_graph == 0)    */
     int nested_iters;     /* outer iterations of the nested start's half-size solve, 0 without one    */
+    double rel_change[4]; /* with field_tol > 0, the last outer update per field: max |e_u| / max |psi|,
+                             max |e_W_i| / max |W_i| (0 before the first update, where the field is
+                             zero, or with field_tol = 0)                                          */
+    int warm_start;       /* learned warm start: 0 not used, 1 its guess was the starting state, 2 its guess
+                             was rejected (non-finite residual), 3 the solve from its guess
+                             failed and was repeated from the cold start (this info describes the repeat,
+                             device_ms and kernel_launches include both)                            */
 } mg_solve_info;
 
 /* Fill *cfg with defaults: order 2, periodic, integrability K, MG_MIXED, tol 1e-10, ... */
@@ -140,26 +166,33 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
  * (non-conformally-flat data is listed as forthcoming in the paper's feature list). */
 mg_status mg_set_conformal_metric(struct mg_ctx *ctx, const double *gt, int on_device);
 
-/* Matter sources: rho = rho0 + psi^-4 rho2; S_i lower-index momentum density.  rho2 may be NULL (0).
+/* Matter sources (the matter projections rho and S_i of the paper's Summary, after eq:Mom, given by a
+ * scalar field: Key features, "Flexibility"): rho = rho0 + psi^-4 rho2; S_i lower-index momentum density.
+ * rho2 may be NULL (0).
  * Returns MG_ERR_INVALID_ARG (and leaves the context without sources) if any value is NaN or
  * infinite; the check runs on the device after the copy, and the call returns once it is done. */
 mg_status mg_set_sources(struct mg_ctx *ctx, const double *rho0, const double *rho2, const double *Sx,
                          const double *Sy, const double *Sz, int on_device);
 
-/* Initial guess for u (N) and W (3N); either may be NULL (zero).  Default: u = 0, W = 0.
+/* Initial guess for u (N) and W (3N) of the CTT unknowns (psi = background + u, W_i of At_ij; Summary,
+ * "Methods"); either may be NULL (zero).  Default: u = 0, W = 0.
  * On periodic boxes the means are projected out at the start of mg_solve.  With cfg.nested, a
  * non-NULL u or W replaces the next solve's nested start; (NULL, NULL) keeps it (a half-size solve
  * that diverges leaves the zero state as the start). */
 mg_status mg_set_initial_guess(struct mg_ctx *ctx, const double *u, const double *W, int on_device);
 
-/* Iterate until max(|H|, |M_i|) <= tol.  info may be NULL. */
+/* Solve the constraints eq:Ham and eq:Mom (Summary) by multigrid (Key features, "Fast"): iterate until
+ * max(|H|, |M_i|) <= tol (and, with field_tol, the per-field test), recording the norms of every
+ * outer iteration (Key features, "Diagnostics").  info may be NULL. */
 mg_status mg_solve(struct mg_ctx *ctx, mg_solve_info *info);
 
-/* Copy out u (N doubles), W (3N doubles) and K; any pointer may be NULL. */
+/* Copy out the solution of the constraint problem (Summary: psi through u, W_i, and K, the mean
+ * curvature of the constant-K slice): u (N doubles), W (3N doubles) and K; any pointer may be NULL. */
 mg_status mg_get_solution(struct mg_ctx *ctx, double *u, double *W, double *K, int on_device);
 
 /*
- * Checkpoint / resume.  mg_checkpoint_save writes the context's state to `path` as a raw
+ * Checkpoint / resume (the paper writes checkpoints to restart from: Key features, "Output"; this
+ * library writes a raw file instead of HDF5).  mg_checkpoint_save writes the context's state to `path` as a raw
  * little-endian file: the 8 bytes "CTTMGCK1", int32 n[3], order, bc, 0, the last K^2 (double),
  * then u (N doubles) and W (3N doubles), x fastest, no ghost cells.  mg_checkpoint_load reads such
  * a file written for the same n, order and bc and makes its (u, W) the next solve's initial guess
@@ -170,10 +203,46 @@ mg_status mg_get_solution(struct mg_ctx *ctx, double *u, double *W, double *K, i
 mg_status mg_checkpoint_save(struct mg_ctx *ctx, const char *path);
 mg_status mg_checkpoint_load(struct mg_ctx *ctx, const char *path);
 
-/* Evaluate the constraints at the current state: out = max |H|, max |M_x|, |M_y|, |M_z|. */
+/*
+ * Learned warm start (not in the paper: the build target's learned initial guess; plain multigrid
+ * stays the fallback and the judge).  mg_warmstart_load reads a trained 3-D U-Net from
+ * `weights_path` (NULL: switch the warm start off) into device memory it allocates (about 70 MB
+ * for a 64^3 network) and attaches it to the context.  From then on, a solve that was given no
+ * initial guess first runs the network (BF16 tcgen05 convolutions, FP32 accumulation; captured
+ * once as a CUDA graph) on the sources: inputs (rho0 + rho2 - <rho>, S_i, and the pre-solve
+ * K = -sqrt(24 pi <rho>)) at the network's size, output (u, W_i) with zero means; a grid finer
+ * than the network's is restricted (8-child means) before and the guess prolongated (cell-centred
+ * trilinear) after.  The multigrid judges the guess: it is the starting state whenever its
+ * residual is finite (otherwise the solve starts as without it: psi = 1, or the nested start), and
+ * if the solve from it does not converge or diverges, the problem is solved again from the cold
+ * start; mg_solve_info.warm_start reports which happened.  (A test of the guess's max(|H|, |M_i|)
+ * against that of psi = 1 would reject useful guesses: the Laplacian weighs a mode of the guess's
+ * error by k^2, so its small-scale error, which the first smoothing sweeps remove, dominates.)
+ *
+ * Serves periodic cubes whose side is the network's size n_net times a power of two; other grids
+ * return MG_ERR_UNSUPPORTED.  The file (little-endian) is: the 8 bytes "CTTUNET1"; int32 n_net
+ * (a multiple of 8, >= 64, (n_net/8)^3 a multiple of 128); int32 count; float32 s_rho, s_S, s_K,
+ * s_u, s_W (input scales of rho - <rho>, S_i, K and output scales of u, W_i, all nonzero); then
+ * count float32 parameters: for each 3x3x3 convolution in the order e0a, e0, e1a, e1, e2a, e2, ba,
+ * b, d2a, d2, d1a, d1, d0a, d0 (channels in -> out: 16->16, 16->16, 16->32, 32->32, 32->64,
+ * 64->64, 64->64, 64->64, 128->64, 64->64, 96->32, 32->32, 48->16, 16->16) its weights
+ * [27][cout][cin] (tap (dz+1)*9 + (dy+1)*3 + (dx+1)) and bias [cout], then the 1x1 head's weights
+ * [4][16] and bias [4]; nothing after them.  A malformed file returns MG_ERR_INVALID_ARG.
+ *
+ * mg_warmstart_predict runs only the network on the current sources: the guess becomes the
+ * context's state (as if given to mg_set_initial_guess) and is copied to u (N doubles) and W (3N
+ * doubles) when they are not NULL (on_device as for mg_get_solution).
+ */
+mg_status mg_warmstart_load(struct mg_ctx *ctx, const char *weights_path);
+mg_status mg_warmstart_predict(struct mg_ctx *ctx, double *u, double *W, int on_device);
+
+/* Evaluate the constraints at the current state (H of eq:Ham, M_i of eq:Mom, the maximum over the grid
+ * of the errors the paper's solver reports every iteration: Key features, "Diagnostics"):
+ * out = max |H|, max |M_x|, |M_y|, |M_z|. */
 mg_status mg_residual_norms(struct mg_ctx *ctx, double out[4]);
 
-/* Write H (N) and M (3N) at the current state (either may be NULL). */
+/* Write the constraint fields H (N, eq:Ham) and M (3N, eq:Mom) at the current state (either may be
+ * NULL). */
 mg_status mg_constraint_fields(struct mg_ctx *ctx, double *H, double *M, int on_device);
 
 /*
@@ -233,15 +302,26 @@ mg_status mg_autotune(const mg_config *base, const double *rho0, const double *r
 void mg_destroy(struct mg_ctx *ctx);
 
 /*
- * Batched solves: many independent problems of uneven grid sizes in one call.
- * All instances must share order, bc, precision and k_mode; sizes, boxes and sources differ.
- * Each instance owns its workspace and a private stream; mg_batch_solve captures the outer
- * iteration of every instance into one CUDA graph (one parallel branch per instance) and
- * replays it, one launch and one host synchronisation per round for the whole batch, until
- * every instance has met its tolerance (converged instances keep iterating in lock step; their
- * residual only decreases further) or the largest max_outer is reached.
+ * Batched solves: many independent problems of uneven grid sizes in one call (not in the paper,
+ * which solves one problem per run: the build target's batched pattern).  All instances must
+ * share order, bc, precision and k_mode; sizes, boxes and sources differ.  Each instance owns its
+ * workspace and a private stream.
+ *
+ * Device-paced (default, use_graph != 2): mg_batch_solve is one CUDA graph launch and one host
+ * synchronisation.  The graph holds every instance's start, then a conditional WHILE node whose
+ * body is one conditional IF node per instance (that instance's captured outer iteration) and a
+ * one-block control kernel; the control kernel reads each instance's scalars on the device,
+ * records its norms, the round it met its tolerance and the time it did (%globaltimer), and sets
+ * the conditions, so an instance drops out of the rounds once it has converged (or its norm became
+ * non-finite, or it used its max_outer) and the loop ends when none is left.  A converged
+ * instance's state is exactly that of a solo mg_solve.  The graph is built on the first call and
+ * reused (rebuilt when the largest max_outer changes).
+ * Host-paced (cfgs[0].use_graph == 2): one graph per round for all instances, checked on the
+ * host after every round; converged instances keep iterating in lock step until the last one
+ * converges (their residual only decreases further).
  *   infos: count entries (may be NULL); infos[b].outer_iters is the round at which instance b
- *   first met its tolerance; infos[b].device_ms the batch time up to the end of that round;
+ *   met its tolerance; infos[b].device_ms the time from the start of the solve to that round
+ *   (device timestamps, or events when host-paced); infos[b].history its norms up to that round;
  *   infos[b].converged = 0 for an instance that did not.  An instance whose norm becomes
  *   non-finite is abandoned (the others continue) and the call returns MG_ERR_DIVERGED.
  */
@@ -251,6 +331,13 @@ mg_status mg_batch_set_sources(mg_batch *bt, int b, const double *rho0, const do
                                const double *Sy, const double *Sz, int on_device);
 mg_status mg_batch_set_initial_guess(mg_batch *bt, int b, const double *u, const double *W, int on_device);
 mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms);
+/* The learned warm start (see mg_warmstart_load) for every instance it serves, the network shared
+ * by them (instances of other sizes start cold).  Before the batch's rounds each such instance
+ * without an initial guess gets the network's guess (kept where its residual is finite); an
+ * instance that does not converge from its guess is solved again alone from its
+ * cold start after the rounds (infos[b].warm_start = 3, its time added to infos[b].device_ms and to
+ * *total_ms).  NULL switches it off. */
+mg_status mg_batch_warmstart_load(mg_batch *bt, const char *weights_path);
 mg_status mg_batch_get_solution(mg_batch *bt, int b, double *u, double *W, double *K, int on_device);
 void mg_batch_destroy(mg_batch *bt);
 

@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # one engine unit per (precision, order, boundary variant): they compile in parallel
 ENGINE = ["mg_engine_f32_o2_periodic.cu", "mg_engine_f32_o2_robin.cu", "mg_engine_f32_o2_sym.cu", "mg_engine_f32_o4_periodic.cu", "mg_engine_f32_o4_robin.cu", "mg_engine_f32_o4_sym.cu", "mg_engine_f64_o2_periodic.cu", "mg_engine_f64_o2_robin.cu", "mg_engine_f64_o2_sym.cu", "mg_engine_f64_o4_periodic.cu", "mg_engine_f64_o4_robin.cu", "mg_engine_f64_o4_sym.cu"]
-SOURCES = ["ctt_mg.cu", *ENGINE, "mg_noalloc.cu", "unet_conv.cu", "unet_glue.cu"]
+SOURCES = ["ctt_mg.cu", *ENGINE, "mg_noalloc.cu", "mg_warmstart.cu", "unet_conv.cu", "unet_glue.cu"]
 
 
 def nvcc():

@@ -10,6 +10,7 @@
 // host synchronisation per iteration is the read of K^2 and the four norms.
 #include "mg_common.cuh"
 #include "mg_nested.cuh"
+#include "mg_batch.cuh"
 
 #include <cudaTypedefs.h>
 #include <nvtx3/nvToolsExt.h>
@@ -72,12 +73,24 @@ mg_status validate(const mg_config *c)
                 return fail(MG_ERR_INVALID_ARG, "puncture momentum or spin not finite");
     if (c->reflect < 0 || c->reflect > 7) return fail(MG_ERR_INVALID_ARG, "reflect must be a mask of 3 bits");
     if (c->reflect != 0 && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "symmetry planes need a Robin box");
+    if (c->extrap < 0 || c->extrap > 63) return fail(MG_ERR_INVALID_ARG, "extrap must be a mask of 6 bits");
+    if (c->extrap != 0 && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "extrapolating faces need a Robin box");
+    for (int a = 0; a < 3; ++a)
+        if (((c->reflect >> a) & 1) && ((c->extrap >> (2 * a)) & 1))
+            return fail(MG_ERR_INVALID_ARG, "a lower face cannot be both a symmetry plane and extrapolating");
+    if (c->bc == MG_BC_ROBIN) {
+        int special = c->extrap;
+        for (int a = 0; a < 3; ++a) special |= ((c->reflect >> a) & 1) << (2 * a);
+        if (special == 63) return fail(MG_ERR_UNSUPPORTED, "a Robin box needs at least one Robin face");
+    }
     for (int a = 0; a < 3; ++a)
         if (((c->reflect >> a) & 1) && c->lo[a] != 0.0)
             return fail(MG_ERR_INVALID_ARG, "a symmetry plane must be the face x_a = 0 (lo[a] = 0)");
     if (c->nested != 0 && c->nested != 1) return fail(MG_ERR_INVALID_ARG, "nested must be 0 or 1");
     if (c->nested_min != 0 && c->nested_min < 3) return fail(MG_ERR_INVALID_ARG, "nested_min must be 0 or >= 3");
     if (!(c->nested_tol >= 0.0) || !std::isfinite(c->nested_tol)) return fail(MG_ERR_INVALID_ARG, "bad nested_tol");
+    if (!(c->field_tol >= 0.0) || !std::isfinite(c->field_tol)) return fail(MG_ERR_INVALID_ARG, "bad field_tol");
+    if (c->use_graph < 0 || c->use_graph > 2) return fail(MG_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
     int lv = c->levels > 0 ? c->levels : auto_levels(c->n);
     for (int l = 0; l + 1 < lv; ++l)
         for (int a = 0; a < 3; ++a) {
@@ -118,7 +131,25 @@ bool nested_child_config(const mg_config *c, mg_config *cc)
     for (int a = 0; a < 3; ++a) cc->n[a] = c->n[a] / 2;
     cc->levels = c->levels > 1 ? c->levels - 1 : 0;
     cc->tol = std::max(c->tol, c->nested_tol > 0.0 ? c->nested_tol : kNestedTol);
+    cc->field_tol = 0.0;   // the half-size solve only supplies a starting state
     return true;
+}
+
+// The per-field part of the stopping test: every field's last update at most field_tol times the
+// field's size (always true when field_tol is off; false before the first update).
+bool fields_settled(const mg_config &c, const Scalars &s, int updates)
+{
+    if (c.field_tol <= 0.0) return true;
+    if (updates < 1) return false;
+    for (int a = 0; a < 4; ++a)
+        if (!(s.change[a] <= c.field_tol * s.change[4 + a])) return false;
+    return true;
+}
+
+void fill_rel_change(const mg_config &c, const Scalars &s, int updates, double out[4])
+{
+    const bool on = c.field_tol > 0.0 && updates > 0;
+    for (int a = 0; a < 4; ++a) out[a] = (on && s.change[4 + a] > 0.0) ? s.change[a] / s.change[4 + a] : 0.0;
 }
 
 struct Layout {
@@ -214,7 +245,7 @@ mg_status with_engine(const mg_ctx *x, Fn &&fn)
 {
     auto by_bc = [&](auto t, auto o) -> mg_status {
         if (x->cfg.bc == MG_BC_PERIODIC) return fn(t, o, std::integral_constant<int, BC_PERIODIC>());
-        if (x->cfg.reflect == 0) return fn(t, o, std::integral_constant<int, BC_ROBIN>());
+        if (x->cfg.reflect == 0 && x->cfg.extrap == 0) return fn(t, o, std::integral_constant<int, BC_ROBIN>());
         return fn(t, o, std::integral_constant<int, BC_SYM>());
     };
     using O2 = std::integral_constant<int, 2>;
@@ -276,6 +307,82 @@ mg_status capture(mg_ctx *x, Fn &&fn, cudaGraphExec_t *exec, long long *kernels)
         return fail(MG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
     }
     return MG_OK;
+}
+
+// Gauge projection + residual of the current state (captured graph or direct launches), then wait
+// for its scalars.
+mg_status run_start(mg_ctx *x, long long *launches)
+{
+    if (x->cfg.use_graph) {
+        if (!x->graph_start) CKS(capture(x, start_any, &x->graph_start, &x->launches_start));
+        CK(cudaGraphLaunch(x->graph_start, x->stream));
+        *launches += x->launches_start;
+    } else {
+        CKS(start_any(x));
+    }
+    CK(cudaStreamSynchronize(x->stream));
+    return MG_OK;
+}
+
+double max_norm(const Scalars &s)
+{
+    double m = 0.0;
+    for (int a = 0; a < 4; ++a) m = std::isfinite(s.norms[a]) ? std::max(m, s.norms[a]) : INFINITY;
+    return m;
+}
+
+// The network's guess for the current sources into X (captured once per context).
+mg_status warm_infer(mg_ctx *x, long long *launches)
+{
+    if (x->cfg.use_graph) {
+        if (!x->warm_graph) {
+            // one direct run first: it allocates the network's level buffers for this grid size,
+            // which a capture must not do
+            CKS(warm_enqueue(x->warm, x, x->stream));
+            CK(cudaStreamSynchronize(x->stream));
+            CKS(capture(x, [](mg_ctx *c) { return warm_enqueue(c->warm, c, c->stream); }, &x->warm_graph,
+                        &x->launches_warm));
+        }
+        CK(cudaGraphLaunch(x->warm_graph, x->stream));
+        *launches += x->launches_warm;
+    } else {
+        CKS(warm_enqueue(x->warm, x, x->stream));
+    }
+    if (warm_timed_out(x->warm, x->stream))
+        return fail(MG_ERR_TIMEOUT, "a bounded wait of the warm start's tensor-core kernels gave up");
+    return MG_OK;
+}
+
+// The learned start.  The multigrid judges it: the guess is the starting state whenever its
+// residual is finite (state 1: X holds it, its residual evaluated), else X = 0 (state 2); a solve
+// that then fails is repeated from the cold start by the caller.  A max-norm residual test against
+// psi = 1 would be the wrong filter: the guess's small-scale error dominates its max |H| (the
+// Laplacian weighs a mode by k^2) although the first smoothing sweeps remove it.
+mg_status warm_start(mg_ctx *x, int *state, long long *launches)
+{
+    CKS(warm_infer(x, launches));
+    CKS(run_start(x, launches));
+    if (std::isfinite(max_norm(*x->host_scal))) {
+        *state = 1;
+        x->guess_set = true;
+        return MG_OK;
+    }
+    *state = 2;
+    CK(cudaMemsetAsync(x->X, 0, 4 * x->N * sizeof(double), x->stream));
+    return MG_OK;
+}
+
+void warm_drop(mg_ctx *x)
+{
+    if (x->warm_graph) cudaGraphExecDestroy(x->warm_graph);
+    x->warm_graph = nullptr;
+    x->launches_warm = 0;
+    if (x->warm && x->warm_owned) {
+        cudaStreamSynchronize(x->stream);
+        warm_free(x->warm);
+    }
+    x->warm = nullptr;
+    x->warm_owned = false;
 }
 
 mg_status copy_in(double *dst, const double *src, size_t n, int on_device, cudaStream_t st)
@@ -409,6 +516,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
                 g.hf[a] = (float)g.h[a];
             }
             g.reflect = cfg->bc == MG_BC_ROBIN ? cfg->reflect : 0;
+            g.extrap = cfg->bc == MG_BC_ROBIN ? cfg->extrap : 0;
             g.npunct = cfg->npunct;
             for (int p = 0; p < cfg->npunct; ++p) {
                 g.pm[p] = cfg->punct_m[p];
@@ -473,7 +581,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         if (cfg->bc == MG_BC_ROBIN) {
             double *rt = (double *)(b + lay.RT);
             const size_t M = (size_t)(cfg->n[0] + 4) * (cfg->n[1] + 4) * (cfg->n[2] + 4);
-            if (cfg->reflect)
+            if (cfg->reflect || cfg->extrap)
                 k_fill_robin_table<BC_SYM><<<grid_for(M), kThreads, 0, x->stream>>>(x->lev[0].geo, rt);
             else
                 k_fill_robin_table<BC_ROBIN><<<grid_for(M), kThreads, 0, x->stream>>>(x->lev[0].geo, rt);
@@ -497,7 +605,9 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         }
         if (x->dense && x->nlev >= 2) {
             const LevelBufs &L1 = x->lev[x->nlev - 2], &Lc = x->lev[x->nlev - 1];
-            x->fused = cfg->smoother == 0 && L1.N <= (size_t)kFusedMaxCells &&
+            // extrapolating faces take the unfused path (the fused cycle's ghost table holds one
+            // scaled cell per ghost; an extrapolated ghost needs two)
+            x->fused = cfg->smoother == 0 && cfg->extrap == 0 && L1.N <= (size_t)kFusedMaxCells &&
                        fused_smem_bytes((int)L1.N, (int)Lc.N, x->tbytes,
                                         fused_ratio_cells(L1.geo, cfg->bc == MG_BC_ROBIN)) <= kMaxCoarseSmem;
         }
@@ -582,8 +692,12 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
     NvtxRange solve_range(x->child ? "mg_solve (nested)" : "mg_solve");
     x->history.clear();
     long long launches = 0;
-    int nested_iters = 0;
+    int nested_iters = 0, warm_state = 0;
     CK(cudaEventRecord(x->ev0, x->stream));
+    if (x->warm && !x->guess_set && warm_supported(x->warm, x)) {
+        NvtxRange warm_range("learned warm start");
+        CKS(warm_start(x, &warm_state, &launches));
+    }
     if (x->child && !x->guess_set) {
         NvtxRange nested_range("nested start: half-size solve + tricubic interpolation");
         // nested start: solve the half-size problem from zero (nesting in turn), interpolate its solution
@@ -598,7 +712,7 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
             const dim3 nb = prolong_cubic_grid(c->lev[0].geo);
             if (x->cfg.bc == MG_BC_PERIODIC)
                 k_prolong_cubic<BC_PERIODIC><<<nb, 256, 0, x->stream>>>(c->lev[0].geo, x->lev[0].geo, c->X, x->X);
-            else if (x->cfg.reflect)
+            else if (x->cfg.reflect || x->cfg.extrap)
                 k_prolong_cubic<BC_SYM><<<nb, 256, 0, x->stream>>>(c->lev[0].geo, x->lev[0].geo, c->X, x->X);
             else
                 k_prolong_cubic<BC_ROBIN><<<nb, 256, 0, x->stream>>>(c->lev[0].geo, x->lev[0].geo, c->X, x->X);
@@ -608,14 +722,7 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
         nested_iters = ci.outer_iters;
     }
     x->guess_set = false;
-    if (x->cfg.use_graph) {
-        if (!x->graph_start) CKS(capture(x, start_any, &x->graph_start, &x->launches_start));
-        CK(cudaGraphLaunch(x->graph_start, x->stream));
-        launches += x->launches_start;
-    } else {
-        CKS(start_any(x));
-    }
-    CK(cudaStreamSynchronize(x->stream));
+    if (warm_state != 1) CKS(run_start(x, &launches));   // an accepted warm start has evaluated it
     mg_status result = MG_ERR_NOT_CONVERGED;
     int it = 0, grow = 0;
     double prev = INFINITY;
@@ -630,8 +737,10 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
         }
         if (s.err) { result = fail(MG_ERR_TIMEOUT, "a bounded device wait gave up (spin_limit)"); break; }
         if (!finite || !std::isfinite(s.K2)) { result = fail(MG_ERR_DIVERGED, "constraint norm is not finite"); break; }
-        if (mx <= x->cfg.tol) { result = MG_OK; break; }
-        grow = mx > prev ? grow + 1 : 0;
+        if (mx <= x->cfg.tol && fields_settled(x->cfg, s, it)) { result = MG_OK; break; }
+        // growth counts only above tol: below it (the per-field test still waiting) the norm sits
+        // at its rounding floor and may wobble
+        grow = (mx > prev && mx > x->cfg.tol) ? grow + 1 : 0;
         if (grow >= 3) { result = fail(MG_ERR_DIVERGED, "constraint norm grew for 3 outer iterations"); break; }
         prev = mx;
         if (it >= x->cfg.max_outer) { result = fail(MG_ERR_NOT_CONVERGED, "max_outer reached"); break; }
@@ -648,8 +757,26 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
     }
     CK(cudaEventRecord(x->ev1, x->stream));
     CK(cudaEventSynchronize(x->ev1));
+    if (warm_state == 1 && (result == MG_ERR_NOT_CONVERGED || result == MG_ERR_DIVERGED)) {
+        // the multigrid judges the learned start: it failed, so solve again from psi = 1
+        float first = 0.f;
+        cudaEventElapsedTime(&first, x->ev0, x->ev1);
+        ctt::WarmNet *w = x->warm;
+        x->warm = nullptr;
+        CK(cudaMemsetAsync(x->X, 0, 4 * x->N * sizeof(double), x->stream));
+        x->guess_set = false;   // the context's own cold start (psi = 1, or its nested start)
+        mg_status again = mg_solve_impl(x, info);
+        x->warm = w;
+        if (info) {
+            info->warm_start = 3;
+            info->device_ms += first;
+            if (info->kernel_launches) info->kernel_launches += launches;
+        }
+        return again;
+    }
     if (info) {
         const Scalars &s = *x->host_scal;
+        info->warm_start = warm_state;
         info->outer_iters = it;
         info->converged = result == MG_OK;
         info->K2 = s.K2;
@@ -663,6 +790,7 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
         info->device_ms = ms;
         info->kernel_launches = x->cfg.use_graph ? launches : 0;
         info->nested_iters = nested_iters;
+        fill_rel_change(x->cfg, s, it, info->rel_change);
     }
     return result;
 }
@@ -795,6 +923,40 @@ mg_status mg_get_solution(mg_ctx *x, double *u, double *W, double *K, int on_dev
     MG_WRAP(mg_get_solution_impl(x, u, W, K, on_device));
 }
 mg_status mg_residual_norms(mg_ctx *x, double out[4]) { MG_WRAP(mg_residual_norms_impl(x, out)); }
+static mg_status mg_warmstart_load_impl(mg_ctx *x, const char *path)
+{
+    warm_drop(x);
+    if (!path) return MG_OK;
+    ctt::WarmNet *w = nullptr;
+    CKS(warm_load(path, x->stream, &w));
+    if (!warm_supported(w, x)) {
+        warm_free(w);
+        return fail(MG_ERR_UNSUPPORTED, "the learned warm start serves periodic cubes whose side is the network's "
+                                        "size times a power of two");
+    }
+    x->warm = w;
+    x->warm_owned = true;
+    return MG_OK;
+}
+
+static mg_status mg_warmstart_predict_impl(mg_ctx *x, double *u, double *W, int on_device)
+{
+    if (!x->warm) return fail(MG_ERR_STATE, "no warm start loaded (mg_warmstart_load)");
+    if (!x->have_sources) return fail(MG_ERR_STATE, "mg_set_sources must come before mg_warmstart_predict");
+    long long launches = 0;
+    CKS(warm_infer(x, &launches));
+    x->guess_set = true;
+    CKS(copy_out(u, x->X, x->N, on_device, x->stream));
+    CKS(copy_out(W, x->X + x->N, 3 * x->N, on_device, x->stream));
+    CK(cudaStreamSynchronize(x->stream));
+    return MG_OK;
+}
+
+mg_status mg_warmstart_load(mg_ctx *x, const char *path) { MG_WRAP(mg_warmstart_load_impl(x, path)); }
+mg_status mg_warmstart_predict(mg_ctx *x, double *u, double *W, int on_device)
+{
+    MG_WRAP(mg_warmstart_predict_impl(x, u, W, on_device));
+}
 mg_status mg_checkpoint_save(mg_ctx *x, const char *path) { MG_WRAP(mg_checkpoint_save_impl(x, path)); }
 mg_status mg_checkpoint_load(mg_ctx *x, const char *path) { MG_WRAP(mg_checkpoint_load_impl(x, path)); }
 mg_status mg_constraint_fields(mg_ctx *x, double *H, double *M, int on_device)
@@ -810,6 +972,7 @@ void mg_destroy(mg_ctx *x)
 {
     if (!x) return;
     if (x->child) mg_destroy(x->child);
+    warm_drop(x);
     if (x->graph_exec) cudaGraphExecDestroy(x->graph_exec);
     if (x->graph_start) cudaGraphExecDestroy(x->graph_start);
     if (x->ev0) cudaEventDestroy(x->ev0);
@@ -860,6 +1023,14 @@ struct mg_batch {
     std::vector<cudaEvent_t> ev_join, ev_round;
     cudaGraphExec_t graph_start = nullptr, graph_iter = nullptr;
     long long launches_start = 0, launches_iter = 0;
+    ctt::WarmNet *warm = nullptr;   // learned warm start shared by the instances it serves
+    // device-paced rounds: the whole solve as one graph (mg_batch.cuh)
+    cudaGraphExec_t graph_all = nullptr;
+    void *ctl_mem = nullptr;
+    ctt::BatchCtlArgs ctl{};
+    int ctl_maxr = -1;
+    std::vector<long long> kernels_iter;
+    long long kernels_start = 0;
 };
 
 namespace {
@@ -933,7 +1104,10 @@ void mg_batch_destroy(mg_batch *bt)
     if (bt->stream) cudaStreamSynchronize(bt->stream);
     if (bt->graph_start) cudaGraphExecDestroy(bt->graph_start);
     if (bt->graph_iter) cudaGraphExecDestroy(bt->graph_iter);
+    if (bt->graph_all) cudaGraphExecDestroy(bt->graph_all);
+    if (bt->ctl_mem) cudaFree(bt->ctl_mem);
     for (mg_ctx *x : bt->ctx) mg_destroy(x);
+    warm_free(bt->warm);
     for (auto e : bt->ev_join) cudaEventDestroy(e);
     for (auto e : bt->ev_round) cudaEventDestroy(e);
     if (bt->ev_fork) cudaEventDestroy(bt->ev_fork);
@@ -997,6 +1171,309 @@ mg_status mg_batch_get_solution(mg_batch *bt, int b, double *u, double *W, doubl
     return mg_get_solution(bt->ctx[b], u, W, K, on_device);
 }
 
+mg_status mg_batch_warmstart_load(mg_batch *bt, const char *path)
+{
+    if (!bt) return fail(MG_ERR_INVALID_ARG, "null batch");
+    CKS(batch_enter(bt));
+    mg_status st = MG_OK;
+    for (mg_ctx *x : bt->ctx) warm_drop(x);
+    cudaStreamSynchronize(bt->stream);
+    warm_free(bt->warm);
+    bt->warm = nullptr;
+    if (path) {
+        st = warm_load(path, bt->stream, &bt->warm);
+        if (st == MG_OK)
+            for (mg_ctx *x : bt->ctx)
+                if (warm_supported(bt->warm, x)) x->warm = bt->warm;   // shared, not owned
+    }
+    return batch_leave(bt, st);
+}
+
+}  // extern "C"
+
+namespace {
+
+// What the rounds of a batched solve leave behind, per instance.
+struct BatchOutcome {
+    std::vector<int> conv;        // round at which the instance met its tolerance, -1 if it did not
+    std::vector<int> rounds;      // outer iterations it made
+    std::vector<char> bad;        // a norm became non-finite
+    std::vector<float> conv_ms;   // time from the start of the solve to its convergence
+    std::vector<std::vector<double>> hist;   // 4 norms per recorded round
+    std::vector<long long> launches;
+    float total_ms = 0.f;
+    bool timeout = false;
+};
+
+// Host-paced rounds (use_graph == 2): one graph per round for all instances, read back and
+// checked on the host after every round; converged instances keep iterating in lock step.
+mg_status batch_rounds_host(mg_batch *bt, int max_outer, BatchOutcome &o)
+{
+    const int nb = (int)bt->ctx.size();
+    while ((int)bt->ev_round.size() < max_outer + 1) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(MG_ERR_CUDA, "event creation");
+        bt->ev_round.push_back(e);
+    }
+    if (!bt->graph_start) CKS(capture_batch(bt, start_any, &bt->graph_start, &bt->launches_start));
+    if (!bt->graph_iter) CKS(capture_batch(bt, iteration_any, &bt->graph_iter, &bt->launches_iter));
+    cudaEvent_t t0 = bt->ev_round[0];
+    if (cudaEventRecord(t0, bt->stream) != cudaSuccess || cudaGraphLaunch(bt->graph_start, bt->stream) != cudaSuccess ||
+        cudaStreamSynchronize(bt->stream) != cudaSuccess)
+        return fail(MG_ERR_CUDA, "batch start");
+    int round = 0, done = 0;
+    for (;;) {
+        float ms = 0.f;
+        if (round > 0) cudaEventElapsedTime(&ms, t0, bt->ev_round[round]);
+        for (int b = 0; b < nb; ++b) {
+            mg_ctx *x = bt->ctx[b];
+            const Scalars &s = *x->host_scal;
+            double mx = 0.0;
+            bool finite = std::isfinite(s.K2);
+            const bool live = o.conv[b] < 0 && !o.bad[b];   // still iterating: its row is recorded
+            for (int a = 0; a < 4; ++a) {
+                if (live) o.hist[b].push_back(s.norms[a]);
+                finite = finite && std::isfinite(s.norms[a]);
+                mx = std::max(mx, s.norms[a]);
+            }
+            if (o.conv[b] < 0 && !o.bad[b] && !finite) {
+                o.bad[b] = 1;
+                o.rounds[b] = round;
+                ++done;
+            }
+            if (o.conv[b] < 0 && !o.bad[b] && mx <= x->cfg.tol && fields_settled(x->cfg, s, round)) {
+                o.conv[b] = round;
+                o.conv_ms[b] = ms;
+                o.rounds[b] = round;
+                ++done;
+            }
+        }
+        for (int b = 0; b < nb; ++b) o.timeout = o.timeout || bt->ctx[b]->host_scal->err != 0;
+        if (o.timeout || done == nb || round >= max_outer) break;
+        if (cudaGraphLaunch(bt->graph_iter, bt->stream) != cudaSuccess ||
+            cudaEventRecord(bt->ev_round[round + 1], bt->stream) != cudaSuccess ||
+            cudaStreamSynchronize(bt->stream) != cudaSuccess)
+            return fail(MG_ERR_CUDA, "batch iteration");
+        ++round;
+    }
+    cudaEventElapsedTime(&o.total_ms, t0, bt->ev_round[round]);
+    for (int b = 0; b < nb; ++b) {
+        if (o.conv[b] < 0 && !o.bad[b]) o.rounds[b] = round;
+        o.launches[b] = (bt->launches_start + (long long)round * bt->launches_iter) / nb;
+    }
+    return MG_OK;
+}
+
+long long count_kernels(cudaGraph_t g)
+{
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    cudaGraphGetNodes(g, nodes.data(), &n);
+    long long k = 0;
+    for (auto &nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
+// The device-paced graph of the batch (built once per batch and round limit; see mg_batch.cuh).
+mg_status build_device_graph(mg_batch *bt, int maxr)
+{
+    const int nb = (int)bt->ctx.size();
+    if (bt->graph_all) {
+        cudaGraphExecDestroy(bt->graph_all);
+        bt->graph_all = nullptr;
+    }
+    if (bt->ctl_mem) {
+        cudaFree(bt->ctl_mem);
+        bt->ctl_mem = nullptr;
+    }
+    // control block: BatchCtl, scal pointers, tol, ftol, maxo, conv, bad, tconv, handles, history
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    const size_t oc = take(sizeof(BatchCtl)), os = take(nb * sizeof(Scalars *)), ot = take(nb * 8),
+                 of = take(nb * 8), om = take(nb * 4), ov = take(nb * 4), ob = take(nb * 4), oT = take(nb * 8),
+                 oh = take(nb * sizeof(cudaGraphConditionalHandle)), oH = take((size_t)(maxr + 1) * nb * 4 * 8);
+    CK(cudaMalloc(&bt->ctl_mem, off));
+    char *m = (char *)bt->ctl_mem;
+    BatchCtlArgs &a = bt->ctl;
+    a.c = (BatchCtl *)(m + oc);
+    a.scal = (Scalars *const *)(m + os);
+    a.tol = (const double *)(m + ot);
+    a.ftol = (const double *)(m + of);
+    a.maxo = (const int *)(m + om);
+    a.conv = (int *)(m + ov);
+    a.bad = (int *)(m + ob);
+    a.tconv = (unsigned long long *)(m + oT);
+    a.h = (const cudaGraphConditionalHandle *)(m + oh);
+    a.hist = (double *)(m + oH);
+    a.nb = nb;
+    a.maxr = maxr;
+    bt->ctl_maxr = maxr;
+    std::vector<Scalars *> sp(nb);
+    std::vector<double> tl(nb), ft(nb);
+    std::vector<int> mo(nb);
+    for (int b = 0; b < nb; ++b) {
+        sp[b] = bt->ctx[b]->scal;
+        tl[b] = bt->ctx[b]->cfg.tol;
+        ft[b] = bt->ctx[b]->cfg.field_tol;
+        mo[b] = bt->ctx[b]->cfg.max_outer;
+    }
+    cudaGraph_t G = nullptr;
+    CK(cudaGraphCreate(&G, 0));
+    std::vector<cudaGraphConditionalHandle> h(nb);
+    cudaError_t e = cudaGraphConditionalHandleCreate(&a.hw, G, 0, 0);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaGraphConditionalHandleCreate(&h[b], G, 0, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(m + os, sp.data(), nb * sizeof(Scalars *), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m + ot, tl.data(), nb * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m + of, ft.data(), nb * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m + om, mo.data(), nb * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m + oh, h.data(), nb * sizeof(cudaGraphConditionalHandle), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(G);
+        return fail(MG_ERR_CUDA, std::string("batch control set-up: ") + cudaGetErrorString(e));
+    }
+    mg_status st = MG_OK;
+    cudaGraph_t cap = nullptr;
+    for (mg_ctx *x : bt->ctx) x->device_paced = true;
+    // the starts of all instances and the first control step, then the WHILE node after them
+    e = cudaStreamBeginCaptureToGraph(bt->stream, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        k_batch_begin<<<1, 256, 0, bt->stream>>>(a);
+        e = cudaEventRecord(bt->ev_fork, bt->stream);
+        for (int b = 0; b < nb && st == MG_OK && e == cudaSuccess; ++b) {
+            mg_ctx *x = bt->ctx[b];
+            e = cudaStreamWaitEvent(x->stream, bt->ev_fork, 0);
+            if (e == cudaSuccess) st = start_any(x);
+            if (st == MG_OK && e == cudaSuccess) e = cudaEventRecord(bt->ev_join[b], x->stream);
+            if (st == MG_OK && e == cudaSuccess) e = cudaStreamWaitEvent(bt->stream, bt->ev_join[b], 0);
+        }
+        if (st == MG_OK && e == cudaSuccess) {
+            k_batch_control<<<1, 256, 0, bt->stream>>>(a);
+            e = cudaGetLastError();
+        }
+        cudaGraphNode_t wnode = nullptr;
+        cudaGraph_t body = nullptr;
+        if (st == MG_OK && e == cudaSuccess) {
+            cudaStreamCaptureStatus cs;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t ndeps = 0;
+            e = cudaStreamGetCaptureInfo(bt->stream, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+            cudaGraphNodeParams wp = {};
+            wp.type = cudaGraphNodeTypeConditional;
+            wp.conditional.handle = a.hw;
+            wp.conditional.type = cudaGraphCondTypeWhile;
+            wp.conditional.size = 1;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, G, deps, nullptr, ndeps, &wp);
+            if (e == cudaSuccess) {
+                body = wp.conditional.phGraph_out[0];
+                e = cudaStreamUpdateCaptureDependencies(bt->stream, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+            }
+        }
+        cudaError_t e2 = cudaStreamEndCapture(bt->stream, &cap);
+        if (e == cudaSuccess) e = e2;
+        // the loop body: one IF node per instance (its outer iteration), then the control step
+        std::vector<cudaGraphNode_t> ifs(nb);
+        bt->kernels_iter.assign(nb, 0);
+        for (int b = 0; b < nb && st == MG_OK && e == cudaSuccess; ++b) {
+            mg_ctx *x = bt->ctx[b];
+            cudaGraphNodeParams ip = {};
+            ip.type = cudaGraphNodeTypeConditional;
+            ip.conditional.handle = h[b];
+            ip.conditional.type = cudaGraphCondTypeIf;
+            ip.conditional.size = 1;
+            e = cudaGraphAddNode(&ifs[b], body, nullptr, nullptr, 0, &ip);
+            if (e != cudaSuccess) break;
+            cudaGraph_t ib = ip.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(x->stream, ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) break;
+            st = iteration_any(x);
+            cudaGraph_t tmp = nullptr;
+            e2 = cudaStreamEndCapture(x->stream, &tmp);
+            if (e == cudaSuccess) e = e2;
+            bt->kernels_iter[b] = count_kernels(ib);
+        }
+        if (st == MG_OK && e == cudaSuccess) {
+            e = cudaStreamBeginCaptureToGraph(bt->stream, body, ifs.data(), nullptr, nb, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                k_batch_control<<<1, 256, 0, bt->stream>>>(a);
+                cudaGraph_t tmp = nullptr;
+                e2 = cudaStreamEndCapture(bt->stream, &tmp);
+                e = cudaGetLastError() != cudaSuccess ? cudaErrorLaunchFailure : e2;
+            }
+        }
+        if (st == MG_OK && e == cudaSuccess) bt->kernels_start = count_kernels(G) - 1;   // less the first control step
+    }
+    for (mg_ctx *x : bt->ctx) x->device_paced = false;
+    if (st == MG_OK && e == cudaSuccess) e = cudaGraphInstantiate(&bt->graph_all, G, 0);
+    cudaGraphDestroy(G);
+    if (st != MG_OK) return st;
+    if (e != cudaSuccess) {
+        bt->graph_all = nullptr;
+        return fail(MG_ERR_CUDA, std::string("device-paced batch graph: ") + cudaGetErrorString(e));
+    }
+    return MG_OK;
+}
+
+// Device-paced rounds (default): the whole solve is one graph launch and one synchronisation.
+mg_status batch_rounds_device(mg_batch *bt, int max_outer, BatchOutcome &o)
+{
+    const int nb = (int)bt->ctx.size();
+    if (!bt->graph_all || bt->ctl_maxr != max_outer) CKS(build_device_graph(bt, max_outer));
+    if (bt->ev_round.empty()) {
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            return fail(MG_ERR_CUDA, "event creation");
+        bt->ev_round.push_back(e0);
+        bt->ev_round.push_back(e1);
+    }
+    CK(cudaEventRecord(bt->ev_round[0], bt->stream));
+    CK(cudaGraphLaunch(bt->graph_all, bt->stream));
+    CK(cudaEventRecord(bt->ev_round[1], bt->stream));
+    CK(cudaStreamSynchronize(bt->stream));
+    CK(cudaEventElapsedTime(&o.total_ms, bt->ev_round[0], bt->ev_round[1]));
+    BatchCtl c;
+    std::vector<int> conv(nb), bad(nb);
+    std::vector<unsigned long long> tconv(nb);
+    CK(cudaMemcpy(&c, bt->ctl.c, sizeof(c), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(conv.data(), bt->ctl.conv, nb * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(bad.data(), bt->ctl.bad, nb * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tconv.data(), bt->ctl.tconv, nb * 8, cudaMemcpyDeviceToHost));
+    const int recorded = std::min(c.round, max_outer + 1);   // rounds 0 .. recorded - 1
+    std::vector<double> hist((size_t)recorded * nb * 4);
+    CK(cudaMemcpy(hist.data(), bt->ctl.hist, hist.size() * 8, cudaMemcpyDeviceToHost));
+    o.timeout = c.timeout != 0;
+    for (int b = 0; b < nb; ++b) {
+        mg_ctx *x = bt->ctx[b];
+        CK(cudaMemcpy(x->host_scal, x->scal, sizeof(Scalars), cudaMemcpyDeviceToHost));
+        o.conv[b] = conv[b];
+        o.bad[b] = (char)bad[b];
+        // the last round in which the instance was still iterating (or the one it stopped at)
+        int last = recorded - 1;
+        if (conv[b] >= 0) last = conv[b];
+        else last = std::min(last, x->cfg.max_outer);
+        if (bad[b]) {   // the first round recorded with a non-finite norm
+            for (int r = 0; r < recorded; ++r) {
+                bool fin = true;
+                for (int k = 0; k < 4; ++k) fin = fin && std::isfinite(hist[((size_t)r * nb + b) * 4 + k]);
+                if (!fin) { last = r; break; }
+            }
+        }
+        o.rounds[b] = last;
+        for (int r = 0; r <= last && r < recorded; ++r)
+            for (int k = 0; k < 4; ++k) o.hist[b].push_back(hist[((size_t)r * nb + b) * 4 + k]);
+        o.conv_ms[b] = conv[b] >= 0 ? (float)((double)(tconv[b] - c.t0) * 1e-6) : o.total_ms;
+        o.launches[b] = (bt->kernels_start / nb) + (long long)last * (bt->kernels_iter[b] + 1);
+    }
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms)
 {
     if (!bt) return fail(MG_ERR_INVALID_ARG, "null batch");
@@ -1006,93 +1483,87 @@ mg_status mg_batch_solve(mg_batch *bt, mg_solve_info *infos, double *total_ms)
         if (!x->have_sources) return fail(MG_ERR_STATE, "every instance needs mg_batch_set_sources first");
     CKS(batch_enter(bt));
     mg_status result = MG_OK;
-    do {
-        int max_outer = 0;
-        for (mg_ctx *x : bt->ctx) {
-            x->history.clear();
-            max_outer = std::max(max_outer, x->cfg.max_outer);
+    std::vector<int> warm_state(nb, 0);
+    for (int b = 0; b < nb && result == MG_OK; ++b) {   // learned starts, each judged by its residual
+        mg_ctx *x = bt->ctx[b];
+        long long dummy = 0;
+        if (x->warm && !x->guess_set) {
+            NvtxRange warm_range("learned warm start");
+            result = warm_start(x, &warm_state[b], &dummy);
         }
-        while ((int)bt->ev_round.size() < max_outer + 1) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) { result = fail(MG_ERR_CUDA, "event creation"); break; }
-            bt->ev_round.push_back(e);
+    }
+    BatchOutcome o;
+    o.conv.assign(nb, -1);
+    o.rounds.assign(nb, 0);
+    o.bad.assign(nb, 0);
+    o.conv_ms.assign(nb, 0.f);
+    o.hist.assign(nb, {});
+    o.launches.assign(nb, 0);
+    int max_outer = 0;
+    for (mg_ctx *x : bt->ctx) max_outer = std::max(max_outer, x->cfg.max_outer);
+    if (result == MG_OK)
+        result = bt->ctx[0]->cfg.use_graph == 2 ? batch_rounds_host(bt, max_outer, o) : batch_rounds_device(bt, max_outer, o);
+    if (result == MG_OK) {
+        int nconv = 0, nbad = 0;
+        for (int b = 0; b < nb; ++b) {
+            nconv += o.conv[b] >= 0;
+            nbad += o.bad[b] != 0;
         }
-        if (result != MG_OK) break;
-        if (!bt->graph_start &&
-            (result = capture_batch(bt, start_any, &bt->graph_start, &bt->launches_start)) != MG_OK)
-            break;
-        if (!bt->graph_iter && (result = capture_batch(bt, iteration_any, &bt->graph_iter, &bt->launches_iter)) != MG_OK)
-            break;
-        cudaEvent_t t0 = bt->ev_round[0];
-        if (cudaEventRecord(t0, bt->stream) != cudaSuccess || cudaGraphLaunch(bt->graph_start, bt->stream) != cudaSuccess ||
-            cudaStreamSynchronize(bt->stream) != cudaSuccess) {
-            result = fail(MG_ERR_CUDA, "batch start");
-            break;
+        if (o.timeout) result = fail(MG_ERR_TIMEOUT, "a bounded device wait gave up (spin_limit)");
+        else if (nbad) result = fail(MG_ERR_DIVERGED, "a batch instance's norm is not finite");
+        else if (nconv < nb) result = fail(MG_ERR_NOT_CONVERGED, "max_outer reached in the batch");
+        if (total_ms) *total_ms = o.total_ms;
+        for (int b = 0; b < nb; ++b) {
+            mg_ctx *x = bt->ctx[b];
+            x->history = o.hist[b];
+            x->guess_set = false;
+            if (!infos) continue;
+            const Scalars &s = *x->host_scal;
+            mg_solve_info &in = infos[b];
+            in.outer_iters = o.rounds[b];
+            in.converged = o.conv[b] >= 0;
+            in.K2 = s.K2;
+            in.K = -std::sqrt(std::max(0.0, s.K2));
+            for (int a = 0; a < 4; ++a) in.norms[a] = s.norms[a];
+            for (int a = 0; a < 3; ++a) in.mom_mean[a] = s.msrc[a];
+            in.history = x->history.data();
+            in.history_len = (int)(x->history.size() / 4);
+            in.device_ms = o.conv[b] >= 0 ? o.conv_ms[b] : o.total_ms;
+            in.kernel_launches = o.launches[b];
+            in.nested_iters = 0;
+            in.warm_start = warm_state[b];
+            fill_rel_change(x->cfg, s, o.rounds[b], in.rel_change);
         }
-        std::vector<int> conv_round(nb, -1);
-        std::vector<float> conv_ms(nb, 0.f);
-        std::vector<char> bad(nb, 0);   // a norm became non-finite: the instance is abandoned
-        int round = 0, done = 0, nbad = 0;
-        for (;;) {
-            float ms = 0.f;
-            if (round > 0) cudaEventElapsedTime(&ms, t0, bt->ev_round[round]);
-            for (int b = 0; b < nb; ++b) {
-                mg_ctx *x = bt->ctx[b];
-                const Scalars &s = *x->host_scal;
-                double mx = 0.0;
-                bool finite = std::isfinite(s.K2);
-                for (int a = 0; a < 4; ++a) {
-                    x->history.push_back(s.norms[a]);
-                    finite = finite && std::isfinite(s.norms[a]);
-                    mx = std::max(mx, s.norms[a]);
-                }
-                if (conv_round[b] < 0 && !bad[b] && !finite) {
-                    bad[b] = 1;
-                    ++nbad;
-                }
-                if (conv_round[b] < 0 && !bad[b] && mx <= x->cfg.tol) {
-                    conv_round[b] = round;
-                    conv_ms[b] = ms;
-                    ++done;
-                }
-            }
-            bool timeout = false;
-            for (int b = 0; b < nb; ++b) timeout = timeout || bt->ctx[b]->host_scal->err != 0;
-            if (timeout) { result = fail(MG_ERR_TIMEOUT, "a bounded device wait gave up (spin_limit)"); break; }
-            if (done + nbad == nb) {
-                if (nbad) result = fail(MG_ERR_DIVERGED, "a batch instance's norm is not finite");
+        // the multigrid judges the learned starts: an instance that failed from its warm start is
+        // solved again, alone, from its cold start
+        for (int b = 0; b < nb && (result == MG_ERR_NOT_CONVERGED || result == MG_ERR_DIVERGED); ++b) {
+            if (warm_state[b] != 1 || o.conv[b] >= 0) continue;
+            mg_ctx *x = bt->ctx[b];
+            mg_solve_info again{};
+            ctt::WarmNet *w = x->warm;
+            x->warm = nullptr;
+            mg_status sb = mg_set_initial_guess(x, nullptr, nullptr, 1);
+            if (sb == MG_OK) sb = mg_solve_impl(x, &again);
+            x->warm = w;
+            if (sb != MG_OK && sb != MG_ERR_NOT_CONVERGED && sb != MG_ERR_DIVERGED) {
+                result = sb;
                 break;
             }
-            if (round >= max_outer) { result = fail(MG_ERR_NOT_CONVERGED, "max_outer reached in the batch"); break; }
-            if (cudaGraphLaunch(bt->graph_iter, bt->stream) != cudaSuccess ||
-                cudaEventRecord(bt->ev_round[round + 1], bt->stream) != cudaSuccess ||
-                cudaStreamSynchronize(bt->stream) != cudaSuccess) {
-                result = fail(MG_ERR_CUDA, "batch iteration");
-                break;
+            if (infos) {
+                again.warm_start = 3;
+                again.device_ms += o.total_ms;
+                infos[b] = again;
             }
-            ++round;
+            if (total_ms) *total_ms += again.device_ms - o.total_ms;
+            o.conv[b] = sb == MG_OK ? again.outer_iters : -1;
+            o.bad[b] = sb == MG_ERR_DIVERGED;
         }
-        float total = 0.f;
-        cudaEventElapsedTime(&total, t0, bt->ev_round[round]);
-        if (total_ms) *total_ms = total;
-        if (infos) {
-            for (int b = 0; b < nb; ++b) {
-                mg_ctx *x = bt->ctx[b];
-                const Scalars &s = *x->host_scal;
-                mg_solve_info &in = infos[b];
-                in.outer_iters = conv_round[b] >= 0 ? conv_round[b] : round;
-                in.converged = conv_round[b] >= 0;
-                in.K2 = s.K2;
-                in.K = -std::sqrt(std::max(0.0, s.K2));
-                for (int a = 0; a < 4; ++a) in.norms[a] = s.norms[a];
-                for (int a = 0; a < 3; ++a) in.mom_mean[a] = s.msrc[a];
-                in.history = x->history.data();
-                in.history_len = (int)(x->history.size() / 4);
-                in.device_ms = conv_round[b] >= 0 ? conv_ms[b] : total;
-                in.kernel_launches = (bt->launches_start + (long long)round * bt->launches_iter) / nb;
-            }
+        if (result == MG_ERR_NOT_CONVERGED || result == MG_ERR_DIVERGED) {
+            bool all = true;
+            for (int b = 0; b < nb; ++b) all = all && o.conv[b] >= 0;
+            if (all) result = MG_OK;
         }
-    } while (0);
+    }
     return batch_leave(bt, result);
 }
 

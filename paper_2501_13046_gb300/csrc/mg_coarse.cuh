@@ -48,10 +48,18 @@ __global__ void __launch_bounds__(512) k_dense_psi_assemble(Geo g, Coef<T> cf, c
                     c[ax] -= c[ax] >= g.n[ax] ? g.n[ax] : 0;
                     row[c[0] + g.n[0] * (c[1] + g.n[1] * c[2])] += (C)w;
                 } else {   // psi is even across symmetry planes: mirror, or clamp with the 1/r ratio
-                    int bc[3], mirror;
-                    double ratio = 1.0;
-                    if (bc_cell<BC>(g, c, bc, mirror)) ratio = robin_ratio<double>(g, bc[0], bc[1], bc[2], c[0], c[1], c[2]);
-                    row[bc[0] + g.n[0] * (bc[1] + g.n[1] * bc[2])] += (C)(w * ratio);
+                    auto add = [&](const int q[3], double wq) {
+                        int bc[3], mirror;
+                        double ratio = 1.0;
+                        if (bc_cell<BC>(g, q, bc, mirror)) ratio = robin_ratio<double>(g, bc[0], bc[1], bc[2], q[0], q[1], q[2]);
+                        row[bc[0] + g.n[0] * (bc[1] + g.n[1] * bc[2])] += (C)(wq * ratio);
+                    };
+                    int q[8][3], wx[8], ns = 0;
+                    if constexpr (BC == BC_SYM) ns = g.extrap ? extrap_split(g, c, q, wx) : 0;
+                    if (ns)   // beyond an extrapolating face: the weighted in-box cells
+                        for (int t = 0; t < ns; ++t) add(q[t], w * wx[t]);
+                    else
+                        add(c, w);
                 }
             }
         if (periodic) {
@@ -305,9 +313,13 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
                     const int q = i + g.n[0] * row, qo = q + 1 - 2 * par;   // the pair's other cell
                     T Je[4], ctr[4];
                     apply(cur, i, j, k, cs[q], cs[N + q], Je, ctr);
-                    alt[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * cf.dl + cs[N + q]) * cf.iom);
+                    T dpsi = 0, dW[3] = {0, 0, 0};
+                    if constexpr (BC != BC_PERIODIC)
+                        if (near_face(g, i, j, k)) boundary_diag<T, ORDER, BC>(g, cf.ih2[0], cf.ih2[1], cf.ih2[2], i, j, k, &dpsi, dW);
+                    alt[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * (cf.dl + dpsi) + cs[N + q]) * cf.iom);
                     for (int a = 0; a < 3; ++a)
-                        alt[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
+                        alt[(1 + a) * N + q] =
+                            ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * shifted_idW(cf.idW[a], cf.iom, dW[a]);
                     for (int a = 0; a < 4; ++a) alt[a * N + qo] = cur[a * N + qo];
                 }
                 __syncthreads();

@@ -210,6 +210,17 @@ inline size_t direct_smem_bytes(size_t Nc, int periodic, size_t tb)
 
 }  // namespace ctt
 
+struct mg_ctx;
+namespace ctt {
+// The learned warm start (mg_warmstart.cu).
+struct WarmNet;
+mg_status warm_load(const char *path, cudaStream_t st, WarmNet **out);
+void warm_free(WarmNet *w);
+bool warm_supported(const WarmNet *w, const mg_ctx *x);
+mg_status warm_enqueue(WarmNet *w, mg_ctx *x, cudaStream_t st);
+bool warm_timed_out(WarmNet *w, cudaStream_t st);
+}  // namespace ctt
+
 struct mg_ctx {
     mg_config cfg;
     cudaStream_t user_stream = nullptr;   // the caller's stream (may be the legacy default stream)
@@ -250,6 +261,11 @@ struct mg_ctx {
     std::vector<double> history;
     mg_ctx *child = nullptr;   // half-size problem of the nested start (its workspace is carved from ws)
     bool guess_set = false;    // the caller gave an initial guess since the previous solve
+    ctt::WarmNet *warm = nullptr;           // learned warm start (mg_warmstart_load); a batch's is shared
+    bool warm_owned = false;                // this context frees it
+    cudaGraphExec_t warm_graph = nullptr;   // the inference, captured for this context's buffers
+    long long launches_warm = 0;
+    bool device_paced = false;              // enqueue-time: a batch controller kernel reads the scalars on the device
 };
 
 namespace ctt {

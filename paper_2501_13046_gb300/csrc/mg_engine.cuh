@@ -247,7 +247,8 @@ mg_status enqueue_residual(mg_ctx *x, double *HM)
     k_outer_pass2<T><<<g1, kThreads, 0, x->stream>>>(L0.geo, x->X, x->R, x->SRC, x->scal, (T *)L0.f, (T *)L0.c, HM,
                                                      x->partial, L0.split, 1);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(x->host_scal, x->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, x->stream));
+    // the scalars go to the host, unless a device-side controller reads them (device-paced batch)
+    if (!x->device_paced) CK(cudaMemcpyAsync(x->host_scal, x->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, x->stream));
     return MG_OK;
 }
 
@@ -322,8 +323,11 @@ mg_status enqueue_iteration(mg_ctx *x)
         k_sum4<T><<<g, kThreads, 0, x->stream>>>((const T *)L0.cur(), x->N, x->partial, x->scal->emean,
                                                  &x->scal->ticket[2]);
     }
-    k_update<T><<<grid_for(x->N), kThreads, 0, x->stream>>>(L0.geo, x->X, (const T *)L0.cur(), x->N,
-                                                            periodic ? x->scal->emean : nullptr, L0.split);
+    // the size of the update is reduced only for the per-field stopping test (field_tol > 0)
+    const bool sized = x->cfg.field_tol > 0.0;
+    k_update<T><<<sized ? grid_for(x->N, kRedBlocks) : grid_for(x->N), kThreads, 0, x->stream>>>(
+        L0.geo, x->X, (const T *)L0.cur(), x->N, periodic ? x->scal->emean : nullptr, L0.split, x->partial,
+        sized ? x->scal : nullptr);
     CK(cudaGetLastError());
     return enqueue_residual<T, ORDER, BC>(x, nullptr);
 }

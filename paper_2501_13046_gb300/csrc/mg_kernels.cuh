@@ -34,6 +34,8 @@ struct Geo {
     float lof[3], hf[3];   // lo and h rounded to FP32 (FP32 Robin ratios; set with lo and h)
     int reflect;           // Robin boxes: bit a set = the lower face of axis a (at x_a = 0) is a
                            // reflection-symmetry plane instead of a Robin face
+    int extrap;            // Robin boxes: bit 2a (lower) / 2a + 1 (upper) = that face of axis a is
+                           // extrapolating (linear extrapolation along its normal; see extrap_split)
     int npunct;
     double pm[2];
     double px[2][3];
@@ -147,6 +149,48 @@ __device__ __forceinline__ bool bc_cell(const Geo &g, const int p[3], int b[3], 
     return clamped;
 }
 
+// Extrapolating faces (Robin boxes with symmetry planes and/or extrapolating faces: the BC_SYM
+// variant).  A cell beyond such a face at distance d along its normal takes the linear
+// extrapolation (1 + d) v(b) - d v(b') through the boundary cell b of its line and the next cell
+// b' in; beyond several such faces the rule applies axis by axis (linear maps commute), and
+// bc_cell then resolves any remaining out-of-box coordinate.  Splits p into ns <= 8 cells, inside
+// the box along every extrapolating axis, with integer weights w (sum of w_s v(q_s)); returns 0
+// when p lies beyond no extrapolating face.
+__device__ __forceinline__ int extrap_split(const Geo &g, const int p[3], int q[8][3], int w[8])
+{
+    int ns = 1;
+    q[0][0] = p[0];
+    q[0][1] = p[1];
+    q[0][2] = p[2];
+    w[0] = 1;
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int d = 0, b0 = 0, b1 = 0;
+        if (p[a] < 0 && ((g.extrap >> (2 * a)) & 1)) {
+            d = -p[a];
+            b1 = 1;
+        } else if (p[a] >= g.n[a] && ((g.extrap >> (2 * a + 1)) & 1)) {
+            d = p[a] - (g.n[a] - 1);
+            b0 = g.n[a] - 1;
+            b1 = g.n[a] - 2;
+        }
+        if (d == 0) continue;
+        any = true;
+        for (int s = 0; s < ns; ++s) {
+            q[ns + s][0] = q[s][0];
+            q[ns + s][1] = q[s][1];
+            q[ns + s][2] = q[s][2];
+            q[ns + s][a] = b1;
+            w[ns + s] = -d * w[s];
+            q[s][a] = b0;
+            w[s] *= 1 + d;
+        }
+        ns *= 2;
+    }
+    return any ? ns : 0;
+}
+
 // Sign of field fi (0 = u, 1..3 = W_x..W_z) at a cell mirrored across the planes in `mirror`:
 // the component of W normal to a symmetry plane is odd across it, everything else even.
 __device__ __forceinline__ int bc_sign(int mirror, int fi) { return (fi >= 1 && ((mirror >> (fi - 1)) & 1)) ? -1 : 1; }
@@ -222,15 +266,81 @@ __device__ __forceinline__ T fetch_bc(const T *f, int fi, const Geo &g, int i, i
         k += (k < 0) ? g.n[2] : 0; k -= (k >= g.n[2]) ? g.n[2] : 0;
         return f[i + g.n[0] * (j + g.n[1] * k)];
     } else {
+        auto one = [&](const int p[3]) {
+            int b[3], mirror;
+            const bool clamped = bc_cell<BC>(g, p, b, mirror);
+            const T v = bc_signed<BC>(f[b[0] + g.n[0] * (b[1] + g.n[1] * b[2])], mirror, fi);
+            if (!clamped) return v;
+            if constexpr (std::is_same<T, double>::value) return v * robin_ratio_f64(g, b[0], b[1], b[2], p[0], p[1], p[2]);
+            else return v * robin_ratio<T>(g, b[0], b[1], b[2], p[0], p[1], p[2]);
+        };
         const int p[3] = {i, j, k};
-        int b[3], mirror;
-        const bool clamped = bc_cell<BC>(g, p, b, mirror);
-        const T v = bc_signed<BC>(f[b[0] + g.n[0] * (b[1] + g.n[1] * b[2])], mirror, fi);
-        if (!clamped) return v;
-        if constexpr (std::is_same<T, double>::value) return v * robin_ratio_f64(g, b[0], b[1], b[2], i, j, k);
-        else return v * robin_ratio<T>(g, b[0], b[1], b[2], i, j, k);
+        if constexpr (BC == BC_SYM) {
+            if (g.extrap) {
+                int q[8][3], w[8];
+                const int ns = extrap_split(g, p, q, w);
+                if (ns) {
+                    T s = 0;
+                    for (int t = 0; t < ns; ++t) s += (T)w[t] * one(q[t]);
+                    return s;
+                }
+            }
+        }
+        return one(p);
     }
 }
+
+// Diagonal shifts of the inner operator's rows at a cell next to a Robin face, a symmetry plane or
+// an extrapolating face.  A colour pass divides a row's residual by the row's diagonal; at such a
+// cell some stencil taps lie beyond the box, and their boundary value depends on the cell itself
+// (the 1/r ratio when it is the clamped cell, a mirror image of it, a weight of an extrapolation),
+// so the row's true diagonal is the interior one plus each such tap's weight times that
+// dependence.  dpsi: shift of the Laplacian's diagonal (psi row: a (dl + dpsi) + b); dW[A]: shift
+// of row A's diagonal (Lap W_A + (1/3) D_AA W_A acting on W_A).  ih2: 1/h^2 per axis.  Zero away
+// from the faces; periodic boxes never call it.
+template <typename T, int ORDER, int BC>
+__device__ __noinline__ void boundary_diag(const Geo &g, T ih20, T ih21, T ih22, int i, int j, int k, T *dpsi, T *dW)
+{
+    const T ih2[3] = {ih20, ih21, ih22};
+    const T k1 = ORDER == 2 ? (T)1 : (T)(16.0 / 12.0), k2 = ORDER == 2 ? (T)0 : (T)(-1.0 / 12.0);
+    T sp = 0, sw[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a)
+        for (int s = -2; s <= 2; ++s) {
+            if (s == 0 || (ORDER == 2 && (s == 2 || s == -2))) continue;
+            int c[3] = {i, j, k};
+            c[a] += s;
+            if (c[a] >= 0 && c[a] < g.n[a]) continue;
+            T kap[4] = {0, 0, 0, 0};   // d(boundary value at c) / d(value at the cell), per field
+            auto add = [&](const int q[3], T w) {
+                int b[3], mirror;
+                const bool clamped = bc_cell<BC>(g, q, b, mirror);
+                if (b[0] != i || b[1] != j || b[2] != k) return;
+                if (clamped) w *= robin_ratio<T>(g, b[0], b[1], b[2], q[0], q[1], q[2]);
+                for (int f = 0; f < 4; ++f) kap[f] += (BC == BC_SYM && bc_sign(mirror, f) < 0) ? -w : w;
+            };
+            int q[8][3], w8[8], ns = 0;
+            if constexpr (BC == BC_SYM) ns = g.extrap ? extrap_split(g, c, q, w8) : 0;
+            if (ns)
+                for (int t = 0; t < ns; ++t) add(q[t], (T)w8[t]);
+            else
+                add(c, (T)1);
+            const T w = ((s == 1 || s == -1) ? k1 : k2) * ih2[a];
+            sp += w * kap[0];
+            for (int A = 0; A < 3; ++A) sw[A] += (a == A ? (T)(4.0 / 3.0) : (T)1) * w * kap[1 + A];
+        }
+    *dpsi = sp;
+    for (int A = 0; A < 3; ++A) dW[A] = sw[A];
+}
+
+// Whether a cell is within 2 cells of a face (where boundary_diag may be nonzero).
+__device__ __forceinline__ bool near_face(const Geo &g, int i, int j, int k)
+{
+    return i < 2 || j < 2 || k < 2 || i >= g.n[0] - 2 || j >= g.n[1] - 2 || k >= g.n[2] - 2;
+}
+
+// A row's relaxation factor omega / (m0 + d) from omega / m0 (idW) and 1 / omega (iom).
+template <typename T>
+__device__ __forceinline__ T shifted_idW(T idW, T iom, T d) { return idW / ((T)1 + d * idW * iom); }
 
 // Accessors: value at cell p + (dx, dy, dz) of one field.
 template <typename T>
@@ -381,9 +491,8 @@ struct AccB2 {
     const Geo *g;
     size_t N;
     int i, j, k, c;
-    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
+    __device__ __forceinline__ T one(const int p[3]) const
     {
-        int p[3] = {i + dx, j + dy, k + dz};
         int q[3], mirror;
         const bool outside = bc_cell<BC>(*g, p, q, mirror);
         int c2 = (q[0] + q[1] + q[2]) & 1;
@@ -397,6 +506,22 @@ struct AccB2 {
                 return v * robin_ratio<T>(*g, q[0], q[1], q[2], p[0], p[1], p[2]);
         }
         return v;
+    }
+    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
+    {
+        const int p[3] = {i + dx, j + dy, k + dz};
+        if constexpr (BC == BC_SYM) {
+            if (g->extrap) {
+                int q[8][3], w[8];
+                const int ns = extrap_split(*g, p, q, w);
+                if (ns) {
+                    T s = 0;
+                    for (int t = 0; t < ns; ++t) s += (T)w[t] * one(q[t]);
+                    return s;
+                }
+            }
+        }
+        return one(p);
     }
 };
 
@@ -512,9 +637,13 @@ __device__ __forceinline__ void smooth_cell(const Geo &g, const Coef<T> &cf, con
     T Je[4], ctr[4];
     if (interior) apply_J_split<T, ORDER, BC, true>(X, O, N, g, i, j, k, ca, cb, cf, Je, ctr);
     else apply_J_split<T, ORDER, BC, false>(X, O, N, g, i, j, k, ca, cb, cf, Je, ctr);
-    Y[q] = ctr[0] + (f[q] - Je[0]) / ((ca * cf.dl + cb) * cf.iom);
+    T dpsi = 0, dW[3] = {0, 0, 0};
+    if constexpr (BC != BC_PERIODIC)
+        if (!interior && near_face(g, i, j, k)) boundary_diag<T, ORDER, BC>(g, cf.ih2[0], cf.ih2[1], cf.ih2[2], i, j, k, &dpsi, dW);
+    Y[q] = ctr[0] + (f[q] - Je[0]) / ((ca * (cf.dl + dpsi) + cb) * cf.iom);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (f[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
+    for (int a = 0; a < 3; ++a)
+        Y[(1 + a) * N + q] = ctr[1 + a] + (f[(1 + a) * N + q] - Je[1 + a]) * shifted_idW(cf.idW[a], cf.iom, dW[a]);
 }
 
 // The shell path is a call: only shell blocks execute it, and it leaves the interior path its registers.
@@ -652,11 +781,29 @@ __global__ void __launch_bounds__(256) k_prolong_add(Geo g, Geo gc, const T *__r
         unsigned idx[8];
         T w[8];
         int mir[8];   // symmetry planes crossed to reach parent d (signs per field: bc_sign)
+        // per axis the near parent (weight 3/4) and the far one (1/4); a far parent beyond an
+        // extrapolating face is 2 v(near) - v(next in), which moves its weight onto those two
+        int ia[3][2] = {{I, I + sx}, {J, J + sy}, {K, K + sz}};
+        T wa[3][2] = {{(T)0.75, (T)0.25}, {(T)0.75, (T)0.25}, {(T)0.75, (T)0.25}};
+        if constexpr (BC == BC_SYM) {
+            if (gc.extrap) {
+                const int st[3] = {sx, sy, sz};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int far = ia[a][1];
+                    if ((far < 0 && ((gc.extrap >> (2 * a)) & 1)) || (far >= gc.n[a] && ((gc.extrap >> (2 * a + 1)) & 1))) {
+                        wa[a][0] += 2 * wa[a][1];
+                        wa[a][1] = -wa[a][1];
+                        ia[a][1] = ia[a][0] - st[a];
+                    }
+                }
+            }
+        }
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             const int dx = d & 1, dy = (d >> 1) & 1, dz = d >> 2;
-            const int c[3] = {I + dx * sx, J + dy * sy, K + dz * sz};
-            T wd = (T)((dx ? 0.25 : 0.75) * (dy ? 0.25 : 0.75) * (dz ? 0.25 : 0.75));
+            const int c[3] = {ia[0][dx], ia[1][dy], ia[2][dz]};
+            T wd = wa[0][dx] * wa[1][dy] * wa[2][dz];
             int b[3];
             if (bc_cell<BC>(gc, c, b, mir[d])) wd *= robin_ratio<T>(gc, b[0], b[1], b[2], c[0], c[1], c[2]);
             const unsigned lin = (unsigned)b[0] + (unsigned)ncx * ((unsigned)b[1] + (unsigned)ncy * (unsigned)b[2]);
@@ -765,7 +912,8 @@ struct Scalars {
     double sums[8];
     unsigned int err;         // nonzero: a bounded wait of a pipelined kernel gave up (MG_ERR_TIMEOUT)
     unsigned int nonfinite;   // nonzero: a source value is NaN or infinite (set by k_flag_nonfinite)
-    unsigned int ticket[3];   // last-block counters: pass-B sums, pass-2 norms, means of e (finalize_last)
+    double change[8];         // last update: max |e_a - <e_a>| (a = 0..3), then max |psi|, |W_x|, |W_y|, |W_z| after it
+    unsigned int ticket[4];   // last-block counters: pass-B sums, pass-2 norms, means of e, update maxima
 };
 
 // K^2 (integrability or fixed) and the momentum-source means from the pass-1 sums.
@@ -873,25 +1021,41 @@ __global__ void __launch_bounds__(256) k_sub_mean4(T *__restrict__ x, size_t N, 
 }
 
 // State update u += e - <e>, W_i += e_i - <e_i> (means only on periodic boxes); e is stored in
-// the finest level's layout (colour-split when split != 0).
+// the finest level's layout (colour-split when split != 0).  With s set, the last block also
+// leaves the size of the update in s->change: per field the largest applied correction and the
+// largest |psi|, |W_i| after it (psi = background + u), for the per-field stopping test.
+// Launched on at most kRedBlocks blocks (partial holds 8 values per block).
 template <typename T>
 __global__ void __launch_bounds__(256) k_update(Geo g, double *__restrict__ x, const T *__restrict__ e, size_t N,
-                                                const double *__restrict__ means, int split)
+                                                const double *__restrict__ means, int split,
+                                                double *__restrict__ partial, Scalars *s)
 {
     double m[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) m[a] = means ? means[a] : 0.0;
+    double mx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const unsigned nx = (unsigned)g.n[0], ny = (unsigned)g.n[1];   // grids hold < 2^31 cells
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-        size_t q = p;
-        if (split) {
-            const unsigned pu = (unsigned)p, rest = pu / nx;
-            const unsigned par = (pu - rest * nx) + (rest % ny) + rest / ny;
-            q = ((par & 1) ? N / 2 : 0) + (p >> 1);
-        }
+        const unsigned pu = (unsigned)p, rest = pu / nx;
+        const unsigned i = pu - rest * nx, j = rest % ny, k = rest / ny;
+        const size_t q = split ? (((i + j + k) & 1) ? N / 2 : 0) + (p >> 1) : p;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) x[a * N + p] += (double)e[a * N + q] - m[a];
+        for (int a = 0; a < 4; ++a) {
+            const double d = (double)e[a * N + q] - m[a];
+            const double v = x[a * N + p] + d;
+            x[a * N + p] = v;
+            if (s) {
+                mx[a] = fmax(mx[a], absnan(d));
+                mx[4 + a] = fmax(mx[4 + a], absnan(a == 0 ? psi_bg(g, (int)i, (int)j, (int)k, p) + v : v));
+            }
+        }
     }
+    if (!s) return;
+    double r[8];
+    block_max<8>(mx, r);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 8; ++a) partial[blockIdx.x * 8 + a] = r[a];
+    finalize_last<8, true>(partial, gridDim.x, s->change, &s->ticket[3]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1067,8 +1231,12 @@ __global__ void __launch_bounds__(512) k_coarse_solve(Geo g, Coef<T> cf, const T
                     AccB<T, BC> a0{eA, 0, &g, i, j, k}, a1{eA + N, 1, &g, i, j, k}, a2{eA + 2 * N, 2, &g, i, j, k},
                         a3{eA + 3 * N, 3, &g, i, j, k};
                     apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
-                    eB[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * cf.dl + cs[N + q]) * cf.iom);
-                    for (int a = 0; a < 3; ++a) eB[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * cf.idW[a];
+                    T dpsi = 0, dW[3] = {0, 0, 0};
+                    if constexpr (BC != BC_PERIODIC)
+                        if (near_face(g, i, j, k)) boundary_diag<T, ORDER, BC>(g, cf.ih2[0], cf.ih2[1], cf.ih2[2], i, j, k, &dpsi, dW);
+                    eB[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * (cf.dl + dpsi) + cs[N + q]) * cf.iom);
+                    for (int a = 0; a < 3; ++a)
+                        eB[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * shifted_idW(cf.idW[a], cf.iom, dW[a]);
                 } else {
                     for (int a = 0; a < 4; ++a) eB[a * N + q] = eA[a * N + q];
                 }

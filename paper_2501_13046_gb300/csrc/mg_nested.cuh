@@ -60,17 +60,27 @@ __global__ void __launch_bounds__(256) k_prolong_cubic(Geo gc, Geo g, const doub
         for (int e = t; e < kPhX * kPhY * kPhZ; e += blockDim.x) {
             const int lx = e % kPhX, ly = (e / kPhX) % kPhY, lz = e / (kPhX * kPhY);
             const int p[3] = {I0 - 2 + lx, J0 - 2 + ly, K0 - 2 + lz};
-            int b[3];
-            bool outside = false;
-            int mirror = 0;
-            if (BC == BC_PERIODIC) {
-                for (int a = 0; a < 3; ++a) b[a] = ((p[a] % gc.n[a]) + gc.n[a]) % gc.n[a];
-            } else {   // the halo reaches at most 2 cells below the box, where the mirror applies
-                outside = bc_cell<BC>(gc, p, b, mirror);
-            }
-            double v = src[(size_t)b[0] + (size_t)nc0 * ((size_t)b[1] + (size_t)nc1 * b[2])];
-            v = bc_signed<BC>(v, mirror, f);
-            if (BC != BC_PERIODIC && outside) v *= (double)robin_ratio<float>(gc, b[0], b[1], b[2], p[0], p[1], p[2]);
+            auto one = [&](const int c[3]) {
+                int b[3];
+                bool outside = false;
+                int mirror = 0;
+                if (BC == BC_PERIODIC) {
+                    for (int a = 0; a < 3; ++a) b[a] = ((c[a] % gc.n[a]) + gc.n[a]) % gc.n[a];
+                } else {   // the halo reaches at most 2 cells below the box, where the mirror applies
+                    outside = bc_cell<BC>(gc, c, b, mirror);
+                }
+                double v = src[(size_t)b[0] + (size_t)nc0 * ((size_t)b[1] + (size_t)nc1 * b[2])];
+                v = bc_signed<BC>(v, mirror, f);
+                if (BC != BC_PERIODIC && outside) v *= (double)robin_ratio<float>(gc, b[0], b[1], b[2], c[0], c[1], c[2]);
+                return v;
+            };
+            double v = 0.0;
+            int q[8][3], w[8], ns = 0;
+            if constexpr (BC == BC_SYM) ns = gc.extrap ? extrap_split(gc, p, q, w) : 0;
+            if (ns)
+                for (int s = 0; s < ns; ++s) v += w[s] * one(q[s]);
+            else
+                v = one(p);
             tin[lz][ly][lx] = (float)v;
         }
         __syncthreads();

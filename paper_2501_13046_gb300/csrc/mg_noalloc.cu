@@ -132,6 +132,8 @@ mg_status check_config(const mg_config *c)
             if (c->punct_P[p][a] != 0.0 || c->punct_S[p][a] != 0.0)
                 return fail(MG_ERR_UNSUPPORTED, "Bowen-York punctures are not supported by the allocation-free norms");
     if (c->reflect != 0) return fail(MG_ERR_UNSUPPORTED, "symmetry planes are not supported by the allocation-free norms");
+    if (c->extrap != 0)
+        return fail(MG_ERR_UNSUPPORTED, "extrapolating faces are not supported by the allocation-free norms");
     if (!std::isfinite(c->K)) return fail(MG_ERR_INVALID_ARG, "K not finite");
     // each product is checked before the next one is formed, so no cell count wraps around
     const char *msg = "mg_residual_norms_noalloc: the grid exceeds the static scratch limit of 262144 cells (64^3)";

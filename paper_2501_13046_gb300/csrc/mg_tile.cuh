@@ -130,16 +130,31 @@ __device__ __forceinline__ T tile_fetch(const Geo &g, const T *X, const T *O, in
                                         int f)
 {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int p[3] = {2 * P + ((h + y + z) & 1), y, z};
-    int b[3], mirror;
-    const bool clamped = bc_cell<BC>(g, p, b, mirror);   // wrap; or mirror / clamp (field f's sign)
-    const int hb = (b[0] + b[1] + b[2]) & 1;
     const size_t N = (size_t)nx * ny * nz;
-    const size_t idx = (size_t)f * N + (hb ? N / 2 : 0) + (size_t)(b[0] >> 1) + (size_t)(nx >> 1) * (b[1] + (size_t)ny * b[2]);
-    T v = (hb == colour ? X : O)[idx];
-    v = bc_signed<BC>(v, mirror, f);
-    if (BC != BC_PERIODIC && clamped) v *= robin_ratio<T>(g, b[0], b[1], b[2], p[0], p[1], p[2]);
-    return v;
+    auto one = [&](const int c[3]) {
+        int b[3], mirror;
+        const bool clamped = bc_cell<BC>(g, c, b, mirror);   // wrap; or mirror / clamp (field f's sign)
+        const int hb = (b[0] + b[1] + b[2]) & 1;
+        const size_t idx =
+            (size_t)f * N + (hb ? N / 2 : 0) + (size_t)(b[0] >> 1) + (size_t)(nx >> 1) * (b[1] + (size_t)ny * b[2]);
+        T v = (hb == colour ? X : O)[idx];
+        v = bc_signed<BC>(v, mirror, f);
+        if (BC != BC_PERIODIC && clamped) v *= robin_ratio<T>(g, b[0], b[1], b[2], c[0], c[1], c[2]);
+        return v;
+    };
+    const int p[3] = {2 * P + ((h + y + z) & 1), y, z};
+    if constexpr (BC == BC_SYM) {   // beyond an extrapolating face: the weighted in-box cells
+        if (g.extrap) {
+            int q[8][3], w[8];
+            const int ns = extrap_split(g, p, q, w);
+            if (ns) {
+                T s = 0;
+                for (int t = 0; t < ns; ++t) s += (T)w[t] * one(q[t]);
+                return s;
+            }
+        }
+    }
+    return one(p);
 }
 
 // ---------------------------------------------------------------- the plane ring
@@ -449,9 +464,17 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
             T Je[4], ctr[4];
             if ((COLOUR + y + z) & 1) tile_apply<T, ORDER, COLOUR, 1>(ring.sm, ob, ca, cb, tc, Je, ctr);
             else tile_apply<T, ORDER, COLOUR, 0>(ring.sm, ob, ca, cb, tc, Je, ctr);
-            Y[q] = ctr[0] + (fq[0] - Je[0]) / ((ca * tc.dl + cb) * tc.iom);
+            T dpsi = 0, dW[3] = {0, 0, 0};
+            if constexpr (BC != BC_PERIODIC) {   // the true diagonal next to a face
+                const int x = 2 * (ring.P0 + lane) + ((COLOUR + y + z) & 1);
+                if (near_face(g, x, y, z))
+                    boundary_diag<T, ORDER, BC>(g, (T)(1.0 / (g.h[0] * g.h[0])), (T)(1.0 / (g.h[1] * g.h[1])),
+                                                (T)(1.0 / (g.h[2] * g.h[2])), x, y, z, &dpsi, dW);
+            }
+            Y[q] = ctr[0] + (fq[0] - Je[0]) / ((ca * (tc.dl + dpsi) + cb) * tc.iom);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (fq[1 + a] - Je[1 + a]) * tc.idW[a];
+            for (int a = 0; a < 3; ++a)
+                Y[(1 + a) * N + q] = ctr[1 + a] + (fq[1 + a] - Je[1 + a]) * shifted_idW(tc.idW[a], tc.iom, dW[a]);
         }
     }
     ring.finish(failed, err);

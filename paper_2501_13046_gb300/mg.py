@@ -26,7 +26,8 @@ EXPORTS = ("mg_config_default", "mg_workspace_size", "mg_create", "mg_set_confor
            "mg_set_initial_guess", "mg_solve", "mg_get_solution", "mg_residual_norms", "mg_constraint_fields",
            "mg_time_kernel", "mg_residual_norms_noalloc", "mg_destroy", "mg_status_string", "mg_last_error",
            "mg_batch_create", "mg_batch_set_sources", "mg_batch_set_initial_guess", "mg_batch_solve",
-           "mg_batch_get_solution", "mg_batch_destroy", "mg_autotune", "mg_checkpoint_save", "mg_checkpoint_load")
+           "mg_batch_get_solution", "mg_batch_destroy", "mg_autotune", "mg_checkpoint_save", "mg_checkpoint_load",
+           "mg_warmstart_load", "mg_warmstart_predict", "mg_batch_warmstart_load")
 
 
 class mg_config(C.Structure):
@@ -39,6 +40,7 @@ class mg_config(C.Structure):
         ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double), ("nested", C.c_int),
         ("nested_min", C.c_int), ("nested_tol", C.c_double),
         ("punct_P", (C.c_double * 3) * 2), ("punct_S", (C.c_double * 3) * 2), ("reflect", C.c_int),
+        ("field_tol", C.c_double), ("extrap", C.c_int),
     ]
 
 
@@ -47,7 +49,7 @@ class mg_solve_info(C.Structure):
         ("outer_iters", C.c_int), ("converged", C.c_int), ("K", C.c_double), ("K2", C.c_double),
         ("norms", C.c_double * 4), ("mom_mean", C.c_double * 3), ("history", C.POINTER(C.c_double)),
         ("history_len", C.c_int), ("device_ms", C.c_double), ("kernel_launches", C.c_longlong),
-        ("nested_iters", C.c_int),
+        ("nested_iters", C.c_int), ("rel_change", C.c_double * 4), ("warm_start", C.c_int),
     ]
 
 
@@ -77,6 +79,9 @@ def _load():
     L.mg_destroy.argtypes = [vp]
     L.mg_checkpoint_save.argtypes = [vp, C.c_char_p]
     L.mg_checkpoint_load.argtypes = [vp, C.c_char_p]
+    L.mg_warmstart_load.argtypes = [vp, C.c_char_p]
+    L.mg_warmstart_predict.argtypes = [vp, vp, vp, C.c_int]
+    L.mg_batch_warmstart_load.argtypes = [vp, C.c_char_p]
     L.mg_destroy.restype = None
     L.mg_batch_create.argtypes = [C.c_int, C.POINTER(mg_config), vp, C.POINTER(vp)]
     L.mg_batch_set_sources.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, C.c_int]
@@ -167,7 +172,8 @@ def mg_solve(ctx, allow=(MG_ERR_NOT_CONVERGED,)):
     return st, dict(outer_iters=info.outer_iters, converged=bool(info.converged), K=info.K, K2=info.K2,
                     norms=np.array(info.norms[:]), mom_mean=np.array(info.mom_mean[:]), history=hist,
                     device_ms=info.device_ms, kernel_launches=info.kernel_launches,
-                    nested_iters=info.nested_iters)
+                    nested_iters=info.nested_iters, rel_change=np.array(info.rel_change[:]),
+                    warm_start=info.warm_start)
 
 
 def mg_get_solution(ctx, u=None, W=None):
@@ -204,6 +210,20 @@ def mg_residual_norms_noalloc(cfg, u, W, rho0, rho2, S, stream=0):
     _check(_lib.mg_residual_norms_noalloc(C.byref(cfg), ptr(u), ptr(W), ptr(rho0), ptr(rho2), ptr(S), out,
                                           C.byref(k2), C.c_void_p(stream or None)), "mg_residual_norms_noalloc")
     return np.array(out[:]), k2.value
+
+
+def mg_warmstart_load(ctx, path):
+    """Attach the learned warm start stored at `path` (None: detach)."""
+    _check(_lib.mg_warmstart_load(ctx, None if path is None else os.fsencode(path)), "mg_warmstart_load")
+
+
+def mg_warmstart_predict(ctx, u=None, W=None):
+    (pu, du), (pw, dw) = _ptr(u), _ptr(W)
+    _check(_lib.mg_warmstart_predict(ctx, pu, pw, max(du, dw)), "mg_warmstart_predict")
+
+
+def mg_batch_warmstart_load(bt, path):
+    _check(_lib.mg_batch_warmstart_load(bt, None if path is None else os.fsencode(path)), "mg_batch_warmstart_load")
 
 
 def mg_checkpoint_save(ctx, path):
@@ -247,7 +267,8 @@ def mg_batch_solve(bt, count, allow=(MG_ERR_NOT_CONVERGED,)):
             if inf.history_len > 0 else np.zeros((0, 4))
         out.append(dict(outer_iters=inf.outer_iters, converged=bool(inf.converged), K=inf.K, K2=inf.K2,
                         norms=np.array(inf.norms[:]), history=hist, device_ms=inf.device_ms,
-                        kernel_launches=inf.kernel_launches))
+                        kernel_launches=inf.kernel_launches, rel_change=np.array(inf.rel_change[:]),
+                        warm_start=inf.warm_start))
     return st, out, tot.value
 
 
@@ -290,6 +311,7 @@ def config_for(problem, precision=MG_MIXED, **overrides):
     cfg.precision = precision
     cfg.npunct = len(problem["punctures"])
     cfg.reflect = problem.get("reflect", 0)
+    cfg.extrap = problem.get("extrap", 0)
     for p, pun in enumerate(problem["punctures"]):
         m, x = pun[0], pun[1]
         cfg.punct_m[p] = m

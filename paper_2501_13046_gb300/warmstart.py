@@ -189,6 +189,17 @@ class Net:
         self._conv_bwd("e0a", self.x0, a["e0a"], g["e0a"], None, s[0], stream)
 
 
+def save_weights(path, P, sc, n_net):
+    """Write the network in the file format mg_warmstart_load reads (include/ctt_mg.h): magic,
+    network size, parameter count, the five scales, then the flat FP32 parameters (little-endian)."""
+    flat = np.asarray(P.state(), dtype="<f4")
+    with open(path, "wb") as f:
+        f.write(b"CTTUNET1")
+        f.write(np.array([n_net, flat.size], dtype="<i4").tobytes())
+        f.write(np.array([sc.s_rho, sc.s_S, sc.s_K, sc.s_u, sc.s_W], dtype="<f4").tobytes())
+        f.write(flat.tobytes())
+
+
 class Scales:
     """Input and output normalisation fixed from the training set."""
 
