@@ -98,7 +98,31 @@ def test_symmetry_plane_validation(lib):
         assert e.value.status == lib.MG_ERR_INVALID_ARG
 
 
+def test_extrapolating_face_validation(lib):
+    """extrap needs a Robin box, a 6-bit mask, no lower face that is also a symmetry plane, and at
+    least one face left Robin; it adds no workspace."""
+    def cfg_for(bc, extrap, reflect=0):
+        cfg = lib.mg_config_default()
+        cfg.n[0] = cfg.n[1] = cfg.n[2] = 32
+        cfg.bc, cfg.k_mode, cfg.extrap, cfg.reflect = bc, lib.MG_K_FIXED, extrap, reflect
+        for a in range(3):
+            cfg.lo[a], cfg.hi[a] = 0.0, 16.0
+        return cfg
+    assert lib.mg_workspace_size(cfg_for(lib.MG_BC_ROBIN, 0b000011)) == lib.mg_workspace_size(cfg_for(lib.MG_BC_ROBIN, 0))
+    lib.mg_workspace_size(cfg_for(lib.MG_BC_ROBIN, 0b101010, reflect=1))   # one lower face stays Robin
+    for bad in (cfg_for(lib.MG_BC_PERIODIC, 1), cfg_for(lib.MG_BC_ROBIN, 64), cfg_for(lib.MG_BC_ROBIN, -1),
+                cfg_for(lib.MG_BC_ROBIN, 0b000001, reflect=1)):
+        with pytest.raises(lib.MGError) as e:
+            lib.mg_workspace_size(bad)
+        assert e.value.status == lib.MG_ERR_INVALID_ARG
+    for none_left in (cfg_for(lib.MG_BC_ROBIN, 63), cfg_for(lib.MG_BC_ROBIN, 0b101010, reflect=7)):
+        with pytest.raises(lib.MGError) as e:
+            lib.mg_workspace_size(none_left)
+        assert e.value.status == lib.MG_ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("field,value,status", [
+    ("field_tol", -1e-10, 1), ("field_tol", float("nan"), 1), ("use_graph", 3, 1),
     ("order", 3, 1), ("bc", 7, 1), ("precision", 5, 1), ("levels", 6, 1), ("coarse_sweeps", 0, 1),
     ("nested", 2, 1), ("nested_min", 2, 1), ("nested_tol", -1.0, 1),
 ])

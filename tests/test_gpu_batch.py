@@ -1,5 +1,7 @@
-"""Batched solves of uneven grids (one captured graph per round for all instances) against
-solo solves through the same C ABI, and against the oracle's residual."""
+"""Batched solves of uneven grids against solo solves through the same C ABI, and against the
+oracle's residual, in both pacings: device-paced (default: the whole solve one graph launch, a
+WHILE node over per-instance IF nodes, converged instances dropping out on the device) and
+host-paced (use_graph = 2: one graph per round, checked on the host, lock step)."""
 import numpy as np
 import pytest
 
@@ -60,9 +62,13 @@ def batch(mg, ps, **over):
     return st, infos, total, sols
 
 
-def test_batch_equals_solo_after_the_same_rounds(mg):
+PACING = {"device": 1, "host": 2}
+
+
+@pytest.mark.parametrize("pacing", list(PACING))
+def test_batch_equals_solo_after_the_same_rounds(mg, pacing):
     ps = problems()
-    st, infos, total, sols = batch(mg, ps, tol=0.0, max_outer=4)
+    st, infos, total, sols = batch(mg, ps, tol=0.0, max_outer=4, use_graph=PACING[pacing])
     assert st == mg.MG_ERR_NOT_CONVERGED and total > 0
     for p, (u, W), inf in zip(ps, sols, infos):
         info, u1, W1 = solo(mg, p, tol=0.0, max_outer=4)
@@ -70,17 +76,44 @@ def test_batch_equals_solo_after_the_same_rounds(mg):
         assert np.array_equal(inf["history"], info["history"])
 
 
-def test_batch_converges_and_reports_rounds(mg):
+@pytest.mark.parametrize("pacing", list(PACING))
+def test_batch_converges_and_reports_rounds(mg, pacing):
     ps = problems()
-    st, infos, total, sols = batch(mg, ps, tol=1e-10, max_outer=40)
+    st, infos, total, sols = batch(mg, ps, tol=1e-10, max_outer=40, use_graph=PACING[pacing])
     assert st == mg.MG_OK
     for p, (u, W), inf in zip(ps, sols, infos):
-        info, _, _ = solo(mg, p, tol=1e-10, max_outer=40)
+        info, u1, W1 = solo(mg, p, tol=1e-10, max_outer=40)
         assert inf["converged"] and inf["outer_iters"] == info["outer_iters"]
+        assert np.array_equal(inf["history"], info["history"])
+        if pacing == "device":   # a converged instance stops where the solo solve stops
+            assert np.array_equal(u, u1) and np.array_equal(W, W1)
         assert 0 < inf["device_ms"] <= total
         g = O.make_grid(p["n"], p["lo"], p["hi"], p["order"], p["bc"])
         res = O.residual(g, u, W, p["rho0"], p["rho2"], p["S"], O.K_INTEGRABILITY)
         assert res["norms"].max() <= 1e-10
+
+
+def test_device_paced_batch_repeats_and_per_field_stop(mg):
+    """The cached graph serves a second solve from psi = 1; field_tol works on the device too."""
+    ps = problems()
+    cfgs = [mg.config_for(p, mg.MG_MIXED, tol=1e-10, max_outer=40, field_tol=1e-10) for p in ps]
+    bt = mg.mg_batch_create(cfgs, torch.cuda.current_stream().cuda_stream)
+    try:
+        for b, p in enumerate(ps):
+            mg.mg_batch_set_sources(bt, b, *[dev(a) for a in (p["rho0"], p["rho2"], *p["S"])])
+        runs = []
+        for _ in range(2):
+            for b in range(len(ps)):
+                mg.mg_batch_set_initial_guess(bt, b, None, None)
+            st, infos, total = mg.mg_batch_solve(bt, len(ps))
+            assert st == mg.MG_OK
+            runs.append([(i["outer_iters"], i["history"].copy()) for i in infos])
+            for i in infos:
+                assert i["converged"] and 0 < i["rel_change"].max() <= 1e-10
+    finally:
+        mg.mg_batch_destroy(bt)
+    for (i0, h0), (i1, h1) in zip(*runs):
+        assert i0 == i1 and np.array_equal(h0, h1)
 
 
 def test_batch_rejects_mixed_orders(mg):

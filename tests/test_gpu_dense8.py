@@ -3,10 +3,14 @@
 ``oracle/dense_newton.py`` solves the discrete constraint system (eq:Ham,
 eq:Mom in CTT form) by Newton's method with dense LAPACK solves: the exact root
 of the discrete equations, reached without multigrid.  The CUDA library, called
-through its C ABI, must land on that root: psi (and W_i where it is not ~0)
-to 1e-12 relative max-norm, K^2 to 1e-12 on periodic boxes, in FP64 and in the
-mixed FP32-inner / FP64-outer form.  With the GPU driven to residuals of 1e-13
-and |J^-1| of a few on these boxes, the fields agree to ~1e-13 of their size.
+through its C ABI, in FP64 and in the mixed FP32-inner / FP64-outer form, must
+land on that root.  The bars follow from |error| <~ |J^-1| |residual| with
+|J^-1| ~ (L/2pi)^2 (6.5 for L = 16, 26 for L = 32): the GPU is driven to
+max(|H|, |M_i|) <= 1e-14, and psi must match to 1e-12 relative max-norm, K^2 to
+1e-12 (periodic boxes).  Where W_i is small (3e-5 on the Robin boxes) the FP64
+floor of the momentum residual binds: M_i cannot fall below ~1e-18 (rounding of
+its stencil sums), which leaves |J^-1| * 1e-18 ~ 3e-17 in W_i, 1e-12 of its size;
+W_i is held to 5e-12 relative.
 """
 import numpy as np
 import pytest
@@ -56,7 +60,7 @@ def test_gpu_root_is_the_dense_newton_root(mg, dense_roots, case, precision):
     p, ds, rd = dense_roots[case]
     assert rd["residual"] < 1e-13
     prec = mg.MG_FP64 if precision == "fp64" else mg.MG_MIXED
-    cfg = mg.config_for(p, prec, tol=1e-13, max_outer=80)
+    cfg = mg.config_for(p, prec, tol=1e-14, max_outer=80)
     ctx = mg.mg_create(cfg, torch.cuda.current_stream().cuda_stream)
     try:
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
@@ -72,7 +76,7 @@ def test_gpu_root_is_the_dense_newton_root(mg, dense_roots, case, precision):
     assert rel(ds.psibg + u, ds.psibg + rd["u"]) <= 1e-12
     for i in range(3):
         if np.abs(rd["W"][i]).max() > 1e-12:
-            assert rel(W[i], rd["W"][i]) <= 1e-12, i
+            assert rel(W[i], rd["W"][i]) <= 5e-12, i
         else:
             assert np.abs(W[i]).max() <= 1e-13
     if p["bc"] == fields.PERIODIC:
