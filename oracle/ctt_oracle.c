@@ -38,7 +38,12 @@
  *   v(g) = v(b) |x_b| / |x_g| with b the cell obtained by clamping g into the box.  On a Robin box
  *   a lower face x_a = 0 may instead be a reflection-symmetry plane (Key features, "Boundary
  *   conditions": reflective): below it g_a -> -1 - g_a (the mirror cell), with the sign of W_a,
- *   the component normal to the plane, flipped and every other field kept.
+ *   the component normal to the plane, flipped and every other field kept.  A face of a Robin box
+ *   may instead be extrapolating (same passage: extrapolating): a cell beyond it at distance
+ *   d (1 or 2) along the face normal takes the linear extrapolation through the two nearest cells
+ *   of its line, v = (1 + d) v(b) - d v(b'), b the boundary cell and b' its inner neighbour;
+ *   extrapolating axes are resolved first (the rule is linear, so their order does not matter), then
+ *   the remaining coordinates by the rules above.
  *
  * Solver (any convergent method reaches the same discrete solution): an outer
  * defect-correction loop in FP64 (residual, integrability K^2, norms), with an
@@ -74,6 +79,7 @@ typedef struct {
     double pP[2][3]; /* Bowen-York linear momentum of each puncture (0: bare) */
     double pS[2][3]; /* Bowen-York spin of each puncture (0: bare) */
     int reflect;     /* Robin boxes: bit a = the lower face of axis a (x_a = 0) is a symmetry plane */
+    int extrap;      /* Robin boxes: bit 2a (lower) / 2a + 1 (upper) = that face of axis a is extrapolating */
 } ora_grid;
 
 static long ncells(const ora_grid *g) { return (long)g->n[0] * g->n[1] * g->n[2]; }
@@ -90,6 +96,22 @@ static double cellx(const ora_grid *g, int a, int i) { return g->lo[a] + (i + 0.
 static double at(const ora_grid *g, int fi, const double *f, int i, int j, int k)
 {
     int p[3] = {i, j, k};
+    if (g->bc != 0 && g->extrap) {
+        /* linear extrapolation through an extrapolating face, one axis at a time */
+        for (int a = 0; a < 3; ++a) {
+            int n = g->n[a], d = 0, b0 = 0, b1 = 0;
+            if (p[a] < 0 && ((g->extrap >> (2 * a)) & 1)) {
+                d = -p[a]; b0 = 0; b1 = 1;
+            } else if (p[a] >= n && ((g->extrap >> (2 * a + 1)) & 1)) {
+                d = p[a] - (n - 1); b0 = n - 1; b1 = n - 2;
+            }
+            if (d == 0) continue;
+            int q0[3] = {p[0], p[1], p[2]}, q1[3] = {p[0], p[1], p[2]};
+            q0[a] = b0;
+            q1[a] = b1;
+            return (1.0 + d) * at(g, fi, f, q0[0], q0[1], q0[2]) - d * at(g, fi, f, q1[0], q1[1], q1[2]);
+        }
+    }
     int b[3];
     int outside = 0;
     double sign = 1.0;

@@ -16,8 +16,10 @@ K_ij = psi^-2 At_ij + gamma_ij K/3, At_ij = D_i W_j + D_j W_i - (2/3) delta_ij D
 on a cell-centred grid (x_i = lo + (i + 1/2) h) with the centred stencils of
 order 2 or 4 (first derivative D_a, compact second derivative D_aa, mixed
 D_a D_b as the tensor product of two first-derivative stencils), values outside
-the box by periodic wrap or by the Robin 1/r rule v(g) = v(clamp(g)) |x_clamp| / |x_g|,
-and, with punctures, the Bowen-York curvature added to At_ij before AtAt.
+the box by periodic wrap or by the Robin 1/r rule v(g) = v(clamp(g)) |x_clamp| / |x_g|
+(beyond an extrapolating face of a Robin box: first the linear extrapolation
+(1 + d) v(boundary cell) - d v(its inner neighbour) along that face's normal, d the
+distance), and, with punctures, the Bowen-York curvature added to At_ij before AtAt.
 
 Every operator is assembled as a dense matrix (one row per cell, entries from
 the stencil weights and the boundary rule), the Jacobian is formed
@@ -39,13 +41,14 @@ class DenseSystem:
     """The discrete constraint system of one problem on a small grid, with dense operators."""
 
     def __init__(self, n, lo, hi, order, bc, punctures=(), rho0=None, rho2=None, S=None, K2=0.0,
-                 k_from_integrability=True):
+                 k_from_integrability=True, extrap=0):
         self.n = [n] * 3 if np.isscalar(n) else list(n)
         lo = [lo] * 3 if np.isscalar(lo) else list(lo)
         hi = [hi] * 3 if np.isscalar(hi) else list(hi)
         self.lo = np.array(lo, dtype=float)
         self.h = np.array([(hi[a] - lo[a]) / self.n[a] for a in range(3)])
         self.order, self.bc = order, bc
+        self.extrap = int(extrap)   # bit 2a (lower) / 2a + 1 (upper): extrapolating face of axis a
         self.periodic = bc == PERIODIC
         self.kint = self.periodic and k_from_integrability
         assert self.kint or not self.periodic, "periodic boxes take K^2 from the integrability condition"
@@ -75,6 +78,25 @@ class DenseSystem:
                     self.Dmix[a][b] = self._mixed(a, b)
 
     # ------------------------------------------------------------ boundary rule and stencils
+    def _sources(self, p):
+        """[(cell index, factor)]: the value at the integer cells p (3, M) is the sum over the list
+        of factor times the value at that cell (one term inside the box or under the Robin rule; the
+        linear extrapolation through extrapolating faces splits a point in two per such axis)."""
+        sets = [(p.copy(), np.ones(p.shape[1]))]
+        if not self.periodic and self.extrap:
+            for a in range(3):
+                n, new = self.n[a], []
+                for q, w in sets:
+                    lo = (q[a] < 0) & bool((self.extrap >> (2 * a)) & 1)
+                    hi = (q[a] >= n) & bool((self.extrap >> (2 * a + 1)) & 1)
+                    d = np.where(lo, -q[a], np.where(hi, q[a] - (n - 1), 0))
+                    q0, q1 = q.copy(), q.copy()
+                    q0[a] = np.where(lo, 0, np.where(hi, n - 1, q[a]))
+                    q1[a] = np.where(lo, 1, np.where(hi, n - 2, q[a]))
+                    new += [(q0, w * (1.0 + d)), (q1, w * -d)]
+                sets = new
+        return [(lin, w * fac) for q, w in sets for lin, fac in [self._source(q)]]
+
     def _source(self, p):
         """(cell index, factor) whose value, times factor, is the value at integer cell p (3, M)."""
         n = np.array(self.n)[:, None]
@@ -92,8 +114,8 @@ class DenseSystem:
 
     def _add(self, M, offset, weight):
         p = self.idx + np.array(offset)[:, None]
-        lin, fac = self._source(p)
-        np.add.at(M, (np.arange(self.N), lin), weight * fac)
+        for lin, fac in self._sources(p):
+            np.add.at(M, (np.arange(self.N), lin), weight * fac)
 
     def _stencil(self, weights, a, second=False):
         M = np.zeros((self.N, self.N))

@@ -37,6 +37,7 @@ class Grid(C.Structure):
         ("pP", (C.c_double * 3) * 2),
         ("pS", (C.c_double * 3) * 2),
         ("reflect", C.c_int),
+        ("extrap", C.c_int),
     ]
 
 
@@ -83,10 +84,11 @@ def lib():
     return _lib
 
 
-def make_grid(n, lo, hi, order, bc, punctures=(), reflect=0):
+def make_grid(n, lo, hi, order, bc, punctures=(), reflect=0, extrap=0):
     """n: int or 3 ints; lo/hi: float or 3 floats; punctures: [(mass, (x, y, z)), ...] or, with
     Bowen-York momentum and spin, [(mass, (x, y, z), (Px, Py, Pz), (Sx, Sy, Sz)), ...];
-    reflect (Robin boxes): bit a makes the lower face x_a = 0 a reflection-symmetry plane."""
+    reflect (Robin boxes): bit a makes the lower face x_a = 0 a reflection-symmetry plane;
+    extrap (Robin boxes): bit 2a (lower) or 2a + 1 (upper) makes that face of axis a extrapolating."""
     n = [n] * 3 if np.isscalar(n) else list(n)
     lo = [lo] * 3 if np.isscalar(lo) else list(lo)
     hi = [hi] * 3 if np.isscalar(hi) else list(hi)
@@ -95,7 +97,7 @@ def make_grid(n, lo, hi, order, bc, punctures=(), reflect=0):
         g.n[a] = int(n[a])
         g.lo[a] = float(lo[a])
         g.h[a] = (float(hi[a]) - float(lo[a])) / int(n[a])
-    g.order, g.bc, g.npunct, g.reflect = int(order), int(bc), len(punctures), int(reflect)
+    g.order, g.bc, g.npunct, g.reflect, g.extrap = int(order), int(bc), len(punctures), int(reflect), int(extrap)
     for p, pun in enumerate(punctures):
         m, x = pun[0], pun[1]
         P = pun[2] if len(pun) > 2 else (0.0, 0.0, 0.0)
