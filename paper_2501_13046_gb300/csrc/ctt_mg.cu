@@ -517,6 +517,7 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
             }
             g.reflect = cfg->bc == MG_BC_ROBIN ? cfg->reflect : 0;
             g.extrap = cfg->bc == MG_BC_ROBIN ? cfg->extrap : 0;
+            g.robin = cfg->bc == MG_BC_ROBIN ? 1 : 0;
             g.npunct = cfg->npunct;
             for (int p = 0; p < cfg->npunct; ++p) {
                 g.pm[p] = cfg->punct_m[p];

@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
                     apply(cur, i, j, k, cs[q], cs[N + q], Je, ctr);
                     T dpsi = 0, dW[3] = {0, 0, 0};
                     if constexpr (BC != BC_PERIODIC)
-                        if (near_face(g, i, j, k)) boundary_diag<T, ORDER, BC>(g, cf.ih2[0], cf.ih2[1], cf.ih2[2], i, j, k, &dpsi, dW);
+                        if (near_face(g, i, j, k)) face_shifts(cf.fd, g, i, j, k, dpsi, dW);
                     alt[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * (cf.dl + dpsi) + cs[N + q]) * cf.iom);
                     for (int a = 0; a < 3; ++a)
                         alt[(1 + a) * N + q] =

@@ -127,6 +127,7 @@ TileCoef<T> make_tile_coef(const Geo &g, int order, double omega = 1.0)
         t.idW[A] = (T)(omega / m0);
     }
     t.iom = (T)(1.0 / omega);
+    face_diag<T>(g, order, t.fd);
     return t;
 }
 
@@ -147,6 +148,7 @@ Coef<T> make_coef(const Geo &g, int order, double omega = 1.0)
     cf.dl = (T)dl;
     for (int a = 0; a < 3; ++a) cf.idW[a] = (T)(omega / (dl + w0 / (g.h[a] * g.h[a]) / 3.0));
     cf.iom = (T)(1.0 / omega);
+    face_diag<T>(g, order, cf.fd);
     return cf;
 }
 

@@ -36,6 +36,7 @@ struct Geo {
                            // reflection-symmetry plane instead of a Robin face
     int extrap;            // Robin boxes: bit 2a (lower) / 2a + 1 (upper) = that face of axis a is
                            // extrapolating (linear extrapolation along its normal; see extrap_split)
+    int robin;             // 1 on Robin boxes (faces with boundary rules), 0 on periodic boxes
     int npunct;
     double pm[2];
     double px[2][3];
@@ -86,6 +87,20 @@ static __global__ void __launch_bounds__(256) k_fill_by(Geo g, ByPunct bp, doubl
     }
 }
 
+// Diagonal shifts of the inner operator's rows next to the faces of a Robin box.  A colour pass
+// divides a row's residual by the row's diagonal; next to a face some stencil taps lie beyond the
+// box and their boundary value depends on the cell itself (the clamped cell of the 1/r rule, a
+// mirror image, a weight of an extrapolation), so the row's true diagonal is the interior one plus
+// each such tap's weight times that dependence.  The taps of the diagonal run along the axes, so
+// the shift is a sum over axes of a term that depends only on the cell's distance to that axis's
+// faces: s[axis][lower/upper face][face cell / next cell][field u, W_x, W_y, W_z], with the 1/r
+// ratio of the Robin rule taken as 1 (the smoother only preconditions; the residual keeps the
+// exact rule).  Zero on periodic boxes.
+template <typename T>
+struct FaceDiag {
+    T s[3][2][2][4];
+};
+
 template <typename T>
 struct Coef {
     T ih[3];    // 1/h
@@ -93,7 +108,63 @@ struct Coef {
     T dl;       // diagonal of the discrete Laplacian
     T idW[3];   // omega / diagonal of the momentum operator row i (relaxation weight folded in)
     T iom;      // 1 / omega: the psi-row update divides by (diagonal * iom)
+    FaceDiag<T> fd;   // diagonal shifts next to the faces (Robin boxes)
 };
+
+// Host: the face table of a level (Geo g with its reflect / extrap masks), order 2 or 4.
+template <typename T>
+inline void face_diag(const Geo &g, int order, FaceDiag<T> &fd)
+{
+    for (int a = 0; a < 3; ++a)
+        for (int sd = 0; sd < 2; ++sd)
+            for (int o = 0; o < 2; ++o)
+                for (int f = 0; f < 4; ++f) fd.s[a][sd][o][f] = 0;
+    if (!g.robin) return;
+    const double k1 = order == 2 ? 1.0 : 16.0 / 12.0, k2 = order == 2 ? 0.0 : -1.0 / 12.0;
+    for (int a = 0; a < 3; ++a) {
+        const int n = g.n[a];
+        const double ih2 = 1.0 / (g.h[a] * g.h[a]);
+        for (int sd = 0; sd < 2; ++sd)
+            for (int o = 0; o < 2; ++o) {
+                const int i = sd == 0 ? o : n - 1 - o;   // the cell's index along a
+                double acc[4] = {0, 0, 0, 0};
+                for (int st = 1; st <= (order == 2 ? 1 : 2); ++st) {
+                    const int c = sd == 0 ? i - st : i + st;   // the tap toward this side's face
+                    if (c >= 0 && c < n) continue;
+                    double kap[4] = {0, 0, 0, 0};
+                    if (sd == 0 && ((g.reflect >> a) & 1)) {         // mirror image across x_a = 0
+                        if (-1 - c == i)
+                            for (int f = 0; f < 4; ++f) kap[f] = f == 1 + a ? -1.0 : 1.0;
+                    } else if ((g.extrap >> (2 * a + sd)) & 1) {     // linear extrapolation
+                        const int d = sd == 0 ? -c : c - (n - 1), b0 = sd == 0 ? 0 : n - 1, b1 = sd == 0 ? 1 : n - 2;
+                        const double kk = (i == b0 ? 1.0 + d : 0.0) + (i == b1 ? -(double)d : 0.0);
+                        for (int f = 0; f < 4; ++f) kap[f] = kk;
+                    } else if (i == (sd == 0 ? 0 : n - 1)) {         // the clamped cell of the 1/r rule
+                        for (int f = 0; f < 4; ++f) kap[f] = 1.0;
+                    }
+                    const double w = (st == 1 ? k1 : k2) * ih2;
+                    acc[0] += w * kap[0];
+                    for (int A = 0; A < 3; ++A) acc[1 + A] += (a == A ? 4.0 / 3.0 : 1.0) * w * kap[1 + A];
+                }
+                for (int f = 0; f < 4; ++f) fd.s[a][sd][o][f] = (T)acc[f];
+            }
+    }
+}
+
+// Device: the shift of field f's row (0: the Laplacian of the psi row, 1 + A: row A) at cell p.
+template <int F, typename T>
+__device__ __forceinline__ T face_shift(const FaceDiag<T> &fd, const Geo &g, int i, int j, int k)
+{
+    const int p[3] = {i, j, k};
+    T d = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int n = g.n[a];
+        d += p[a] == 0 ? fd.s[a][0][0][F] : (p[a] == 1 ? fd.s[a][0][1][F] : (T)0);
+        d += p[a] == n - 1 ? fd.s[a][1][0][F] : (p[a] == n - 2 ? fd.s[a][1][1][F] : (T)0);
+    }
+    return d;
+}
 
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
@@ -191,6 +262,18 @@ __device__ __forceinline__ int extrap_split(const Geo &g, const int p[3], int q[
     return any ? ns : 0;
 }
 
+// Whether p lies beyond an extrapolating face (the cheap test kept inline; the weighted sums over
+// extrap_split's cells are out-of-line functions: that branch is rare, and inlining it into every
+// stencil tap multiplies the code, and the compile time, of the boundary variant).
+__device__ __forceinline__ bool beyond_extrap(const Geo &g, const int p[3])
+{
+    bool b = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        b |= (p[a] < 0 && ((g.extrap >> (2 * a)) & 1)) || (p[a] >= g.n[a] && ((g.extrap >> (2 * a + 1)) & 1));
+    return b;
+}
+
 // Sign of field fi (0 = u, 1..3 = W_x..W_z) at a cell mirrored across the planes in `mirror`:
 // the component of W normal to a symmetry plane is odd across it, everything else even.
 __device__ __forceinline__ int bc_sign(int mirror, int fi) { return (fi >= 1 && ((mirror >> (fi - 1)) & 1)) ? -1 : 1; }
@@ -257,6 +340,30 @@ static __global__ void __launch_bounds__(256) k_fill_psibg(Geo g, double *__rest
 
 // value of field f (index fi, see bc_sign) at a cell that may lie outside the box (offsets are at
 // most +-2 per axis)
+// fetch_bc at an unwrapped cell p that lies beyond no extrapolating face.
+template <typename T, int BC>
+__device__ __forceinline__ T fetch_bc_one(const T *f, int fi, const Geo &g, const int p[3])
+{
+    int b[3], mirror;
+    const bool clamped = bc_cell<BC>(g, p, b, mirror);
+    const T v = bc_signed<BC>(f[b[0] + g.n[0] * (b[1] + g.n[1] * b[2])], mirror, fi);
+    if (!clamped) return v;
+    if constexpr (std::is_same<T, double>::value) return v * robin_ratio_f64(g, b[0], b[1], b[2], p[0], p[1], p[2]);
+    else return v * robin_ratio<T>(g, b[0], b[1], b[2], p[0], p[1], p[2]);
+}
+
+// fetch_bc beyond an extrapolating face: the weighted cells of extrap_split (out of line).
+template <typename T, int BC>
+__device__ __noinline__ T fetch_bc_extrap(const T *f, int fi, const Geo *g, int i, int j, int k)
+{
+    const int p[3] = {i, j, k};
+    int q[8][3], w[8];
+    const int ns = extrap_split(*g, p, q, w);
+    T s = 0;
+    for (int t = 0; t < ns; ++t) s += (T)w[t] * fetch_bc_one<T, BC>(f, fi, *g, q[t]);
+    return s;
+}
+
 template <typename T, int BC>
 __device__ __forceinline__ T fetch_bc(const T *f, int fi, const Geo &g, int i, int j, int k)
 {
@@ -266,76 +373,27 @@ __device__ __forceinline__ T fetch_bc(const T *f, int fi, const Geo &g, int i, i
         k += (k < 0) ? g.n[2] : 0; k -= (k >= g.n[2]) ? g.n[2] : 0;
         return f[i + g.n[0] * (j + g.n[1] * k)];
     } else {
-        auto one = [&](const int p[3]) {
-            int b[3], mirror;
-            const bool clamped = bc_cell<BC>(g, p, b, mirror);
-            const T v = bc_signed<BC>(f[b[0] + g.n[0] * (b[1] + g.n[1] * b[2])], mirror, fi);
-            if (!clamped) return v;
-            if constexpr (std::is_same<T, double>::value) return v * robin_ratio_f64(g, b[0], b[1], b[2], p[0], p[1], p[2]);
-            else return v * robin_ratio<T>(g, b[0], b[1], b[2], p[0], p[1], p[2]);
-        };
         const int p[3] = {i, j, k};
-        if constexpr (BC == BC_SYM) {
-            if (g.extrap) {
-                int q[8][3], w[8];
-                const int ns = extrap_split(g, p, q, w);
-                if (ns) {
-                    T s = 0;
-                    for (int t = 0; t < ns; ++t) s += (T)w[t] * one(q[t]);
-                    return s;
-                }
-            }
-        }
-        return one(p);
+        if constexpr (BC == BC_SYM)
+            if (g.extrap && beyond_extrap(g, p)) return fetch_bc_extrap<T, BC>(f, fi, &g, i, j, k);
+        return fetch_bc_one<T, BC>(f, fi, g, p);
     }
 }
 
-// Diagonal shifts of the inner operator's rows at a cell next to a Robin face, a symmetry plane or
-// an extrapolating face.  A colour pass divides a row's residual by the row's diagonal; at such a
-// cell some stencil taps lie beyond the box, and their boundary value depends on the cell itself
-// (the 1/r ratio when it is the clamped cell, a mirror image of it, a weight of an extrapolation),
-// so the row's true diagonal is the interior one plus each such tap's weight times that
-// dependence.  dpsi: shift of the Laplacian's diagonal (psi row: a (dl + dpsi) + b); dW[A]: shift
-// of row A's diagonal (Lap W_A + (1/3) D_AA W_A acting on W_A).  ih2: 1/h^2 per axis.  Zero away
-// from the faces; periodic boxes never call it.
-template <typename T, int ORDER, int BC>
-__device__ __noinline__ void boundary_diag(const Geo &g, T ih20, T ih21, T ih22, int i, int j, int k, T *dpsi, T *dW)
-{
-    const T ih2[3] = {ih20, ih21, ih22};
-    const T k1 = ORDER == 2 ? (T)1 : (T)(16.0 / 12.0), k2 = ORDER == 2 ? (T)0 : (T)(-1.0 / 12.0);
-    T sp = 0, sw[3] = {0, 0, 0};
-    for (int a = 0; a < 3; ++a)
-        for (int s = -2; s <= 2; ++s) {
-            if (s == 0 || (ORDER == 2 && (s == 2 || s == -2))) continue;
-            int c[3] = {i, j, k};
-            c[a] += s;
-            if (c[a] >= 0 && c[a] < g.n[a]) continue;
-            T kap[4] = {0, 0, 0, 0};   // d(boundary value at c) / d(value at the cell), per field
-            auto add = [&](const int q[3], T w) {
-                int b[3], mirror;
-                const bool clamped = bc_cell<BC>(g, q, b, mirror);
-                if (b[0] != i || b[1] != j || b[2] != k) return;
-                if (clamped) w *= robin_ratio<T>(g, b[0], b[1], b[2], q[0], q[1], q[2]);
-                for (int f = 0; f < 4; ++f) kap[f] += (BC == BC_SYM && bc_sign(mirror, f) < 0) ? -w : w;
-            };
-            int q[8][3], w8[8], ns = 0;
-            if constexpr (BC == BC_SYM) ns = g.extrap ? extrap_split(g, c, q, w8) : 0;
-            if (ns)
-                for (int t = 0; t < ns; ++t) add(q[t], (T)w8[t]);
-            else
-                add(c, (T)1);
-            const T w = ((s == 1 || s == -1) ? k1 : k2) * ih2[a];
-            sp += w * kap[0];
-            for (int A = 0; A < 3; ++A) sw[A] += (a == A ? (T)(4.0 / 3.0) : (T)1) * w * kap[1 + A];
-        }
-    *dpsi = sp;
-    for (int A = 0; A < 3; ++A) dW[A] = sw[A];
-}
-
-// Whether a cell is within 2 cells of a face (where boundary_diag may be nonzero).
+// Whether a cell is within 2 cells of a face (where the face shifts may be nonzero).
 __device__ __forceinline__ bool near_face(const Geo &g, int i, int j, int k)
 {
     return i < 2 || j < 2 || k < 2 || i >= g.n[0] - 2 || j >= g.n[1] - 2 || k >= g.n[2] - 2;
+}
+
+// The four rows' shifts at a cell (psi row's Laplacian, rows W_x, W_y, W_z).
+template <typename T>
+__device__ __forceinline__ void face_shifts(const FaceDiag<T> &fd, const Geo &g, int i, int j, int k, T &dpsi, T dW[3])
+{
+    dpsi = face_shift<0>(fd, g, i, j, k);
+    dW[0] = face_shift<1>(fd, g, i, j, k);
+    dW[1] = face_shift<2>(fd, g, i, j, k);
+    dW[2] = face_shift<3>(fd, g, i, j, k);
 }
 
 // A row's relaxation factor omega / (m0 + d) from omega / m0 (idW) and 1 / omega (iom).
@@ -482,6 +540,40 @@ struct AccS {
     }
 };
 
+// Value of field fi at the unwrapped cell p (beyond no extrapolating face) of a colour-split level:
+// `same` holds the cells of colour c, `other` the rest (both are full field bases).
+template <typename T, int BC>
+__device__ __forceinline__ T split_one(const T *same, const T *other, int fi, const Geo &g, size_t N, int c,
+                                       const int p[3])
+{
+    int q[3], mirror;
+    const bool outside = bc_cell<BC>(g, p, q, mirror);
+    int c2 = (q[0] + q[1] + q[2]) & 1;
+    size_t lin = (size_t)q[0] + (size_t)g.n[0] * ((size_t)q[1] + (size_t)g.n[1] * q[2]);
+    T v = (c2 == c ? same : other)[(c2 ? N / 2 : 0) + (lin >> 1)];
+    v = bc_signed<BC>(v, mirror, fi);
+    if (BC != BC_PERIODIC && outside) {
+        if constexpr (std::is_same<T, double>::value)
+            return v * robin_ratio_f64(g, q[0], q[1], q[2], p[0], p[1], p[2]);
+        else
+            return v * robin_ratio<T>(g, q[0], q[1], q[2], p[0], p[1], p[2]);
+    }
+    return v;
+}
+
+// split_one beyond an extrapolating face: the weighted cells of extrap_split (out of line).
+template <typename T, int BC>
+__device__ __noinline__ T split_extrap(const T *same, const T *other, int fi, const Geo *g, size_t N, int c, int i,
+                                       int j, int k)
+{
+    const int p[3] = {i, j, k};
+    int q[8][3], w[8];
+    const int ns = extrap_split(*g, p, q, w);
+    T s = 0;
+    for (int t = 0; t < ns; ++t) s += (T)w[t] * split_one<T, BC>(same, other, fi, *g, N, c, q[t]);
+    return s;
+}
+
 // Boundary accessor of a colour-split field: cells of the centre's colour c are read from
 // `same`, cells of the other colour from `other` (both are full field bases).
 template <typename T, int BC>
@@ -491,37 +583,12 @@ struct AccB2 {
     const Geo *g;
     size_t N;
     int i, j, k, c;
-    __device__ __forceinline__ T one(const int p[3]) const
-    {
-        int q[3], mirror;
-        const bool outside = bc_cell<BC>(*g, p, q, mirror);
-        int c2 = (q[0] + q[1] + q[2]) & 1;
-        size_t lin = (size_t)q[0] + (size_t)g->n[0] * ((size_t)q[1] + (size_t)g->n[1] * q[2]);
-        T v = (c2 == c ? same : other)[(c2 ? N / 2 : 0) + (lin >> 1)];
-        v = bc_signed<BC>(v, mirror, fi);
-        if (BC != BC_PERIODIC && outside) {
-            if constexpr (std::is_same<T, double>::value)
-                return v * robin_ratio_f64(*g, q[0], q[1], q[2], p[0], p[1], p[2]);
-            else
-                return v * robin_ratio<T>(*g, q[0], q[1], q[2], p[0], p[1], p[2]);
-        }
-        return v;
-    }
     __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
     {
         const int p[3] = {i + dx, j + dy, k + dz};
-        if constexpr (BC == BC_SYM) {
-            if (g->extrap) {
-                int q[8][3], w[8];
-                const int ns = extrap_split(*g, p, q, w);
-                if (ns) {
-                    T s = 0;
-                    for (int t = 0; t < ns; ++t) s += (T)w[t] * one(q[t]);
-                    return s;
-                }
-            }
-        }
-        return one(p);
+        if constexpr (BC == BC_SYM)
+            if (g->extrap && beyond_extrap(*g, p)) return split_extrap<T, BC>(same, other, fi, g, N, c, p[0], p[1], p[2]);
+        return split_one<T, BC>(same, other, fi, *g, N, c, p);
     }
 };
 
@@ -639,7 +706,7 @@ __device__ __forceinline__ void smooth_cell(const Geo &g, const Coef<T> &cf, con
     else apply_J_split<T, ORDER, BC, false>(X, O, N, g, i, j, k, ca, cb, cf, Je, ctr);
     T dpsi = 0, dW[3] = {0, 0, 0};
     if constexpr (BC != BC_PERIODIC)
-        if (!interior && near_face(g, i, j, k)) boundary_diag<T, ORDER, BC>(g, cf.ih2[0], cf.ih2[1], cf.ih2[2], i, j, k, &dpsi, dW);
+        if (!interior && near_face(g, i, j, k)) face_shifts(cf.fd, g, i, j, k, dpsi, dW);
     Y[q] = ctr[0] + (f[q] - Je[0]) / ((ca * (cf.dl + dpsi) + cb) * cf.iom);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -1233,7 +1300,7 @@ __global__ void __launch_bounds__(512) k_coarse_solve(Geo g, Coef<T> cf, const T
                     apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
                     T dpsi = 0, dW[3] = {0, 0, 0};
                     if constexpr (BC != BC_PERIODIC)
-                        if (near_face(g, i, j, k)) boundary_diag<T, ORDER, BC>(g, cf.ih2[0], cf.ih2[1], cf.ih2[2], i, j, k, &dpsi, dW);
+                        if (near_face(g, i, j, k)) face_shifts(cf.fd, g, i, j, k, dpsi, dW);
                     eB[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * (cf.dl + dpsi) + cs[N + q]) * cf.iom);
                     for (int a = 0; a < 3; ++a)
                         eB[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * shifted_idW(cf.idW[a], cf.iom, dW[a]);

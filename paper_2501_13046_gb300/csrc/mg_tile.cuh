@@ -63,6 +63,7 @@ struct TileCoef {
     T dl;                                // diagonal of Lap (psi-row update)
     T idW[3];                            // omega / diagonal of row A
     T iom;                               // 1 / omega
+    FaceDiag<T> fd;                      // diagonal shifts next to the faces (Robin boxes)
 };
 
 // ---------------------------------------------------------------- TMA / mbarrier (inline PTX)
@@ -125,36 +126,43 @@ __device__ __forceinline__ void tile_tma_load(void *dst, const CUtensorMap *map,
 // Value of field f at the cell of colour h in pair P of row (y, z), coordinates unwrapped
 // (at most one period outside the box).  Same colour as the pass: old value from X; other
 // colour: current value from O.
+// tile_fetch's value at the unwrapped cell c (beyond no extrapolating face); f is the field.
+template <typename T, int BC>
+__device__ __forceinline__ T tile_one(const Geo &g, const T *X, const T *O, int colour, int f, const int c[3])
+{
+    const int nx = g.n[0], ny = g.n[1];
+    const size_t N = (size_t)nx * ny * g.n[2];
+    int b[3], mirror;
+    const bool clamped = bc_cell<BC>(g, c, b, mirror);   // wrap; or mirror / clamp (field f's sign)
+    const int hb = (b[0] + b[1] + b[2]) & 1;
+    const size_t idx =
+        (size_t)f * N + (hb ? N / 2 : 0) + (size_t)(b[0] >> 1) + (size_t)(nx >> 1) * (b[1] + (size_t)ny * b[2]);
+    T v = (hb == colour ? X : O)[idx];
+    v = bc_signed<BC>(v, mirror, f);
+    if (BC != BC_PERIODIC && clamped) v *= robin_ratio<T>(g, b[0], b[1], b[2], c[0], c[1], c[2]);
+    return v;
+}
+
+// Beyond an extrapolating face: the weighted in-box cells of extrap_split (out of line).
+template <typename T, int BC>
+__device__ __noinline__ T tile_extrap(const Geo *g, const T *X, const T *O, int colour, int f, int i, int j, int k)
+{
+    const int p[3] = {i, j, k};
+    int q[8][3], w[8];
+    const int ns = extrap_split(*g, p, q, w);
+    T s = 0;
+    for (int t = 0; t < ns; ++t) s += (T)w[t] * tile_one<T, BC>(*g, X, O, colour, f, q[t]);
+    return s;
+}
+
 template <typename T, int BC>
 __device__ __forceinline__ T tile_fetch(const Geo &g, const T *X, const T *O, int colour, int P, int y, int z, int h,
                                         int f)
 {
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const size_t N = (size_t)nx * ny * nz;
-    auto one = [&](const int c[3]) {
-        int b[3], mirror;
-        const bool clamped = bc_cell<BC>(g, c, b, mirror);   // wrap; or mirror / clamp (field f's sign)
-        const int hb = (b[0] + b[1] + b[2]) & 1;
-        const size_t idx =
-            (size_t)f * N + (hb ? N / 2 : 0) + (size_t)(b[0] >> 1) + (size_t)(nx >> 1) * (b[1] + (size_t)ny * b[2]);
-        T v = (hb == colour ? X : O)[idx];
-        v = bc_signed<BC>(v, mirror, f);
-        if (BC != BC_PERIODIC && clamped) v *= robin_ratio<T>(g, b[0], b[1], b[2], c[0], c[1], c[2]);
-        return v;
-    };
     const int p[3] = {2 * P + ((h + y + z) & 1), y, z};
-    if constexpr (BC == BC_SYM) {   // beyond an extrapolating face: the weighted in-box cells
-        if (g.extrap) {
-            int q[8][3], w[8];
-            const int ns = extrap_split(g, p, q, w);
-            if (ns) {
-                T s = 0;
-                for (int t = 0; t < ns; ++t) s += (T)w[t] * one(q[t]);
-                return s;
-            }
-        }
-    }
-    return one(p);
+    if constexpr (BC == BC_SYM)
+        if (g.extrap && beyond_extrap(g, p)) return tile_extrap<T, BC>(&g, X, O, colour, f, p[0], p[1], p[2]);
+    return tile_one<T, BC>(g, X, O, colour, f, p);
 }
 
 // ---------------------------------------------------------------- the plane ring
@@ -467,9 +475,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
             T dpsi = 0, dW[3] = {0, 0, 0};
             if constexpr (BC != BC_PERIODIC) {   // the true diagonal next to a face
                 const int x = 2 * (ring.P0 + lane) + ((COLOUR + y + z) & 1);
-                if (near_face(g, x, y, z))
-                    boundary_diag<T, ORDER, BC>(g, (T)(1.0 / (g.h[0] * g.h[0])), (T)(1.0 / (g.h[1] * g.h[1])),
-                                                (T)(1.0 / (g.h[2] * g.h[2])), x, y, z, &dpsi, dW);
+                if (near_face(g, x, y, z)) face_shifts(tc.fd, g, x, y, z, dpsi, dW);
             }
             Y[q] = ctr[0] + (fq[0] - Je[0]) / ((ca * (tc.dl + dpsi) + cb) * tc.iom);
 #pragma unroll
