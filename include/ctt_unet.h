@@ -22,14 +22,26 @@
 #ifndef CTT_UNET_H
 #define CTT_UNET_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
 
-/* y = act(conv3x3x3_circular(x, w) + bias); act = ReLU when relu != 0.  bias may be NULL. */
+/* y = act(conv3x3x3_circular(x, w) + bias); act = ReLU when relu != 0.  bias may be NULL.
+ * ws: optional FP32 device workspace of ws_bytes bytes (16-byte aligned), owned by the caller and
+ * used by this call only while its kernels run (one workspace per stream).  With ws, grids with
+ * fewer than two 128-voxel tiles per SM split the 27 taps over groups of CTAs and add the
+ * groups' FP32 partial sums in a fixed order (deterministic); with ws == NULL every grid runs
+ * the unsplit kernels.  The two forms round differently (FP32 summation order), each is
+ * deterministic.  ws_bytes below unet_conv3d_fwd_workspace() for the shape returns 1. */
 int unet_conv3d_fwd(const void *x, int xcs, int xc0, const void *w_bf16, const float *bias, void *y, int ycs,
-                    int yc0, int n0, int n1, int n2, int cin, int cout, int relu, long long spin_limit, int *err,
-                    void *stream);
+                    int yc0, int n0, int n1, int n2, int cin, int cout, int relu, float *ws, size_t ws_bytes,
+                    long long spin_limit, int *err, void *stream);
+
+/* Workspace bytes unet_conv3d_fwd needs for its split form on an n0 x n1 x n2 grid with cout
+ * output channels (0: that grid runs unsplit; also 0 for an unsupported shape). */
+size_t unet_conv3d_fwd_workspace(int n0, int n1, int n2, int cout);
 
 /* dw[27][cout][cin] += sum_v dy[v][co] x[v + tap][ci]  (dw FP32, accumulated; zero it first). */
 int unet_conv3d_wgrad(const void *x, int xcs, int xc0, const void *dy, int dcs, int dc0, float *dw, int n0, int n1,

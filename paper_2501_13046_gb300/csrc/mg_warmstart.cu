@@ -11,6 +11,7 @@
 // (cell-centred trilinear), both preserving the periodic means.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <vector>
@@ -60,6 +61,8 @@ struct WarmNet {
          *p2 = nullptr, *e2a = nullptr, *cat2 = nullptr, *p3 = nullptr, *ba = nullptr, *b = nullptr,
          *d2a = nullptr, *d2 = nullptr, *d1a = nullptr, *d1 = nullptr, *d0a = nullptr, *d0 = nullptr;
     float *out = nullptr;
+    float *ws = nullptr;                      // split-K partial sums of the small-grid convolutions
+    size_t ws_bytes = 0;
     int *err = nullptr;
     double *mean = nullptr;                   // means and the partials of their reductions (264)
     std::vector<void *> allocs;
@@ -173,6 +176,10 @@ mg_status warm_load(const char *path, cudaStream_t st, WarmNet **out)
             if ((s = dev_alloc(w, bb.bytes, bb.p)) != MG_OK) break;
         if (s != MG_OK) break;
         if ((s = dev_alloc_t(w, v0 * kHeadOut * sizeof(float), &w->out)) != MG_OK) break;
+        for (int l = 0; l < 14; ++l)
+            for (int m = n; m >= n / 8; m /= 2)
+                w->ws_bytes = std::max(w->ws_bytes, unet_conv3d_fwd_workspace(m, m, m, kConvs[l].cout));
+        if (w->ws_bytes && (s = dev_alloc_t(w, w->ws_bytes, &w->ws)) != MG_OK) break;
         if ((s = dev_alloc_t(w, sizeof(int), &w->err)) != MG_OK) break;
         if ((s = dev_alloc_t(w, 264 * sizeof(double), &w->mean)) != MG_OK) break;
         if (cudaMemsetAsync(w->err, 0, sizeof(int), st) != cudaSuccess ||
@@ -232,7 +239,7 @@ mg_status warm_forward(WarmNet *w, cudaStream_t st)
     const int s0 = w->n_net, s1 = s0 / 2, s2 = s1 / 2, s3 = s2 / 2;
     auto conv = [&](int l, const void *x, int xcs, int xc0, void *y, int ycs, int yc0, int n) {
         return unet_rc(unet_conv3d_fwd(x, xcs, xc0, w->wf[l], w->params + w->boff[l], y, ycs, yc0, n, n, n,
-                                       kConvs[l].cin, kConvs[l].cout, 1, kWarmSpin, w->err, st),
+                                       kConvs[l].cin, kConvs[l].cout, 1, w->ws, w->ws_bytes, kWarmSpin, w->err, st),
                        "convolution");
     };
     auto pool = [&](const void *x, int xcs, int xc0, void *y, int c, int n) {

@@ -23,6 +23,7 @@
 namespace unet {
 
 constexpr int kTile = 128;
+constexpr long long kDrain = 1LL << 26;   // polls allowed for MMAs in flight after a failed wait
 
 struct ConvArgs {
     const __nv_bfloat16 *x;
@@ -272,6 +273,137 @@ __global__ void __launch_bounds__(128) k_conv3d_blk(ConvArgs a)
     if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
+// Split-K form of k_conv3d_tc for grids with few 128-voxel tiles (the network's coarse levels):
+// blockIdx.y selects a group of taps [t0, t1); the CTA accumulates its tile over those taps in TMEM
+// and writes the FP32 partial sums to part[group][voxel][Cout].  k_conv3d_finish then adds the
+// groups in order (deterministic), adds the bias, applies ReLU and stores BF16.  Same gather,
+// double buffering and bounded waits as k_conv3d_tc.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) k_conv3d_split(ConvArgs a, int taps_per_group, float *__restrict__ part)
+{
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 128, "channel counts");
+    constexpr int NCOLS = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
+    constexpr uint32_t A_BYTES = kTile * CIN * 2, B_BYTES = COUT * CIN * 2;
+    constexpr uint32_t SBO_A = (CIN / 8) * 128, SBO_B = (CIN / 8) * 128;
+    constexpr uint32_t IDESC = idesc_bf16(kTile, COUT);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *Abuf = smem;
+    unsigned char *Bbuf = smem + 2 * A_BYTES;
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nx = a.n0, ny = a.n1, nz = a.n2;
+    const int v0 = blockIdx.x * kTile;
+    const int t0 = blockIdx.y * taps_per_group, t1 = min(27, t0 + taps_per_group), nt = t1 - t0;
+    if (warp == 0) tmem_alloc(&tmem_slot, NCOLS);
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    int issued = 0;
+    for (int s = 0; s < nt; ++s) {
+        const int buf = s & 1, tap = t0 + s;
+        if (s >= 2) {
+            if (tid == 0 && !failed && !mbar_wait_bounded(&mbar[buf], ((s - 2) >> 1) & 1, a.spin_limit)) failed = 1;
+            __syncthreads();
+            if (failed) break;
+        }
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        unsigned char *A = Abuf + buf * A_BYTES;
+        unsigned char *B = Bbuf + buf * B_BYTES;
+        constexpr int CH = CIN / 8;
+        for (int idx = tid; idx < kTile * CH; idx += 128) {
+            int r = idx / CH, c = idx - r * CH;
+            int v = v0 + r;
+            int i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
+            int nb = wrapi(i + dx, nx) + nx * (wrapi(j + dy, ny) + ny * wrapi(k + dz, nz));
+            uint4 val = *reinterpret_cast<const uint4 *>(a.x + (size_t)nb * a.xcs + a.xc0 + c * 8);
+            *reinterpret_cast<uint4 *>(A + (r >> 3) * SBO_A + c * 128 + (r & 7) * 16) = val;
+        }
+        const __nv_bfloat16 *wt = a.w + (size_t)tap * COUT * CIN;
+        for (int idx = tid; idx < COUT * CH; idx += 128) {
+            int r = idx / CH, c = idx - r * CH;
+            uint4 val = *reinterpret_cast<const uint4 *>(wt + r * CIN + c * 8);
+            *reinterpret_cast<uint4 *>(B + (r >> 3) * SBO_B + c * 128 + (r & 7) * 16) = val;
+        }
+        fence_proxy_async();
+        fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after_sync();
+            const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+#pragma unroll
+            for (int kk = 0; kk < CIN / 16; ++kk)
+                mma_bf16(tmem, smem_desc(a0 + kk * 256, 128, SBO_A), smem_desc(b0 + kk * 256, 128, SBO_B), IDESC,
+                         (s > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&mbar[buf]);
+        }
+        ++issued;
+    }
+    // the last group member's commit on its buffer; MMAs complete in order.  After a failed wait the
+    // drain gets a floor (kDrain polls) so that no MMA still reads shared memory when the CTA exits.
+    if (tid == 0 && issued > 0) {
+        const int last = issued - 1;
+        bool ok = !failed && mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, a.spin_limit);
+        if (!ok) {
+            failed = 1;
+            mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, a.spin_limit > kDrain ? a.spin_limit : kDrain);
+        }
+    }
+    __syncthreads();
+    fence_after_sync();
+    if (!failed && issued > 0) {
+        const int row = warp * 32 + lane;
+        float *dst = part + ((size_t)blockIdx.y * a.n0 * a.n1 * a.n2 + (size_t)(v0 + row)) * COUT;
+#pragma unroll
+        for (int cc = 0; cc < COUT / 16; ++cc) {
+            float acc[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc * 16, acc);
+#pragma unroll
+            for (int q = 0; q < 16; q += 4)
+                *reinterpret_cast<float4 *>(dst + cc * 16 + q) = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
+        }
+    } else if (failed && tid == 0) {
+        atomicExch(a.err, 1);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+// y = act(sum over groups of part + bias), BF16, 8 output channels per thread.
+template <int COUT>
+__global__ void __launch_bounds__(256) k_conv3d_finish(ConvArgs a, int groups, const float *__restrict__ part)
+{
+    const long long nvox = (long long)a.n0 * a.n1 * a.n2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nvox * (COUT / 8);
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long v = e / (COUT / 8);
+        const int c0 = (int)(e - v * (COUT / 8)) * 8;
+        float t[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t[q] = a.bias ? a.bias[c0 + q] : 0.f;
+        for (int g = 0; g < groups; ++g) {
+            const float *pp = part + ((size_t)g * nvox + v) * COUT + c0;
+            const float4 lo = *reinterpret_cast<const float4 *>(pp), hi = *reinterpret_cast<const float4 *>(pp + 4);
+            t[0] += lo.x; t[1] += lo.y; t[2] += lo.z; t[3] += lo.w;
+            t[4] += hi.x; t[5] += hi.y; t[6] += hi.z; t[7] += hi.w;
+        }
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = __float2bfloat16_rn(a.relu ? fmaxf(t[q], 0.f) : t[q]);
+        *reinterpret_cast<uint4 *>(a.y + v * a.ycs + a.yc0 + c0) = *reinterpret_cast<uint4 *>(o);
+    }
+}
+
 struct WgradArgs {
     const __nv_bfloat16 *x;
     int xcs, xc0;
@@ -416,9 +548,45 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad_tc(WgradArgs a)
 namespace unet {
 namespace {
 
-template <int CIN, int COUT>
-int launch_fwd(const ConvArgs &a, int nvox, cudaStream_t st)
+constexpr int kSms = 152;
+
+// Split-K plan of a forward convolution: taps per group and number of groups (1: no split).  The
+// taps are split where the grid has fewer than two 128-voxel tiles per SM, into enough groups for
+// about two CTAs per SM in all.
+struct SplitPlan {
+    int tpg, groups;
+};
+
+SplitPlan split_plan(long long nvox)
 {
+    const long long tiles = nvox / kTile;
+    if (tiles <= 0 || tiles >= 2 * kSms) return {27, 1};
+    const int want = (int)std::min<long long>(27, (2 * kSms + tiles - 1) / tiles);
+    const int tpg = (27 + want - 1) / want;
+    return {tpg, (27 + tpg - 1) / tpg};
+}
+
+template <int CIN, int COUT>
+int launch_fwd(const ConvArgs &a, int nvox, float *ws, cudaStream_t st)
+{
+    constexpr size_t smem = 2 * (kTile * CIN * 2) + 2 * (COUT * CIN * 2);
+    const int tiles = nvox / kTile;
+    const SplitPlan sp = split_plan(nvox);
+    if (ws && sp.groups > 1) {
+        const int groups = sp.groups, tpg = sp.tpg;
+        float *part = ws;
+        static bool attr_split = false;
+        if (!attr_split) {
+            if (cudaFuncSetAttribute(k_conv3d_split<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return 3;
+            attr_split = true;
+        }
+        k_conv3d_split<CIN, COUT><<<dim3(tiles, groups), 128, smem, st>>>(a, tpg, part);
+        const long long work = (long long)nvox * (COUT / 8);
+        k_conv3d_finish<COUT><<<(int)std::min<long long>((work + 255) / 256, 152LL * 16), 256, 0, st>>>(a, groups, part);
+        return cudaGetLastError() == cudaSuccess ? 0 : 3;
+    }
     // block-tile kernel where the grid tiles evenly and the block and all weights fit in shared memory
     constexpr int ZT = 2;
     constexpr size_t bsm = blk_smem_bytes<CIN, COUT, ZT>();
@@ -436,7 +604,6 @@ int launch_fwd(const ConvArgs &a, int nvox, cudaStream_t st)
             return cudaGetLastError() == cudaSuccess ? 0 : 3;
         }
     }
-    constexpr size_t smem = 2 * (kTile * CIN * 2) + 2 * (COUT * CIN * 2);
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(k_conv3d_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -444,7 +611,7 @@ int launch_fwd(const ConvArgs &a, int nvox, cudaStream_t st)
             return 3;
         attr = true;
     }
-    k_conv3d_tc<CIN, COUT><<<nvox / kTile, 128, smem, st>>>(a);
+    k_conv3d_tc<CIN, COUT><<<tiles, 128, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
@@ -478,31 +645,41 @@ int launch_wgrad(const WgradArgs &a0, int nvox, cudaStream_t st)
 
 using namespace unet;
 
+extern "C" size_t unet_conv3d_fwd_workspace(int n0, int n1, int n2, int cout)
+{
+    const long long nvox = (long long)n0 * n1 * n2;
+    if (n0 <= 0 || n1 <= 0 || n2 <= 0 || cout <= 0 || nvox % kTile) return 0;
+    const SplitPlan sp = split_plan(nvox);
+    return sp.groups > 1 ? (size_t)sp.groups * (size_t)nvox * (size_t)cout * sizeof(float) : 0;
+}
+
 extern "C" int unet_conv3d_fwd(const void *x, int xcs, int xc0, const void *w_bf16, const float *bias, void *y,
-                               int ycs, int yc0, int n0, int n1, int n2, int cin, int cout, int relu,
-                               long long spin_limit, int *err, void *stream)
+                               int ycs, int yc0, int n0, int n1, int n2, int cin, int cout, int relu, float *ws,
+                               size_t ws_bytes, long long spin_limit, int *err, void *stream)
 {
     long long nvox = (long long)n0 * n1 * n2;
     if (!x || !w_bf16 || !y || !err || nvox <= 0 || nvox % kTile || (xcs | xc0 | ycs | yc0) % 8 ||
         xc0 + cin > xcs || yc0 + cout > ycs)
         return 1;
+    if (ws && (ws_bytes < unet_conv3d_fwd_workspace(n0, n1, n2, cout) || (reinterpret_cast<size_t>(ws) & 15)))
+        return 1;
     ConvArgs a{(const __nv_bfloat16 *)x, xcs, xc0, (const __nv_bfloat16 *)w_bf16, bias, (__nv_bfloat16 *)y,
                ycs, yc0, n0, n1, n2, relu, spin_limit, err};
     cudaStream_t st = (cudaStream_t)stream;
     switch (PAIR(cin, cout)) {
-    case PAIR(16, 16): return launch_fwd<16, 16>(a, (int)nvox, st);
-    case PAIR(16, 32): return launch_fwd<16, 32>(a, (int)nvox, st);
-    case PAIR(16, 48): return launch_fwd<16, 48>(a, (int)nvox, st);
-    case PAIR(32, 16): return launch_fwd<32, 16>(a, (int)nvox, st);
-    case PAIR(32, 32): return launch_fwd<32, 32>(a, (int)nvox, st);
-    case PAIR(32, 64): return launch_fwd<32, 64>(a, (int)nvox, st);
-    case PAIR(32, 96): return launch_fwd<32, 96>(a, (int)nvox, st);
-    case PAIR(48, 16): return launch_fwd<48, 16>(a, (int)nvox, st);
-    case PAIR(64, 32): return launch_fwd<64, 32>(a, (int)nvox, st);
-    case PAIR(64, 64): return launch_fwd<64, 64>(a, (int)nvox, st);
-    case PAIR(64, 128): return launch_fwd<64, 128>(a, (int)nvox, st);
-    case PAIR(96, 32): return launch_fwd<96, 32>(a, (int)nvox, st);
-    case PAIR(128, 64): return launch_fwd<128, 64>(a, (int)nvox, st);
+    case PAIR(16, 16): return launch_fwd<16, 16>(a, (int)nvox, ws, st);
+    case PAIR(16, 32): return launch_fwd<16, 32>(a, (int)nvox, ws, st);
+    case PAIR(16, 48): return launch_fwd<16, 48>(a, (int)nvox, ws, st);
+    case PAIR(32, 16): return launch_fwd<32, 16>(a, (int)nvox, ws, st);
+    case PAIR(32, 32): return launch_fwd<32, 32>(a, (int)nvox, ws, st);
+    case PAIR(32, 64): return launch_fwd<32, 64>(a, (int)nvox, ws, st);
+    case PAIR(32, 96): return launch_fwd<32, 96>(a, (int)nvox, ws, st);
+    case PAIR(48, 16): return launch_fwd<48, 16>(a, (int)nvox, ws, st);
+    case PAIR(64, 32): return launch_fwd<64, 32>(a, (int)nvox, ws, st);
+    case PAIR(64, 64): return launch_fwd<64, 64>(a, (int)nvox, ws, st);
+    case PAIR(64, 128): return launch_fwd<64, 128>(a, (int)nvox, ws, st);
+    case PAIR(96, 32): return launch_fwd<96, 32>(a, (int)nvox, ws, st);
+    case PAIR(128, 64): return launch_fwd<128, 64>(a, (int)nvox, ws, st);
     default: return 1;
     }
 }

@@ -11,7 +11,8 @@ _lib = _mg.lib()
 vp, i32, i64, f32, f64 = C.c_void_p, C.c_int, C.c_longlong, C.c_float, C.c_double
 
 _SIGS = {
-    "unet_conv3d_fwd": [vp, i32, i32, vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, i64, vp, vp],
+    "unet_conv3d_fwd": [vp, i32, i32, vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, C.c_size_t, i64, vp,
+                        vp],
     "unet_conv3d_wgrad": [vp, i32, i32, vp, i32, i32, vp, i32, i32, i32, i32, i32, i64, vp, vp],
     "unet_pack_weights": [vp, i32, i32, i32, vp, vp],
     "unet_avgpool2": [vp, i32, i32, vp, i32, i32, i32, i32, i32, i32, vp],
@@ -33,6 +34,8 @@ _SIGS = {
 for _n, _a in _SIGS.items():
     getattr(_lib, _n).argtypes = _a
     getattr(_lib, _n).restype = C.c_int
+_lib.unet_conv3d_fwd_workspace.argtypes = [i32, i32, i32, i32]
+_lib.unet_conv3d_fwd_workspace.restype = C.c_size_t
 
 SPIN = 1 << 22
 
@@ -60,10 +63,17 @@ def as_slice(t):
     return t if isinstance(t, Slice) else Slice(t)
 
 
-def conv3d_fwd(x, w_bf16, bias, y, n, cin, cout, relu, err, stream=0):
+def conv3d_workspace(n, cout):
+    """Bytes of FP32 workspace conv3d_fwd's split form needs on grid n with cout channels (0: none)."""
+    return int(_lib.unet_conv3d_fwd_workspace(n[0], n[1], n[2], cout))
+
+
+def conv3d_fwd(x, w_bf16, bias, y, n, cin, cout, relu, err, stream=0, ws=None):
+    """ws: optional FP32 device tensor (the split-K workspace); None runs the unsplit kernels."""
     x, y = as_slice(x), as_slice(y)
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _call("unet_conv3d_fwd", _p(x.buf), x.cs, x.c0, _p(w_bf16), _p(bias), _p(y.buf), y.cs, y.c0, n[0], n[1], n[2],
-          cin, cout, int(relu), SPIN, _p(err), stream)
+          cin, cout, int(relu), _p(ws), wsb, SPIN, _p(err), stream)
 
 
 def conv3d_wgrad(x, dy, dw, n, cin, cout, err, stream=0):

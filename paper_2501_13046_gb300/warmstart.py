@@ -99,6 +99,10 @@ class Net:
         self.out = torch.zeros((sz[0], sz[0], sz[0], COUT), dtype=torch.float32, device=device)
         self.err = torch.zeros(1, dtype=torch.int32, device=device)
         self.mean = torch.zeros(264, dtype=torch.float64, device=device)   # means + reduction partials
+        # split-K workspace of the small-grid convolutions (forward and input-gradient), the largest any takes
+        wsb = max(U.conv3d_workspace((m, m, m), c) for m in sz for c in sorted({c[1] for c in CONVS} |
+                                                                              {c[2] for c in CONVS}))
+        self.ws = torch.empty(max(wsb // 4, 4), dtype=torch.float32, device=device)
         if train:
             self.g = {k: torch.zeros_like(v) for k, v in self.a.items()}
             self.gcat0, self.gcat1, self.gcat2 = (torch.zeros_like(self.cat0), torch.zeros_like(self.cat1),
@@ -119,7 +123,7 @@ class Net:
     def _conv(self, name, x, y, n, stream):
         _, cin, cout = next(c for c in CONVS if c[0] == name)
         _, b = self.P.view(self.P.p, name)
-        U.conv3d_fwd(x, self.P.wf[name], b, y, (n, n, n), cin, cout, True, self.err, stream)
+        U.conv3d_fwd(x, self.P.wf[name], b, y, (n, n, n), cin, cout, True, self.err, stream, self.ws)
 
     def forward(self, stream=0):
         a, s = self.a, self.sz
@@ -155,7 +159,7 @@ class Net:
         U.bias_grad(dy, db, cout, nvox, stream)
         U.conv3d_wgrad(x, dy, dW, (n, n, n), cin, cout, self.err, stream)
         if dx is not None:
-            U.conv3d_fwd(dy, self.P.wb[name], None, dx, (n, n, n), cout, cin, False, self.err, stream)
+            U.conv3d_fwd(dy, self.P.wb[name], None, dx, (n, n, n), cout, cin, False, self.err, stream, self.ws)
 
     def backward(self, stream=0):
         """Gradients of the MSE loss (self.dout must hold dL/d out) accumulated into P.g."""

@@ -9,12 +9,13 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "ctt_mg.h")
+UNET_HEADER = os.path.join(ROOT, "include", "ctt_unet.h")
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER, prefix="mg_"):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mg_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(%s[a-z_0-9]+)\s*\(" % prefix, text)))
 
 
 @pytest.fixture(scope="module")
@@ -32,6 +33,36 @@ def test_library_exports_every_declared_symbol(lib):
     for n in names:
         assert hasattr(raw, n), n
     assert set(names) <= set(lib.EXPORTS) | {"mg_config_default"}
+
+
+def test_library_exports_every_network_entry_point(lib):
+    names = declared_functions(UNET_HEADER, "unet_")
+    assert "unet_conv3d_fwd" in names and "unet_conv3d_fwd_workspace" in names
+    raw = C.CDLL(lib.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+
+
+def test_split_convolution_workspace_query(lib):
+    """Host-side plan of the split-K convolutions: grids with fewer than 2 x 152 tiles of 128
+    voxels split the 27 taps into groups for about two CTAs per SM; the workspace holds one FP32
+    partial per group, voxel and output channel."""
+    from paper_2501_13046_gb300 import unet as U
+    f = 4
+
+    def groups(tiles):
+        want = min(27, -(-304 // tiles))
+        tpg = -(-27 // want)
+        return -(-27 // tpg)
+
+    assert groups(4) == 27 and groups(32) == 9 and groups(256) == 2
+    assert U.conv3d_workspace((8, 8, 8), 64) == 27 * 512 * 64 * f          # 4 tiles: one tap per group
+    assert U.conv3d_workspace((16, 16, 16), 64) == 9 * 4096 * 64 * f       # 32 tiles: 3 taps per group
+    assert U.conv3d_workspace((32, 32, 32), 32) == 2 * 32768 * 32 * f      # 256 tiles: 14 + 13 taps
+    assert U.conv3d_workspace((64, 32, 19), 16) == 0                        # 304 tiles: unsplit
+    assert U.conv3d_workspace((64, 64, 64), 16) == 0
+    assert U.conv3d_workspace((8, 8, 3), 16) == 0                           # not a multiple of 128 voxels
+    assert U.conv3d_workspace((0, 8, 8), 16) == 0
 
 
 def test_config_defaults_and_workspace_size(lib):

@@ -169,3 +169,73 @@ def test_conv_block_tiles_on_channel_slices_and_input_gradient(U):
     assert int(err.item()) == 0
     scale2 = R.conv_dgrad(np.abs(dy), np.abs(w2))
     assert np.all(np.abs(tohost(dx) - ref2) <= 2 ** -8 * np.abs(ref2) + 1e-5 * scale2 + 1e-6)
+
+
+SPLIT_SHAPES = [(8, 8, 8), (16, 8, 4), (16, 16, 16), (32, 16, 32)]   # 4, 4, 32 and 128 tiles: 27, 27, 9, 3 groups
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 64), (64, 64), (128, 64), (96, 32), (48, 16)])
+@pytest.mark.parametrize("shape", SPLIT_SHAPES)
+def test_conv_forward_split_taps(U, cin, cout, shape):
+    """The split-K form (taps in groups of CTAs, FP32 partials added in group order): the same bound
+    against the FP64 oracle, bitwise repeatable, and a workspace below the query is rejected."""
+    nz, ny, nx = shape[2], shape[1], shape[0]
+    rng = np.random.default_rng(cin * 31 + cout * 7 + nx * ny * nz)
+    x = R.bf16_round(rng.standard_normal((nz, ny, nx, cin)))
+    w = R.bf16_round(rng.standard_normal((27, cout, cin)) / np.sqrt(27 * cin))
+    b = rng.standard_normal(cout).astype(np.float32)
+    wp = torch.empty(w.shape, dtype=torch.bfloat16, device="cuda")
+    U.pack_weights(torch.from_numpy(w.astype(np.float32)).cuda(), cin, cout, 0, wp)
+    wsb = U.conv3d_workspace((nx, ny, nz), cout)
+    assert wsb > 0
+    ws = torch.full((wsb // 4,), float("nan"), dtype=torch.float32, device="cuda")
+    xt, bt = bf16(x), torch.from_numpy(b).cuda()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for relu in (False, True):
+        ref = R.conv_fwd(x, w, b.astype(np.float64), relu=relu)
+        ys = []
+        for _ in range(2):
+            y = torch.zeros((nz, ny, nx, cout), dtype=torch.bfloat16, device="cuda")
+            U.conv3d_fwd(xt, wp, bt, y, (nx, ny, nz), cin, cout, relu, err, ws=ws)
+            ys.append(y)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        assert torch.equal(ys[0], ys[1])
+        scale = R.conv_fwd(np.abs(x), np.abs(w))
+        assert np.all(np.abs(tohost(ys[0]) - ref) <= 2 ** -8 * np.abs(ref) + 1e-5 * scale + 1e-6)
+    with pytest.raises(RuntimeError):
+        U.conv3d_fwd(xt, wp, bt, ys[0], (nx, ny, nz), cin, cout, False, err, ws=ws[: wsb // 4 - 4])
+
+
+def test_conv_split_taps_on_channel_slices_and_input_gradient(U):
+    """Split-K form on channel slices (input [16, 48) of 64, output [32, 48) of 48; the rest
+    untouched) and as the input gradient of a (32 -> 96) layer on a 16^3 grid."""
+    from paper_2501_13046_gb300.unet import Slice
+    nx, ny, nz, cin, cout = 16, 16, 16, 32, 16
+    rng = np.random.default_rng(55)
+    big = R.bf16_round(rng.standard_normal((nz, ny, nx, 64)))
+    w = R.bf16_round(rng.standard_normal((27, cout, cin)) / 20)
+    ref = R.conv_fwd(big[..., 16:48], w)
+    wp = torch.empty(w.shape, dtype=torch.bfloat16, device="cuda")
+    U.pack_weights(torch.from_numpy(w.astype(np.float32)).cuda(), cin, cout, 0, wp)
+    ws = torch.empty(U.conv3d_workspace((nx, ny, nz), 96) // 4, dtype=torch.float32, device="cuda")
+    ybuf = torch.full((nz, ny, nx, 48), 7.0, dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U.conv3d_fwd(Slice(bf16(big), 16, 32), wp, None, Slice(ybuf, 32, 16), (nx, ny, nz), cin, cout, False, err,
+                 ws=ws)
+    torch.cuda.synchronize()
+    out = tohost(ybuf)
+    assert np.all(out[..., :32] == 7.0)
+    scale = R.conv_fwd(np.abs(big[..., 16:48]), np.abs(w))
+    assert np.all(np.abs(out[..., 32:48] - ref) <= 2 ** -8 * np.abs(ref) + 1e-5 * scale + 1e-6)
+    dy = R.bf16_round(rng.standard_normal((nz, ny, nx, 96)))
+    w2 = R.bf16_round(rng.standard_normal((27, 96, 32)) / 10)
+    ref2 = R.conv_dgrad(dy, w2)
+    wp2 = torch.empty((27, 32, 96), dtype=torch.bfloat16, device="cuda")
+    U.pack_weights(torch.from_numpy(w2.astype(np.float32)).cuda(), 32, 96, 1, wp2)
+    dx = torch.zeros((nz, ny, nx, 32), dtype=torch.bfloat16, device="cuda")
+    U.conv3d_fwd(bf16(dy), wp2, None, dx, (nx, ny, nz), 96, 32, False, err, ws=ws)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    scale2 = R.conv_dgrad(np.abs(dy), np.abs(w2))
+    assert np.all(np.abs(tohost(dx) - ref2) <= 2 ** -8 * np.abs(ref2) + 1e-5 * scale2 + 1e-6)
