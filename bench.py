@@ -35,6 +35,14 @@ WORKLOAD = dict(workload="periodic random-mode cosmology, L=32, 128^3, 4th-order
                 n=128, order=4, bc="periodic", levels=6, tol=1e-10, cells=128 ** 3)
 
 
+_T0 = time.perf_counter()
+
+
+def phase(name):
+    """Progress of the benchmark's phases on stderr (the result line goes to stdout)."""
+    print("[bench %7.1f s] %s" % (time.perf_counter() - _T0, name), file=sys.stderr, flush=True)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -503,6 +511,7 @@ def main():
     __graft_entry__.build()
     from paper_2501_13046_gb300 import mg
 
+    phase("inputs")
     p = make_problem()
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
@@ -522,6 +531,7 @@ def main():
         mg.mg_set_sources(ctx, *src_dev)
         return ctx, work
 
+    phase("fp64 context and tuning")
     # ---- plain FP64 multigrid (context for the comparison)
     ctx64, w64 = context(mg.MG_FP64)
     solve_loop(mg, torch, ctx64, 1, stream)
@@ -530,6 +540,7 @@ def main():
     mg.mg_destroy(ctx64)
     del w64
 
+    phase("mixed context and tuning")
     # ---- the benchmarked path: mixed FP32/FP64
     ctx, work = context(mg.MG_MIXED)
     solve_loop(mg, torch, ctx, args.warmup, stream)
@@ -544,6 +555,7 @@ def main():
     value = replicas.job_throughput(args.steps, secs, ws)
     launches = info["kernel_launches"] * args.steps
 
+    phase("timed region done")
     # per-field error of the timed solve (the last one) against the oracle's stored root
     gold = golden("modes_periodic_%d" % WORKLOAD["n"])
     shape = p["rho0"].shape
@@ -593,6 +605,7 @@ def main():
     mg.mg_destroy(ctx)
     del work
     torch.cuda.empty_cache()
+    phase("shell")
     shell = {}
     q = fields_mod().puncture_shell(n=256)
     qsrc = [dev(a) for a in (q["rho0"], q["rho2"], *q["S"])]
@@ -647,6 +660,7 @@ def main():
     del qosrc
     del qsrc
     torch.cuda.empty_cache()
+    phase("binary")
     # Bowen-York binary (two boosted, spinning punctures and a scalar shell), 128^3, nested start
     bq = fields_mod().bowen_york_binary(n=128)
     bsrc = [dev(a) for a in (bq["rho0"], bq["rho2"], *bq["S"])]
@@ -669,6 +683,7 @@ def main():
         break
     del bsrc
     torch.cuda.empty_cache()
+    phase("sine 32")
     # the 32^3 sine workload (2nd order, L = 16, 4 levels): both precisions
     c1 = fields_mod().sine_periodic(n=32)
     c1src = [dev(a) for a in (c1["rho0"], c1["rho2"], *c1["S"])]
@@ -682,8 +697,10 @@ def main():
         sine32[name] = {"solves_per_s": 20 / t1, "outer_iters": i1["outer_iters"], "max_norm": float(i1["norms"].max())}
         mg.mg_destroy(cx)
     del c1src
+    phase("batch mixed")
     batch_mixed = batch_measure(mg, torch, sp, mg.MG_MIXED, repeats=2)
     torch.cuda.empty_cache()
+    phase("batch fp64")
     batch_fp64 = batch_measure(mg, torch, sp, mg.MG_FP64, repeats=1)
     torch.cuda.empty_cache()
 
@@ -694,6 +711,7 @@ def main():
         return 0
     cpu = None
     if not args.no_cpu_baseline:
+        phase("oracle baseline")
         ncpu = os.cpu_count() or 1
         v, det = oracle_full_size(p, ncpu)
         v1, det1 = oracle_full_size(p, 1)
@@ -742,6 +760,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic",
             "config": cfgd, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary()}
+    phase("done")
     print(json.dumps(line))
     return 0
 
