@@ -34,7 +34,8 @@ extern "C" {
  * fewer than two 128-voxel tiles per SM split the 27 taps over groups of CTAs and add the
  * groups' FP32 partial sums in a fixed order (deterministic); with ws == NULL every grid runs
  * the unsplit kernels.  The two forms round differently (FP32 summation order), each is
- * deterministic.  ws_bytes below unet_conv3d_fwd_workspace() for the shape returns 1. */
+ * deterministic.  ws_bytes below unet_conv3d_fwd_workspace() for the shape returns 1, and so does
+ * a side of 1024 or more. */
 int unet_conv3d_fwd(const void *x, int xcs, int xc0, const void *w_bf16, const float *bias, void *y, int ycs,
                     int yc0, int n0, int n1, int n2, int cin, int cout, int relu, float *ws, size_t ws_bytes,
                     long long spin_limit, int *err, void *stream);
@@ -51,7 +52,9 @@ int unet_conv3d_wgrad(const void *x, int xcs, int xc0, const void *dy, int dcs, 
  * mode 1 (input gradient) -> [27][cin][cout] with tap t read from 26 - t. */
 int unet_pack_weights(const float *w, int cin, int cout, int mode, void *out_bf16, void *stream);
 
-/* 2x2x2 average pooling (y coarse) and its adjoint (dx fine; accumulate != 0 adds into dx). */
+/* 2x2x2 average pooling (y coarse) and its adjoint (dx fine; accumulate != 0 adds into dx).
+ * unet_avgpool2 and unet_upsample2 move 8 channels (16 bytes) per thread: c, the channel strides
+ * and offsets must be multiples of 8 (else 1). */
 int unet_avgpool2(const void *x, int xcs, int xc0, void *y, int ycs, int yc0, int c, int n0, int n1, int n2,
                   void *stream);
 int unet_avgpool2_bwd(const void *dy, int dcs, int dc0, void *dx, int xcs, int xc0, int c, int n0, int n1, int n2,

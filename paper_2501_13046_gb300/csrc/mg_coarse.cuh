@@ -313,13 +313,11 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
                     const int q = i + g.n[0] * row, qo = q + 1 - 2 * par;   // the pair's other cell
                     T Je[4], ctr[4];
                     apply(cur, i, j, k, cs[q], cs[N + q], Je, ctr);
-                    T dpsi = 0, dW[3] = {0, 0, 0};
-                    if constexpr (BC != BC_PERIODIC)
-                        if (near_face(g, i, j, k)) face_shifts(cf.fd, g, i, j, k, dpsi, dW);
-                    alt[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * (cf.dl + dpsi) + cs[N + q]) * cf.iom);
+                    T dl, kW[3];
+                    relax_factors<BC>(cf.fd, g, i, j, k, true, cf.dl, cf.idW, cf.iom, dl, kW);
+                    alt[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * dl + cs[N + q]) * cf.iom);
                     for (int a = 0; a < 3; ++a)
-                        alt[(1 + a) * N + q] =
-                            ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * shifted_idW(cf.idW[a], cf.iom, dW[a]);
+                        alt[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * kW[a];
                     for (int a = 0; a < 4; ++a) alt[a * N + qo] = cur[a * N + qo];
                 }
                 __syncthreads();

@@ -400,6 +400,29 @@ __device__ __forceinline__ void face_shifts(const FaceDiag<T> &fd, const Geo &g,
 template <typename T>
 __device__ __forceinline__ T shifted_idW(T idW, T iom, T d) { return idW / ((T)1 + d * idW * iom); }
 
+// Relaxation factors of a cell: the psi row's Laplacian diagonal dl and the W rows' omega /
+// diagonal kW.  The interior values, except on boxes with faces for a cell within 2 cells of one
+// (may_be_near: the caller cannot rule that out), where the face shifts are added; periodic
+// levels and interior cells do no extra arithmetic.
+template <int BC, typename T>
+__device__ __forceinline__ void relax_factors(const FaceDiag<T> &fd, const Geo &g, int i, int j, int k,
+                                              bool may_be_near, T dl0, const T idW[3], T iom, T &dl, T kW[3])
+{
+    dl = dl0;
+    kW[0] = idW[0];
+    kW[1] = idW[1];
+    kW[2] = idW[2];
+    if constexpr (BC != BC_PERIODIC) {
+        if (may_be_near && near_face(g, i, j, k)) {
+            T dpsi, dW[3];
+            face_shifts(fd, g, i, j, k, dpsi, dW);
+            dl = dl0 + dpsi;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) kW[a] = shifted_idW(idW[a], iom, dW[a]);
+        }
+    }
+}
+
 // Accessors: value at cell p + (dx, dy, dz) of one field.
 template <typename T>
 struct AccI {   // every offset of the stencil stays inside the box
@@ -704,13 +727,11 @@ __device__ __forceinline__ void smooth_cell(const Geo &g, const Coef<T> &cf, con
     T Je[4], ctr[4];
     if (interior) apply_J_split<T, ORDER, BC, true>(X, O, N, g, i, j, k, ca, cb, cf, Je, ctr);
     else apply_J_split<T, ORDER, BC, false>(X, O, N, g, i, j, k, ca, cb, cf, Je, ctr);
-    T dpsi = 0, dW[3] = {0, 0, 0};
-    if constexpr (BC != BC_PERIODIC)
-        if (!interior && near_face(g, i, j, k)) face_shifts(cf.fd, g, i, j, k, dpsi, dW);
-    Y[q] = ctr[0] + (f[q] - Je[0]) / ((ca * (cf.dl + dpsi) + cb) * cf.iom);
+    T dl, kW[3];
+    relax_factors<BC>(cf.fd, g, i, j, k, !interior, cf.dl, cf.idW, cf.iom, dl, kW);
+    Y[q] = ctr[0] + (f[q] - Je[0]) / ((ca * dl + cb) * cf.iom);
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        Y[(1 + a) * N + q] = ctr[1 + a] + (f[(1 + a) * N + q] - Je[1 + a]) * shifted_idW(cf.idW[a], cf.iom, dW[a]);
+    for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (f[(1 + a) * N + q] - Je[1 + a]) * kW[a];
 }
 
 // The shell path is a call: only shell blocks execute it, and it leaves the interior path its registers.
@@ -1298,12 +1319,11 @@ __global__ void __launch_bounds__(512) k_coarse_solve(Geo g, Coef<T> cf, const T
                     AccB<T, BC> a0{eA, 0, &g, i, j, k}, a1{eA + N, 1, &g, i, j, k}, a2{eA + 2 * N, 2, &g, i, j, k},
                         a3{eA + 3 * N, 3, &g, i, j, k};
                     apply_J<ORDER, T>(a0, a1, a2, a3, cs[q], cs[N + q], cf, Je, ctr);
-                    T dpsi = 0, dW[3] = {0, 0, 0};
-                    if constexpr (BC != BC_PERIODIC)
-                        if (near_face(g, i, j, k)) face_shifts(cf.fd, g, i, j, k, dpsi, dW);
-                    eB[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * (cf.dl + dpsi) + cs[N + q]) * cf.iom);
+                    T dl, kW[3];
+                    relax_factors<BC>(cf.fd, g, i, j, k, true, cf.dl, cf.idW, cf.iom, dl, kW);
+                    eB[q] = ctr[0] + (fs[q] - Je[0]) / ((cs[q] * dl + cs[N + q]) * cf.iom);
                     for (int a = 0; a < 3; ++a)
-                        eB[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * shifted_idW(cf.idW[a], cf.iom, dW[a]);
+                        eB[(1 + a) * N + q] = ctr[1 + a] + (fs[(1 + a) * N + q] - Je[1 + a]) * kW[a];
                 } else {
                     for (int a = 0; a < 4; ++a) eB[a * N + q] = eA[a * N + q];
                 }

@@ -472,15 +472,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
             T Je[4], ctr[4];
             if ((COLOUR + y + z) & 1) tile_apply<T, ORDER, COLOUR, 1>(ring.sm, ob, ca, cb, tc, Je, ctr);
             else tile_apply<T, ORDER, COLOUR, 0>(ring.sm, ob, ca, cb, tc, Je, ctr);
-            T dpsi = 0, dW[3] = {0, 0, 0};
-            if constexpr (BC != BC_PERIODIC) {   // the true diagonal next to a face
-                const int x = 2 * (ring.P0 + lane) + ((COLOUR + y + z) & 1);
-                if (near_face(g, x, y, z)) face_shifts(tc.fd, g, x, y, z, dpsi, dW);
-            }
-            Y[q] = ctr[0] + (fq[0] - Je[0]) / ((ca * (tc.dl + dpsi) + cb) * tc.iom);
+            T dl, kW[3];   // the true diagonal next to a face (boxes with faces only)
+            relax_factors<BC>(tc.fd, g, 2 * (ring.P0 + lane) + ((COLOUR + y + z) & 1), y, z, true, tc.dl, tc.idW, tc.iom,
+                              dl, kW);
+            Y[q] = ctr[0] + (fq[0] - Je[0]) / ((ca * dl + cb) * tc.iom);
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                Y[(1 + a) * N + q] = ctr[1 + a] + (fq[1 + a] - Je[1 + a]) * shifted_idW(tc.idW[a], tc.iom, dW[a]);
+            for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (fq[1 + a] - Je[1 + a]) * kW[a];
         }
     }
     ring.finish(failed, err);

@@ -5,13 +5,16 @@
 // Weights: FP32 master [27 taps][Cout][Cin] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)), packed to
 // BF16 in the same order for the forward pass.
 //
-// Forward / input gradient (k_conv3d_tc): one CTA = 128 consecutive output voxels x all Cout.
-// For each of the 27 taps the CTA gathers the shifted input rows (128 x Cin, wrapped) and the
-// tap's weights (Cout x Cin) into shared memory in the canonical K-major core-matrix layout and
-// thread 0 issues Cin/16 MMAs (M = 128, N = Cout, K = 16) accumulating in TMEM; buffers are
-// double-buffered and recycled when the tap's commit arrives.  Epilogue: TMEM -> registers,
-// + bias, ReLU, BF16, store.  The input gradient of a convolution is the convolution of the
-// output gradient with the tap-flipped, transposed weights, so it reuses this kernel.
+// Forward / input gradient: volumes that tile by 8 x 16 x 2 voxels (with the input block and all
+// weights in shared memory) take the block-tile kernel k_conv3d_blk (below); the others take the
+// per-tap kernel k_conv3d_taps: one CTA = 128 consecutive output voxels x all Cout; for each of
+// the 27 taps the shifted input rows (128 x Cin, wrapped) and the tap's weights (Cout x Cin) are
+// staged in shared memory in the canonical K-major core-matrix layout and thread 0 issues Cin/16
+// MMAs (M = 128, N = Cout, K = 16) accumulating in TMEM; buffers are double-buffered and recycled
+// when the tap's commit arrives.  Epilogue: TMEM -> registers, + bias, ReLU, BF16, store.  Grids
+// with few tiles split the taps over groups of CTAs that write FP32 partials, added in order by
+// k_conv3d_finish.  The input gradient of a convolution is the convolution of the output gradient
+// with the tap-flipped, transposed weights, so it reuses these kernels.
 //
 // Weight gradient (k_conv3d_wgrad_tc): dW[t][co][ci] = sum_v dY[v][co] X[v + t][ci] as a GEMM
 // with M = 128 rows of (tap, ci), N = Cout, K = voxels; each CTA reduces one chunk of voxels in
@@ -40,24 +43,112 @@ struct ConvArgs {
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// Piece idx of a (rows x CH chunks) operand: groups of 8 consecutive pieces are 8 consecutive rows
+// of one 16-byte chunk, so the 8 lanes of a quarter warp store to 8 different 16-byte slots of one
+// 128-byte core-matrix row (no bank conflict in the non-swizzled K-major layout, where the chunks
+// of a row lie 128 bytes apart), and a warp reads 64 contiguous bytes of each of 8 rows.
+template <int CH>
+__device__ __forceinline__ void piece_rc(int idx, int &r, int &c)
+{
+    r = (idx & 7) + ((idx / (8 * CH)) << 3);
+    c = (idx >> 3) % CH;
+}
+
+// The operands one thread stages for every tap of its 128-voxel M-tile at v0: A rows (the input
+// shifted by the tap, wrapped) and the tap's weights, pieces mapped by piece_rc.  The rows' voxel
+// coordinates are computed once (a tap only shifts and wraps them; packed 10 bits per axis, so
+// every side is below 1024).  load() puts all of a tap's pieces in flight at once (registers),
+// store() writes them into shared memory in the canonical K-major core-matrix layout; the kernel
+// issues the next tap's load() right after the current tap's MMAs, before it waits for a buffer.
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) k_conv3d_tc(ConvArgs a)
+struct TapStage {
+    static constexpr int CH = CIN / 8, AIT = kTile * CH / 128, BIT = (COUT * CH + 127) / 128;
+    static constexpr uint32_t SBO = (CIN / 8) * 128;
+    int cijk[AIT];
+    uint4 av[AIT], bv[BIT];
+
+    __device__ __forceinline__ void init(const ConvArgs &a, int v0, int tid)
+    {
+        const int nx = a.n0, ny = a.n1;
+#pragma unroll
+        for (int it = 0; it < AIT; ++it) {
+            int r, c;
+            piece_rc<CH>(tid + it * 128, r, c);
+            const int v = v0 + r;
+            cijk[it] = (v % nx) | (((v / nx) % ny) << 10) | ((v / (nx * ny)) << 20);
+        }
+    }
+
+    __device__ __forceinline__ void load(const ConvArgs &a, int tap, int tid)
+    {
+        const int nx = a.n0, ny = a.n1, nz = a.n2;
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int it = 0; it < AIT; ++it) {
+            int r, c;
+            piece_rc<CH>(tid + it * 128, r, c);
+            int i = (cijk[it] & 1023) + dx, j = ((cijk[it] >> 10) & 1023) + dy, k = (cijk[it] >> 20) + dz;
+            i += i < 0 ? nx : (i >= nx ? -nx : 0);
+            j += j < 0 ? ny : (j >= ny ? -ny : 0);
+            k += k < 0 ? nz : (k >= nz ? -nz : 0);
+            const size_t nb = (size_t)i + (size_t)nx * (j + (size_t)ny * k);
+            av[it] = *reinterpret_cast<const uint4 *>(a.x + nb * a.xcs + a.xc0 + c * 8);
+        }
+        const __nv_bfloat16 *wt = a.w + (size_t)tap * COUT * CIN;
+#pragma unroll
+        for (int it = 0; it < BIT; ++it) {
+            const int idx = tid + it * 128;
+            int r, c;
+            piece_rc<CH>(idx, r, c);
+            if (idx < COUT * CH) bv[it] = *reinterpret_cast<const uint4 *>(wt + r * CIN + c * 8);
+        }
+    }
+
+    __device__ __forceinline__ void store(unsigned char *A, unsigned char *B, int tid) const
+    {
+#pragma unroll
+        for (int it = 0; it < AIT; ++it) {
+            int r, c;
+            piece_rc<CH>(tid + it * 128, r, c);
+            *reinterpret_cast<uint4 *>(A + (r >> 3) * SBO + c * 128 + (r & 7) * 16) = av[it];
+        }
+#pragma unroll
+        for (int it = 0; it < BIT; ++it) {
+            const int idx = tid + it * 128;
+            int r, c;
+            piece_rc<CH>(idx, r, c);
+            if (idx < COUT * CH) *reinterpret_cast<uint4 *>(B + (r >> 3) * SBO + c * 128 + (r & 7) * 16) = bv[it];
+        }
+    }
+};
+
+template <int CIN, int COUT>
+__host__ __device__ constexpr size_t taps_smem_bytes() { return 2 * (size_t)(kTile + COUT) * CIN * 2; }
+
+// Per-tap kernel (k_conv3d_taps): one CTA = 128 consecutive output voxels x all Cout over the taps
+// [t0, t1) of its group (blockIdx.y; one group of all 27 taps when unsplit).  Two shared-memory
+// buffers; thread 0 issues Cin/16 MMAs per tap (M = 128, N = Cout, K = 16, FP32 accumulation in
+// TMEM) and a buffer is refilled once the commit of its previous tap has arrived.  Epilogue:
+// part == NULL: + bias, ReLU, BF16 store into the output slice; else the group's FP32 partial
+// sums to part[group][voxel][Cout] (k_conv3d_finish adds the groups).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) k_conv3d_taps(ConvArgs a, int taps_per_group, float *__restrict__ part)
 {
     static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 128, "channel counts");
     constexpr int NCOLS = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
     constexpr uint32_t A_BYTES = kTile * CIN * 2, B_BYTES = COUT * CIN * 2;
-    constexpr uint32_t SBO_A = (CIN / 8) * 128, SBO_B = (CIN / 8) * 128;
+    constexpr uint32_t SBO = (CIN / 8) * 128;
     constexpr uint32_t IDESC = idesc_bf16(kTile, COUT);
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *Abuf = smem;                       // 2 x A_BYTES
-    unsigned char *Bbuf = smem + 2 * A_BYTES;         // 2 x B_BYTES
+    unsigned char *Abuf = smem;
+    unsigned char *Bbuf = smem + 2 * A_BYTES;
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nx = a.n0, ny = a.n1, nz = a.n2;
     const int v0 = blockIdx.x * kTile;
+    const int t0 = blockIdx.y * taps_per_group, t1 = min(27, t0 + taps_per_group), nt = t1 - t0;
     if (warp == 0) tmem_alloc(&tmem_slot, NCOLS);
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
@@ -65,36 +156,24 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(ConvArgs a)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = 0;
     }
+    TapStage<CIN, COUT> stage;
+    stage.init(a, v0, tid);
+    stage.load(a, t0, tid);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
-
-    for (int tap = 0; tap < 27; ++tap) {
-        const int buf = tap & 1;
-        if (tap >= 2) {   // the MMAs of tap - 2 have finished reading this buffer
-            if (tid == 0 && !failed && !mbar_wait_bounded(&mbar[buf], ((tap - 2) >> 1) & 1, a.spin_limit)) failed = 1;
+    int issued = 0;
+    for (int s = 0; s < nt; ++s) {
+        const int buf = s & 1;
+        if (s >= 2) {   // the MMAs of tap s - 2 have finished reading this buffer
+            if (tid == 0 && !failed && !mbar_wait_bounded(&mbar[buf], ((s - 2) >> 1) & 1, a.spin_limit)) failed = 1;
             __syncthreads();
             if (failed) break;
         }
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
         unsigned char *A = Abuf + buf * A_BYTES;
         unsigned char *B = Bbuf + buf * B_BYTES;
-        constexpr int CH = CIN / 8;   // 16-byte chunks per row
-        for (int idx = tid; idx < kTile * CH; idx += 128) {
-            int r = idx / CH, c = idx - r * CH;
-            int v = v0 + r;
-            int i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
-            int nb = wrapi(i + dx, nx) + nx * (wrapi(j + dy, ny) + ny * wrapi(k + dz, nz));
-            uint4 val = *reinterpret_cast<const uint4 *>(a.x + (size_t)nb * a.xcs + a.xc0 + c * 8);
-            *reinterpret_cast<uint4 *>(A + (r >> 3) * SBO_A + c * 128 + (r & 7) * 16) = val;
-        }
-        const __nv_bfloat16 *wt = a.w + (size_t)tap * COUT * CIN;
-        for (int idx = tid; idx < COUT * CH; idx += 128) {
-            int r = idx / CH, c = idx - r * CH;
-            uint4 val = *reinterpret_cast<const uint4 *>(wt + r * CIN + c * 8);
-            *reinterpret_cast<uint4 *>(B + (r >> 3) * SBO_B + c * 128 + (r & 7) * 16) = val;
-        }
+        stage.store(A, B, tid);
         fence_proxy_async();
         fence_before_sync();
         __syncthreads();
@@ -103,42 +182,51 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(ConvArgs a)
             const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
 #pragma unroll
             for (int kk = 0; kk < CIN / 16; ++kk)
-                mma_bf16(tmem, smem_desc(a0 + kk * 256, 128, SBO_A), smem_desc(b0 + kk * 256, 128, SBO_B), IDESC,
-                         (tap > 0 || kk > 0) ? 1u : 0u);
+                mma_bf16(tmem, smem_desc(a0 + kk * 256, 128, SBO), smem_desc(b0 + kk * 256, 128, SBO), IDESC,
+                         (s > 0 || kk > 0) ? 1u : 0u);
             mma_commit(&mbar[buf]);
         }
+        ++issued;
+        if (s + 1 < nt) stage.load(a, t0 + s + 1, tid);   // in flight during the next buffer wait
     }
-    // wait for the last tap (tap 26 on buffer 0, its 14th use: parity 1); the MMAs complete in order
-    if (tid == 0) {
-        bool ok = !failed && mbar_wait_bounded(&mbar[0], 1, a.spin_limit);
+    // the last issued tap's commit; the MMAs complete in order.  After a failed wait the drain gets
+    // a floor (kDrain polls) so that no MMA still reads shared memory when the CTA exits.
+    if (tid == 0 && issued > 0) {
+        const int last = issued - 1;
+        bool ok = !failed && mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, a.spin_limit);
         if (!ok) {
             failed = 1;
-            // give any MMA still in flight a second bounded wait before the buffers go away
-            mbar_wait_bounded(&mbar[0], 1, a.spin_limit);
-            mbar_wait_bounded(&mbar[1], 0, a.spin_limit);
+            mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, a.spin_limit > kDrain ? a.spin_limit : kDrain);
         }
     }
     __syncthreads();
     fence_after_sync();
-    if (!failed) {
+    if (!failed && issued > 0) {
         const int row = warp * 32 + lane;
         const size_t v = (size_t)v0 + row;
 #pragma unroll
         for (int cc = 0; cc < COUT / 16; ++cc) {
             float acc[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc * 16, acc);
-            __align__(16) __nv_bfloat16 o[16];
+            if (part) {
+                float *dst = part + ((size_t)blockIdx.y * a.n0 * a.n1 * a.n2 + v) * COUT + cc * 16;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                float t = acc[q] + (a.bias ? a.bias[cc * 16 + q] : 0.f);
-                if (a.relu) t = fmaxf(t, 0.f);
-                o[q] = __float2bfloat16_rn(t);
+                for (int q = 0; q < 16; q += 4)
+                    *reinterpret_cast<float4 *>(dst + q) = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
+            } else {
+                __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    float t = acc[q] + (a.bias ? a.bias[cc * 16 + q] : 0.f);
+                    if (a.relu) t = fmaxf(t, 0.f);
+                    o[q] = __float2bfloat16_rn(t);
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(a.y + v * a.ycs + a.yc0 + cc * 16);
+                dst[0] = reinterpret_cast<uint4 *>(o)[0];
+                dst[1] = reinterpret_cast<uint4 *>(o)[1];
             }
-            uint4 *dst = reinterpret_cast<uint4 *>(a.y + v * a.ycs + a.yc0 + cc * 16);
-            dst[0] = reinterpret_cast<uint4 *>(o)[0];
-            dst[1] = reinterpret_cast<uint4 *>(o)[1];
         }
-    } else if (tid == 0) {
+    } else if (failed && tid == 0) {
         atomicExch(a.err, 1);
     }
     fence_before_sync();
@@ -158,6 +246,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(ConvArgs a)
 // aligned and no data moves per tap: thread 0 issues all 27 x CIN/16 MMAs of every M-tile back
 // to back into TMEM, with all 27 taps' weights resident, and one commit ends the CTA's work.
 constexpr int kBlkX = 8, kBlkY = 16;
+constexpr int kBlkThreads = 256;   // 8 warps: staging in parallel, the epilogue's M-tiles split by warp quad
 
 template <int CIN, int COUT, int ZT>
 __host__ __device__ constexpr size_t blk_in_bytes() { return (size_t)3 * (CIN / 8) * (kBlkY + 2) * (ZT + 2) * 128; }
@@ -165,7 +254,7 @@ template <int CIN, int COUT, int ZT>
 __host__ __device__ constexpr size_t blk_smem_bytes() { return blk_in_bytes<CIN, COUT, ZT>() + (size_t)27 * COUT * CIN * 2; }
 
 template <int CIN, int COUT, int ZT>
-__global__ void __launch_bounds__(128) k_conv3d_blk(ConvArgs a)
+__global__ void __launch_bounds__(kBlkThreads) k_conv3d_blk(ConvArgs a)
 {
     static_assert(CIN % 16 == 0 && COUT % 16 == 0 && ZT * COUT <= 256, "channel counts");
     constexpr int CH = CIN / 8;
@@ -200,23 +289,58 @@ __global__ void __launch_bounds__(128) k_conv3d_blk(ConvArgs a)
     }
     // halo'd input block: one global load per (voxel, chunk), chunks fastest (coalesced), stored
     // into every shifted copy that contains the voxel (block x = bx is row position bx - s of copy s)
-    for (int idx = tid; idx < BX * BY * BZ * CH; idx += 128) {
-        const int vb = idx / CH, c = idx - vb * CH;
-        const int bx = vb % BX, by = (vb / BX) % BY, bz = vb / (BX * BY);
-        const int nb = wrapi(x0 - 1 + bx, nx) + nx * (wrapi(y0 - 1 + by, ny) + ny * wrapi(z0 - 1 + bz, nz));
-        const uint4 val = *reinterpret_cast<const uint4 *>(a.x + (size_t)nb * a.xcs + a.xc0 + c * 8);
+    // (batches of kBatch pieces per thread: all loads of a batch in flight before its stores)
+    constexpr int kBatch = 8;
+    constexpr int IN_TOT = BX * BY * BZ * CH, IN_IT = (IN_TOT + kBlkThreads - 1) / kBlkThreads;
+    for (int i0 = 0; i0 < IN_IT; i0 += kBatch) {
+        uint4 val[kBatch];
 #pragma unroll
-        for (int sft = 0; sft < 3; ++sft) {
-            const int xr = bx - sft;
-            if (xr >= 0 && xr < kBlkX)
-                *reinterpret_cast<uint4 *>(In + sft * COPY + c * CHUNK + bz * PLANE + by * 128 + xr * 16) = val;
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = tid + (i0 + u) * kBlkThreads;
+            if (i0 + u < IN_IT && idx < IN_TOT) {
+                const int bx = idx % BX, rest = idx / BX, c = rest % CH, row = rest / CH, by = row % BY, bz = row / BY;
+                const int nb = wrapi(x0 - 1 + bx, nx) + nx * (wrapi(y0 - 1 + by, ny) + ny * wrapi(z0 - 1 + bz, nz));
+                val[u] = *reinterpret_cast<const uint4 *>(a.x + (size_t)nb * a.xcs + a.xc0 + c * 8);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = tid + (i0 + u) * kBlkThreads;
+            if (i0 + u < IN_IT && idx < IN_TOT) {
+                const int bx = idx % BX, rest = idx / BX, c = rest % CH, row = rest / CH, by = row % BY, bz = row / BY;
+#pragma unroll
+                for (int sft = 0; sft < 3; ++sft) {
+                    const int xr = bx - sft;
+                    if (xr >= 0 && xr < kBlkX)
+                        *reinterpret_cast<uint4 *>(In + sft * COPY + c * CHUNK + bz * PLANE + by * 128 + xr * 16) = val[u];
+                }
+            }
         }
     }
     // weights of the 27 taps, each in the K-major core-matrix layout of the B operand
-    for (int idx = tid; idx < 27 * COUT * CH; idx += 128) {
-        const int t = idx / (COUT * CH), rem = idx - t * (COUT * CH), r = rem / CH, c = rem - r * CH;
-        const uint4 val = *reinterpret_cast<const uint4 *>(a.w + ((size_t)t * COUT + r) * CIN + c * 8);
-        *reinterpret_cast<uint4 *>(Wt + t * W_TAP + (r >> 3) * SBO_B + c * 128 + (r & 7) * 16) = val;
+    constexpr int W_TOT = 27 * COUT * CH, W_IT = (W_TOT + kBlkThreads - 1) / kBlkThreads;
+    for (int i0 = 0; i0 < W_IT; i0 += kBatch) {
+        uint4 val[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = tid + (i0 + u) * kBlkThreads;
+            if (i0 + u < W_IT && idx < W_TOT) {
+                const int t = idx / (COUT * CH);
+                int r, c;
+                piece_rc<CH>(idx - t * (COUT * CH), r, c);
+                val[u] = *reinterpret_cast<const uint4 *>(a.w + ((size_t)t * COUT + r) * CIN + c * 8);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = tid + (i0 + u) * kBlkThreads;
+            if (i0 + u < W_IT && idx < W_TOT) {
+                const int t = idx / (COUT * CH);
+                int r, c;
+                piece_rc<CH>(idx - t * (COUT * CH), r, c);
+                *reinterpret_cast<uint4 *>(Wt + t * W_TAP + (r >> 3) * SBO_B + c * 128 + (r & 7) * 16) = val[u];
+            }
+        }
     }
     fence_proxy_async();
     fence_before_sync();
@@ -224,35 +348,37 @@ __global__ void __launch_bounds__(128) k_conv3d_blk(ConvArgs a)
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
     if (tid == 0) {
-        const uint32_t in0 = smem_u32(In), w0 = smem_u32(Wt);
+        // every MMA's descriptors are the block's base descriptors plus a compile-time offset (in
+        // 16-byte units of the start-address field; the block lies below 256 KB, so no carry)
+        const uint64_t da = smem_desc(smem_u32(In), CHUNK, 128), db = smem_desc(smem_u32(Wt), 128, SBO_B);
+#pragma unroll
         for (int zt = 0; zt < ZT; ++zt)
+#pragma unroll
             for (int tap = 0; tap < 27; ++tap) {
                 const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                const uint32_t ab = in0 + (uint32_t)(dx + 1) * COPY + (uint32_t)(zt + dz + 1) * PLANE +
-                                    (uint32_t)(dy + 1) * 128;
-                const uint32_t bb = w0 + tap * W_TAP;
+                const uint32_t ab = (uint32_t)(dx + 1) * COPY + (uint32_t)(zt + dz + 1) * PLANE + (uint32_t)(dy + 1) * 128;
 #pragma unroll
                 for (int kk = 0; kk < CIN / 16; ++kk)
-                    mma_bf16(tmem + zt * COUT, smem_desc(ab + kk * 2 * CHUNK, CHUNK, 128),
-                             smem_desc(bb + kk * 256, 128, SBO_B), IDESC, (tap > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(tmem + zt * COUT, da + ((ab + kk * 2 * CHUNK) >> 4), db + ((tap * W_TAP + kk * 256) >> 4),
+                             IDESC, (tap > 0 || kk > 0) ? 1u : 0u);
             }
         mma_commit(&mbar);
         if (!mbar_wait_bounded(&mbar, 0, a.spin_limit)) {
             failed = 1;
-            mbar_wait_bounded(&mbar, 0, a.spin_limit);   // a second bounded wait before smem goes away
+            mbar_wait_bounded(&mbar, 0, a.spin_limit > kDrain ? a.spin_limit : kDrain);   // before smem goes away
         }
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (!failed) {
-        const int row = warp * 32 + lane;
-        for (int zt = 0; zt < ZT; ++zt) {
+    if (!failed) {   // warp w reads TMEM lanes 32 (w % 4) ..: M-tile zt = w / 4, w / 4 + 2, ...
+        const int row = (warp & 3) * 32 + lane;
+        for (int zt = warp >> 2; zt < ZT; zt += kBlkThreads / 128) {
             const size_t v = (size_t)(x0 + (row & 7)) + (size_t)nx * ((y0 + (row >> 3)) + (size_t)ny * (z0 + zt));
 #pragma unroll
             for (int cc = 0; cc < COUT / 16; ++cc) {
                 float acc[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + zt * COUT + cc * 16, acc);
+                tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + zt * COUT + cc * 16, acc);
                 __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -266,112 +392,6 @@ __global__ void __launch_bounds__(128) k_conv3d_blk(ConvArgs a)
             }
         }
     } else if (tid == 0) {
-        atomicExch(a.err, 1);
-    }
-    fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, NCOLS);
-}
-
-// Split-K form of k_conv3d_tc for grids with few 128-voxel tiles (the network's coarse levels):
-// blockIdx.y selects a group of taps [t0, t1); the CTA accumulates its tile over those taps in TMEM
-// and writes the FP32 partial sums to part[group][voxel][Cout].  k_conv3d_finish then adds the
-// groups in order (deterministic), adds the bias, applies ReLU and stores BF16.  Same gather,
-// double buffering and bounded waits as k_conv3d_tc.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) k_conv3d_split(ConvArgs a, int taps_per_group, float *__restrict__ part)
-{
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 128, "channel counts");
-    constexpr int NCOLS = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
-    constexpr uint32_t A_BYTES = kTile * CIN * 2, B_BYTES = COUT * CIN * 2;
-    constexpr uint32_t SBO_A = (CIN / 8) * 128, SBO_B = (CIN / 8) * 128;
-    constexpr uint32_t IDESC = idesc_bf16(kTile, COUT);
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *Abuf = smem;
-    unsigned char *Bbuf = smem + 2 * A_BYTES;
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ uint32_t tmem_slot;
-    __shared__ int failed;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nx = a.n0, ny = a.n1, nz = a.n2;
-    const int v0 = blockIdx.x * kTile;
-    const int t0 = blockIdx.y * taps_per_group, t1 = min(27, t0 + taps_per_group), nt = t1 - t0;
-    if (warp == 0) tmem_alloc(&tmem_slot, NCOLS);
-    if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        failed = 0;
-    }
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    const uint32_t tmem = tmem_slot;
-    int issued = 0;
-    for (int s = 0; s < nt; ++s) {
-        const int buf = s & 1, tap = t0 + s;
-        if (s >= 2) {
-            if (tid == 0 && !failed && !mbar_wait_bounded(&mbar[buf], ((s - 2) >> 1) & 1, a.spin_limit)) failed = 1;
-            __syncthreads();
-            if (failed) break;
-        }
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        unsigned char *A = Abuf + buf * A_BYTES;
-        unsigned char *B = Bbuf + buf * B_BYTES;
-        constexpr int CH = CIN / 8;
-        for (int idx = tid; idx < kTile * CH; idx += 128) {
-            int r = idx / CH, c = idx - r * CH;
-            int v = v0 + r;
-            int i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
-            int nb = wrapi(i + dx, nx) + nx * (wrapi(j + dy, ny) + ny * wrapi(k + dz, nz));
-            uint4 val = *reinterpret_cast<const uint4 *>(a.x + (size_t)nb * a.xcs + a.xc0 + c * 8);
-            *reinterpret_cast<uint4 *>(A + (r >> 3) * SBO_A + c * 128 + (r & 7) * 16) = val;
-        }
-        const __nv_bfloat16 *wt = a.w + (size_t)tap * COUT * CIN;
-        for (int idx = tid; idx < COUT * CH; idx += 128) {
-            int r = idx / CH, c = idx - r * CH;
-            uint4 val = *reinterpret_cast<const uint4 *>(wt + r * CIN + c * 8);
-            *reinterpret_cast<uint4 *>(B + (r >> 3) * SBO_B + c * 128 + (r & 7) * 16) = val;
-        }
-        fence_proxy_async();
-        fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            fence_after_sync();
-            const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
-#pragma unroll
-            for (int kk = 0; kk < CIN / 16; ++kk)
-                mma_bf16(tmem, smem_desc(a0 + kk * 256, 128, SBO_A), smem_desc(b0 + kk * 256, 128, SBO_B), IDESC,
-                         (s > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(&mbar[buf]);
-        }
-        ++issued;
-    }
-    // the last group member's commit on its buffer; MMAs complete in order.  After a failed wait the
-    // drain gets a floor (kDrain polls) so that no MMA still reads shared memory when the CTA exits.
-    if (tid == 0 && issued > 0) {
-        const int last = issued - 1;
-        bool ok = !failed && mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, a.spin_limit);
-        if (!ok) {
-            failed = 1;
-            mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, a.spin_limit > kDrain ? a.spin_limit : kDrain);
-        }
-    }
-    __syncthreads();
-    fence_after_sync();
-    if (!failed && issued > 0) {
-        const int row = warp * 32 + lane;
-        float *dst = part + ((size_t)blockIdx.y * a.n0 * a.n1 * a.n2 + (size_t)(v0 + row)) * COUT;
-#pragma unroll
-        for (int cc = 0; cc < COUT / 16; ++cc) {
-            float acc[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc * 16, acc);
-#pragma unroll
-            for (int q = 0; q < 16; q += 4)
-                *reinterpret_cast<float4 *>(dst + cc * 16 + q) = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
-        }
-    } else if (failed && tid == 0) {
         atomicExch(a.err, 1);
     }
     fence_before_sync();
@@ -468,31 +488,63 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad_tc(WgradArgs a)
             int r = idx / (KV / 8), kc = idx % (KV / 8);
             if (r >= ntap * CIN) *reinterpret_cast<uint4 *>(A + (r >> 3) * SBO + kc * 128 + (r & 7) * 16) = make_uint4(0, 0, 0, 0);
         }
-        for (int idx = tid; idx < ntap * KV * (CIN / 8); idx += 128) {
-            int c = idx % (CIN / 8);
-            int kv = (idx / (CIN / 8)) % KV;
-            int tl = idx / ((CIN / 8) * KV);
-            int tap = tap0 + tl;
-            int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-            int v = vbase + kv;
-            int i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
-            int nb = wrapi(i + dx, nx) + nx * (wrapi(j + dy, ny) + ny * wrapi(k + dz, nz));
-            uint4 val = *reinterpret_cast<const uint4 *>(a.x + (size_t)nb * a.xcs + a.xc0 + c * 8);
-            const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&val);
+        // (batches of 8 pieces per thread: all loads of a batch in flight before its stores)
+        constexpr int A_IT = TPG * KV * (CIN / 8) / 128;
+        const int a_tot = ntap * KV * (CIN / 8);
+        for (int i0 = 0; i0 < A_IT; i0 += 8) {
+            uint4 val[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                int r = tl * CIN + c * 8 + q;
-                *reinterpret_cast<__nv_bfloat16 *>(A + (r >> 3) * SBO + (kv >> 3) * 128 + (r & 7) * 16 + (kv & 7) * 2) = e[q];
+            for (int u = 0; u < 8; ++u) {
+                const int idx = tid + (i0 + u) * 128;
+                if (i0 + u < A_IT && idx < a_tot) {
+                    const int c = idx % (CIN / 8), kv = (idx / (CIN / 8)) % KV, tl = idx / ((CIN / 8) * KV);
+                    const int tap = tap0 + tl;
+                    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                    const int v = vbase + kv;
+                    const int i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
+                    const int nb = wrapi(i + dx, nx) + nx * (wrapi(j + dy, ny) + ny * wrapi(k + dz, nz));
+                    val[u] = *reinterpret_cast<const uint4 *>(a.x + (size_t)nb * a.xcs + a.xc0 + c * 8);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = tid + (i0 + u) * 128;
+                if (i0 + u < A_IT && idx < a_tot) {
+                    const int c = idx % (CIN / 8), kv = (idx / (CIN / 8)) % KV, tl = idx / ((CIN / 8) * KV);
+                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&val[u]);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int r = tl * CIN + c * 8 + q;
+                        *reinterpret_cast<__nv_bfloat16 *>(A + (r >> 3) * SBO + (kv >> 3) * 128 + (r & 7) * 16 +
+                                                           (kv & 7) * 2) = e[q];
+                    }
+                }
             }
         }
-        for (int idx = tid; idx < KV * (COUT / 8); idx += 128) {
-            int c = idx % (COUT / 8), kv = idx / (COUT / 8);
-            uint4 val = *reinterpret_cast<const uint4 *>(a.dy + (size_t)(vbase + kv) * a.dcs + a.dc0 + c * 8);
-            const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&val);
+        constexpr int B_IT = (KV * (COUT / 8) + 127) / 128;
+        for (int i0 = 0; i0 < B_IT; i0 += 8) {
+            uint4 val[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                int r = c * 8 + q;
-                *reinterpret_cast<__nv_bfloat16 *>(B + (r >> 3) * SBO + (kv >> 3) * 128 + (r & 7) * 16 + (kv & 7) * 2) = e[q];
+            for (int u = 0; u < 8; ++u) {
+                const int idx = tid + (i0 + u) * 128;
+                if (i0 + u < B_IT && idx < KV * (COUT / 8)) {
+                    const int c = idx % (COUT / 8), kv = idx / (COUT / 8);
+                    val[u] = *reinterpret_cast<const uint4 *>(a.dy + (size_t)(vbase + kv) * a.dcs + a.dc0 + c * 8);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = tid + (i0 + u) * 128;
+                if (i0 + u < B_IT && idx < KV * (COUT / 8)) {
+                    const int c = idx % (COUT / 8), kv = idx / (COUT / 8);
+                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&val[u]);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int r = c * 8 + q;
+                        *reinterpret_cast<__nv_bfloat16 *>(B + (r >> 3) * SBO + (kv >> 3) * 128 + (r & 7) * 16 +
+                                                           (kv & 7) * 2) = e[q];
+                    }
+                }
             }
         }
         fence_proxy_async();
@@ -512,9 +564,9 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad_tc(WgradArgs a)
     if (tid == 0 && issued > 0) {
         const int last = issued - 1;
         bool ok = !failed && mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, a.spin_limit);
-        if (!ok) {
+        if (!ok) {   // the drain gets a floor (kDrain polls): no MMA may still read shared memory at exit
             failed = 1;
-            mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, a.spin_limit);
+            mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, a.spin_limit > kDrain ? a.spin_limit : kDrain);
         }
     }
     __syncthreads();
@@ -550,9 +602,9 @@ namespace {
 
 constexpr int kSms = 152;
 
-// Split-K plan of a forward convolution: taps per group and number of groups (1: no split).  The
-// taps are split where the grid has fewer than two 128-voxel tiles per SM, into enough groups for
-// about two CTAs per SM in all.
+// Split-K plan of a per-tap forward convolution: taps per group and number of groups (1: no
+// split).  The taps are split where the grid has fewer than four 128-voxel tiles per SM, into
+// enough groups for about four CTAs per SM in all.
 struct SplitPlan {
     int tpg, groups;
 };
@@ -560,8 +612,8 @@ struct SplitPlan {
 SplitPlan split_plan(long long nvox)
 {
     const long long tiles = nvox / kTile;
-    if (tiles <= 0 || tiles >= 2 * kSms) return {27, 1};
-    const int want = (int)std::min<long long>(27, (2 * kSms + tiles - 1) / tiles);
+    if (tiles <= 0 || tiles >= 4 * kSms) return {27, 1};
+    const int want = (int)std::min<long long>(27, (4 * kSms + tiles - 1) / tiles);
     const int tpg = (27 + want - 1) / want;
     return {tpg, (27 + tpg - 1) / tpg};
 }
@@ -569,25 +621,8 @@ SplitPlan split_plan(long long nvox)
 template <int CIN, int COUT>
 int launch_fwd(const ConvArgs &a, int nvox, float *ws, cudaStream_t st)
 {
-    constexpr size_t smem = 2 * (kTile * CIN * 2) + 2 * (COUT * CIN * 2);
-    const int tiles = nvox / kTile;
-    const SplitPlan sp = split_plan(nvox);
-    if (ws && sp.groups > 1) {
-        const int groups = sp.groups, tpg = sp.tpg;
-        float *part = ws;
-        static bool attr_split = false;
-        if (!attr_split) {
-            if (cudaFuncSetAttribute(k_conv3d_split<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
-                return 3;
-            attr_split = true;
-        }
-        k_conv3d_split<CIN, COUT><<<dim3(tiles, groups), 128, smem, st>>>(a, tpg, part);
-        const long long work = (long long)nvox * (COUT / 8);
-        k_conv3d_finish<COUT><<<(int)std::min<long long>((work + 255) / 256, 152LL * 16), 256, 0, st>>>(a, groups, part);
-        return cudaGetLastError() == cudaSuccess ? 0 : 3;
-    }
-    // block-tile kernel where the grid tiles evenly and the block and all weights fit in shared memory
+    // block-tile kernel where the grid tiles evenly and the block and all weights fit in shared
+    // memory: it reads each input voxel about 3 times (halo), the per-tap kernel 27 times (L2)
     constexpr int ZT = 2;
     constexpr size_t bsm = blk_smem_bytes<CIN, COUT, ZT>();
     if constexpr (bsm <= 220 * 1024) {
@@ -596,22 +631,31 @@ int launch_fwd(const ConvArgs &a, int nvox, float *ws, cudaStream_t st)
             if (!attr_blk) {
                 if (cudaFuncSetAttribute(k_conv3d_blk<CIN, COUT, ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bsm) != cudaSuccess)
-                    return 2;
+                    return 3;
                 attr_blk = true;
             }
             const int grid = (a.n0 / kBlkX) * (a.n1 / kBlkY) * (a.n2 / ZT);
-            k_conv3d_blk<CIN, COUT, ZT><<<grid, 128, bsm, st>>>(a);
+            k_conv3d_blk<CIN, COUT, ZT><<<grid, kBlkThreads, bsm, st>>>(a);
             return cudaGetLastError() == cudaSuccess ? 0 : 3;
         }
     }
+    constexpr size_t smem = taps_smem_bytes<CIN, COUT>();
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_conv3d_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(k_conv3d_taps<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return 3;
         attr = true;
     }
-    k_conv3d_tc<CIN, COUT><<<tiles, 128, smem, st>>>(a);
+    const int tiles = nvox / kTile;
+    const SplitPlan sp = split_plan(nvox);
+    if (ws && sp.groups > 1) {   // few tiles: the taps in groups, FP32 partials added in order
+        k_conv3d_taps<CIN, COUT><<<dim3(tiles, sp.groups), 128, smem, st>>>(a, sp.tpg, ws);
+        const long long work = (long long)nvox * (COUT / 8);
+        k_conv3d_finish<COUT><<<(int)std::min<long long>((work + 255) / 256, 152LL * 16), 256, 0, st>>>(a, sp.groups, ws);
+        return cudaGetLastError() == cudaSuccess ? 0 : 3;
+    }
+    k_conv3d_taps<CIN, COUT><<<tiles, 128, smem, st>>>(a, 27, nullptr);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
@@ -659,7 +703,7 @@ extern "C" int unet_conv3d_fwd(const void *x, int xcs, int xc0, const void *w_bf
 {
     long long nvox = (long long)n0 * n1 * n2;
     if (!x || !w_bf16 || !y || !err || nvox <= 0 || nvox % kTile || (xcs | xc0 | ycs | yc0) % 8 ||
-        xc0 + cin > xcs || yc0 + cout > ycs)
+        xc0 + cin > xcs || yc0 + cout > ycs || n0 >= 1024 || n1 >= 1024 || n2 >= 1024)
         return 1;
     if (ws && (ws_bytes < unet_conv3d_fwd_workspace(n0, n1, n2, cout) || (reinterpret_cast<size_t>(ws) & 15)))
         return 1;

@@ -31,21 +31,41 @@ __global__ void k_pack_weights(const float *w, int cin, int cout, int mode, __nv
 
 __device__ __forceinline__ long long vox(int i, int j, int k, int n0, int n1) { return i + (long long)n0 * (j + (long long)n1 * k); }
 
-// n = fine size
+// Row-parallel launches (the inference path): blockIdx.x = one output row (j + n1 * k [+ field]),
+// blockIdx.y * blockDim.x + threadIdx.x = the position along it (voxel x, times 8-channel chunks
+// for the BF16 tensors), so the per-thread index arithmetic is one 32-bit division.
+struct RowLaunch {
+    dim3 grid, block;
+};
+
+inline RowLaunch row_launch(long long rows, int per_row)
+{
+    const int t = std::min(256, std::max(32, (per_row + 31) / 32 * 32));
+    return {dim3((unsigned)rows, (unsigned)((per_row + t - 1) / t)), dim3(t)};
+}
+
+// 2x2x2 average pooling, n = fine size; 8 channels (16 bytes) per thread.
 __global__ void k_avgpool2(const __nv_bfloat16 *x, int xcs, int xc0, __nv_bfloat16 *y, int ycs, int yc0, int c,
                            int n0, int n1, int n2)
 {
-    const int m0 = n0 / 2, m1 = n1 / 2, m2 = n2 / 2;
-    const long long n = (long long)m0 * m1 * m2 * c;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        int ch = (int)(q % c);
-        long long V = q / c;
-        int I = (int)(V % m0), J = (int)((V / m0) % m1), K = (int)(V / ((long long)m0 * m1));
-        float s = 0.f;
-        for (int d = 0; d < 8; ++d)
-            s += __bfloat162float(x[vox(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), n0, n1) * xcs + xc0 + ch]);
-        y[V * ycs + yc0 + ch] = __float2bfloat16_rn(0.125f * s);
+    const int m0 = n0 / 2, m1 = n1 / 2, cc = c / 8;
+    const int J = blockIdx.x % m1, K = blockIdx.x / m1;
+    const int piece = blockIdx.y * blockDim.x + threadIdx.x;
+    if (piece >= m0 * cc) return;
+    const int I = piece / cc, ch = (piece - I * cc) * 8;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(
+            x + vox(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), n0, n1) * xcs + xc0 + ch);
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s[q] += __bfloat162float(e[q]);
     }
+    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) o[q] = __float2bfloat16_rn(0.125f * s[q]);
+    *reinterpret_cast<uint4 *>(y + vox(I, J, K, m0, m1) * ycs + yc0 + ch) = *reinterpret_cast<const uint4 *>(o);
 }
 
 __global__ void k_avgpool2_bwd(const __nv_bfloat16 *dy, int dcs, int dc0, __nv_bfloat16 *dx, int xcs, int xc0,
@@ -63,18 +83,17 @@ __global__ void k_avgpool2_bwd(const __nv_bfloat16 *dy, int dcs, int dc0, __nv_b
     }
 }
 
-// n = coarse size
+// nearest 2x upsampling, n = coarse size; 8 channels (16 bytes) per thread.
 __global__ void k_upsample2(const __nv_bfloat16 *x, int xcs, int xc0, __nv_bfloat16 *y, int ycs, int yc0, int c,
                             int n0, int n1, int n2)
 {
-    const int f0 = 2 * n0, f1 = 2 * n1;
-    const long long n = 8LL * n0 * n1 * n2 * c;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        int ch = (int)(q % c);
-        long long v = q / c;
-        int i = (int)(v % f0), j = (int)((v / f0) % f1), k = (int)(v / ((long long)f0 * f1));
-        y[v * ycs + yc0 + ch] = x[vox(i / 2, j / 2, k / 2, n0, n1) * xcs + xc0 + ch];
-    }
+    const int f0 = 2 * n0, f1 = 2 * n1, cc = c / 8;
+    const int j = blockIdx.x % f1, k = blockIdx.x / f1;
+    const int piece = blockIdx.y * blockDim.x + threadIdx.x;
+    if (piece >= f0 * cc) return;
+    const int i = piece / cc, ch = (piece - i * cc) * 8;
+    *reinterpret_cast<uint4 *>(y + vox(i, j, k, f0, f1) * ycs + yc0 + ch) =
+        *reinterpret_cast<const uint4 *>(x + vox(i / 2, j / 2, k / 2, n0, n1) * xcs + xc0 + ch);
 }
 
 __global__ void k_upsample2_bwd(const __nv_bfloat16 *dy, int dcs, int dc0, __nv_bfloat16 *dx, int xcs, int xc0,
@@ -284,15 +303,14 @@ __global__ void k_pack_target(const double *u, const double *W, float s_u, float
 __global__ void k_restrict2_f64(const double *fine, double *coarse, int nf, int m0, int m1, int m2)
 {
     const long long nc = (long long)m0 * m1 * m2, nfv = 8 * nc;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nc * nf; q += (long long)gridDim.x * blockDim.x) {
-        int f = (int)(q / nc);
-        long long V = q - f * nc;
-        int I = (int)(V % m0), J = (int)((V / m0) % m1), K = (int)(V / ((long long)m0 * m1));
-        double s = 0.0;
-        for (int d = 0; d < 8; ++d)
-            s += fine[f * nfv + vox(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), 2 * m0, 2 * m1)];
-        coarse[f * nc + V] = 0.125 * s;
-    }
+    const int row = blockIdx.x, J = row % m1, K = (row / m1) % m2, f = row / (m1 * m2);
+    const int I = blockIdx.y * blockDim.x + threadIdx.x;
+    if (I >= m0) return;
+    const double *src = fine + f * nfv;
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) s += src[vox(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), 2 * m0, 2 * m1)];
+    coarse[f * nc + vox(I, J, K, m0, m1)] = 0.125 * s;
 }
 
 // cell-centred trilinear interpolation (weights 3/4, 1/4 per axis, periodic) of nf FP64 fields
@@ -300,22 +318,25 @@ __global__ void k_restrict2_f64(const double *fine, double *coarse, int nf, int 
 __global__ void k_prolong2_f64(const double *coarse, double *fine, int nf, int m0, int m1, int m2)
 {
     const long long nc = (long long)m0 * m1 * m2, nfv = 8 * nc;
-    const int f0 = 2 * m0, f1 = 2 * m1;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nfv * nf; q += (long long)gridDim.x * blockDim.x) {
-        int f = (int)(q / nfv);
-        long long v = q - f * nfv;
-        int i = (int)(v % f0), j = (int)((v / f0) % f1), k = (int)(v / ((long long)f0 * f1));
-        int I = i >> 1, J = j >> 1, K = k >> 1;
-        int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
-        double s = 0.0;
-        for (int c = 0; c < 8; ++c) {
-            int a = c & 1, b = (c >> 1) & 1, e = c >> 2;
-            double w = (a ? 0.25 : 0.75) * (b ? 0.25 : 0.75) * (e ? 0.25 : 0.75);
-            int ii = (I + a * sx + m0) % m0, jj = (J + b * sy + m1) % m1, kk = (K + e * sz + m2) % m2;
-            s += w * coarse[f * nc + vox(ii, jj, kk, m0, m1)];
-        }
-        fine[f * nfv + v] = s;
+    const int f0 = 2 * m0, f1 = 2 * m1, f2 = 2 * m2;
+    const int row = blockIdx.x, j = row % f1, k = (row / f1) % f2, f = row / (f1 * f2);
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= f0) return;
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
+    const double *src = coarse + f * nc;
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int a = c & 1, b = (c >> 1) & 1, e = c >> 2;
+        const double w = (a ? 0.25 : 0.75) * (b ? 0.25 : 0.75) * (e ? 0.25 : 0.75);
+        int ii = I + a * sx, jj = J + b * sy, kk = K + e * sz;
+        ii += ii < 0 ? m0 : (ii >= m0 ? -m0 : 0);
+        jj += jj < 0 ? m1 : (jj >= m1 ? -m1 : 0);
+        kk += kk < 0 ? m2 : (kk >= m2 ? -m2 : 0);
+        s += w * src[vox(ii, jj, kk, m0, m1)];
     }
+    fine[f * nfv + vox(i, j, k, f0, f1)] = s;
 }
 
 inline int ok() { return cudaGetLastError() == cudaSuccess ? 0 : 3; }
@@ -333,9 +354,11 @@ int unet_pack_weights(const float *w, int cin, int cout, int mode, void *out, vo
 
 int unet_avgpool2(const void *x, int xcs, int xc0, void *y, int ycs, int yc0, int c, int n0, int n1, int n2, void *stream)
 {
-    if (!x || !y || (n0 | n1 | n2) & 1) return 1;
-    k_avgpool2<<<blocks((long long)n0 * n1 * n2 / 8 * c), kT, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16 *)x, xcs, xc0, (__nv_bfloat16 *)y, ycs, yc0, c, n0, n1, n2);
+    if (!x || !y || (n0 | n1 | n2) & 1 || n0 <= 0 || n1 <= 0 || n2 <= 0 || c <= 0 || (c | xcs | xc0 | ycs | yc0) & 7)
+        return 1;
+    const RowLaunch L = row_launch((long long)(n1 / 2) * (n2 / 2), n0 / 2 * (c / 8));
+    k_avgpool2<<<L.grid, L.block, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)x, xcs, xc0, (__nv_bfloat16 *)y,
+                                                             ycs, yc0, c, n0, n1, n2);
     return ok();
 }
 
@@ -350,9 +373,10 @@ int unet_avgpool2_bwd(const void *dy, int dcs, int dc0, void *dx, int xcs, int x
 
 int unet_upsample2(const void *x, int xcs, int xc0, void *y, int ycs, int yc0, int c, int n0, int n1, int n2, void *stream)
 {
-    if (!x || !y) return 1;
-    k_upsample2<<<blocks(8LL * n0 * n1 * n2 * c), kT, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16 *)x, xcs, xc0, (__nv_bfloat16 *)y, ycs, yc0, c, n0, n1, n2);
+    if (!x || !y || n0 <= 0 || n1 <= 0 || n2 <= 0 || c <= 0 || (c | xcs | xc0 | ycs | yc0) & 7) return 1;
+    const RowLaunch L = row_launch(4LL * n1 * n2, 2 * n0 * (c / 8));
+    k_upsample2<<<L.grid, L.block, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)x, xcs, xc0, (__nv_bfloat16 *)y,
+                                                              ycs, yc0, c, n0, n1, n2);
     return ok();
 }
 
@@ -443,17 +467,17 @@ int unet_unpack_output(const float *out4, float s_u, float s_W, double *u, doubl
 
 int unet_restrict2_fields(const double *fine, double *coarse, int nfields, int m0, int m1, int m2, void *stream)
 {
-    if (!fine || !coarse || nfields < 1) return 1;
-    k_restrict2_f64<<<blocks((long long)m0 * m1 * m2 * nfields), kT, 0, (cudaStream_t)stream>>>(fine, coarse, nfields,
-                                                                                                 m0, m1, m2);
+    if (!fine || !coarse || nfields < 1 || m0 <= 0 || m1 <= 0 || m2 <= 0) return 1;
+    const RowLaunch L = row_launch((long long)m1 * m2 * nfields, m0);
+    k_restrict2_f64<<<L.grid, L.block, 0, (cudaStream_t)stream>>>(fine, coarse, nfields, m0, m1, m2);
     return ok();
 }
 
 int unet_prolong2_fields(const double *coarse, double *fine, int nfields, int m0, int m1, int m2, void *stream)
 {
-    if (!fine || !coarse || nfields < 1) return 1;
-    k_prolong2_f64<<<blocks(8LL * m0 * m1 * m2 * nfields), kT, 0, (cudaStream_t)stream>>>(coarse, fine, nfields, m0,
-                                                                                           m1, m2);
+    if (!fine || !coarse || nfields < 1 || m0 <= 0 || m1 <= 0 || m2 <= 0) return 1;
+    const RowLaunch L = row_launch(4LL * m1 * m2 * nfields, 2 * m0);
+    k_prolong2_f64<<<L.grid, L.block, 0, (cudaStream_t)stream>>>(coarse, fine, nfields, m0, m1, m2);
     return ok();
 }
 

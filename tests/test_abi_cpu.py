@@ -44,22 +44,22 @@ def test_library_exports_every_network_entry_point(lib):
 
 
 def test_split_convolution_workspace_query(lib):
-    """Host-side plan of the split-K convolutions: grids with fewer than 2 x 152 tiles of 128
-    voxels split the 27 taps into groups for about two CTAs per SM; the workspace holds one FP32
-    partial per group, voxel and output channel."""
+    """Host-side plan of the split-K per-tap convolutions: grids with fewer than 4 x 152 tiles of
+    128 voxels split the 27 taps into groups for about four CTAs per SM; the workspace holds one
+    FP32 partial per group, voxel and output channel."""
     from paper_2501_13046_gb300 import unet as U
     f = 4
 
     def groups(tiles):
-        want = min(27, -(-304 // tiles))
+        want = min(27, -(-608 // tiles))
         tpg = -(-27 // want)
         return -(-27 // tpg)
 
-    assert groups(4) == 27 and groups(32) == 9 and groups(256) == 2
+    assert groups(4) == 27 and groups(32) == 14 and groups(256) == 3
     assert U.conv3d_workspace((8, 8, 8), 64) == 27 * 512 * 64 * f          # 4 tiles: one tap per group
-    assert U.conv3d_workspace((16, 16, 16), 64) == 9 * 4096 * 64 * f       # 32 tiles: 3 taps per group
-    assert U.conv3d_workspace((32, 32, 32), 32) == 2 * 32768 * 32 * f      # 256 tiles: 14 + 13 taps
-    assert U.conv3d_workspace((64, 32, 19), 16) == 0                        # 304 tiles: unsplit
+    assert U.conv3d_workspace((16, 16, 16), 64) == 14 * 4096 * 64 * f      # 32 tiles: 2 taps per group
+    assert U.conv3d_workspace((32, 32, 32), 32) == 3 * 32768 * 32 * f      # 256 tiles: 9 taps per group
+    assert U.conv3d_workspace((64, 32, 38), 16) == 0                        # 608 tiles: unsplit
     assert U.conv3d_workspace((64, 64, 64), 16) == 0
     assert U.conv3d_workspace((8, 8, 3), 16) == 0                           # not a multiple of 128 voxels
     assert U.conv3d_workspace((0, 8, 8), 16) == 0

@@ -49,6 +49,48 @@ def test_pool_upsample_and_adjoints(mods):
     np.testing.assert_allclose(host(dc), f.reshape(4, 2, 4, 2, 4, 2, 16).sum(axis=(1, 3, 5)), rtol=2 ** -7, atol=1e-5)
 
 
+def test_row_parallel_glue_on_slices_non_cubes_and_fields(mods):
+    """Pooling and upsampling on channel slices of non-cubic grids (8 channels per thread), and the
+    FP64 restriction (8-child mean) and prolongation (cell-centred trilinear, periodic) of several
+    fields, against numpy; a channel count that is not a multiple of 8 is rejected."""
+    U = mods[0]
+    from paper_2501_13046_gb300.unet import Slice
+    rng = np.random.default_rng(7)
+    nz, ny, nx = 4, 8, 16
+    big = R.bf16_round(rng.standard_normal((nz, ny, nx, 48)))
+    ybuf = torch.full((nz // 2, ny // 2, nx // 2, 32), 3.0, dtype=torch.bfloat16, device="cuda")
+    U.avgpool2(Slice(bf16t(big), 16, 24), Slice(ybuf, 8, 24), 24, (nx, ny, nz))
+    out = host(ybuf)
+    want = big[..., 16:40].reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2, 24).mean(axis=(1, 3, 5))
+    np.testing.assert_allclose(out[..., 8:32], want, rtol=2 ** -7, atol=1e-6)
+    assert np.all(out[..., :8] == 3.0)
+    ubuf = torch.full((nz, ny, nx, 40), 5.0, dtype=torch.bfloat16, device="cuda")
+    U.upsample2(Slice(ybuf, 8, 24), Slice(ubuf, 16, 24), 24, (nx // 2, ny // 2, nz // 2))
+    up = host(ubuf)
+    np.testing.assert_array_equal(up[..., 16:40], np.repeat(np.repeat(np.repeat(out[..., 8:32], 2, 0), 2, 1), 2, 2))
+    assert np.all(up[..., :16] == 5.0)
+    with pytest.raises(RuntimeError):
+        U.avgpool2(bf16t(big[..., :12]), ybuf[..., :12].contiguous(), 12, (nx, ny, nz))
+    # FP64 fields: restriction and prolongation of 3 fields on a (16, 8, 4) grid
+    f = rng.standard_normal((3, nz, ny, nx))
+    fd = torch.from_numpy(f).cuda()
+    c = torch.empty((3, nz // 2, ny // 2, nx // 2), dtype=torch.float64, device="cuda")
+    U.restrict2_fields(fd, c, 3, (nx // 2, ny // 2, nz // 2))
+    want_c = f.reshape(3, nz // 2, 2, ny // 2, 2, nx // 2, 2).mean(axis=(2, 4, 6))
+    np.testing.assert_allclose(c.cpu().numpy(), want_c, rtol=1e-14, atol=1e-15)
+    fine = torch.empty((3, nz, ny, nx), dtype=torch.float64, device="cuda")
+    U.prolong2_fields(c, fine, 3, (nx // 2, ny // 2, nz // 2))
+    cc = c.cpu().numpy()
+
+    def lin(a, axis):   # cell-centred linear 2x along one axis, periodic: 3/4 own + 1/4 neighbour
+        lo = 0.75 * a + 0.25 * np.roll(a, 1, axis)
+        hi = 0.75 * a + 0.25 * np.roll(a, -1, axis)
+        return np.stack([lo, hi], axis=axis + 1).reshape(a.shape[:axis] + (2 * a.shape[axis],) + a.shape[axis + 1:])
+
+    want_f = lin(lin(lin(cc, 1), 2), 3)
+    np.testing.assert_allclose(fine.cpu().numpy(), want_f, rtol=1e-13, atol=1e-14)
+
+
 def test_head_mse_bias_relu_adam(mods):
     U = mods[0]
     rng = np.random.default_rng(2)
