@@ -76,7 +76,8 @@ typedef struct {
     int coarse_sweeps;    /* red-black sweeps on the coarsest level (default 60)                  */
     int use_graph;        /* 1 = replay each outer iteration as a captured CUDA graph (default 1); 0 = direct
                              launches; 2 = as 1, and a batch (mg_batch_solve) is paced from the host     */
-    long long spin_limit; /* bound on any device-side wait, in polls (default 1<<24)              */
+    long long spin_limit; /* bound on any device-side wait, in polls (default 1<<24; 0: every wait
+                             gives up at once and the solve returns MG_ERR_TIMEOUT)                 */
     int inner_cycles;     /* V-cycles per outer iteration, 0 = auto (1 for MG_FP64, 2 for MG_MIXED) */
     int block_threads;    /* threads per block of the global-memory stencil kernels: 0 = 256, else 64, 128 or 256 */
     int smoother;         /* 0 = auto: the TMA-tiled colour pass and restriction on FP32 levels with nx, ny

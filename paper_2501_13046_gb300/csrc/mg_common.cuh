@@ -119,11 +119,11 @@ TileCoef<T> make_tile_coef(const Geo &g, int order, double omega = 1.0)
             const double ih2 = 1.0 / (g.h[a] * g.h[a]), s = a == A ? 4.0 / 3.0 : 1.0;
             t.mk1[A][a] = (T)(s * k1 * ih2);
             t.mnk2[A][a] = (T)(s * k2 * ih2);
-            const double x = 1.0 / (3.0 * g.h[A] * g.h[a]);
-            t.x11[A][a] = (T)(c1 * c1 * x);
-            t.x12[A][a] = (T)(-c1 * c2 * x);
-            t.x22[A][a] = (T)(c2 * c2 * x);
         }
+        t.d1[A] = (T)(c1 / g.h[A]);
+        t.d2[A] = (T)(c2 / g.h[A]);
+        t.t1[A] = (T)(c1 / (3.0 * g.h[A]));
+        t.t2[A] = (T)(c2 / (3.0 * g.h[A]));
         t.idW[A] = (T)(omega / m0);
     }
     t.iom = (T)(1.0 / omega);

@@ -2,19 +2,31 @@
 // pass of the smoother and the fused residual + restriction.
 //
 // A CTA owns a tile of 32 colour pairs (64 cells) in x by 8 rows in y and marches through a
-// chunk of z planes.  Each plane of the 4 correction fields (both colour halves, the tile plus
-// its stencil halo) is brought into a ring of shared-memory slots by two TMA tensor loads
-// (cp.async.bulk.tensor, one per colour half) completing on an mbarrier; the stencils then read
-// only shared memory.  Halo cells outside the box (periodic wrap, the Robin 1/r ghost value
-// v(clamp(g)) |x_clamp| / |x_g|, or a mirror image across a symmetry plane with W's normal component
-// negated) are not addressable by the tensor load, which fills them with
-// zeros: the CTA fetches them with plain loads one plane ahead and writes them over the zero
-// fill once the plane's TMA has completed.  One barrier per plane orders everything: before it
-// the plane about to enter the stencil window is completed (TMA wait + halo), after it the slot
-// of the plane that left the window is refilled while the current plane is computed.
+// chunk of z planes; thread (lane, warp) keeps the pair `lane` of row `warp` for the whole march.
+// Each plane of the 4 correction fields (both colour halves, the tile plus its stencil halo in x
+// and y) is brought into a ring of shared-memory slots by two TMA tensor loads
+// (cp.async.bulk.tensor, one per colour half) completing on an mbarrier.  Halo cells outside the
+// box (periodic wrap, the Robin 1/r ghost value v(clamp(g)) |x_clamp| / |x_g|, a mirror image
+// across a symmetry plane with W's normal component negated, or an extrapolated value) are not
+// addressable by the tensor load, which fills them with zeros: the CTA fetches them with plain
+// loads while the plane is in flight and writes them over the zero fill once its TMA has completed.
 //
-// The operator is that of apply_J (same discrete stencils and reads) with the grid spacing,
-// the 1/3 of the grad-div term and the tensor-product weights folded into per-level constants.
+// Only the plane being computed is read from shared memory.  Its contribution to every stencil
+// that reaches it along z is pushed into per-thread pending sums of the planes z - H .. z + H
+// (registers), and a cell is finished H planes later, once its last z tap has arrived:
+//  * the z taps of the four Laplacians take the pair's own two cells;
+//  * the mixed terms that involve z are applied as a z derivative of an in-plane first
+//    derivative, D_A D_z f = D_z (D_A f) (A = x, y), so D_x W_x, D_y W_y, D_x W_z and D_y W_z are
+//    formed once per plane at both cells of the pair;
+//  * the in-plane parts (x and y taps, D_x D_y) are summed from the plane directly.
+// That is 74 shared-memory reads per updated cell in the colour pass (the direct form of the
+// whole stencil takes 148) and 44 per cell in the residual.  The ring holds the plane being
+// computed plus five in flight (a chunk of two planes is issued whole); one barrier per plane orders
+// everything.  The 2H halo planes of a chunk only push their z taps (no in-plane part).
+//
+// The operator is that of apply_J (the same discrete stencils on the same values) with the grid
+// spacing, the 1/3 of the grad-div term and the tensor-product weights folded into per-level
+// constants; only the FP rounding order differs.
 //
 // Requirements (checked on the host): colour-split level, nx and ny multiples of 8 and >= 16,
 // nz >= 8 (and even chunks for the restriction), so every TMA x coordinate and stride is
@@ -32,22 +44,38 @@ constexpr int kTilePad = 4;                     // pairs loaded left of the tile
 constexpr int kTileW = kTileP + 2 * kTilePad;   // pairs per loaded row (40)
 constexpr int kTileThreads = kTileP * kTileY;   // 256
 constexpr int kTileFix = 3;                     // halo fix-up elements per thread and plane
+constexpr int kColourSlots = 5;                 // colour pass ring: the plane being computed + 4 in flight
+constexpr int kRestrictSlots = 4;               // residual ring: + 3 in flight
+constexpr int kColourAhead = 3;                 // planes ahead at which a cell's right-hand side is fetched
+constexpr int kRestrictAhead = 2;
+constexpr int kColourVals = 6;                  // fetched per thread and plane: a, b, f_0..3 of one cell
+constexpr int kRestrictVals = 12;               // ... of both cells of the pair
 constexpr long long kTileDrain = 1LL << 26;     // polls allowed for in-flight loads after a failed wait
 
 template <int ORDER> __host__ __device__ constexpr int tile_rows() { return kTileY + ORDER; }   // 8 + 2 halo
-template <int ORDER> __host__ __device__ constexpr int tile_slots() { return ORDER + 2; }      // 2H+1 + 1
 template <int ORDER> __host__ __device__ constexpr int tile_field_elems() { return tile_rows<ORDER>() * kTileW; }
 template <int ORDER> __host__ __device__ constexpr int tile_half_elems() { return 4 * tile_field_elems<ORDER>(); }
 template <int ORDER> __host__ __device__ constexpr int tile_slot_elems() { return 2 * tile_half_elems<ORDER>(); }
+// shared memory: the ring's slots, its mbarriers (16-byte padded), then the per-thread staging of
+// the fetched right-hand sides ([plane slot][value][thread]); the restriction adds the hand-over of
+// the odd rows' partial sums (4 warps x 32 lanes x 4 fields)
+template <typename T, int ORDER, int S> __host__ __device__ constexpr size_t tile_ring_bytes()
+{
+    return (size_t)S * tile_slot_elems<ORDER>() * sizeof(T) + 16 * ((8 * S + 15) / 16);
+}
 template <typename T, int ORDER> __host__ __device__ constexpr size_t tile_smem_bytes()
 {
-    return (size_t)tile_slots<ORDER>() * tile_slot_elems<ORDER>() * sizeof(T) + 8 * tile_slots<ORDER>();
+    return tile_ring_bytes<T, ORDER, kColourSlots>() + (size_t)(kColourAhead + 1) * kColourVals * kTileThreads * sizeof(T);
 }
-// restriction: plus the staging of the odd rows' partial sums (4 warps x 32 lanes x 4 fields)
 template <typename T, int ORDER> __host__ __device__ constexpr size_t tile_restrict_smem_bytes()
 {
-    return tile_smem_bytes<T, ORDER>() + 16 + (size_t)(kTileY / 2) * 32 * 4 * sizeof(T);
+    return tile_ring_bytes<T, ORDER, kRestrictSlots>() +
+           (size_t)(kRestrictAhead + 1) * kRestrictVals * kTileThreads * sizeof(T) + (size_t)(kTileY / 2) * 32 * 4 * sizeof(T);
 }
+static_assert(tile_smem_bytes<double, 4>() <= 227 * 1024 && tile_restrict_smem_bytes<double, 4>() <= 227 * 1024,
+              "tiles fit the shared memory of one CTA");
+static_assert(2 * tile_smem_bytes<float, 4>() <= 227 * 1024 && 2 * tile_restrict_smem_bytes<float, 4>() <= 227 * 1024,
+              "two FP32 CTAs fit one SM");
 
 struct TileGrid {
     int ntx, nty;   // tiles along x (pairs) and y (rows)
@@ -59,7 +87,8 @@ template <typename T>
 struct TileCoef {
     T lk0, lk1[3], lnk2[3];              // Lap f = lk0 f + sum_a lk1 (f+a + f-a) + lnk2 (f+2a + f-2a)
     T mk0[3], mk1[3][3], mnk2[3][3];     // row A: Lap W_A + (1/3) D_AA W_A, same form
-    T x11[3][3], x12[3][3], x22[3][3];   // (1/3) D_A D_B f = x11 g11 + x12 (g12 + g21) + x22 g22
+    T d1[3], d2[3];                      // D_a f = d1 (f+a - f-a) - d2 (f+2a - f-2a)
+    T t1[3], t2[3];                      // the same with the 1/3 of the grad-div term: (1/3) D_a
     T dl;                                // diagonal of Lap (psi-row update)
     T idW[3];                            // omega / diagonal of row A
     T iom;                               // 1 / omega
@@ -110,6 +139,20 @@ __device__ __forceinline__ bool tile_mbar_wait(uint64_t *mb, uint32_t parity, lo
 
 // generic-proxy accesses of shared memory are ordered before later async-proxy (TMA) writes
 __device__ __forceinline__ void tile_fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Per-thread asynchronous copy of one element from global into shared memory; it completes with the
+// thread's cp.async groups (commit / wait), so only the issuing thread reads it back.
+template <typename T>
+__device__ __forceinline__ void tile_copy_async(T *dst, const T *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sm_addr(dst)), "l"(__cvta_generic_to_global(src)),
+                 "n"((int)sizeof(T))
+                 : "memory");
+}
+__device__ __forceinline__ void tile_copy_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void tile_copy_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void tile_copy_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // 5-D tiled tensor load into shared memory, completing its bytes on the mbarrier.
 __device__ __forceinline__ void tile_tma_load(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
@@ -167,11 +210,14 @@ __device__ __forceinline__ T tile_fetch(const Geo &g, const T *X, const T *O, in
 
 // ---------------------------------------------------------------- the plane ring
 // Loading side of a tiled kernel: geometry of the CTA's tile, the TMA ring and the halo fix-ups.
-// Usage: prologue(); then for every plane z of the chunk: advance(z) (false: stop, the CTA
-// failed a bounded wait) followed by the plane's computation; finally finish(failed).
-template <typename T, int ORDER, int BC>
+// Relative plane p = 0 .. NP-1 is plane zs + p (zs = z0 - H: the chunk plus H halo planes on each
+// side) and lives in slot p % S; its tensor loads are issued DEP = S - 1 planes ahead, its halo
+// values fetched one plane ahead (while the previous plane is computed).  Usage: prologue(); then
+// for every p: advance(p) (false: stop, the CTA failed a bounded wait) followed by the plane's
+// computation from slot(p); finally finish(failed).
+template <typename T, int ORDER, int BC, int S>
 struct TileRing {
-    static constexpr int H = ORDER / 2, RY = tile_rows<ORDER>(), S = tile_slots<ORDER>();
+    static constexpr int H = ORDER / 2, RY = tile_rows<ORDER>(), DEP = S - 1;
     static constexpr int FE = tile_field_elems<ORDER>(), HE = tile_half_elems<ORDER>(), SE = tile_slot_elems<ORDER>();
 
     T *sm;
@@ -184,7 +230,7 @@ struct TileRing {
     int P0, y0, z0, z1, tpt, zs, NP, tid;
     int npos, done, issued;
     int fo[kTileFix], fP[kTileFix], fy[kTileFix], fh[kTileFix], ff[kTileFix];
-    T fv[kTileFix];   // halo values of the plane issued last, stored after its TMA completes
+    T fv[kTileFix];   // halo values of the next plane, stored once its tensor loads have landed
 
     __device__ __forceinline__ void setup(unsigned char *smem_raw, const Geo &geo, const T *X_, const T *O_,
                                           const CUtensorMap *mX, const CUtensorMap *mO, int col, const TileGrid &tg,
@@ -252,6 +298,8 @@ struct TileRing {
 
     __device__ __forceinline__ bool ghost(int p) const { return BC != BC_PERIODIC && (zs + p < 0 || zs + p >= g->n[2]); }
 
+    __device__ __forceinline__ T *slot(int p) const { return sm + (p % S) * SE; }
+
     __device__ __forceinline__ void issue(int p)   // one thread: start the loads of relative plane p
     {
         uint64_t *mb = bar + p % S;
@@ -259,7 +307,7 @@ struct TileRing {
         int z = zs + p;
         const int nz = g->n[2];
         if (BC == BC_PERIODIC) { z += z < 0 ? nz : 0; z -= z >= nz ? nz : 0; }
-        T *dst = sm + (p % S) * SE;
+        T *dst = slot(p);
         tile_mbar_expect_tx(mb, (uint32_t)(2 * HE * sizeof(T)));
         tile_tma_load(dst + colour * HE, tmX, P0 - kTilePad, y0 - H, z, 0, colour, mb);
         tile_tma_load(dst + (1 - colour) * HE, tmO, P0 - kTilePad, y0 - H, z, 0, 1 - colour, mb);
@@ -267,7 +315,7 @@ struct TileRing {
 
     __device__ __forceinline__ void fill_plane(int p)   // every element of a Robin ghost plane
     {
-        T *dst = sm + (p % S) * SE;
+        T *dst = slot(p);
         const int tot = 8 * RY * npos;
         for (int e = tid; e < tot; e += kTileThreads) {
             const int hf = e & 7, h = hf >> 2, fld = hf & 3;
@@ -286,10 +334,18 @@ struct TileRing {
 
     __device__ __forceinline__ void store_fix(int p)
     {
-        T *dst = sm + (p % S) * SE;
+        T *dst = slot(p);
 #pragma unroll
         for (int i = 0; i < kTileFix; ++i)
             if (fo[i] >= 0) dst[fo[i]] = fv[i];
+    }
+
+    // one plane ahead: fill plane p (ghost plane; its slot receives no tensor load) or fetch its
+    // halo values (stored once its tensor loads have landed)
+    __device__ __forceinline__ void stage(int p)
+    {
+        if (ghost(p)) fill_plane(p);
+        else load_fix(p);
     }
 
     __device__ __forceinline__ bool wait(int p, long long limit)
@@ -297,46 +353,37 @@ struct TileRing {
         return tile_mbar_wait(bar + p % S, (uint32_t)((p / S) & 1), limit);
     }
 
-    // planes 0 .. 2H: issue all, complete 0 .. 2H-1 here, stage the halo of 2H
+    // issue planes 0 .. DEP-1, stage plane 0
     __device__ __forceinline__ bool prologue()
     {
         if (tid < S) tile_mbar_init(bar + tid, 1);
         tile_mbar_init_fence();
         __syncthreads();
+        const int np = min(DEP, NP);
         if (tid == 0)
-            for (int p = 0; p <= 2 * H; ++p) issue(p);
-        issued = 2 * H;
-        bool ok = true;
-        for (int p = 0; p < 2 * H; ++p) {
-            if (ghost(p)) { fill_plane(p); continue; }
-            ok = ok && wait(p, spin);
-            load_fix(p);
-            store_fix(p);
-        }
-        if (ghost(2 * H)) fill_plane(2 * H);
-        else load_fix(2 * H);
-        return ok;
+            for (int p = 0; p < np; ++p) issue(p);
+        issued = np - 1;
+        stage(0);
+        return true;
     }
 
-    // Before computing plane z: complete plane z + H, then (after the barrier) refill the slot of
-    // plane z - H - 1 with plane z + H + 1.  Returns false, for every thread, if a wait gave up.
-    __device__ __forceinline__ bool advance(int z, bool ok)
+    // Before computing plane p: complete it, then (after the barrier) reuse the slot of plane p - 1
+    // for plane p + DEP and stage plane p + 1.  Returns false, for every thread, if a wait gave up.
+    __device__ __forceinline__ bool advance(int p, bool ok)
     {
-        const int p = z - zs;
-        ok = ok && wait(p + H, spin);
-        if (!ghost(p + H)) store_fix(p + H);
+        ok = ok && wait(p, spin);
+        if (!ghost(p)) store_fix(p);
         if (__syncthreads_or(!ok)) return false;
-        done = p + H;
-        const int pn = p + H + 1;
+        done = p;
+        const int pn = p + DEP;
         if (pn < NP) {
             if (tid == 0) {
                 tile_fence_proxy_async();
                 issue(pn);
             }
             issued = pn;
-            if (ghost(pn)) fill_plane(pn);
-            else load_fix(pn);
         }
+        if (p + 1 < NP) stage(p + 1);
         return true;
     }
 
@@ -348,93 +395,229 @@ struct TileRing {
         // tensor load of an in-bounds box always completes; the bound only guards the poll)
         for (int p = done + 1; p <= issued; ++p) wait(p, spin > kTileDrain ? spin : kTileDrain);
     }
+};
 
-    // offset of the cell (lane, warp row w, plane z) in the colour half `half` of each window plane
-    __device__ __forceinline__ void bases(int z, int w, int lane, int half, int (&ob)[2 * H + 1]) const
+// ---------------------------------------------------------------- one plane of the tile
+// Field F at the cell of x-bit `bit` in pair P + dp, row y + dy of a plane (HB: the colour of the
+// pair's even-x cell in row y; s: pair P, row y, field 0 of colour half 0 of the plane's slot).
+template <typename T, int ORDER, int HB>
+struct PlaneView {
+    const T *s;
+    __device__ __forceinline__ T operator()(int F, int bit, int dp, int dy) const
     {
-        const int p = z - zs;
-#pragma unroll
-        for (int d = -H; d <= H; ++d) ob[d + H] = ((p + d) % S) * SE + half * HE + (w + H) * kTileW + kTilePad + lane;
+        return s[((bit + HB + dy) & 1) * tile_half_elems<ORDER>() + F * tile_field_elems<ORDER>() + dy * kTileW + dp];
     }
 };
 
-// Shared-memory accessor of one field around a cell: ob[dz + H] is the cell's offset in its
-// colour half of plane z + dz, OH moves to the other colour half, PA is the cell's x parity (a
-// neighbour at odd dx sits in pair m + PA + (dx-1)/2); fo is the field offset.
-template <typename T, int ORDER, int OH, int PA>
-struct AccT {
-    const T *sm;
-    const int *ob;
-    int fo;
-    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
-    {
-        int o = ob[dz + ORDER / 2] + fo + dy * kTileW;
-        if ((dx + dy + dz) & 1) o += OH;
-        o += (dx & 1) ? PA + ((dx - 1) >> 1) : (dx >> 1);
-        return sm[o];
-    }
-};
+// column tap j of c[bit][j] is row offset col_dy(j): -H .. -1, 1 .. H
+__host__ __device__ constexpr int col_dy(int j, int H) { return j < H ? j - H : j - H + 1; }
 
-// ---------------------------------------------------------------- folded operator
-template <int ORDER, typename T, class F>
-__device__ __forceinline__ T lap_fold(const F &f, T c, T k0, const T *k1, const T *nk2)
+// row y of field F: r[k] is the cell x = 2P - 2 + k (k = 0 .. 5; ORDER 2 reads 1 .. 4)
+template <int ORDER, typename T, class V>
+__device__ __forceinline__ void tile_row(const V &v, int F, T (&r)[6])
 {
-    T s = k0 * c;
-    s = fma(k1[0], f(1, 0, 0) + f(-1, 0, 0), s);
-    s = fma(k1[1], f(0, 1, 0) + f(0, -1, 0), s);
-    s = fma(k1[2], f(0, 0, 1) + f(0, 0, -1), s);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r[k] = (ORDER == 4 || (k >= 1 && k <= 4)) ? v(F, k & 1, (k >> 1) - 1, 0) : (T)0;
+}
+
+// columns of the pair's two cells: c[bit][j] at row y + col_dy(j)
+template <int ORDER, typename T, class V>
+__device__ __forceinline__ void tile_cols(const V &v, int F, T (&c)[2][ORDER])
+{
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int j = 0; j < ORDER; ++j) c[b][j] = v(F, b, 0, col_dy(j, ORDER / 2));
+}
+
+// first derivative along x at the pair's cell of bit b, from its row
+template <int ORDER, typename T>
+__device__ __forceinline__ T dx_row(const T (&r)[6], int b, T d1, T d2)
+{
+    T s = d1 * (r[3 + b] - r[1 + b]);
+    if constexpr (ORDER == 4) s = fma(-d2, r[4 + b] - r[b], s);
+    return s;
+}
+
+// first derivative along a column (taps col_dy(j))
+template <int ORDER, typename T>
+__device__ __forceinline__ T d_col(const T (&c)[ORDER], T d1, T d2)
+{
+    constexpr int H = ORDER / 2;
+    T s = d1 * (c[H] - c[H - 1]);
+    if constexpr (ORDER == 4) s = fma(-d2, c[3] - c[0], s);
+    return s;
+}
+
+// in-plane part (centre, x and y taps) of a Laplacian-form stencil at the pair's cell of bit b
+template <int ORDER, typename T>
+__device__ __forceinline__ T lap_xy(const T (&r)[6], const T (&c)[ORDER], int b, T k0, const T *k1, const T *nk2)
+{
+    constexpr int H = ORDER / 2;
+    T s = k0 * r[2 + b];
+    s = fma(k1[0], r[1 + b] + r[3 + b], s);
+    s = fma(k1[1], c[H - 1] + c[H], s);
     if constexpr (ORDER == 4) {
-        s = fma(nk2[0], f(2, 0, 0) + f(-2, 0, 0), s);
-        s = fma(nk2[1], f(0, 2, 0) + f(0, -2, 0), s);
-        s = fma(nk2[2], f(0, 0, 2) + f(0, 0, -2), s);
+        s = fma(nk2[0], r[b] + r[4 + b], s);
+        s = fma(nk2[1], c[0] + c[3], s);
     }
     return s;
 }
 
-// (1/3) D_A D_B f from the antisymmetric corner sums g(a, b) = f(a,b) + f(-a,-b) - f(a,-b) - f(-a,b)
-template <int ORDER, int A, int B, typename T, class F>
-__device__ __forceinline__ T dmix_fold(const F &f, T x11, T x12, T x22)
+// (1/3) D_x D_y f at the pair's cell of bit b: D_x along the rows y + dy, then (1/3) D_y of those.
+// own: the pair's columns of f (tile_cols); the neighbouring pairs' columns are read here.
+template <int ORDER, typename T, class V>
+__device__ __forceinline__ T mix_xy(const V &v, int F, const T (&own)[2][ORDER], int b, const TileCoef<T> &tc)
 {
-    auto gq = [&](int a, int b) {
-        return (ax2<A, B>(f, a, b) + ax2<A, B>(f, -a, -b)) - (ax2<A, B>(f, a, -b) + ax2<A, B>(f, -a, b));
-    };
-    T r = x11 * gq(1, 1);
-    if constexpr (ORDER == 4) {
-        r = fma(x12, gq(1, 2) + gq(2, 1), r);
-        r = fma(x22, gq(2, 2), r);
+    T u[ORDER];
+#pragma unroll
+    for (int j = 0; j < ORDER; ++j) {
+        const int dy = col_dy(j, ORDER / 2);
+        auto col = [&](int k) -> T { return (k == 2 || k == 3) ? own[k - 2][j] : v(F, k & 1, (k >> 1) - 1, dy); };
+        T s = tc.d1[0] * (col(3 + b) - col(1 + b));
+        if constexpr (ORDER == 4) s = fma(-tc.d2[0], col(4 + b) - col(b), s);
+        u[j] = s;
     }
-    return r;
+    return d_col<ORDER>(u, tc.t1[1], tc.t2[1]);
 }
 
-// out = J e at one cell (the operator of apply_J), centre values in ctr.
-template <int ORDER, typename T, class F>
-__device__ __forceinline__ void apply_J_fold(const F &e0, const F &e1, const F &e2, const F &e3, T ca, T cb,
-                                             const TileCoef<T> &tc, T out[4], T ctr[4])
+// Pushes of one plane's value into the pending sums acc(k) of planes zq - H + k: a symmetric z tap
+// (Laplacian weights w1 at distance 1, w2 at 2; vq: the value seen at distance 1, vp at distance 2)
+template <int ORDER, typename T, class A>
+__device__ __forceinline__ void push_lap(A &&acc, T vq, T vp, T w1, T w2)
 {
-    ctr[0] = e0(0, 0, 0);
-    ctr[1] = e1(0, 0, 0);
-    ctr[2] = e2(0, 0, 0);
-    ctr[3] = e3(0, 0, 0);
-    out[0] = fma(ca, lap_fold<ORDER>(e0, ctr[0], tc.lk0, tc.lk1, tc.lnk2), cb * ctr[0]);
-    out[1] = lap_fold<ORDER>(e1, ctr[1], tc.mk0[0], tc.mk1[0], tc.mnk2[0]) +
-             (dmix_fold<ORDER, 0, 1>(e2, tc.x11[0][1], tc.x12[0][1], tc.x22[0][1]) +
-              dmix_fold<ORDER, 0, 2>(e3, tc.x11[0][2], tc.x12[0][2], tc.x22[0][2]));
-    out[2] = lap_fold<ORDER>(e2, ctr[2], tc.mk0[1], tc.mk1[1], tc.mnk2[1]) +
-             (dmix_fold<ORDER, 1, 0>(e1, tc.x11[1][0], tc.x12[1][0], tc.x22[1][0]) +
-              dmix_fold<ORDER, 1, 2>(e3, tc.x11[1][2], tc.x12[1][2], tc.x22[1][2]));
-    out[3] = lap_fold<ORDER>(e3, ctr[3], tc.mk0[2], tc.mk1[2], tc.mnk2[2]) +
-             (dmix_fold<ORDER, 2, 0>(e1, tc.x11[2][0], tc.x12[2][0], tc.x22[2][0]) +
-              dmix_fold<ORDER, 2, 1>(e2, tc.x11[2][1], tc.x12[2][1], tc.x22[2][1]));
+    constexpr int H = ORDER / 2;
+    acc(H - 1) = fma(w1, vq, acc(H - 1));
+    acc(H + 1) = fma(w1, vq, acc(H + 1));
+    if constexpr (ORDER == 4) {
+        acc(0) = fma(w2, vp, acc(0));
+        acc(4) = fma(w2, vp, acc(4));
+    }
 }
 
-// J e of the cell with x parity PA in colour half HALF (both compile-time) from the window.
-template <typename T, int ORDER, int HALF, int PA>
-__device__ __forceinline__ void tile_apply(const T *sm, const int *ob, T ca, T cb, const TileCoef<T> &tc, T Je[4],
-                                           T ctr[4])
+// ... and an antisymmetric one: the z derivative t1 (g(z+1) - g(z-1)) - t2 (g(z+2) - g(z-2))
+template <int ORDER, typename T, class A>
+__device__ __forceinline__ void push_dz(A &&acc, T gq, T gp, T t1, T t2)
 {
-    constexpr int FE = tile_field_elems<ORDER>(), OH = (1 - 2 * HALF) * tile_half_elems<ORDER>();
-    AccT<T, ORDER, OH, PA> a0{sm, ob, 0}, a1{sm, ob, FE}, a2{sm, ob, 2 * FE}, a3{sm, ob, 3 * FE};
-    apply_J_fold<ORDER, T>(a0, a1, a2, a3, ca, cb, tc, Je, ctr);
+    constexpr int H = ORDER / 2;
+    acc(H - 1) = fma(t1, gq, acc(H - 1));    // this plane is the +1 tap of plane zq - 1
+    acc(H + 1) = fma(-t1, gq, acc(H + 1));   // and the -1 tap of plane zq + 1
+    if constexpr (ORDER == 4) {
+        acc(0) = fma(-t2, gp, acc(0));
+        acc(4) = fma(t2, gp, acc(4));
+    }
+}
+
+// Colour pass: contributions of the current plane to the pending sums acc[k][row] (planes
+// zq - H + k, each at its cell of the pass's colour), with the cell of this plane at x-bit PQ.
+// The cell of plane zq +- 1 sits at the other bit, that of zq +- 2 at PQ.  FULL = false: a halo
+// plane of the chunk, whose own cell is not updated (z taps only).
+template <typename T, int ORDER, int HB, int PQ, bool FULL>
+__device__ __forceinline__ void colour_plane(const T *s, const TileCoef<T> &tc, T (&acc)[ORDER + 1][4], T (&ctr)[4])
+{
+    constexpr int H = ORDER / 2, Q = 1 - PQ;
+    const PlaneView<T, ORDER, HB> v{s};
+    T r[6], c[2][ORDER];
+    auto row = [&](int a) { return [&acc, a](int k) -> T & { return acc[k][a]; }; };
+    // psi row: Laplacian
+    tile_row<ORDER>(v, 0, r);
+    tile_cols<ORDER>(v, 0, c);
+    if constexpr (FULL) {
+        ctr[0] = r[2 + PQ];
+        acc[H][0] += lap_xy<ORDER>(r, c[PQ], PQ, tc.lk0, tc.lk1, tc.lnk2);
+    }
+    push_lap<ORDER>(row(0), r[2 + Q], r[2 + PQ], tc.lk1[2], tc.lnk2[2]);
+    // W_x: its row's Laplacian, (1/3) D_z D_x W_x of the z row, (1/3) D_y D_x W_x of the y row
+    tile_row<ORDER>(v, 1, r);
+    tile_cols<ORDER>(v, 1, c);
+    if constexpr (FULL) {
+        ctr[1] = r[2 + PQ];
+        acc[H][1] += lap_xy<ORDER>(r, c[PQ], PQ, tc.mk0[0], tc.mk1[0], tc.mnk2[0]);
+        acc[H][2] += mix_xy<ORDER>(v, 1, c, PQ, tc);
+    }
+    push_lap<ORDER>(row(1), r[2 + Q], r[2 + PQ], tc.mk1[0][2], tc.mnk2[0][2]);
+    push_dz<ORDER>(row(3), dx_row<ORDER>(r, Q, tc.d1[0], tc.d2[0]), dx_row<ORDER>(r, PQ, tc.d1[0], tc.d2[0]),
+                   tc.t1[2], tc.t2[2]);
+    // W_y: its row's Laplacian, (1/3) D_z D_y W_y of the z row, (1/3) D_x D_y W_y of the x row
+    tile_row<ORDER>(v, 2, r);
+    tile_cols<ORDER>(v, 2, c);
+    if constexpr (FULL) {
+        ctr[2] = r[2 + PQ];
+        acc[H][2] += lap_xy<ORDER>(r, c[PQ], PQ, tc.mk0[1], tc.mk1[1], tc.mnk2[1]);
+        acc[H][1] += mix_xy<ORDER>(v, 2, c, PQ, tc);
+    }
+    push_lap<ORDER>(row(2), r[2 + Q], r[2 + PQ], tc.mk1[1][2], tc.mnk2[1][2]);
+    push_dz<ORDER>(row(3), d_col<ORDER>(c[Q], tc.d1[1], tc.d2[1]), d_col<ORDER>(c[PQ], tc.d1[1], tc.d2[1]), tc.t1[2],
+                   tc.t2[2]);
+    // W_z: its row's Laplacian, (1/3) D_z D_x W_z of the x row, (1/3) D_z D_y W_z of the y row
+    tile_row<ORDER>(v, 3, r);
+    tile_cols<ORDER>(v, 3, c);
+    if constexpr (FULL) {
+        ctr[3] = r[2 + PQ];
+        acc[H][3] += lap_xy<ORDER>(r, c[PQ], PQ, tc.mk0[2], tc.mk1[2], tc.mnk2[2]);
+    }
+    push_lap<ORDER>(row(3), r[2 + Q], r[2 + PQ], tc.mk1[2][2], tc.mnk2[2][2]);
+    push_dz<ORDER>(row(1), dx_row<ORDER>(r, Q, tc.d1[0], tc.d2[0]), dx_row<ORDER>(r, PQ, tc.d1[0], tc.d2[0]),
+                   tc.t1[2], tc.t2[2]);
+    push_dz<ORDER>(row(2), d_col<ORDER>(c[Q], tc.d1[1], tc.d2[1]), d_col<ORDER>(c[PQ], tc.d1[1], tc.d2[1]), tc.t1[2],
+                   tc.t2[2]);
+}
+
+// Residual: contributions of the current plane at both cells of the pair (acc[k][bit][row]; every
+// z tap of a cell comes from the same bit of the other planes); cp: the psi values (the psi row's
+// b coefficient multiplies its centre value when the cell is finished).  FULL = false: a halo plane.
+template <typename T, int ORDER, int HB, bool FULL>
+__device__ __forceinline__ void residual_plane(const T *s, const TileCoef<T> &tc, T (&acc)[ORDER + 1][2][4],
+                                               T (&cp)[2])
+{
+    constexpr int H = ORDER / 2;
+    const PlaneView<T, ORDER, HB> v{s};
+    T r[6], c[2][ORDER];
+    auto row = [&](int b, int a) { return [&acc, b, a](int k) -> T & { return acc[k][b][a]; }; };
+    tile_row<ORDER>(v, 0, r);
+    tile_cols<ORDER>(v, 0, c);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        if constexpr (FULL) {
+            cp[b] = r[2 + b];
+            acc[H][b][0] += lap_xy<ORDER>(r, c[b], b, tc.lk0, tc.lk1, tc.lnk2);
+        }
+        push_lap<ORDER>(row(b, 0), r[2 + b], r[2 + b], tc.lk1[2], tc.lnk2[2]);
+    }
+    tile_row<ORDER>(v, 1, r);
+    tile_cols<ORDER>(v, 1, c);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        if constexpr (FULL) {
+            acc[H][b][1] += lap_xy<ORDER>(r, c[b], b, tc.mk0[0], tc.mk1[0], tc.mnk2[0]);
+            acc[H][b][2] += mix_xy<ORDER>(v, 1, c, b, tc);
+        }
+        push_lap<ORDER>(row(b, 1), r[2 + b], r[2 + b], tc.mk1[0][2], tc.mnk2[0][2]);
+        const T gx = dx_row<ORDER>(r, b, tc.d1[0], tc.d2[0]);
+        push_dz<ORDER>(row(b, 3), gx, gx, tc.t1[2], tc.t2[2]);
+    }
+    tile_row<ORDER>(v, 2, r);
+    tile_cols<ORDER>(v, 2, c);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        if constexpr (FULL) {
+            acc[H][b][2] += lap_xy<ORDER>(r, c[b], b, tc.mk0[1], tc.mk1[1], tc.mnk2[1]);
+            acc[H][b][1] += mix_xy<ORDER>(v, 2, c, b, tc);
+        }
+        push_lap<ORDER>(row(b, 2), r[2 + b], r[2 + b], tc.mk1[1][2], tc.mnk2[1][2]);
+        const T gy = d_col<ORDER>(c[b], tc.d1[1], tc.d2[1]);
+        push_dz<ORDER>(row(b, 3), gy, gy, tc.t1[2], tc.t2[2]);
+    }
+    tile_row<ORDER>(v, 3, r);
+    tile_cols<ORDER>(v, 3, c);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        if constexpr (FULL) acc[H][b][3] += lap_xy<ORDER>(r, c[b], b, tc.mk0[2], tc.mk1[2], tc.mnk2[2]);
+        push_lap<ORDER>(row(b, 3), r[2 + b], r[2 + b], tc.mk1[2][2], tc.mnk2[2][2]);
+        const T gx = dx_row<ORDER>(r, b, tc.d1[0], tc.d2[0]), gy = d_col<ORDER>(c[b], tc.d1[1], tc.d2[1]);
+        push_dz<ORDER>(row(b, 1), gx, gx, tc.t1[2], tc.t2[2]);
+        push_dz<ORDER>(row(b, 2), gy, gy, tc.t1[2], tc.t2[2]);
+    }
 }
 
 // ---------------------------------------------------------------- colour pass
@@ -447,39 +630,83 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int H = ORDER / 2;
-    TileRing<T, ORDER, BC> ring;
+    TileRing<T, ORDER, BC, kColourSlots> ring;
     ring.setup(smem_raw, g, X, O, &tmX, &tmO, COLOUR, tg, spin);
     if (ring.z0 >= ring.z1) return;
     const int nxh = g.n[0] >> 1, ny = g.n[1];
     const unsigned N = (unsigned)g.n[0] * ny * g.n[2];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, y = ring.y0 + w;
     const bool act = lane < ring.tpt;
-    bool ok = ring.prologue(), failed = false;
-    for (int z = ring.z0; z < ring.z1; ++z) {
-        const int y = ring.y0 + w;
-        const unsigned q = (COLOUR ? N / 2 : 0u) + (unsigned)(ring.P0 + lane) + (unsigned)nxh * ((unsigned)y + (unsigned)ny * z);
-        T ca = 0, cb = 0, fq[4] = {0, 0, 0, 0};
-        if (act) {   // in flight during the wait and the barrier
-            ca = ab[q];
-            cb = ab[N + q];
+    T acc[2 * H + 1][4], ctr[H + 1][4];   // pending sums of planes zq - H .. zq + H; centre values
 #pragma unroll
-            for (int a = 0; a < 4; ++a) fq[a] = f[a * N + q];
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int k = 0; k <= 2 * H; ++k) acc[k][a] = 0;
+#pragma unroll
+        for (int k = 0; k <= H; ++k) ctr[k][a] = 0;
+    }
+    // the psi-row coefficients and right-hand side of the cell finished at iteration p, copied into
+    // this thread's staging kColourAhead iterations ahead: [slot][value][thread]
+    T *fst = reinterpret_cast<T *>(smem_raw + tile_ring_bytes<T, ORDER, kColourSlots>()) + threadIdx.x;
+    auto cell = [&](int zu) {
+        return (COLOUR ? N / 2 : 0u) + (unsigned)(ring.P0 + lane) + (unsigned)nxh * ((unsigned)y + (unsigned)ny * zu);
+    };
+    auto fetch = [&](int p) {
+        const int zu = ring.zs + p - H;
+        if (act && p < ring.NP && zu >= ring.z0) {
+            const unsigned q = cell(zu);
+            T *d = fst + (p % (kColourAhead + 1)) * kColourVals * kTileThreads;
+            tile_copy_async(d, ab + q);
+            tile_copy_async(d + kTileThreads, ab + N + q);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) tile_copy_async(d + (2 + a) * kTileThreads, f + a * N + q);
         }
-        if (!ring.advance(z, ok)) { failed = true; break; }
+        tile_copy_commit();
+    };
+    for (int p = 0; p < kColourAhead; ++p) fetch(p);
+    bool ok = ring.prologue(), failed = false;
+    for (int p = 0; p < ring.NP; ++p) {
+        const int zq = ring.zs + p, zu = zq - H;   // zu: the plane finished after this one
+        const bool fin = act && zu >= ring.z0;
+        fetch(p + kColourAhead);
+        if (!ring.advance(p, ok)) { failed = true; break; }
         if (act) {
-            int ob[2 * H + 1];
-            ring.bases(z, w, lane, COLOUR, ob);
-            T Je[4], ctr[4];
-            if ((COLOUR + y + z) & 1) tile_apply<T, ORDER, COLOUR, 1>(ring.sm, ob, ca, cb, tc, Je, ctr);
-            else tile_apply<T, ORDER, COLOUR, 0>(ring.sm, ob, ca, cb, tc, Je, ctr);
-            T dl, kW[3];   // the true diagonal next to a face (boxes with faces only)
-            relax_factors<BC>(tc.fd, g, 2 * (ring.P0 + lane) + ((COLOUR + y + z) & 1), y, z, true, tc.dl, tc.idW, tc.iom,
-                              dl, kW);
-            Y[q] = ctr[0] + (fq[0] - Je[0]) / ((ca * dl + cb) * tc.iom);
+            const T *s = ring.slot(p) + (w + H) * kTileW + kTilePad + lane;
+            const bool own = zq >= ring.z0 && zq < ring.z1;   // a plane of the chunk, not a halo plane
+            if ((y + zq) & 1) {
+                if (own) colour_plane<T, ORDER, 1, (COLOUR + 1) & 1, true>(s, tc, acc, ctr[H]);
+                else colour_plane<T, ORDER, 1, (COLOUR + 1) & 1, false>(s, tc, acc, ctr[H]);
+            } else {
+                if (own) colour_plane<T, ORDER, 0, COLOUR, true>(s, tc, acc, ctr[H]);
+                else colour_plane<T, ORDER, 0, COLOUR, false>(s, tc, acc, ctr[H]);
+            }
+        }
+        if (fin) {
+            tile_copy_wait<kColourAhead>();
+            const T *d = fst + (p % (kColourAhead + 1)) * kColourVals * kTileThreads;
+            const T ca = d[0], cb = d[kTileThreads];
+            T fq[4];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[1 + a] + (fq[1 + a] - Je[1 + a]) * kW[a];
+            for (int a = 0; a < 4; ++a) fq[a] = d[(2 + a) * kTileThreads];
+            const unsigned q = cell(zu);
+            const T Je0 = fma(ca, acc[0][0], cb * ctr[0][0]);
+            T dl, kW[3];   // the true diagonal next to a face (boxes with faces only)
+            relax_factors<BC>(tc.fd, g, 2 * (ring.P0 + lane) + ((COLOUR + y + zu) & 1), y, zu, true, tc.dl, tc.idW,
+                              tc.iom, dl, kW);
+            Y[q] = ctr[0][0] + (fq[0] - Je0) / ((ca * dl + cb) * tc.iom);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Y[(1 + a) * N + q] = ctr[0][1 + a] + (fq[1 + a] - acc[0][1 + a]) * kW[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int k = 0; k < 2 * H; ++k) acc[k][a] = acc[k + 1][a];
+            acc[2 * H][a] = 0;
+#pragma unroll
+            for (int k = 0; k < H; ++k) ctr[k][a] = ctr[k + 1][a];
         }
     }
+    tile_copy_wait_all();   // no copy may land after the CTA has left (a failed wait breaks out early)
     ring.finish(failed, err);
 }
 
@@ -496,75 +723,119 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 2 : 1)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int H = ORDER / 2;
-    TileRing<T, ORDER, BC> ring;
+    TileRing<T, ORDER, BC, kRestrictSlots> ring;
     ring.setup(smem_raw, g, e, e, &tm, &tm, 0, tg, spin);
     if (ring.z0 >= ring.z1) return;
-    T *stage = reinterpret_cast<T *>(smem_raw + tile_smem_bytes<T, ORDER>() + 16);   // [4 rows][32 lanes][4]
+    // staging of the fetched a, b, f of both cells ([slot][value][thread]), then the odd rows' sums
+    T *fst = reinterpret_cast<T *>(smem_raw + tile_ring_bytes<T, ORDER, kRestrictSlots>()) + threadIdx.x;
+    T *stage = reinterpret_cast<T *>(smem_raw + tile_ring_bytes<T, ORDER, kRestrictSlots>()) +
+               (kRestrictAhead + 1) * kRestrictVals * kTileThreads;   // [4 rows][32 lanes][4]
     const int nxh = g.n[0] >> 1, ny = g.n[1];
     const unsigned N = (unsigned)g.n[0] * ny * g.n[2];
     const unsigned Nc = (unsigned)gc.n[0] * gc.n[1] * gc.n[2];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, y = ring.y0 + w;
     const bool act = lane < ring.tpt;
-    T acc[4] = {0, 0, 0, 0};
+    T acc[2 * H + 1][2][4], cp[H + 1][2], racc[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+#pragma unroll
+        for (int k = 0; k <= 2 * H; ++k)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[k][b][a] = 0;
+#pragma unroll
+        for (int k = 0; k <= H; ++k) cp[k][b] = 0;
+    }
     auto flush = [&](int K) {   // even warps: add the odd row's sums and write coarse plane K's cell
         if ((w & 1) == 0 && act) {
-            const int I = ring.P0 + lane, J = (ring.y0 + w) >> 1;
+            const int I = ring.P0 + lane, J = y >> 1;
             const unsigned linc = (unsigned)I + (unsigned)gc.n[0] * ((unsigned)J + (unsigned)gc.n[1] * (unsigned)K);
             const unsigned pc = csplit ? (((I + J + K) & 1) ? Nc / 2 : 0u) + (linc >> 1) : linc;
             const T *st = stage + ((w >> 1) * 32 + lane) * 4;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) fc[a * Nc + pc] = (acc[a] + st[a]) * (T)0.125;
+            for (int a = 0; a < 4; ++a) fc[a * Nc + pc] = (racc[a] + st[a]) * (T)0.125;
         }
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a] = 0;
+        for (int a = 0; a < 4; ++a) racc[a] = 0;
     };
-    bool ok = ring.prologue(), failed = false;
-    for (int z = ring.z0; z < ring.z1; ++z) {
-        const int y = ring.y0 + w;
-        const unsigned m = (unsigned)(ring.P0 + lane) + (unsigned)nxh * ((unsigned)y + (unsigned)ny * z);
-        const int c0 = (y + z) & 1;   // colour of the pair's even-x cell
-        const unsigned q0 = (c0 ? N / 2 : 0u) + m, q1 = (c0 ? 0u : N / 2) + m;
-        T a0 = 0, b0 = 0, a1 = 0, b1 = 0, f0[4] = {0, 0, 0, 0}, f1[4] = {0, 0, 0, 0};
-        if (act) {
-            a0 = ab[q0];
-            b0 = ab[N + q0];
-            a1 = ab[q1];
-            b1 = ab[N + q1];
+    // the pair's two cells in plane zu: colour of the even-x cell, pair index, and their offsets
+    auto cells = [&](int zu, unsigned &q0, unsigned &q1) {
+        const unsigned m = (unsigned)(ring.P0 + lane) + (unsigned)nxh * ((unsigned)y + (unsigned)ny * zu);
+        const int c0 = (y + zu) & 1;
+        q0 = (c0 ? N / 2 : 0u) + m;
+        q1 = (c0 ? 0u : N / 2) + m;
+    };
+    auto fetch = [&](int p) {   // a, b, f of both cells finished at iteration p, kRestrictAhead ahead
+        const int zu = ring.zs + p - H;
+        if (act && p < ring.NP && zu >= ring.z0) {
+            unsigned q0, q1;
+            cells(zu, q0, q1);
+            T *d = fst + (p % (kRestrictAhead + 1)) * kRestrictVals * kTileThreads;
+            tile_copy_async(d, ab + q0);
+            tile_copy_async(d + kTileThreads, ab + N + q0);
+            tile_copy_async(d + 2 * kTileThreads, ab + q1);
+            tile_copy_async(d + 3 * kTileThreads, ab + N + q1);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                f0[a] = f[a * N + q0];
-                f1[a] = f[a * N + q1];
+                tile_copy_async(d + (4 + a) * kTileThreads, f + a * N + q0);
+                tile_copy_async(d + (8 + a) * kTileThreads, f + a * N + q1);
             }
         }
-        if (!ring.advance(z, ok)) { failed = true; break; }
-        if ((z & 1) == 0 && z > ring.z0) flush((z >> 1) - 1);   // the previous coarse plane
+        tile_copy_commit();
+    };
+    for (int p = 0; p < kRestrictAhead; ++p) fetch(p);
+    bool ok = ring.prologue(), failed = false;
+    for (int p = 0; p < ring.NP; ++p) {
+        const int zq = ring.zs + p, zu = zq - H;   // zu: the plane finished after this one
+        const bool fin = zu >= ring.z0;
+        fetch(p + kRestrictAhead);
+        if (!ring.advance(p, ok)) { failed = true; break; }
+        if (fin && (zu & 1) == 0 && zu > ring.z0) flush((zu >> 1) - 1);   // the previous coarse plane
         if (act) {
-            int obA[2 * H + 1], obB[2 * H + 1];
-            ring.bases(z, w, lane, c0, obA);       // even-x cell, colour c0
-            ring.bases(z, w, lane, 1 - c0, obB);   // odd-x cell, the other colour
-            T Je[4], ctr[4];
-            if (c0 == 0) tile_apply<T, ORDER, 0, 0>(ring.sm, obA, a0, b0, tc, Je, ctr);
-            else tile_apply<T, ORDER, 1, 0>(ring.sm, obA, a0, b0, tc, Je, ctr);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) acc[a] += f0[a] - Je[a];
-            if (c0 == 0) tile_apply<T, ORDER, 1, 1>(ring.sm, obB, a1, b1, tc, Je, ctr);
-            else tile_apply<T, ORDER, 0, 1>(ring.sm, obB, a1, b1, tc, Je, ctr);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) acc[a] += f1[a] - Je[a];
+            const T *s = ring.slot(p) + (w + H) * kTileW + kTilePad + lane;
+            const bool own = zq >= ring.z0 && zq < ring.z1;   // a plane of the chunk, not a halo plane
+            if ((y + zq) & 1) {
+                if (own) residual_plane<T, ORDER, 1, true>(s, tc, acc, cp[H]);
+                else residual_plane<T, ORDER, 1, false>(s, tc, acc, cp[H]);
+            } else {
+                if (own) residual_plane<T, ORDER, 0, true>(s, tc, acc, cp[H]);
+                else residual_plane<T, ORDER, 0, false>(s, tc, acc, cp[H]);
+            }
         }
-        if ((z & 1) && (w & 1)) {   // odd row of a coarse row: hand the sums to the even warp
+        if (act && fin) {
+            tile_copy_wait<kRestrictAhead>();
+            const T *d = fst + (p % (kRestrictAhead + 1)) * kRestrictVals * kTileThreads;
+            const T a0 = d[0], b0 = d[kTileThreads], a1 = d[2 * kTileThreads], b1 = d[3 * kTileThreads];
+            racc[0] += (d[4 * kTileThreads] - fma(a0, acc[0][0][0], b0 * cp[0][0])) +
+                       (d[8 * kTileThreads] - fma(a1, acc[0][1][0], b1 * cp[0][1]));
+#pragma unroll
+            for (int a = 1; a < 4; ++a)
+                racc[a] += (d[(4 + a) * kTileThreads] - acc[0][0][a]) + (d[(8 + a) * kTileThreads] - acc[0][1][a]);
+        }
+        if (fin && (zu & 1) && (w & 1)) {   // odd row of a coarse row: hand the sums to the even warp
             T *st = stage + ((w >> 1) * 32 + lane) * 4;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                st[a] = acc[a];
-                acc[a] = 0;
+                st[a] = racc[a];
+                racc[a] = 0;
             }
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                for (int k = 0; k < 2 * H; ++k) acc[k][b][a] = acc[k + 1][b][a];
+                acc[2 * H][b][a] = 0;
+            }
+#pragma unroll
+            for (int k = 0; k < H; ++k) cp[k][b] = cp[k + 1][b];
         }
     }
     if (!failed) {
         __syncthreads();
         flush((ring.z1 >> 1) - 1);
     }
+    tile_copy_wait_all();   // no copy may land after the CTA has left (a failed wait breaks out early)
     ring.finish(failed, err);
 }
 
