@@ -205,8 +205,8 @@ mg_status mg_checkpoint_save(struct mg_ctx *ctx, const char *path);
 mg_status mg_checkpoint_load(struct mg_ctx *ctx, const char *path);
 
 /*
- * Learned warm start (not in the paper: the build target's learned initial guess; plain multigrid
- * stays the fallback and the judge).  mg_warmstart_load reads a trained 3-D U-Net from
+ * Learned warm start (not in the paper: a learned initial guess added to its multigrid solver; plain
+ * multigrid stays the fallback, and the multigrid solve decides every result).  mg_warmstart_load reads a trained 3-D U-Net from
  * `weights_path` (NULL: switch the warm start off) into device memory it allocates (about 70 MB
  * for a 64^3 network) and attaches it to the context.  From then on, a solve that was given no
  * initial guess first runs the network (BF16 tcgen05 convolutions, FP32 accumulation; captured
@@ -304,7 +304,7 @@ void mg_destroy(struct mg_ctx *ctx);
 
 /*
  * Batched solves: many independent problems of uneven grid sizes in one call (not in the paper,
- * which solves one problem per run: the build target's batched pattern).  All instances must
+ * which solves one problem per run).  All instances must
  * share order, bc, precision and k_mode; sizes, boxes and sources differ.  Each instance owns its
  * workspace and a private stream.
  *

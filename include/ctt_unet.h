@@ -3,8 +3,8 @@
  * convolutions run as implicit GEMMs on the 5th-generation tensor cores (tcgen05, FP32
  * accumulation in tensor memory), and the glue kernels of its training (pooling, upsampling,
  * 1x1 head, MSE loss, gradients, Adam).  Not in the paper: the learned warm start and its
- * training are the "AI-systems pattern (4)" of the build target; plain multigrid from psi = 1
- * remains the fallback and judges every accepted result.
+ * training are an addition to its multigrid solver.  Plain multigrid from psi = 1 remains the
+ * fallback, and the multigrid solve decides every accepted result.
  *
  * Conventions:
  *   - Activations are NDHWC BF16 (x fastest, a voxel's channels contiguous).  A tensor may be

@@ -1,8 +1,8 @@
 // mg_warmstart.cu -- the learned warm start inside the library: a trained 3-D U-Net (BF16
 // tcgen05 convolutions with FP32 accumulation, the kernels of ctt_unet.h) maps a context's
 // sources (rho, S_i, and the pre-solve K) to an initial guess (u, W_i) before the multigrid
-// solve.  Not in the paper: the learned start is the build target's "AI-systems pattern"; plain
-// multigrid from psi = 1 remains the fallback and the judge of every result.
+// solve.  Not in the paper: the learned start is an addition to its multigrid solver.  Plain
+// multigrid from psi = 1 remains the fallback, and the multigrid solve decides every result.
 //
 // Network (4 levels, 16/32/64/64 channels): two 3x3x3 circular convolutions + ReLU per level,
 // 2x average pooling down, nearest 2x upsampling and concatenation [upsampled | skip] up, a 1x1

@@ -268,8 +268,8 @@ def solve_batch(mg, ps, precision, tol=1e-10, stream=0, guesses=None):
 
 
 def make_dataset(mg, fields, seeds, n=64, chunk=64, stream=0, a_range=(2e-5, 8e-5)):
-    """Solver-generated training pairs: config-2-style random periodic fields with a0 ~ U[a_range]
-    drawn per seed, solved to 1e-10 by the mixed-precision batched multigrid."""
+    """Solver-generated training pairs: random-mode periodic fields (as the 128^3 workload) with
+    a0 ~ U[a_range] drawn per seed, solved to 1e-10 by the mixed-precision batched multigrid."""
     data = []
     for s0 in range(0, len(seeds), chunk):
         ps = []
