@@ -123,6 +123,9 @@ typedef struct {
                              chosen: at least one face must stay Robin (MG_ERR_UNSUPPORTED otherwise), and some
                              sets (e.g. the three lower faces) give a nearly singular system that does not
                              converge.  A lower face cannot be both extrapolating and a symmetry plane.  0 = none. */
+    int tile_waves;       /* launch shape of the TMA-tiled colour pass and restriction: each tile column is cut
+                             into z chunks so that the grid holds about tile_waves CTAs per SM (1..8; chunks of
+                             at least 2 planes).  0 = 2, the CTAs one SM holds at once (mg_autotune picks it). */
 } mg_config;
 
 typedef struct {
@@ -260,6 +263,14 @@ mg_status mg_constraint_fields(struct mg_ctx *ctx, double *H, double *M, int on_
 mg_status mg_time_kernel(struct mg_ctx *ctx, int which, int reps, double *ms_per_launch, double *bytes_per_launch);
 
 /*
+ * Measurement aid: the FP64 FMA rate of the GPU the context runs on, in TFLOP/s (an FMA counts as
+ * two flops).  A probe kernel runs 8 independent FMA chains per thread on every SM (enough to keep
+ * the FP64 pipe busy) on the context's stream, once untimed and `reps` times between CUDA events.
+ * It is the denominator of the FP64 residual's roofline.  The solver state is not changed.
+ */
+mg_status mg_fp64_fma_rate(struct mg_ctx *ctx, int reps, double *tflops);
+
+/*
  * mg_residual_norms_noalloc -- the constraint norms of mg_residual_norms for a state held by the
  * caller, computed without allocating anything.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc or any other allocator, for example a host
@@ -290,8 +301,10 @@ mg_status mg_residual_norms_noalloc(const mg_config *cfg, const double *u, const
  * Autotuner: times candidate settings of (inner_cycles in {1, 2, 3} ({1, 2} for MG_FP64),
  * nu_pre = nu_post in {1, 2, 3}, omega in {1, 1.15, 1.3}; V-cycles) on the
  * given problem (sources as for mg_set_sources; each candidate runs one untimed and one timed solve
- * from psi = 1 on a private context) and writes the fastest setting that meets base->tol into
- * *best (the other fields copied from *base), with its solve time in *best_ms.  Results are cached
+ * from psi = 1 on a private context), then, for MG_MIXED with the tiled kernels, the launch shape
+ * of those kernels (tile_waves in {1, 2, 3, 4}) at the winning setting, and writes the fastest
+ * setting that meets base->tol into *best (the other fields copied from *base), with its solve
+ * time in *best_ms.  Results are cached
  * per (grid size, order, bc, precision, k_mode, nested) for the process, and, when cache_path is not NULL,
  * in that text file (one line per key; read before tuning, rewritten after).  A cache hit runs no
  * solve.  Returns MG_ERR_NOT_CONVERGED if no candidate met the tolerance.

@@ -73,6 +73,7 @@ mg_status validate(const mg_config *c)
                 return fail(MG_ERR_INVALID_ARG, "puncture momentum or spin not finite");
     if (c->reflect < 0 || c->reflect > 7) return fail(MG_ERR_INVALID_ARG, "reflect must be a mask of 3 bits");
     if (c->reflect != 0 && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "symmetry planes need a Robin box");
+    if (c->tile_waves < 0 || c->tile_waves > 8) return fail(MG_ERR_INVALID_ARG, "tile_waves must be 0..8");
     if (c->extrap < 0 || c->extrap > 63) return fail(MG_ERR_INVALID_ARG, "extrap must be a mask of 6 bits");
     if (c->extrap != 0 && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "extrapolating faces need a Robin box");
     for (int a = 0; a < 3; ++a)
@@ -548,8 +549,9 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
                     st = fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a level buffer");
                     break;
                 }
-                L.tg = tile_grid(L.geo, x->sms, x->tbytes == 4 ? 2 : 1);
-                L.tgr = tile_grid(L.geo, x->sms, x->tbytes == 4 ? 2 : 1, true);
+                const int waves = cfg->tile_waves ? cfg->tile_waves : 2;
+                L.tg = tile_grid(L.geo, x->sms, waves);
+                L.tgr = tile_grid(L.geo, x->sms, waves, true);
                 L.tiled = 1;
             }
             if (st != MG_OK) break;
@@ -896,6 +898,41 @@ static mg_status mg_time_kernel_impl(mg_ctx *x, int which, int reps, double *ms_
     return MG_OK;
 }
 
+// FP64 FMA probe: 8 independent FMA chains per thread, folded into one value that is compared
+// with a constant it never equals, so that no chain is optimised away.
+__global__ void __launch_bounds__(256) k_fp64_probe(int iters, double seed, double *sink)
+{
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = seed * (double)(threadIdx.x + k + 1);
+    const double b = 0.999999999, c = 1e-12;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == 42.0) sink[0] = s;
+}
+
+static mg_status mg_fp64_fma_rate_impl(mg_ctx *x, int reps, double *tflops)
+{
+    if (reps < 1 || !tflops) return fail(MG_ERR_INVALID_ARG, "bad argument");
+    const int blocks = x->sms * 8, iters = 2048;
+    k_fp64_probe<<<blocks, 256, 0, x->stream>>>(iters, 1e-3, x->partial);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(x->ev0, x->stream));
+    for (int r = 0; r < reps; ++r) k_fp64_probe<<<blocks, 256, 0, x->stream>>>(iters, 1e-3, x->partial);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(x->ev1, x->stream));
+    CK(cudaEventSynchronize(x->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, x->ev0, x->ev1));
+    const double flops = 2.0 * 8.0 * iters * (double)blocks * 256.0 * reps;
+    *tflops = flops / (ms * 1e-3) / 1e12;
+    return MG_OK;
+}
+
 // ---- public entry points: argument check, stream ordering, then the implementation
 #define MG_WRAP(call)                                                                                  \
     do {                                                                                               \
@@ -968,6 +1005,7 @@ mg_status mg_time_kernel(mg_ctx *x, int which, int reps, double *ms_per_launch, 
 {
     MG_WRAP(mg_time_kernel_impl(x, which, reps, ms_per_launch, bytes_per_launch));
 }
+mg_status mg_fp64_fma_rate(mg_ctx *x, int reps, double *tflops) { MG_WRAP(mg_fp64_fma_rate_impl(x, reps, tflops)); }
 
 void mg_destroy(mg_ctx *x)
 {
@@ -1582,6 +1620,7 @@ namespace {
 struct TuneResult {
     int inner, nu, threads;
     double omega;
+    int waves;   // tile_waves
     double ms;
 };
 
@@ -1607,7 +1646,7 @@ void tune_load(const char *path)
         TuneResult r;
         std::string extra;
         if (in >> n0 >> n1 >> n2 >> order >> bc >> prec >> km >> nested >> r.inner >> r.nu >> r.threads >> r.omega >>
-                r.ms &&
+                r.waves >> r.ms &&
             !(in >> extra)) {
             std::ostringstream k;
             k << n0 << ' ' << n1 << ' ' << n2 << ' ' << order << ' ' << bc << ' ' << prec << ' ' << km << ' ' << nested;
@@ -1622,7 +1661,7 @@ void tune_save(const char *path)
     std::ofstream f(path, std::ios::trunc);
     for (auto &kv : g_tune_cache)
         f << kv.first << ' ' << kv.second.inner << ' ' << kv.second.nu << ' ' << kv.second.threads << ' '
-          << kv.second.omega << ' ' << kv.second.ms << '\n';
+          << kv.second.omega << ' ' << kv.second.waves << ' ' << kv.second.ms << '\n';
 }
 
 }  // namespace
@@ -1638,7 +1677,7 @@ extern "C" mg_status mg_autotune(const mg_config *base, const double *rho0, cons
     tune_load(cache_path);
     const std::string key = tune_key(base);
     auto hit = g_tune_cache.find(key);
-    TuneResult win{0, 0, 0, 1.0, INFINITY};
+    TuneResult win{0, 0, 0, 1.0, 0, INFINITY};
     if (hit != g_tune_cache.end()) {
         win = hit->second;
     } else {
@@ -1648,26 +1687,45 @@ extern "C" mg_status mg_autotune(const mg_config *base, const double *rho0, cons
         const int *inners = base->precision == MG_FP64 ? inners_fp64 : inners_mixed;
         const int ninner = base->precision == MG_FP64 ? 2 : 3;
         const int th = base->block_threads;
+        // one timed solve (after an untimed one that captures the graphs) of a candidate setting
+        auto trial = [&](int inner, int nu, double om, int waves, double *ms) -> mg_status {
+            mg_config c = *base;
+            c.inner_cycles = inner;
+            c.nu_pre = c.nu_post = nu;
+            c.omega = om;
+            c.tile_waves = waves;
+            c.use_graph = 1;
+            mg_ctx *x = nullptr;
+            CKS(mg_create(&c, cuda_stream, nullptr, 0, &x));
+            mg_status st = mg_set_sources(x, rho0, rho2, Sx, Sy, Sz, on_device);
+            mg_solve_info info;
+            if (st == MG_OK) st = mg_solve(x, &info);
+            if (st == MG_OK) st = mg_set_initial_guess(x, nullptr, nullptr, 1);
+            if (st == MG_OK) st = mg_solve(x, &info);
+            mg_destroy(x);
+            *ms = st == MG_OK ? info.device_ms : INFINITY;
+            return st == MG_ERR_NOT_CONVERGED || st == MG_ERR_DIVERGED ? MG_OK : st;
+        };
+        // solver settings first, at the base launch shape
         for (int ii = 0; ii < ninner; ++ii)
             for (int nu : nus)
                 for (double om : omegas) {
-                    mg_config c = *base;
-                    c.inner_cycles = inners[ii];
-                    c.nu_pre = c.nu_post = nu;
-                    c.omega = om;
-                    c.use_graph = 1;
-                    mg_ctx *x = nullptr;
-                    CKS(mg_create(&c, cuda_stream, nullptr, 0, &x));
-                    mg_status st = mg_set_sources(x, rho0, rho2, Sx, Sy, Sz, on_device);
-                    mg_solve_info info;
-                    if (st == MG_OK) st = mg_solve(x, &info);            // untimed: captures the graphs
-                    if (st == MG_OK) st = mg_set_initial_guess(x, nullptr, nullptr, 1);
-                    if (st == MG_OK) st = mg_solve(x, &info);
-                    mg_destroy(x);
-                    if (st == MG_OK && info.device_ms < win.ms) win = TuneResult{inners[ii], nu, th, om, info.device_ms};
-                    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED && st != MG_ERR_DIVERGED) return st;
+                    double ms;
+                    CKS(trial(inners[ii], nu, om, base->tile_waves, &ms));
+                    if (ms < win.ms) win = TuneResult{inners[ii], nu, th, om, base->tile_waves, ms};
                 }
         if (!std::isfinite(win.ms)) return fail(MG_ERR_NOT_CONVERGED, "no autotuner candidate met the tolerance");
+        // then the z chunking of the tiled kernels (CTAs per SM the grid aims at), for the winner
+        if (base->precision == MG_MIXED && base->smoother == 0)
+            for (int waves : {1, 2, 3, 4}) {
+                if (waves == (win.waves ? win.waves : 2)) continue;
+                double ms;
+                CKS(trial(win.inner, win.nu, win.omega, waves, &ms));
+                if (ms < win.ms) {
+                    win.waves = waves;
+                    win.ms = ms;
+                }
+            }
         g_tune_cache[key] = win;
         tune_save(cache_path);
     }
@@ -1676,6 +1734,7 @@ extern "C" mg_status mg_autotune(const mg_config *base, const double *rho0, cons
     best->nu_pre = best->nu_post = win.nu;
     best->block_threads = win.threads;
     best->omega = win.omega;
+    best->tile_waves = win.waves;
     if (best_ms) *best_ms = win.ms;
     return MG_OK;
 }

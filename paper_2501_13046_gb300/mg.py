@@ -24,7 +24,7 @@ MG_K_FIXED, MG_K_INTEGRABILITY = 0, 1
 
 EXPORTS = ("mg_config_default", "mg_workspace_size", "mg_create", "mg_set_conformal_metric", "mg_set_sources",
            "mg_set_initial_guess", "mg_solve", "mg_get_solution", "mg_residual_norms", "mg_constraint_fields",
-           "mg_time_kernel", "mg_residual_norms_noalloc", "mg_destroy", "mg_status_string", "mg_last_error",
+           "mg_time_kernel", "mg_fp64_fma_rate", "mg_residual_norms_noalloc", "mg_destroy", "mg_status_string", "mg_last_error",
            "mg_batch_create", "mg_batch_set_sources", "mg_batch_set_initial_guess", "mg_batch_solve",
            "mg_batch_get_solution", "mg_batch_destroy", "mg_autotune", "mg_checkpoint_save", "mg_checkpoint_load",
            "mg_warmstart_load", "mg_warmstart_predict", "mg_batch_warmstart_load")
@@ -40,7 +40,7 @@ class mg_config(C.Structure):
         ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double), ("nested", C.c_int),
         ("nested_min", C.c_int), ("nested_tol", C.c_double),
         ("punct_P", (C.c_double * 3) * 2), ("punct_S", (C.c_double * 3) * 2), ("reflect", C.c_int),
-        ("field_tol", C.c_double), ("extrap", C.c_int),
+        ("field_tol", C.c_double), ("extrap", C.c_int), ("tile_waves", C.c_int),
     ]
 
 
@@ -75,6 +75,7 @@ def _load():
     L.mg_residual_norms.argtypes = [vp, dp]
     L.mg_constraint_fields.argtypes = [vp, vp, vp, C.c_int]
     L.mg_time_kernel.argtypes = [vp, C.c_int, C.c_int, dp, dp]
+    L.mg_fp64_fma_rate.argtypes = [vp, C.c_int, dp]
     L.mg_residual_norms_noalloc.argtypes = [C.POINTER(mg_config), vp, vp, vp, vp, vp, dp, dp, vp]
     L.mg_destroy.argtypes = [vp]
     L.mg_checkpoint_save.argtypes = [vp, C.c_char_p]
@@ -199,6 +200,13 @@ def mg_time_kernel(ctx, which, reps):
     ms, b = C.c_double(0.0), C.c_double(0.0)
     _check(_lib.mg_time_kernel(ctx, which, reps, C.byref(ms), C.byref(b)), "mg_time_kernel")
     return ms.value, b.value
+
+
+def mg_fp64_fma_rate(ctx, reps=3):
+    """FP64 FMA rate of the context's GPU in TFLOP/s (probe kernel on the context's stream)."""
+    r = C.c_double(0.0)
+    _check(_lib.mg_fp64_fma_rate(ctx, reps, C.byref(r)), "mg_fp64_fma_rate")
+    return r.value
 
 
 def mg_residual_norms_noalloc(cfg, u, W, rho0, rho2, S, stream=0):

@@ -42,6 +42,8 @@ def test_autotune_picks_a_converging_candidate(mg, tmp_path, precision):
     assert best.inner_cycles in ((1, 2, 3) if prec == mg.MG_MIXED else (1, 2))
     assert best.nu_pre == best.nu_post and best.nu_pre in (1, 2, 3)
     assert best.omega in (1.0, 1.15, 1.3)
+    # the tiled kernels' z chunking is tuned for the mixed form only (the FP64 form has no tiled level)
+    assert best.tile_waves in ((1, 2, 3, 4) if prec == mg.MG_MIXED else (0,))
     assert best.tol == base.tol and list(best.n) == list(base.n)
     # the cache file holds this shape's entry
     lines = cache.read_text().split("\n")
@@ -64,7 +66,8 @@ def test_autotune_picks_a_converging_candidate(mg, tmp_path, precision):
 
     # a second call is a cache hit: same choice, same recorded time
     best2, ms2 = mg.mg_autotune(base, *src, stream=sp, cache_path=str(cache))
-    assert (best2.inner_cycles, best2.nu_pre, best2.omega) == (best.inner_cycles, best.nu_pre, best.omega)
+    assert (best2.inner_cycles, best2.nu_pre, best2.omega, best2.tile_waves) == \
+        (best.inner_cycles, best.nu_pre, best.omega, best.tile_waves)
     assert ms2 == ms
 
 
@@ -73,10 +76,35 @@ def test_autotune_reads_cache_file(mg, tmp_path):
     p = fields.modes_periodic(n=24)
     base = mg.config_for(p, mg.MG_MIXED, tol=1e-10, max_outer=40)
     cache = tmp_path / "tune.txt"
-    # key (n, order, bc, precision, k_mode, nested), then inner, nu, threads, omega, ms
-    cache.write_text("24 24 24 4 0 %d %d 0 3 1 128 1.15 1.5\n" % (mg.MG_MIXED, base.k_mode))
+    # key (n, order, bc, precision, k_mode, nested), then inner, nu, threads, omega, tile_waves, ms
+    cache.write_text("24 24 24 4 0 %d %d 0 3 1 128 1.15 3 1.5\n" % (mg.MG_MIXED, base.k_mode))
     best, ms = mg.mg_autotune(base, *sources(p), stream=torch.cuda.current_stream().cuda_stream,
                               cache_path=str(cache))
-    assert (best.inner_cycles, best.nu_pre, best.nu_post, best.block_threads) == (3, 1, 1, 128)
+    assert (best.inner_cycles, best.nu_pre, best.nu_post, best.block_threads, best.tile_waves) == (3, 1, 1, 128, 3)
     assert best.omega == 1.15
     assert ms == 1.5
+
+
+@pytest.mark.parametrize("case", ["periodic_o4_n64", "robin_o4_n48"])
+def test_tile_waves_change_the_launch_shape_not_the_result(mg, case):
+    """The z chunking of the tiled kernels (tile_waves) changes only which CTA computes which planes:
+    every cell receives the same plane contributions in the same order, so the solve is bit for
+    bit the same for any chunking."""
+    p = fields.modes_periodic(n=64, a0=5e-5) if case.startswith("periodic") else fields.puncture_shell(n=48, half=24.0)
+    sp = torch.cuda.current_stream().cuda_stream
+    out = []
+    for waves in (1, 3):
+        cfg = mg.config_for(p, mg.MG_MIXED, tol=1e-10, max_outer=40, tile_waves=waves)
+        ctx = mg.mg_create(cfg, sp)
+        try:
+            mg.mg_set_sources(ctx, *sources(p))
+            st, info = mg.mg_solve(ctx)
+            assert st == mg.MG_OK
+            u = np.empty(p["rho0"].shape)
+            W = np.empty((3,) + p["rho0"].shape)
+            mg.mg_get_solution(ctx, u, W)
+            out.append((u, W, np.asarray(info["history"])))
+        finally:
+            mg.mg_destroy(ctx)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
