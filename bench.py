@@ -295,6 +295,10 @@ FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes of one 128^3 pass-B launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture of the kernel as it stands (profiles/outer_pass1q_128cube_periodic_o4.md); None if none
 PASSB_TRAFFIC_128 = 374079744
+# the same for the finest colour pass and residual + restriction at 128^3
+# (profiles/smooth_tile_128cube_periodic_o4.md, profiles/restrict_tile_128cube_periodic_o4.md)
+COLOUR_TRAFFIC_128 = 59366656 + 1694976
+RESTRICT_TRAFFIC_128 = 85024512 + 2426368
 
 
 def kernel_rooflines(mg, ctx, N):
@@ -316,10 +320,12 @@ def kernel_rooflines(mg, ctx, N):
             "colour_pass": {"bound": "hbm", "kernel": "k_smooth_tile<float,4,periodic,c> (finest, one colour)",
                             "ms_per_launch": ms0, "algorithmic_bytes": bytes0, "achieved": sm_gbs,
                             "unit": "GB/s", "peak": pk["hbm_gbs"], "frac": sm_gbs / pk["hbm_gbs"],
+                            "traffic": COLOUR_TRAFFIC_128 if N == 128 ** 3 else None,
                             "peak_source": src + " hbm_gbs (copy test)"},
             "residual_restrict": {"bound": "hbm", "kernel": "k_restrict_tile<float,4,periodic> (finest)",
                                   "ms_per_launch": ms1, "algorithmic_bytes": bytes1, "achieved": rr_gbs,
-                                  "unit": "GB/s", "peak": pk["hbm_gbs"], "frac": rr_gbs / pk["hbm_gbs"]}}
+                                  "unit": "GB/s", "peak": pk["hbm_gbs"], "frac": rr_gbs / pk["hbm_gbs"],
+                                  "traffic": RESTRICT_TRAFFIC_128 if N == 128 ** 3 else None}}
 
 
 def unet_fwd_flops(n_net):
