@@ -593,6 +593,22 @@ def main():
                  "field_err": field_errors(gold, u_d.cpu().numpy(), W_d.cpu().numpy()) if gold else None,
                  "stop": "max(|H|,|M_i|) <= 1e-10 and every field's last update <= 1e-10 of its max-norm"}
     mg.mg_destroy(ctx_f)
+    # ... and with each field's remaining error estimated from its last two updates (field_est)
+    cfg_e = mg.config_for(p, mg.MG_MIXED, tol=WORKLOAD["tol"], max_outer=60, nested=args.nested, field_tol=1e-10,
+                          field_est=1)
+    apply_tuned(cfg_e, tuned_params[mg.MG_MIXED])
+    ctx_e = mg.mg_create(cfg_e, sp)
+    mg.mg_set_sources(ctx_e, *src_dev)
+    solve_loop(mg, torch, ctx_e, 2, stream)
+    te, info_e = solve_loop(mg, torch, ctx_e, fsteps, stream)
+    mg.mg_get_solution(ctx_e, u_d, W_d)
+    field_est = {"solves_per_s": fsteps / te, "outer_iters": info_e["outer_iters"],
+                 "nested_outer_iters": info_e["nested_iters"], "final_norms": list(info_e["norms"]),
+                 "last_update_rel": list(info_e["rel_change"]),
+                 "field_err": field_errors(gold, u_d.cpu().numpy(), W_d.cpu().numpy()) if gold else None,
+                 "stop": "max(|H|,|M_i|) <= 1e-10 and every field's estimated remaining error (last update x "
+                         "rho / (1 - rho), rho the ratio of its last two updates) <= 1e-10 of its max-norm"}
+    mg.mg_destroy(ctx_e)
     del u_d, W_d
 
     # ---- end to end through the public API with host buffers
@@ -747,7 +763,7 @@ def main():
     cfgd = dict(WORKLOAD, outer_iters=info["outer_iters"], final_norms=list(info["norms"]), K=info["K"],
                 field_err=field_err, field_err_note="max over 4096+ stored cells of |gpu - oracle| / max|oracle field|, "
                                                     "oracle root to its FP64 floor (tests/golden)",
-                field_accurate=field_acc,
+                field_accurate=field_acc, field_estimated=field_est,
                 start="nested: half-size solve, tricubic start" if args.nested else "psi = 1, W = 0",
                 nested_outer_iters=info["nested_iters"],
                 fp64_plain_solves_per_s=fp64_solves_per_s, fp64_plain_outer_iters=info64["outer_iters"],

@@ -126,6 +126,11 @@ typedef struct {
     int tile_waves;       /* launch shape of the TMA-tiled colour pass and restriction: each tile column is cut
                              into z chunks so that the grid holds about tile_waves CTAs per SM (1..8; chunks of
                              at least 2 planes).  0 = 2, the CTAs one SM holds at once (mg_autotune picks it). */
+    int field_est;        /* with field_tol > 0: 1 = compare each field's estimated remaining error, not its last
+                             update, with field_tol.  The estimate is rel rho / (1 - rho), where rel is the last
+                             update relative to the field's size and rho = rel / (the previous update's rel) is the
+                             observed contraction (used when rho < 1/2; otherwise the update itself is compared).
+                             It saves the outer iteration that only confirms a small update.  0 = off.       */
 } mg_config;
 
 typedef struct {

@@ -74,6 +74,7 @@ mg_status validate(const mg_config *c)
     if (c->reflect < 0 || c->reflect > 7) return fail(MG_ERR_INVALID_ARG, "reflect must be a mask of 3 bits");
     if (c->reflect != 0 && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "symmetry planes need a Robin box");
     if (c->tile_waves < 0 || c->tile_waves > 8) return fail(MG_ERR_INVALID_ARG, "tile_waves must be 0..8");
+    if (c->field_est != 0 && c->field_est != 1) return fail(MG_ERR_INVALID_ARG, "field_est must be 0 or 1");
     if (c->extrap < 0 || c->extrap > 63) return fail(MG_ERR_INVALID_ARG, "extrap must be a mask of 6 bits");
     if (c->extrap != 0 && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "extrapolating faces need a Robin box");
     for (int a = 0; a < 3; ++a)
@@ -136,15 +137,11 @@ bool nested_child_config(const mg_config *c, mg_config *cc)
     return true;
 }
 
-// The per-field part of the stopping test: every field's last update at most field_tol times the
-// field's size (always true when field_tol is off; false before the first update).
-bool fields_settled(const mg_config &c, const Scalars &s, int updates)
+// The per-field part of the stopping test (field_test; always true when field_tol is off, false
+// before the first update); prev carries the last relative updates between calls.
+bool fields_settled(const mg_config &c, const Scalars &s, int updates, double prev[4])
 {
-    if (c.field_tol <= 0.0) return true;
-    if (updates < 1) return false;
-    for (int a = 0; a < 4; ++a)
-        if (!(s.change[a] <= c.field_tol * s.change[4 + a])) return false;
-    return true;
+    return field_test(c.field_tol, c.field_est, s.change, prev, updates);
 }
 
 void fill_rel_change(const mg_config &c, const Scalars &s, int updates, double out[4])
@@ -728,7 +725,7 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
     if (warm_state != 1) CKS(run_start(x, &launches));   // an accepted warm start has evaluated it
     mg_status result = MG_ERR_NOT_CONVERGED;
     int it = 0, grow = 0;
-    double prev = INFINITY;
+    double prev = INFINITY, prev_rel[4] = {0, 0, 0, 0};
     for (;;) {
         const Scalars &s = *x->host_scal;
         double mx = 0.0;
@@ -740,7 +737,8 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
         }
         if (s.err) { result = fail(MG_ERR_TIMEOUT, "a bounded device wait gave up (spin_limit)"); break; }
         if (!finite || !std::isfinite(s.K2)) { result = fail(MG_ERR_DIVERGED, "constraint norm is not finite"); break; }
-        if (mx <= x->cfg.tol && fields_settled(x->cfg, s, it)) { result = MG_OK; break; }
+        const bool settled = fields_settled(x->cfg, s, it, prev_rel);
+        if (mx <= x->cfg.tol && settled) { result = MG_OK; break; }
         // growth counts only above tol: below it (the per-field test still waiting) the norm sits
         // at its rounding floor and may wobble
         grow = (mx > prev && mx > x->cfg.tol) ? grow + 1 : 0;
@@ -1261,6 +1259,7 @@ mg_status batch_rounds_host(mg_batch *bt, int max_outer, BatchOutcome &o)
         cudaStreamSynchronize(bt->stream) != cudaSuccess)
         return fail(MG_ERR_CUDA, "batch start");
     int round = 0, done = 0;
+    std::vector<double> prev_rel(4 * (size_t)nb, 0.0);
     for (;;) {
         float ms = 0.f;
         if (round > 0) cudaEventElapsedTime(&ms, t0, bt->ev_round[round]);
@@ -1280,7 +1279,8 @@ mg_status batch_rounds_host(mg_batch *bt, int max_outer, BatchOutcome &o)
                 o.rounds[b] = round;
                 ++done;
             }
-            if (o.conv[b] < 0 && !o.bad[b] && mx <= x->cfg.tol && fields_settled(x->cfg, s, round)) {
+            const bool settled = o.conv[b] < 0 && !o.bad[b] && fields_settled(x->cfg, s, round, &prev_rel[4 * b]);
+            if (o.conv[b] < 0 && !o.bad[b] && mx <= x->cfg.tol && settled) {
                 o.conv[b] = round;
                 o.conv_ms[b] = ms;
                 o.rounds[b] = round;
@@ -1329,12 +1329,14 @@ mg_status build_device_graph(mg_batch *bt, int maxr)
         cudaFree(bt->ctl_mem);
         bt->ctl_mem = nullptr;
     }
-    // control block: BatchCtl, scal pointers, tol, ftol, maxo, conv, bad, tconv, handles, history
+    // control block: BatchCtl, scal pointers, tol, ftol, maxo, conv, bad, tconv, handles, history,
+    // field_est, the last relative updates
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     const size_t oc = take(sizeof(BatchCtl)), os = take(nb * sizeof(Scalars *)), ot = take(nb * 8),
                  of = take(nb * 8), om = take(nb * 4), ov = take(nb * 4), ob = take(nb * 4), oT = take(nb * 8),
-                 oh = take(nb * sizeof(cudaGraphConditionalHandle)), oH = take((size_t)(maxr + 1) * nb * 4 * 8);
+                 oh = take(nb * sizeof(cudaGraphConditionalHandle)), oH = take((size_t)(maxr + 1) * nb * 4 * 8),
+                 oe = take(nb * 4), op = take(nb * 4 * 8);
     CK(cudaMalloc(&bt->ctl_mem, off));
     char *m = (char *)bt->ctl_mem;
     BatchCtlArgs &a = bt->ctl;
@@ -1348,17 +1350,20 @@ mg_status build_device_graph(mg_batch *bt, int maxr)
     a.tconv = (unsigned long long *)(m + oT);
     a.h = (const cudaGraphConditionalHandle *)(m + oh);
     a.hist = (double *)(m + oH);
+    a.fest = (const int *)(m + oe);
+    a.prev = (double *)(m + op);
     a.nb = nb;
     a.maxr = maxr;
     bt->ctl_maxr = maxr;
     std::vector<Scalars *> sp(nb);
     std::vector<double> tl(nb), ft(nb);
-    std::vector<int> mo(nb);
+    std::vector<int> mo(nb), fe(nb);
     for (int b = 0; b < nb; ++b) {
         sp[b] = bt->ctx[b]->scal;
         tl[b] = bt->ctx[b]->cfg.tol;
         ft[b] = bt->ctx[b]->cfg.field_tol;
         mo[b] = bt->ctx[b]->cfg.max_outer;
+        fe[b] = bt->ctx[b]->cfg.field_est;
     }
     cudaGraph_t G = nullptr;
     CK(cudaGraphCreate(&G, 0));
@@ -1368,6 +1373,7 @@ mg_status build_device_graph(mg_batch *bt, int maxr)
     if (e == cudaSuccess) e = cudaMemcpy(m + os, sp.data(), nb * sizeof(Scalars *), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m + ot, tl.data(), nb * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m + of, ft.data(), nb * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m + oe, fe.data(), nb * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m + om, mo.data(), nb * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m + oh, h.data(), nb * sizeof(cudaGraphConditionalHandle), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

@@ -31,6 +31,8 @@ struct BatchCtlArgs {
     const cudaGraphConditionalHandle *h;     // per instance: its IF node
     cudaGraphConditionalHandle hw;           // the WHILE node
     double *hist;                            // [maxr + 1][nb][4] norms per round
+    const int *fest;                         // per instance: field_est
+    double *prev;                            // per instance: [4] last relative updates (field_test)
     int nb, maxr;
 };
 
@@ -53,6 +55,7 @@ __global__ void k_batch_begin(BatchCtlArgs a)
         a.conv[b] = -1;
         a.bad[b] = 0;
         a.tconv[b] = 0;
+        for (int k = 0; k < 4; ++k) a.prev[4 * b + k] = 0.0;
     }
 }
 
@@ -79,19 +82,15 @@ __global__ void k_batch_control(BatchCtlArgs a)
         }
         if (s->err) late = 1;
         if (a.conv[b] < 0 && !a.bad[b]) {
+            // the per-field part of the stopping test (see mg_config.field_tol, field_est)
+            double change[8];
+            for (int k = 0; k < 8; ++k) change[k] = s->change[k];
+            const bool settled = field_test(a.ftol[b], a.fest[b], change, a.prev + 4 * b, r);
             if (!finite) {
                 a.bad[b] = 1;
-            } else if (mx <= a.tol[b]) {
-                // the per-field part of the stopping test (see mg_config.field_tol)
-                bool settled = a.ftol[b] <= 0.0;
-                if (!settled && r >= 1) {
-                    settled = true;
-                    for (int k = 0; k < 4; ++k) settled = settled && s->change[k] <= a.ftol[b] * s->change[4 + k];
-                }
-                if (settled) {
-                    a.conv[b] = r;
-                    a.tconv[b] = now;
-                }
+            } else if (mx <= a.tol[b] && settled) {
+                a.conv[b] = r;
+                a.tconv[b] = now;
             }
         }
         const int active = a.conv[b] < 0 && !a.bad[b] && r < a.maxo[b];

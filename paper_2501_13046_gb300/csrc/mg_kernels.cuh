@@ -1004,6 +1004,32 @@ struct Scalars {
     unsigned int ticket[4];   // last-block counters: pass-B sums, pass-2 norms, means of e, update maxima
 };
 
+// Per-field part of the stopping test (mg_config.field_tol, field_est), shared by the host loops
+// and the device-paced batch.  rel_a = max |e_a| / max |field_a| of the last outer update.  Plain
+// test: every rel_a <= ftol.  With est, field a's remaining error is estimated from the contraction
+// rho_a = rel_a / prev_a of the last two updates as rel_a rho_a / (1 - rho_a) (the tail of a
+// geometric series of updates) when rho_a < 1/2, and that estimate is compared with ftol; else the
+// plain test applies.  prev[4] carries rel_a from one call to the next (zero before the first
+// update); call it once per outer iteration, with the number of updates made so far.
+__host__ __device__ inline bool field_test(double ftol, int est, const double change[8], double prev[4], int updates)
+{
+    if (ftol <= 0.0) return true;
+    if (updates < 1) return false;
+    bool ok = true;
+    for (int a = 0; a < 4; ++a) {
+        const double size = change[4 + a];
+        const double rel = size > 0.0 ? change[a] / size : (change[a] > 0.0 ? HUGE_VAL : 0.0);
+        double bound = rel;
+        if (est && updates >= 2 && prev[a] > 0.0) {
+            const double rho = rel / prev[a];
+            if (rho < 0.5) bound = rel * rho / (1.0 - rho);
+        }
+        ok = ok && bound <= ftol;
+        prev[a] = rel;
+    }
+    return ok;
+}
+
 // K^2 (integrability or fixed) and the momentum-source means from the pass-1 sums.
 __device__ __forceinline__ void outer_scalars(Scalars *s, size_t N, int kmode_integrability, double K2_fixed,
                                               int periodic)

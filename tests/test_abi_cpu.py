@@ -155,7 +155,7 @@ def test_extrapolating_face_validation(lib):
 @pytest.mark.parametrize("field,value,status", [
     ("field_tol", -1e-10, 1), ("field_tol", float("nan"), 1), ("use_graph", 3, 1),
     ("order", 3, 1), ("bc", 7, 1), ("precision", 5, 1), ("levels", 6, 1), ("coarse_sweeps", 0, 1),
-    ("nested", 2, 1), ("nested_min", 2, 1), ("nested_tol", -1.0, 1), ("tile_waves", -1, 1), ("tile_waves", 9, 1),
+    ("nested", 2, 1), ("nested_min", 2, 1), ("nested_tol", -1.0, 1), ("tile_waves", -1, 1), ("tile_waves", 9, 1), ("field_est", 2, 1),
 ])
 def test_invalid_configs_are_rejected_on_the_host(lib, field, value, status):
     cfg = lib.mg_config_default()

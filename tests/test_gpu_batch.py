@@ -114,6 +114,27 @@ def test_device_paced_batch_repeats_and_per_field_stop(mg):
         mg.mg_batch_destroy(bt)
     for (i0, h0), (i1, h1) in zip(*runs):
         assert i0 == i1 and np.array_equal(h0, h1)
+    # the contraction estimate of the per-field test on the device: every instance stops no later,
+    # and at the same round as its solo solve with the same settings (the host loop's test)
+    cfge = [mg.config_for(p, mg.MG_MIXED, tol=1e-10, max_outer=40, field_tol=1e-10, field_est=1) for p in ps]
+    bt = mg.mg_batch_create(cfge, torch.cuda.current_stream().cuda_stream)
+    try:
+        for b, p in enumerate(ps):
+            mg.mg_batch_set_sources(bt, b, *[dev(a) for a in (p["rho0"], p["rho2"], *p["S"])])
+            mg.mg_batch_set_initial_guess(bt, b, None, None)
+        st, infos, total = mg.mg_batch_solve(bt, len(ps))
+        assert st == mg.MG_OK
+    finally:
+        mg.mg_batch_destroy(bt)
+    for b, (i, (i0, _)) in enumerate(zip(infos, runs[0])):
+        assert i["converged"] and i["outer_iters"] <= i0
+        ctx = mg.mg_create(cfge[b], torch.cuda.current_stream().cuda_stream)
+        try:
+            mg.mg_set_sources(ctx, *[dev(a) for a in (ps[b]["rho0"], ps[b]["rho2"], *ps[b]["S"])])
+            st1, solo = mg.mg_solve(ctx)
+        finally:
+            mg.mg_destroy(ctx)
+        assert st1 == mg.MG_OK and solo["outer_iters"] == i["outer_iters"]
 
 
 def test_batch_rejects_mixed_orders(mg):

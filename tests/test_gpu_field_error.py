@@ -18,6 +18,10 @@ Two stopping rules:
   The test asserts those bounds and records the measured errors.
 * the same plus field_tol = 1e-10 (every field's last outer update at most 1e-10
   of its size): the fields then match the oracle to <= 1e-10 relative each.
+* field_tol = 1e-10 with field_est = 1 (each field's remaining error estimated
+  from the contraction of its last two updates): the same bar, in no more outer
+  iterations (one fewer when the estimate stops the solve before an update
+  below 1e-10 has confirmed it).
 The oracle's own root is accurate to ~1e-11 relative (its H floor 2.7e-12 at
 128^3, M floor 1e-17), ten times below the bar.
 """
@@ -100,8 +104,13 @@ def test_field_errors_against_the_oracle_root(mg, n, precision):
     assert max(err2.values()) <= 1e-10, (err, err2, info2["rel_change"])
     assert info2["rel_change"].max() <= 1e-10
     assert info2["K2"] == pytest.approx(gold["K2"], rel=1e-10)
-    print("n=%d %s: tol only %s (%d outer); + field_tol %s (%d outer)"
-          % (n, precision, err, info["outer_iters"], err2, info2["outer_iters"]))
+    # the estimated remaining error instead of the last update: the same accuracy, no more iterations
+    info3, u3, W3 = solve(mg, p, prec, field_tol=1e-10, field_est=1)
+    err3 = field_errors(gold, u3, W3)
+    assert max(err3.values()) <= 1e-10, (err3, info3["rel_change"])
+    assert info3["outer_iters"] <= info2["outer_iters"]
+    print("n=%d %s: tol only %s (%d outer); + field_tol %s (%d outer); estimated %s (%d outer)"
+          % (n, precision, err, info["outer_iters"], err2, info2["outer_iters"], err3, info3["outer_iters"]))
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
