@@ -13,6 +13,7 @@
 // CTA; a V-cycle then spends one small matrix-vector kernel on its coarsest level.
 #pragma once
 #include "mg_kernels.cuh"
+#include "mg_tile.cuh"
 
 namespace ctt {
 
@@ -242,12 +243,15 @@ struct AccRT {
     }
 };
 
+// gsm = 1: the shared memory also holds the coarsest level's dense inverses (Gpsi's Nc x Nc block,
+// then GW's 3Nc x 3Nc block); their per-thread cp.async copies are issued first and land while the
+// level is smoothed, so the coarsest solve reads shared memory instead of waiting on global loads.
 template <typename T, int ORDER, int BC>
 __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef<T> cf, Geo gc, const T *__restrict__ f,
                                                        const T *__restrict__ ab, const T *__restrict__ e_in,
                                                        T *__restrict__ e_out, int zero, int nu_pre, int nu_post,
                                                        const T *__restrict__ Gpsi, int mpsi,
-                                                       const T *__restrict__ GW, int mw)
+                                                       const T *__restrict__ GW, int mw, int gsm)
 {
     extern __shared__ unsigned char smem_raw[];
     const int N = g.n[0] * g.n[1] * g.n[2], Nc = gc.n[0] * gc.n[1] * gc.n[2];
@@ -259,6 +263,19 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
     T *fc = cs + 2 * N;
     T *ec = fc + 4 * Nc;
     T *rt = ec + 4 * Nc;   // Robin: ghost ratios of the level over its box padded by 2
+    T *sG = rt + (BC != BC_PERIODIC ? (g.n[0] + 4) * (g.n[1] + 4) * (g.n[2] + 4) : 0);   // staged inverses
+    const int M3 = 3 * Nc;
+    if (gsm) {
+        for (int e = threadIdx.x; e < Nc * Nc; e += blockDim.x) {
+            const int r = e / Nc;
+            tile_copy_async(sG + e, Gpsi + (size_t)r * mpsi + (e - r * Nc));
+        }
+        for (int e = threadIdx.x; e < M3 * M3; e += blockDim.x) {
+            const int r = e / M3;
+            tile_copy_async(sG + Nc * Nc + e, GW + (size_t)r * mw + (e - r * M3));
+        }
+        tile_copy_commit();
+    }
     auto ijk = [&](int q, int &i, int &j, int &k) {
         i = q % g.n[0];
         j = (q / g.n[0]) % g.n[1];
@@ -346,15 +363,16 @@ __global__ void __launch_bounds__(fused_threads<T>()) k_coarse_cycle(Geo g, Coef
         }
         fc[t] = sum * (T)0.125;
     }
+    if (gsm) tile_copy_wait_all();
     __syncthreads();
     // coarsest level: e_c = G f_c (psi rows: Gpsi, W rows: GW), one warp per row
     for (int r = tid >> 5; r < 4 * Nc; r += bs >> 5) {
         T acc = 0;
         if (r < Nc) {
-            const T *gr = Gpsi + (size_t)r * mpsi;
+            const T *gr = gsm ? sG + r * Nc : Gpsi + (size_t)r * mpsi;
             for (int j = tid & 31; j < Nc; j += 32) acc = fma(gr[j], fc[j], acc);
         } else {
-            const T *gr = GW + (size_t)(r - Nc) * mw;
+            const T *gr = gsm ? sG + Nc * Nc + (r - Nc) * M3 : GW + (size_t)(r - Nc) * mw;
             for (int j = tid & 31; j < 3 * Nc; j += 32) acc = fma(gr[j], fc[Nc + j], acc);
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);

@@ -179,13 +179,16 @@ mg_status enqueue_cycle(mg_ctx *x, int l, bool zero)
             x->join_pending = false;
         }
         const T *ein = zero ? (const T *)L.eA : (const T *)L.cur();
-        const size_t smem =
+        size_t smem =
             fused_smem_bytes((int)L.N, (int)C.N, sizeof(T), fused_ratio_cells(L.geo, x->cfg.bc == MG_BC_ROBIN));
+        const size_t gbytes = (size_t)10 * C.N * C.N * sizeof(T);   // Nc^2 + (3 Nc)^2 dense entries
+        const int gsm = smem + gbytes <= kMaxCoarseSmem ? 1 : 0;
+        if (gsm) smem += gbytes;
         with_bc<BC>([&](auto B) {
             k_coarse_cycle<T, ORDER, decltype(B)::value><<<1, fused_threads<T>(), smem, x->stream>>>(
                 L.geo, make_coef<T>(L.geo, x->cfg.order, x->omega), C.geo, (const T *)L.f, (const T *)L.c, ein,
                 (T *)L.eA, zero ? 1 : 0, x->cfg.nu_pre, x->cfg.nu_post, (const T *)x->Gpsi, x->mpsi,
-                (const T *)x->GW, x->mw);
+                (const T *)x->GW, x->mw, gsm);
         });
         CK(cudaGetLastError());
         L.curB = 0;
