@@ -21,8 +21,11 @@
 //  * the in-plane parts (x and y taps, D_x D_y) are summed from the plane directly.
 // That is 74 shared-memory reads per updated cell in the colour pass (the direct form of the
 // whole stencil takes 148) and 44 per cell in the residual.  The ring holds the plane being
-// computed plus five in flight (a chunk of two planes is issued whole); one barrier per plane orders
-// everything.  The 2H halo planes of a chunk only push their z taps (no in-plane part).
+// computed plus four (colour pass) or three (residual) in flight; one barrier per plane orders
+// everything.  The 2H halo planes of a chunk only push their z taps (no in-plane part).  The
+// per-cell inputs of a finished cell (psi-row coefficients a, b and the right-hand side f) arrive
+// by per-thread cp.async copies into a shared staging ring a few planes ahead, so their DRAM
+// latency is hidden behind the stencil work of the planes in between.
 //
 // The operator is that of apply_J (the same discrete stencils on the same values) with the grid
 // spacing, the 1/3 of the grad-div term and the tensor-product weights folded into per-level
