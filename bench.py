@@ -289,9 +289,9 @@ def batch_measure(mg, torch, sp, precision, repeats=1):
 # FP64 flops of the residual pass B per interior cell, counted from its source (an FMA is 2):
 # Lap u 19, three momentum rows 75, AtAt 55, nonlinear terms and outputs 30.
 PASSB_FLOPS_PER_CELL = 179
-# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz (context
-# beside the measured rate of the library's FMA probe, which is the denominator).
-FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 peak from unit counts and clocks (the denominator of an ALU-bound kernel): 152 SMs x 2 FP64
+# FMA lanes x 2 flops x 2.07 GHz.  The rate of the library's FMA probe is reported beside it.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes of one 128^3 pass-B launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture of the kernel as it stands (profiles/outer_pass1q_128cube_periodic_o4.md); None if none
 PASSB_TRAFFIC_128 = 374079744
@@ -307,16 +307,16 @@ def kernel_rooflines(mg, ctx, N):
     msb, bytesb = mg.mg_time_kernel(ctx, 3, 10)   # FP64 residual pass B alone
     ms0, bytes0 = mg.mg_time_kernel(ctx, 0, 40)   # finest FP32 colour pass
     ms1, bytes1 = mg.mg_time_kernel(ctx, 1, 20)   # finest residual + restriction
-    fp64 = mg.mg_fp64_fma_rate(ctx, 3)           # measured FP64 FMA rate (library probe, same stream)
+    fp64 = mg.mg_fp64_fma_rate(ctx, 3)           # FP64 FMA rate of the library probe (context)
     ach = PASSB_FLOPS_PER_CELL * N / (msb * 1e-3) / 1e12
     sm_gbs = bytes0 / (ms0 * 1e-3) / 1e9
     rr_gbs = bytes1 / (ms1 * 1e-3) / 1e9
-    return {"bound": "alu", "achieved": ach, "peak": fp64, "unit": "TFLOP/s",
-            "frac": ach / fp64, "traffic": PASSB_TRAFFIC_128,
+    return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": PASSB_TRAFFIC_128,
             "kernel": "k_outer_pass1q<4,periodic> (FP64 residual pass B, 128^3; FP64 pipe bound)",
             "ms_per_launch": msb, "algorithmic_flops": PASSB_FLOPS_PER_CELL * N, "algorithmic_bytes": bytesb,
-            "peak_source": "measured: mg_fp64_fma_rate (8 FMA chains per thread on every SM, this run)",
-            "peak_nominal": FP64_NOMINAL_TFLOPS,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz",
+            "fp64_probe_tflops": fp64, "frac_of_probe": ach / fp64,
             "colour_pass": {"bound": "hbm", "kernel": "k_smooth_tile<float,4,periodic,c> (finest, one colour)",
                             "ms_per_launch": ms0, "algorithmic_bytes": bytes0, "achieved": sm_gbs,
                             "unit": "GB/s", "peak": pk["hbm_gbs"], "frac": sm_gbs / pk["hbm_gbs"],

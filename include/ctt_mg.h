@@ -271,7 +271,7 @@ mg_status mg_time_kernel(struct mg_ctx *ctx, int which, int reps, double *ms_per
  * Measurement aid: the FP64 FMA rate of the GPU the context runs on, in TFLOP/s (an FMA counts as
  * two flops).  A probe kernel runs 8 independent FMA chains per thread on every SM (enough to keep
  * the FP64 pipe busy) on the context's stream, once untimed and `reps` times between CUDA events.
- * It is the denominator of the FP64 residual's roofline.  The solver state is not changed.
+ * bench.py reports it beside the unit-count FP64 peak.  The solver state is not changed.
  */
 mg_status mg_fp64_fma_rate(struct mg_ctx *ctx, int reps, double *tflops);
 

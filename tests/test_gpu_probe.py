@@ -1,4 +1,4 @@
-"""The FP64 FMA-rate probe that bench.py divides the FP64 residual's flop rate by: on a GB300 (2 FP64
+"""The FP64 FMA-rate probe that bench.py reports beside the unit-count FP64 peak: on a GB300 (2 FP64
 FMA lanes per SM per clock, 152 SMs, up to 2.07 GHz) it must report a rate near, and not above,
 152 x 2 x 2 x 2.07 GHz = 1.26 TFLOP/s; a rate far off would mean the probe does not keep the FP64
 pipe busy or is optimised away."""
