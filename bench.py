@@ -228,13 +228,18 @@ def run_reference(args):
     p = None
     for _ in range(args.warmup):
         oracle_sample(p, seconds_budget=0.0)
-    times, det = [], None
+    times, walls, det = [], [], None
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         v, det = oracle_sample(p, seconds_budget=0.0)
+        walls.append(time.perf_counter() - t0)
         times.append(1.0 / v)
     value = 1.0 / statistics.mean(times)
+    # ms_per_step: the wall time of one step as run (one bounded sample); the 128^3 solve time the
+    # sample stands for is reported beside it
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(walls) * 1e3,
+            "extrapolated_ms_per_solve": statistics.mean(times) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": WORKLOAD,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
