@@ -89,7 +89,9 @@ inline TileGrid tile_grid(const Geo &g, int sms, int ctas_per_sm, bool even = fa
     t.ntx = (g.n[0] / 2 + kTileP - 1) / kTileP;
     t.nty = g.n[1] / kTileY;
     int chunks = std::max(1, sms * ctas_per_sm / (t.ntx * t.nty));
-    t.zc = std::max(2, (g.n[2] + chunks - 1) / chunks);
+    // a colour pass may take single planes (small levels: fewer serial plane steps per CTA); the
+    // restriction pairs planes
+    t.zc = std::max(even ? 2 : 1, (g.n[2] + chunks - 1) / chunks);
     if (even) t.zc += t.zc & 1;
     return t;
 }
