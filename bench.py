@@ -765,7 +765,8 @@ def main():
                "single_thread": {"value": v1, "solve_s": det1["solve_s"], "t_iteration_s": det1["t_iteration_s"]},
                "cpu_model": cpu_model(),
                "note": "the oracle's Gauss-Seidel sweeps are sequential; only its pointwise loops use OpenMP"}
-    cfgd = dict(WORKLOAD, outer_iters=info["outer_iters"], final_norms=list(info["norms"]), K=info["K"],
+    cfgd = dict(WORKLOAD, gridpoints_per_s=value * WORKLOAD["n"] ** 3,
+                outer_iters=info["outer_iters"], final_norms=list(info["norms"]), K=info["K"],
                 field_err=field_err, field_err_note="max over 4096+ stored cells of |gpu - oracle| / max|oracle field|, "
                                                     "oracle root to its FP64 floor (tests/golden)",
                 field_accurate=field_acc, field_estimated=field_est,
