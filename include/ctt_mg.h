@@ -191,8 +191,8 @@ mg_status mg_set_sources(struct mg_ctx *ctx, const double *rho0, const double *r
 mg_status mg_set_initial_guess(struct mg_ctx *ctx, const double *u, const double *W, int on_device);
 
 /* Solve the constraints eq:Ham and eq:Mom (Summary) by multigrid (Key features, "Fast"): iterate until
- * max(|H|, |M_i|) <= tol (and, with field_tol, the per-field test), recording the norms of every
- * outer iteration (Key features, "Diagnostics").  info may be NULL. */
+ * max(|H|, |M_i|) <= tol (and, with field_tol, the per-field test of field_tol / field_est), recording
+ * the norms of every outer iteration (Key features, "Diagnostics").  info may be NULL. */
 mg_status mg_solve(struct mg_ctx *ctx, mg_solve_info *info);
 
 /* Copy out the solution of the constraint problem (Summary: psi through u, W_i, and K, the mean
