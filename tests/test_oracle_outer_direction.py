@@ -62,3 +62,23 @@ def test_lagged_k2_not_the_decoupling_limits_the_outer_iteration():
     assert k_dec[2] < 0.1 * const_dec[2] and k_dec[3] < 1e-3 * const_dec[3], (k_dec, const_dec)
     assert k_dec[-1] < 1e-13 and len(k_dec) <= 5 and k_cpl[-1] < 1e-13 and len(k_cpl) <= 5, (k_dec, k_cpl)
     assert len(const_dec) >= 7
+
+
+def test_psi_row_has_a_near_null_mode_close_to_the_constant():
+    """Why more inner cycles do not help the library's step: with K^2 from the integrability
+    condition the psi row's coefficient c averages to ~0, so L_psi = Lap + diag(c) has an eigenvalue
+    ~30 times below the next one, with an almost constant eigenvector.  An inner solve of L_psi e = r
+    amplifies that mode, and removing the plain mean afterwards leaves its non-constant part."""
+    p = fields.modes_periodic(n=8)
+    ds = DenseSystem(8, p["lo"], p["hi"], p["order"], PERIODIC, rho0=p["rho0"], rho2=p["rho2"], S=p["S"])
+    root = ds.solve()
+    J, _ = ds.jacobian(root["u"], root["W"], root["K2"])
+    L = J[:ds.N, :ds.N]
+    w, V = np.linalg.eig(L)
+    order = np.argsort(np.abs(w))
+    v0 = np.real(V[:, order[0]])
+    v0 /= np.linalg.norm(v0)
+    assert np.abs(w[order[0]]) * 20 < np.abs(w[order[1]]), w[order[:3]]
+    assert abs(v0.sum()) / np.sqrt(ds.N) > 0.95
+    c = np.diag(L) - np.diag(ds.Lap)
+    assert abs(c.mean()) < 0.02 * np.abs(c).max()
