@@ -131,6 +131,13 @@ typedef struct {
                              update relative to the field's size and rho = rel / (the previous update's rel) is the
                              observed contraction (used when rho < 1/2; otherwise the update itself is compared).
                              It saves the outer iteration that only confirms a small update.  0 = off.       */
+    int k2_newton;        /* periodic boxes with K from integrability: 1 = remove the mean of each outer psi
+                             correction along z = L_psi^-1 dF_psi/dK^2 (K^2 as a Newton unknown of the psi row)
+                             instead of along the constant vector; z comes from one extra inner solve at the
+                             start of each solve.  With K from integrability the psi row has a near-null mode
+                             close to the constant, which the plain mean removal leaves partly in place.
+                             Ignored elsewhere, by mg_batch_* and by the nested start's half-size solve.
+                             0 = off (default).                                                         */
 } mg_config;
 
 typedef struct {

@@ -75,6 +75,7 @@ mg_status validate(const mg_config *c)
     if (c->reflect != 0 && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "symmetry planes need a Robin box");
     if (c->tile_waves < 0 || c->tile_waves > 8) return fail(MG_ERR_INVALID_ARG, "tile_waves must be 0..8");
     if (c->field_est != 0 && c->field_est != 1) return fail(MG_ERR_INVALID_ARG, "field_est must be 0 or 1");
+    if (c->k2_newton != 0 && c->k2_newton != 1) return fail(MG_ERR_INVALID_ARG, "k2_newton must be 0 or 1");
     if (c->extrap < 0 || c->extrap > 63) return fail(MG_ERR_INVALID_ARG, "extrap must be a mask of 6 bits");
     if (c->extrap != 0 && c->bc != MG_BC_ROBIN) return fail(MG_ERR_INVALID_ARG, "extrapolating faces need a Robin box");
     for (int a = 0; a < 3; ++a)
@@ -134,6 +135,7 @@ bool nested_child_config(const mg_config *c, mg_config *cc)
     cc->levels = c->levels > 1 ? c->levels - 1 : 0;
     cc->tol = std::max(c->tol, c->nested_tol > 0.0 ? c->nested_tol : kNestedTol);
     cc->field_tol = 0.0;   // the half-size solve only supplies a starting state
+    cc->k2_newton = 0;
     return true;
 }
 
@@ -150,8 +152,14 @@ void fill_rel_change(const mg_config &c, const Scalars &s, int updates, double o
     for (int a = 0; a < 4; ++a) out[a] = (on && s.change[4 + a] > 0.0) ? s.change[a] / s.change[4 + a] : 0.0;
 }
 
+// k2_newton applies to periodic boxes whose K comes from the integrability condition.
+bool k2_newton_on(const mg_config *c)
+{
+    return c->k2_newton == 1 && c->bc == MG_BC_PERIODIC && c->k_mode == MG_K_INTEGRABILITY;
+}
+
 struct Layout {
-    size_t X, SRC, R, D, PB, RT, BY, partial, scal, Gpsi, GW, gj, own, child, total;
+    size_t X, SRC, R, D, PB, RT, BY, partial, scal, Z, ZR, Gpsi, GW, gj, own, child, total;
     int dense, mpsi, mw, has_child;
     std::vector<size_t> eA, eB, f, c;
 };
@@ -180,6 +188,10 @@ Layout layout_for(const mg_config *c)
     }
     L.partial = take((size_t)kRedBlocks * 8 * 8);
     L.scal = take(sizeof(Scalars));
+    if (k2_newton_on(c)) {
+        L.Z = take(4 * N * tb);
+        L.ZR = take(4 * N * tb);
+    }
     {
         const int periodic = c->bc == MG_BC_PERIODIC;
         int nc[3];
@@ -260,6 +272,23 @@ mg_status with_engine(const mg_ctx *x, Fn &&fn)
 mg_status residual_any(mg_ctx *x, double *HM) { return ENGINE_CALL(engine_residual, x, HM); }
 
 mg_status iteration_any(mg_ctx *x) { return ENGINE_CALL(engine_iteration, x); }
+
+// k2_newton: the z solve (the inner cycles on zrhs, at the current linearisation), then its means.
+mg_status zsolve_any(mg_ctx *x)
+{
+    x->zsolve = true;
+    mg_status st = ENGINE_CALL(engine_iteration, x);
+    x->zsolve = false;
+    return st;
+}
+
+__global__ void k_fill_value(void *p, size_t n, int tb, double v)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (tb == 4) ((float *)p)[i] = (float)v;
+        else ((double *)p)[i] = v;
+    }
+}
 
 // Periodic gauge <u> = <W_i> = 0: the means (one grid reduction, finished in its last block) removed.
 mg_status project_gauge(mg_ctx *x)
@@ -502,6 +531,10 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
         }
         x->partial = (double *)(b + lay.partial);
         x->scal = (Scalars *)(b + lay.scal);
+        if (k2_newton_on(cfg)) {
+            x->zbuf = b + lay.Z;
+            x->zrhs = b + lay.ZR;
+        }
         for (int l = 0; l < x->nlev; ++l) {
             LevelBufs L;
             Geo &g = L.geo;
@@ -612,6 +645,15 @@ mg_status mg_create(const mg_config *cfg, void *cuda_stream, void *workspace, si
                                         fused_ratio_cells(L1.geo, cfg->bc == MG_BC_ROBIN)) <= kMaxCoarseSmem;
         }
         if (x->dense && (st = ENGINE_CALL(engine_dense_setup, x)) != MG_OK) break;
+        if (x->zrhs) {   // the z solve's right-hand side: dF_psi/dK^2 = -psi^5/12 in the psi row's inner form
+            cudaError_t e = cudaMemsetAsync(x->zrhs, 0, 4 * x->N * x->tbytes, x->stream);
+            if (e == cudaSuccess) {
+                k_fill_value<<<grid_for(x->N), kThreads, 0, x->stream>>>(x->zrhs, x->N, (int)x->tbytes, -1.0 / 12.0);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+            if (e != cudaSuccess) { st = fail(MG_ERR_CUDA, cudaGetErrorString(e)); break; }
+        }
         if ((st = leave(x, MG_OK)) != MG_OK) break;
         if (lay.has_child) {
             mg_config cc;
@@ -723,6 +765,15 @@ static mg_status mg_solve_impl(mg_ctx *x, mg_solve_info *info)
     }
     x->guess_set = false;
     if (warm_state != 1) CKS(run_start(x, &launches));   // an accepted warm start has evaluated it
+    if (x->zbuf) {   // k2_newton: z at the starting state's linearisation, kept for the whole solve
+        if (x->cfg.use_graph) {
+            if (!x->graph_z) CKS(capture(x, zsolve_any, &x->graph_z, &x->launches_z));
+            CK(cudaGraphLaunch(x->graph_z, x->stream));
+            launches += x->launches_z;
+        } else {
+            CKS(zsolve_any(x));
+        }
+    }
     mg_status result = MG_ERR_NOT_CONVERGED;
     int it = 0, grow = 0;
     double prev = INFINITY, prev_rel[4] = {0, 0, 0, 0};
@@ -1012,6 +1063,7 @@ void mg_destroy(mg_ctx *x)
     warm_drop(x);
     if (x->graph_exec) cudaGraphExecDestroy(x->graph_exec);
     if (x->graph_start) cudaGraphExecDestroy(x->graph_start);
+    if (x->graph_z) cudaGraphExecDestroy(x->graph_z);
     if (x->ev0) cudaEventDestroy(x->ev0);
     if (x->ev1) cudaEventDestroy(x->ev1);
     if (x->stream) {
@@ -1175,6 +1227,7 @@ mg_status mg_batch_create(int count, const mg_config *cfgs, void *cuda_stream, m
         mg_ctx *x = nullptr;
         mg_config cb = cfgs[b];
         cb.nested = 0;   // the batch replays one graph per round: no per-instance nested start
+        cb.k2_newton = 0;   // nor a per-instance z solve
         st = mg_create(&cb, cuda_stream, nullptr, 0, &x);
         if (st == MG_OK) bt->ctx.push_back(x);
         cudaEvent_t e;

@@ -270,6 +270,11 @@ struct mg_ctx {
     cudaGraphExec_t warm_graph = nullptr;   // the inference, captured for this context's buffers
     long long launches_warm = 0;
     bool device_paced = false;              // enqueue-time: a batch controller kernel reads the scalars on the device
+    void *zbuf = nullptr;                   // k2_newton: the z solve's result, 4N T in the finest layout (psi: z)
+    void *zrhs = nullptr;                   // k2_newton: its right-hand side, 4N T (psi row -1/12, W rows 0)
+    bool zsolve = false;                    // enqueue-time: the next inner solve is the z solve
+    cudaGraphExec_t graph_z = nullptr;      // the z solve, captured
+    long long launches_z = 0;
 };
 
 namespace ctt {

@@ -318,9 +318,22 @@ mg_status enqueue_iteration(mg_ctx *x)
     }
     CK(cudaGetLastError());
     if (x->dense) CKS(enqueue_dense_psi_inverse<T, ORDER, BC>(x));
+    LevelBufs &L0 = x->lev[0];
+    if (x->zsolve) {   // z = L^-1 (dF/dK^2) in the inner form: the cycles on zrhs, its means
+        void *f = L0.f;
+        L0.f = x->zrhs;
+        mg_status st = MG_OK;
+        for (int cyc = 0; cyc < x->cfg.inner_cycles && st == MG_OK; ++cyc) st = enqueue_vcycle<T, ORDER, BC>(x, cyc == 0);
+        L0.f = f;
+        CKS(st);
+        CK(cudaMemcpyAsync(x->zbuf, L0.cur(), 4 * x->N * sizeof(T), cudaMemcpyDeviceToDevice, x->stream));
+        k_sum4<T><<<grid_for(x->N, kRedBlocks), kThreads, 0, x->stream>>>((const T *)x->zbuf, x->N, x->partial,
+                                                                        x->scal->zmean, &x->scal->ticket[2]);
+        CK(cudaGetLastError());
+        return MG_OK;
+    }
     for (int cyc = 0; cyc < x->cfg.inner_cycles; ++cyc) CKS(enqueue_vcycle<T, ORDER, BC>(x, cyc == 0));
     int periodic = x->cfg.bc == MG_BC_PERIODIC;
-    LevelBufs &L0 = x->lev[0];
     if (periodic) {
         int g = grid_for(x->N, kRedBlocks);
         k_sum4<T><<<g, kThreads, 0, x->stream>>>((const T *)L0.cur(), x->N, x->partial, x->scal->emean,
@@ -330,7 +343,7 @@ mg_status enqueue_iteration(mg_ctx *x)
     const bool sized = x->cfg.field_tol > 0.0;
     k_update<T><<<sized ? grid_for(x->N, kRedBlocks) : grid_for(x->N), kThreads, 0, x->stream>>>(
         L0.geo, x->X, (const T *)L0.cur(), x->N, periodic ? x->scal->emean : nullptr, L0.split, x->partial,
-        sized ? x->scal : nullptr);
+        sized ? x->scal : nullptr, x->zbuf && periodic ? (const T *)x->zbuf : nullptr, x->scal->zmean);
     CK(cudaGetLastError());
     return enqueue_residual<T, ORDER, BC>(x, nullptr);
 }

@@ -1002,6 +1002,7 @@ struct Scalars {
     unsigned int nonfinite;   // nonzero: a source value is NaN or infinite (set by k_flag_nonfinite)
     double change[8];         // last update: max |e_a - <e_a>| (a = 0..3), then max |psi|, |W_x|, |W_y|, |W_z| after it
     unsigned int ticket[4];   // last-block counters: pass-B sums, pass-2 norms, means of e, update maxima
+    double zmean[4];          // k2_newton: means of the z solve's result (component 0: z of the psi row)
 };
 
 // Per-field part of the stopping test (mg_config.field_tol, field_est), shared by the host loops
@@ -1142,8 +1143,11 @@ __global__ void __launch_bounds__(256) k_sub_mean4(T *__restrict__ x, size_t N, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_update(Geo g, double *__restrict__ x, const T *__restrict__ e, size_t N,
                                                 const double *__restrict__ means, int split,
-                                                double *__restrict__ partial, Scalars *s)
+                                                double *__restrict__ partial, Scalars *s, const T *__restrict__ z,
+                                                const double *__restrict__ zmean)
 {
+    // z (k2_newton): the psi correction's mean is removed along z, scaled so that the mean goes
+    const double zr = z ? means[0] / zmean[0] : 0.0;
     double m[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) m[a] = means ? means[a] : 0.0;
@@ -1155,7 +1159,7 @@ __global__ void __launch_bounds__(256) k_update(Geo g, double *__restrict__ x, c
         const size_t q = split ? (((i + j + k) & 1) ? N / 2 : 0) + (p >> 1) : p;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const double d = (double)e[a * N + q] - m[a];
+            const double d = (z && a == 0) ? (double)e[q] - zr * (double)z[q] : (double)e[a * N + q] - m[a];
             const double v = x[a * N + p] + d;
             x[a * N + p] = v;
             if (s) {

@@ -40,7 +40,7 @@ class mg_config(C.Structure):
         ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double), ("nested", C.c_int),
         ("nested_min", C.c_int), ("nested_tol", C.c_double),
         ("punct_P", (C.c_double * 3) * 2), ("punct_S", (C.c_double * 3) * 2), ("reflect", C.c_int),
-        ("field_tol", C.c_double), ("extrap", C.c_int), ("tile_waves", C.c_int), ("field_est", C.c_int),
+        ("field_tol", C.c_double), ("extrap", C.c_int), ("tile_waves", C.c_int), ("field_est", C.c_int), ("k2_newton", C.c_int),
     ]
 
 

@@ -155,7 +155,7 @@ def test_extrapolating_face_validation(lib):
 @pytest.mark.parametrize("field,value,status", [
     ("field_tol", -1e-10, 1), ("field_tol", float("nan"), 1), ("use_graph", 3, 1),
     ("order", 3, 1), ("bc", 7, 1), ("precision", 5, 1), ("levels", 6, 1), ("coarse_sweeps", 0, 1),
-    ("nested", 2, 1), ("nested_min", 2, 1), ("nested_tol", -1.0, 1), ("tile_waves", -1, 1), ("tile_waves", 9, 1), ("field_est", 2, 1),
+    ("nested", 2, 1), ("nested_min", 2, 1), ("nested_tol", -1.0, 1), ("tile_waves", -1, 1), ("tile_waves", 9, 1), ("field_est", 2, 1), ("k2_newton", 2, 1),
 ])
 def test_invalid_configs_are_rejected_on_the_host(lib, field, value, status):
     cfg = lib.mg_config_default()
@@ -177,3 +177,19 @@ def test_status_strings(lib):
     L = lib.lib()
     assert L.mg_status_string(0) == b"MG_OK"
     assert L.mg_status_string(8) == b"MG_ERR_TIMEOUT"
+
+
+def test_k2_newton_workspace(lib):
+    """k2_newton adds the z solve's result and right-hand side (4N values of the inner type each) on
+    periodic boxes with K from integrability, and nothing elsewhere."""
+    def size(**over):
+        cfg = lib.mg_config_default()
+        for a in range(3):
+            cfg.n[a] = 32
+        for k, v in over.items():
+            setattr(cfg, k, v)
+        return lib.mg_workspace_size(cfg)
+    base = size()
+    assert size(k2_newton=1) - base >= 8 * 32 ** 3 * 4
+    robin = dict(bc=lib.MG_BC_ROBIN, k_mode=lib.MG_K_FIXED)
+    assert size(k2_newton=1, **robin) == size(**robin)
